@@ -1,0 +1,254 @@
+/*
+ * libvie: QR-recursive compressed volume-integral-equation solver for arrays of
+ * dielectric meta-atoms, on one NVIDIA GB300 (sm_103a).
+ *
+ * The problem (paper Sec. 2, eq. IntEq): the polarisation current J in the
+ * dielectric region satisfies
+ *     J / (j w eps0 chi) + j w mu0 int J g + (1/(j w eps0)) grad int (div J) g = E0,
+ * g = exp(-j k R) / (4 pi R), e^{j w t} time convention, sigma = 0.
+ * Galerkin discretisation (Sec. 3, eq. matrixeq / eq_vie) gives Z I = v0.  The
+ * meta-atoms are axis-aligned cubes split into nv^3 voxels carrying one
+ * div-conforming rooftop per voxel face (boundary faces included), so an atom
+ * has Np = 3 (nv+1) nv^2 unknowns; unknowns are ordered atom by atom (Sec. 4,
+ * eq. bp) and, inside an atom, x-faces, y-faces, z-faces, each lexicographic in
+ * (i, j, k) with the normal index running 0..nv.
+ *
+ * The library works with the scaled system Zs I = b, Zs = j w eps0 Z,
+ * b = j w eps0 v0, in units eps0 = mu0 = c = 1 (so w = k = 2 pi / lambda).  The
+ * solution vector I is the same as for Z I = v0.
+ *
+ * Conventions for every function below:
+ *  - Return value: VIE_OK (0) or a negative vie_status.  Nothing is thrown
+ *    across this interface.  vie_last_error(ctx) gives a one-line message.
+ *  - Complex numbers are interleaved (re, im) pairs: "c64" = 2 x float,
+ *    "c128" = 2 x double.  Matrices of vectors are column-major n x nrhs with
+ *    a leading dimension ld >= n (in elements).
+ *  - Device pointers are owned by the caller and must stay valid until the
+ *    call's work on `stream` has finished; host pointers are read or written
+ *    before the call returns.  Objects (vie_ctx, vie_op, vie_server) own
+ *    their internal device memory until the matching *_destroy.
+ *  - Calls on one vie_ctx (and on the operators made from it) are not
+ *    thread-safe; a vie_server is safe for concurrent submit/poll.
+ *  - Every wait inside the library is bounded (VIE_ERR_TIMEOUT).
+ */
+#ifndef VIE_H
+#define VIE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vie_ctx vie_ctx;
+typedef struct vie_op vie_op;
+typedef struct vie_server vie_server;
+typedef void* vie_stream; /* a cudaStream_t; NULL = the context's own stream */
+
+enum vie_status {
+    VIE_OK = 0,
+    VIE_ERR_INVALID_ARG = -1,
+    VIE_ERR_OOM = -2,
+    VIE_ERR_CUDA = -3,
+    VIE_ERR_NOT_CONVERGED = -4, /* result and stats are still written */
+    VIE_ERR_BREAKDOWN = -5,
+    VIE_ERR_NAN = -6,
+    VIE_ERR_TIMEOUT = -7,
+    VIE_ERR_ADMISSION = -8,
+    VIE_ERR_STATE = -9
+};
+
+/* Precision of stored factors and of an apply. */
+enum vie_precision {
+    VIE_C64 = 1,    /* complex float32 storage and arithmetic */
+    VIE_C128 = 2,   /* complex float64 storage and arithmetic */
+    VIE_BF16X3 = 3, /* c64 operands split into bf16 hi/lo, three tensor-core
+                       products (hi.hi + hi.lo + lo.hi), float32 accumulation */
+    VIE_C64_ACC64 = 4 /* c64 factors, float64 vectors and accumulation (the
+                         refinement residual) */
+};
+
+/* vie_apply flags */
+#define VIE_APPLY_FUSE_PRECOND 1 /* y = x + Z_D^-1 (far part of Zs x) = P^-1 Zs x */
+
+typedef struct vie_ctx_opts {
+    int device;            /* CUDA device ordinal */
+    size_t hbm_budget;     /* bytes the context may allocate (0 = free memory - 4 GiB) */
+    int verbose;           /* 0 quiet, 1 stage timings on stderr */
+} vie_ctx_opts;
+
+/* Metasurface geometry (host memory, copied by vie_assemble).
+ * Paper Sec. 2: region Omega (the atoms), susceptibility chi = eps_r - 1 per
+ * homogeneous component, angular frequency from `wavelength`. */
+typedef struct vie_geometry {
+    int n_atoms;               /* N >= 1 */
+    const double* centres;     /* [3 N] atom centres (x, y, z); units of length */
+    const int* types;          /* [N] type index in [0, n_types) */
+    int n_types;               /* T >= 1 */
+    const double* sides;       /* [T] cube side */
+    const int* nv;             /* [T] voxels per edge, 1..16; all types must give
+                                  the same Np (VIE_ERR_INVALID_ARG otherwise) */
+    const double* eps;         /* [2 T] relative permittivity (re, im); lossy media
+                                  have im < 0 under e^{j w t}; eps != 1 */
+} vie_geometry;
+
+typedef struct vie_op_info {
+    int n_atoms, np, n_types, levels;
+    int64_t n;                 /* unknowns = N Np */
+    int64_t n_far_blocks;
+    int64_t far_entries;       /* sum over far blocks of m n */
+    int64_t factor_entries;    /* sum over far blocks of (m + n) r */
+    int64_t self_entries;      /* N Np^2 (eq. eqn_cgain's near part) */
+    double gain;               /* G = n^2 / N_QR (eq. eqn_cgain) */
+    int rank_min, rank_max;
+    double rank_mean;
+    int factor_precision;      /* vie_precision of stored factors, 0 before compression */
+    double tol;                /* compression tolerance */
+    int64_t apply_bytes;       /* algorithmic bytes of one single-RHS c64 apply */
+    double t_assemble_s, t_compress_s;
+} vie_op_info;
+
+/* Plane-wave incident fields E0 = p exp(-j k khat . r), one per right-hand side. */
+typedef struct vie_incident {
+    const double* khat;        /* [3 nrhs] unit propagation directions */
+    const double* pol;         /* [6 nrhs] complex polarisation (re x, im x, re y, im y, re z, im z) */
+} vie_incident;
+
+typedef struct vie_solve_opts {
+    double tol;                /* relative residual ||P^-1 (b - Zs I)|| / ||P^-1 b|| (1e-6) */
+    int restart;               /* GMRES restart length m (e.g. 60) */
+    int max_iters;             /* iteration cap (e.g. 2000) */
+    int precision;             /* VIE_C64: FP32 inner applies with FP64 Krylov and FP64
+                                  residual refinement; VIE_C128: all-FP64 (needs C128 factors);
+                                  VIE_BF16X3: block GMRES with tensor-core far applies */
+    int out_on_device;         /* 1: I_out is a device pointer, 0: host pointer */
+    int precond;               /* 1: block-diagonal preconditioner (default), 0: none */
+} vie_solve_opts;
+
+typedef struct vie_solve_stats {
+    int iterations;            /* Arnoldi steps (block steps for block GMRES) */
+    int applies;               /* compressed operator applications */
+    int refinements;           /* FP64 residual recomputations */
+    double residual;           /* final true preconditioned relative residual (max over RHS) */
+    double true_residual;      /* ||b - Zs I|| / ||b|| with the compressed operator (max over RHS) */
+    double t_solve_s;
+    double history[512];       /* estimated residual after each iteration (first 512) */
+    int n_history;
+} vie_solve_stats;
+
+/* ---- context ---------------------------------------------------------------- */
+int vie_create(vie_ctx** out, const vie_ctx_opts* opts);
+void vie_destroy(vie_ctx* ctx);
+const char* vie_last_error(vie_ctx* ctx);
+
+/* ---- operator --------------------------------------------------------------
+ * vie_assemble (paper Sec. 3 entries, Sec. 4 self blocks, Sec. 5 grid):
+ * builds the quadtree and far-block lists (Sec. 5.1 Definition, eq. eq_rec01,
+ * Sec. 5.4), assembles the distinct self blocks Z_ii in float64, factors them
+ * (LU, Sec. 4 eq. diagprecond) and keeps the explicit inverses.  Far blocks
+ * are not formed here.  wavelength > 0 in the units of the geometry. */
+int vie_assemble(vie_ctx* ctx, const vie_geometry* g, double wavelength, vie_op** out);
+
+/* vie_compress (Sec. 5.2 eq. eq_02, Sec. 5.3): forms every far block on the
+ * device, in batches, and replaces it by Q (m x r, orthonormal columns) and
+ * R (r x n) with ||A - Q R||_F <= tol ||A||_F (randomised adaptive range
+ * finder; the bound is enforced with a safety factor on a stochastic
+ * estimate).  factor_precision: VIE_C64 or VIE_C128.  May be called again
+ * with another tolerance or precision; the old factors are freed. */
+int vie_compress(vie_op* op, double tol, int factor_precision);
+
+void vie_op_destroy(vie_op* op);
+int vie_op_get_info(const vie_op* op, vie_op_info* info);
+
+/* vie_apply (Sec. 5.2: y = Z_D x + sum_far Q (R x)):
+ * x, y: device pointers, n x nrhs, leading dimension ld (elements).
+ * precision VIE_C64 (x, y c64), VIE_C128 (c128, needs C128 factors),
+ * VIE_C64_ACC64 (x, y c128, c64 factors), VIE_BF16X3 (c64).
+ * flags: VIE_APPLY_FUSE_PRECOND returns P^-1 Zs x instead of Zs x.
+ * x and y must not overlap.  Asynchronous on `stream`. */
+int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int precision,
+              int flags, vie_stream stream);
+
+/* vie_precond (Sec. 4, eq. diagprecond): y = Z_D^-1 x atom by atom, with the
+ * inverse of the atom's type.  Same pointer conventions as vie_apply;
+ * precision VIE_C64 or VIE_C128. */
+int vie_precond(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int precision,
+                vie_stream stream);
+
+/* vie_rhs: b = j k v0, v0_i = int w_i . E0 (eq. matrixeq), Gauss-Legendre 3 points
+ * per voxel axis; b is a device pointer, c128, n x nrhs, leading dimension ld. */
+int vie_rhs(vie_op* op, const vie_incident* inc, int nrhs, void* b, int64_t ld, vie_stream stream);
+
+/* vie_solve (Sec. 6: left-preconditioned GMRES, Sec. 4 preconditioner):
+ * solves Zs I = b for the plane waves in `inc`; writes I (c128, n x nrhs,
+ * column-major, ld = n) to I_out (host or device per opts->out_on_device).
+ * Returns VIE_ERR_NOT_CONVERGED (I and stats still written) if max_iters is hit. */
+int vie_solve(vie_op* op, const vie_incident* inc, int nrhs, const vie_solve_opts* opts,
+              void* I_out, vie_solve_stats* stats);
+
+/* vie_fields: outputs from a solution I (host c128, n x nrhs, ld = n):
+ * mode 0: far-field amplitude F(rhat) = -j k/(4 pi) (I - rhat rhat) int J exp(j k rhat.r) dV
+ *         for the unit directions dirs[3 npts]; E_out host c128 [3 npts nrhs].
+ * sigma_out (host, may be NULL) [2 nrhs]: extinction Re(I^H v0) and scattering
+ * cross section (closed surface integral of |F|^2, 24 x 48 rule) for |E0| = 1. */
+int vie_fields(vie_op* op, const vie_incident* inc, const void* I, int nrhs, const double* dirs,
+               int npts, int mode, void* E_out, double* sigma_out);
+
+/* ---- debugging / verification ------------------------------------------------
+ * vie_export_block: copies one operator block to host memory.
+ * kind 0: self block of type `a` (c128 Np x Np, col-major);
+ * kind 1: dense interaction block Zs_ab between atoms a != b, assembled on the
+ *         device at `precision` (VIE_C64 -> c64, VIE_C128 -> c128), col-major;
+ * kind 2: explicit inverse of the self block of type `a` (c128).  */
+int vie_export_block(vie_op* op, int kind, int a, int b, int precision, void* out);
+
+/* vie_far_block_info: block `i` of the compressed operator: level, number of
+ * target / source atoms, rank.  vie_export_far_block copies its atom lists
+ * (int) and factors Q (m x r col-major) and R (r x n col-major) as c128. */
+int vie_far_block_info(vie_op* op, int64_t i, int* level, int* n_tatoms, int* n_satoms, int* rank);
+int vie_export_far_block(vie_op* op, int64_t i, int* tatoms, int* satoms, void* Q, void* R);
+
+/* ---- serving (continuous batching) ------------------------------------------
+ * Requests (geometry + plane waves) are admitted while the modelled HBM
+ * footprint of their compressed operator, inverses and Krylov state fits
+ * the budget; admitted requests run concurrently, each on its own CUDA stream. */
+typedef struct vie_serve_opts {
+    int max_inflight;          /* concurrent requests (slots) */
+    size_t hbm_budget;         /* bytes for all in-flight requests (0 = context budget) */
+    double tol;                /* compression tolerance (1e-4) */
+    vie_solve_opts solve;      /* solver options for every request */
+} vie_serve_opts;
+
+typedef struct vie_request {
+    vie_geometry geometry;     /* copied at submit */
+    double wavelength;
+    int nrhs;
+    vie_incident inc;          /* copied at submit */
+} vie_request;
+
+typedef struct vie_result {
+    int status;                /* vie_status of the solve */
+    int64_t n;                 /* unknowns */
+    int nrhs;
+    double* I;                 /* host c128 n x nrhs, owned by the server until vie_result_free */
+    vie_solve_stats stats;
+    double t_submit_s, t_start_s, t_done_s; /* server clock */
+    int64_t footprint_bytes;
+} vie_result;
+
+int vie_serve(vie_server** out, vie_ctx* ctx, const vie_serve_opts* opts);
+int vie_submit(vie_server* s, const vie_request* req, uint64_t* ticket);
+/* Waits up to timeout_ms for the ticket; VIE_ERR_TIMEOUT if not done yet. */
+int vie_poll(vie_server* s, uint64_t ticket, vie_result* out, int timeout_ms);
+void vie_result_free(vie_result* r);
+int vie_server_stop(vie_server* s); /* drains in-flight work, then frees the server */
+
+/* Modelled footprint (bytes) of a request of n unknowns, nrhs right-hand sides,
+ * restart m and the given factor-entry estimate: the admission rule. */
+int64_t vie_footprint_bytes(int64_t n, int np, int nrhs, int restart, int64_t factor_entries);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VIE_H */

@@ -1,0 +1,544 @@
+// C-ABI entry points of libvie (declared in include/vie.h).  Every function
+// catches the library's internal errors and returns a vie_status; nothing is
+// thrown across the interface.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "common.h"
+#include "krylov.h"
+
+struct vie_ctx {
+    vie::Ctx c;
+};
+struct vie_op {
+    vie::Op o;
+};
+
+namespace vie {
+
+// ------------------------------------------------------------------ applies
+static void ensure_F(Op& op, size_t bytes) {
+    if (op.d_F.bytes < bytes) op.d_F.alloc(bytes);
+}
+
+void op_apply_fused32(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s) {
+    if (op.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "float32 applies need VIE_C64 factors");
+    const int64_t n = op.n();
+    ensure_F(op, (size_t)n * nrhs * sizeof(float2));
+    float2* F = op.d_F.as<float2>();
+    apply_far<float2, float2>(op, x, n, F, n, nrhs, s);
+    self_gemm<float2, float2>(op, op.d_inv32.as<float2>(), x, n, F, n, y, n, nrhs, 1, s);
+}
+
+void op_apply64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s) {
+    const int64_t n = op.n();
+    ensure_F(op, (size_t)n * nrhs * sizeof(double2));
+    double2* F = op.d_F.as<double2>();
+    if (op.fprec == VIE_C128) apply_far<double2, double2>(op, x, n, F, n, nrhs, s);
+    else apply_far<float2, double2>(op, x, n, F, n, nrhs, s);
+    self_gemm<double2, double2>(op, op.d_zself64.as<double2>(), x, n, F, n, y, n, nrhs, 0, s);
+}
+
+void op_apply_fused64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s) {
+    const int64_t n = op.n();
+    ensure_F(op, (size_t)n * nrhs * sizeof(double2));
+    double2* F = op.d_F.as<double2>();
+    if (op.fprec == VIE_C128) apply_far<double2, double2>(op, x, n, F, n, nrhs, s);
+    else apply_far<float2, double2>(op, x, n, F, n, nrhs, s);
+    self_gemm<double2, double2>(op, op.d_inv64.as<double2>(), x, n, F, n, y, n, nrhs, 1, s);
+}
+
+void op_precond64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s) {
+    self_gemm<double2, double2>(op, op.d_inv64.as<double2>(), x, op.n(), nullptr, 0, y, op.n(), nrhs, 2, s);
+}
+
+}  // namespace vie
+
+using namespace vie;
+
+namespace {
+
+template <class F>
+int guarded(vie_ctx* ctx, F&& f) {
+    try {
+        f();
+        if (ctx) ctx->c.err.clear();
+        return VIE_OK;
+    } catch (const Error& e) {
+        if (ctx) ctx->c.err = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        if (ctx) ctx->c.err = "host allocation failed";
+        return VIE_ERR_OOM;
+    } catch (const std::exception& e) {
+        if (ctx) ctx->c.err = e.what();
+        return VIE_ERR_INVALID_ARG;
+    }
+}
+
+vie_ctx* ctx_of(vie_op* op) { return op ? reinterpret_cast<vie_ctx*>(op->o.ctx) : nullptr; }
+
+void set_device(Ctx& c) { VIE_CUDA(cudaSetDevice(c.device)); }
+
+}  // namespace
+
+extern "C" {
+
+int vie_create(vie_ctx** out, const vie_ctx_opts* opts) {
+    if (!out) return VIE_ERR_INVALID_ARG;
+    *out = nullptr;
+    auto ctx = std::make_unique<vie_ctx>();
+    int st = guarded(ctx.get(), [&] {
+        Ctx& c = ctx->c;
+        c.device = opts ? opts->device : 0;
+        c.verbose = opts ? opts->verbose : 0;
+        int ndev = 0;
+        VIE_CUDA(cudaGetDeviceCount(&ndev));
+        if (c.device < 0 || c.device >= ndev) fail(VIE_ERR_INVALID_ARG, "no such CUDA device");
+        set_device(c);
+        cudaDeviceProp prop;
+        VIE_CUDA(cudaGetDeviceProperties(&prop, c.device));
+        c.n_sm = prop.multiProcessorCount;
+        VIE_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+        VIE_BLAS(cublasCreate(&c.blas));
+        VIE_BLAS(cublasSetStream(c.blas, c.stream));
+        size_t fr = 0, tot = 0;
+        VIE_CUDA(cudaMemGetInfo(&fr, &tot));
+        size_t reserve = (size_t)4 << 30;
+        c.budget = (opts && opts->hbm_budget) ? opts->hbm_budget : (fr > 2 * reserve ? fr - reserve : fr / 2);
+    });
+    if (st != VIE_OK) {
+        // keep the message readable through a stub context
+        static thread_local std::string last;
+        last = ctx->c.err;
+        return st;
+    }
+    *out = ctx.release();
+    return VIE_OK;
+}
+
+void vie_destroy(vie_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->c.device);
+    if (ctx->c.blas) cublasDestroy(ctx->c.blas);
+    if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
+    delete ctx;
+}
+
+const char* vie_last_error(vie_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "no context"; }
+
+int vie_assemble(vie_ctx* ctx, const vie_geometry* g, double wavelength, vie_op** out) {
+    if (!ctx || !g || !out) return VIE_ERR_INVALID_ARG;
+    *out = nullptr;
+    auto op = std::make_unique<vie_op>();
+    int st = guarded(ctx, [&] {
+        set_device(ctx->c);
+        Op& o = op->o;
+        o.ctx = &ctx->c;
+        double t0 = now_s();
+        if (g->n_atoms < 1 || g->n_types < 1 || !g->centres || !g->types || !g->sides || !g->nv || !g->eps)
+            fail(VIE_ERR_INVALID_ARG, "incomplete geometry");
+        if (!(wavelength > 0) || !std::isfinite(wavelength)) fail(VIE_ERR_INVALID_ARG, "wavelength must be > 0");
+        o.N = g->n_atoms;
+        o.T = g->n_types;
+        o.centres.assign(g->centres, g->centres + 3 * o.N);
+        o.types.assign(g->types, g->types + o.N);
+        o.sides.assign(g->sides, g->sides + o.T);
+        o.nvs.assign(g->nv, g->nv + o.T);
+        for (int t = 0; t < o.T; ++t) {
+            o.eps.emplace_back(g->eps[2 * t], g->eps[2 * t + 1]);
+            if (!(o.sides[t] > 0) || !std::isfinite(o.sides[t])) fail(VIE_ERR_INVALID_ARG, "cube side must be > 0");
+            if (o.nvs[t] < 1 || o.nvs[t] > 16) fail(VIE_ERR_INVALID_ARG, "voxels per edge must be in 1..16");
+            if (o.nvs[t] != o.nvs[0]) fail(VIE_ERR_INVALID_ARG, "all atom types must have the same nv");
+            if (std::abs(o.eps[t] - cd(1.0)) < 1e-12) fail(VIE_ERR_INVALID_ARG, "eps_r = 1 (no scatterer)");
+        }
+        for (int a = 0; a < o.N; ++a) {
+            if (o.types[a] < 0 || o.types[a] >= o.T) fail(VIE_ERR_INVALID_ARG, "atom type out of range");
+            for (int d = 0; d < 3; ++d)
+                if (!std::isfinite(o.centres[3 * a + d])) fail(VIE_ERR_INVALID_ARG, "non-finite atom centre");
+        }
+        // atoms must not touch: the rule between atoms assumes separated cubes
+        for (int a = 0; a < o.N; ++a)
+            for (int b = a + 1; b < o.N; ++b) {
+                double dmax = 0;
+                for (int d = 0; d < 3; ++d) dmax = std::max(dmax, std::fabs(o.centres[3 * a + d] - o.centres[3 * b + d]));
+                if (dmax <= 0.5 * (o.sides[o.types[a]] + o.sides[o.types[b]]))
+                    fail(VIE_ERR_INVALID_ARG, "atoms " + std::to_string(a) + " and " + std::to_string(b) + " overlap or touch");
+            }
+        o.wavelength = wavelength;
+        o.k = 2.0 * M_PI / wavelength;
+        o.mesh = build_mesh(1.0, o.nvs[0]);
+        o.np = o.mesh.np;
+        for (int t = 0; t < o.T; ++t) o.h.push_back(o.sides[t] / o.nvs[t]);
+        // device geometry and mesh topology
+        upload(o.d_centres, o.centres);
+        upload(o.d_types, o.types);
+        upload(o.d_sides, o.sides);
+        std::vector<double2> ichi(o.T);
+        for (int t = 0; t < o.T; ++t) {
+            cd ic = 1.0 / (o.eps[t] - 1.0);
+            ichi[t] = make_double2(ic.real(), ic.imag());
+        }
+        upload(o.d_inv_chi, ichi);
+        std::vector<int4> face(o.np);
+        for (int f = 0; f < o.np; ++f)
+            face[f] = make_int4(o.mesh.face_dir[f], o.mesh.face_lo[f], o.mesh.face_hi[f], o.mesh.face_sheet[f]);
+        upload(o.d_mesh_face, face);
+        upload(o.d_mesh_sign, o.mesh.face_sheet_sign);
+        upload(o.d_mesh_vox, o.mesh.vox_ijk);
+        upload(o.d_mesh_surf, o.mesh.surf_face);
+        o.dmesh = DevMesh{o.mesh.nv, o.mesh.np, o.mesh.nvox, o.mesh.nsurf, o.d_mesh_face.as<int4>(),
+                          o.d_mesh_sign.as<int>(), o.d_mesh_vox.as<int>(), o.d_mesh_surf.as<int>()};
+        o.atoms_of_type.assign(o.T, {});
+        for (int a = 0; a < o.N; ++a) o.atoms_of_type[o.types[a]].push_back(a);
+        std::vector<int> flat;
+        o.type_atom_off.assign(o.T + 1, 0);
+        for (int t = 0; t < o.T; ++t) {
+            flat.insert(flat.end(), o.atoms_of_type[t].begin(), o.atoms_of_type[t].end());
+            o.type_atom_off[t + 1] = (int)flat.size();
+        }
+        upload(o.d_atoms_by_type, flat);
+        // grid hierarchy and far-block lists
+        build_tree(o);
+        // self blocks, their inverses (float64) and float32 copies
+        assemble_self_blocks(o);
+        invert_self_blocks(o);
+        size_t ne = (size_t)o.T * o.np * o.np;
+        o.d_zself32.alloc(ne * sizeof(float2));
+        o.d_inv32.alloc(ne * sizeof(float2));
+        convert_c128_to_c64(o.d_zself64.p, o.d_zself32.p, ne, ctx->c.stream);
+        convert_c128_to_c64(o.d_inv64.p, o.d_inv32.p, ne, ctx->c.stream);
+        VIE_CUDA(cudaStreamSynchronize(ctx->c.stream));
+        o.t_assemble = now_s() - t0;
+        if (ctx->c.verbose)
+            fprintf(stderr, "[vie] assemble: N=%d np=%d levels=%d far blocks=%zu  %.3f s\n", o.N, o.np, o.L,
+                    o.blocks.size(), o.t_assemble);
+    });
+    if (st == VIE_OK) *out = op.release();
+    return st;
+}
+
+int vie_compress(vie_op* op, double tol, int factor_precision) {
+    if (!op) return VIE_ERR_INVALID_ARG;
+    return guarded(ctx_of(op), [&] {
+        set_device(*op->o.ctx);
+        if (!(tol > 0 && tol < 1)) fail(VIE_ERR_INVALID_ARG, "tolerance must be in (0, 1)");
+        if (factor_precision != VIE_C64 && factor_precision != VIE_C128)
+            fail(VIE_ERR_INVALID_ARG, "factor precision must be VIE_C64 or VIE_C128");
+        double t0 = now_s();
+        compress_operator(op->o, tol, factor_precision);
+        op->o.t_compress = now_s() - t0;
+        if (op->o.ctx->verbose)
+            fprintf(stderr, "[vie] compress: %lld factor entries  %.3f s\n", (long long)op->o.factor_entries,
+                    op->o.t_compress);
+    });
+}
+
+void vie_op_destroy(vie_op* op) {
+    if (!op) return;
+    cudaSetDevice(op->o.ctx->device);
+    cudaStreamSynchronize(op->o.ctx->stream);
+    delete op;
+}
+
+int vie_op_get_info(const vie_op* op, vie_op_info* info) {
+    if (!op || !info) return VIE_ERR_INVALID_ARG;
+    const Op& o = op->o;
+    std::memset(info, 0, sizeof(*info));
+    info->n_atoms = o.N;
+    info->np = o.np;
+    info->n_types = o.T;
+    info->levels = o.L;
+    info->n = o.n();
+    info->n_far_blocks = (int64_t)o.blocks.size();
+    int rmin = 1 << 30, rmax = 0;
+    double rsum = 0;
+    for (const auto& b : o.blocks) {
+        info->far_entries += (int64_t)b.m * b.n;
+        rmin = std::min(rmin, b.rank);
+        rmax = std::max(rmax, b.rank);
+        rsum += b.rank;
+    }
+    info->rank_min = o.blocks.empty() ? 0 : rmin;
+    info->rank_max = rmax;
+    info->rank_mean = o.blocks.empty() ? 0 : rsum / o.blocks.size();
+    info->factor_entries = o.factor_entries;
+    info->self_entries = (int64_t)o.N * o.np * o.np;
+    double nqr = (double)o.factor_entries + (double)info->self_entries;
+    info->gain = o.fprec ? (double)o.n() * (double)o.n() / nqr : 0.0;
+    info->factor_precision = o.fprec;
+    info->tol = o.tol;
+    // one single-RHS c64 apply: factors once, distinct self/inverse blocks once,
+    // x read once, y written once
+    info->apply_bytes = 8 * (o.factor_entries + (int64_t)o.T * o.np * o.np + 2 * o.n());
+    info->t_assemble_s = o.t_assemble;
+    info->t_compress_s = o.t_compress;
+    return VIE_OK;
+}
+
+int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int precision, int flags, vie_stream stream) {
+    if (!op) return VIE_ERR_INVALID_ARG;
+    return guarded(ctx_of(op), [&] {
+        Op& o = op->o;
+        set_device(*o.ctx);
+        if (!x || !y || nrhs < 1 || ld != o.n()) fail(VIE_ERR_INVALID_ARG, "vie_apply: bad vectors (ld must be n)");
+        if (o.fprec == 0) fail(VIE_ERR_STATE, "operator is not compressed");
+        cudaStream_t s = stream ? (cudaStream_t)stream : o.ctx->stream;
+        const bool fuse = flags & VIE_APPLY_FUSE_PRECOND;
+        if (precision == VIE_C64) {
+            if (fuse) op_apply_fused32(o, (const float2*)x, (float2*)y, nrhs, s);
+            else {
+                if (o.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "VIE_C64 applies need VIE_C64 factors");
+                ensure_F(o, (size_t)o.n() * nrhs * sizeof(float2));
+                float2* F = o.d_F.as<float2>();
+                apply_far<float2, float2>(o, (const float2*)x, o.n(), F, o.n(), nrhs, s);
+                self_gemm<float2, float2>(o, o.d_zself32.as<float2>(), (const float2*)x, o.n(), F, o.n(),
+                                          (float2*)y, o.n(), nrhs, 0, s);
+            }
+        } else if (precision == VIE_C128 || precision == VIE_C64_ACC64) {
+            if (precision == VIE_C128 && o.fprec != VIE_C128) fail(VIE_ERR_INVALID_ARG, "VIE_C128 applies need VIE_C128 factors");
+            if (precision == VIE_C64_ACC64 && o.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "VIE_C64_ACC64 needs VIE_C64 factors");
+            if (fuse) op_apply_fused64(o, (const double2*)x, (double2*)y, nrhs, s);
+            else op_apply64(o, (const double2*)x, (double2*)y, nrhs, s);
+        } else {
+            fail(VIE_ERR_INVALID_ARG, "unsupported apply precision");
+        }
+    });
+}
+
+int vie_precond(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int precision, vie_stream stream) {
+    if (!op) return VIE_ERR_INVALID_ARG;
+    return guarded(ctx_of(op), [&] {
+        Op& o = op->o;
+        set_device(*o.ctx);
+        if (!x || !y || nrhs < 1 || ld != o.n()) fail(VIE_ERR_INVALID_ARG, "vie_precond: bad vectors (ld must be n)");
+        cudaStream_t s = stream ? (cudaStream_t)stream : o.ctx->stream;
+        if (precision == VIE_C64)
+            self_gemm<float2, float2>(o, o.d_inv32.as<float2>(), (const float2*)x, o.n(), nullptr, 0, (float2*)y,
+                                      o.n(), nrhs, 2, s);
+        else if (precision == VIE_C128)
+            op_precond64(o, (const double2*)x, (double2*)y, nrhs, s);
+        else
+            fail(VIE_ERR_INVALID_ARG, "unsupported precond precision");
+    });
+}
+
+int vie_rhs(vie_op* op, const vie_incident* inc, int nrhs, void* b, int64_t ld, vie_stream stream) {
+    if (!op || !inc || !b || nrhs < 1) return VIE_ERR_INVALID_ARG;
+    return guarded(ctx_of(op), [&] {
+        Op& o = op->o;
+        set_device(*o.ctx);
+        if (ld < o.n()) fail(VIE_ERR_INVALID_ARG, "ld < n");
+        cudaStream_t s = stream ? (cudaStream_t)stream : o.ctx->stream;
+        DevBuf kh(3 * nrhs * sizeof(double)), pl(6 * nrhs * sizeof(double));
+        VIE_CUDA(cudaMemcpyAsync(kh.p, inc->khat, 3 * nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+        VIE_CUDA(cudaMemcpyAsync(pl.p, inc->pol, 6 * nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
+        rhs_kernel_launch(o, kh.as<double>(), pl.as<double>(), nrhs, b, ld, s);
+        VIE_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int vie_solve(vie_op* op, const vie_incident* inc, int nrhs, const vie_solve_opts* opts, void* I_out,
+              vie_solve_stats* stats) {
+    if (!op || !inc || !opts || !I_out || nrhs < 1) return VIE_ERR_INVALID_ARG;
+    int result = VIE_OK;
+    int st = guarded(ctx_of(op), [&] {
+        set_device(*op->o.ctx);
+        result = solve(op->o, inc, nrhs, opts, I_out, stats);
+    });
+    if (st != VIE_OK) return st;
+    if (result != VIE_OK && ctx_of(op)) ctx_of(op)->c.err = "GMRES did not reach the tolerance";
+    return result;
+}
+
+int vie_fields(vie_op* op, const vie_incident* inc, const void* I, int nrhs, const double* dirs, int npts, int mode,
+               void* E_out, double* sigma_out) {
+    if (!op || !I || nrhs < 1) return VIE_ERR_INVALID_ARG;
+    return guarded(ctx_of(op), [&] {
+        Op& o = op->o;
+        set_device(*o.ctx);
+        if (mode != 0) fail(VIE_ERR_INVALID_ARG, "only far-field mode 0 is implemented");
+        cudaStream_t s = o.ctx->stream;
+        const int64_t n = o.n();
+        DevBuf dI((size_t)n * nrhs * sizeof(double2));
+        VIE_CUDA(cudaMemcpyAsync(dI.p, I, dI.bytes, cudaMemcpyHostToDevice, s));
+        auto far = [&](const std::vector<double>& d, std::vector<cd>& F) {
+            int np_ = (int)(d.size() / 3);
+            DevBuf dd(d.size() * sizeof(double)), out((size_t)np_ * nrhs * 3 * sizeof(double2));
+            VIE_CUDA(cudaMemcpyAsync(dd.p, d.data(), dd.bytes, cudaMemcpyHostToDevice, s));
+            far_field_launch(o, dI.p, nrhs, dd.as<double>(), np_, out.p, s);
+            std::vector<cd> N((size_t)np_ * nrhs * 3);
+            VIE_CUDA(cudaMemcpyAsync(N.data(), out.p, out.bytes, cudaMemcpyDeviceToHost, s));
+            VIE_CUDA(cudaStreamSynchronize(s));
+            // F = -j k / (4 pi) (N - rhat (rhat . N))
+            F.resize(N.size());
+            for (int c = 0; c < nrhs; ++c)
+                for (int p = 0; p < np_; ++p) {
+                    const double* r = &d[3 * p];
+                    cd* v = &N[((size_t)c * np_ + p) * 3];
+                    cd dot = r[0] * v[0] + r[1] * v[1] + r[2] * v[2];
+                    for (int e = 0; e < 3; ++e)
+                        F[((size_t)c * np_ + p) * 3 + e] = cd(0, -o.k / (4 * M_PI)) * (v[e] - r[e] * dot);
+                }
+        };
+        if (E_out && dirs && npts > 0) {
+            std::vector<double> d(dirs, dirs + 3 * npts);
+            std::vector<cd> F;
+            far(d, F);
+            std::memcpy(E_out, F.data(), F.size() * sizeof(cd));
+        }
+        if (sigma_out) {
+            if (!inc) fail(VIE_ERR_INVALID_ARG, "cross sections need the incident field");
+            // 24-point Gauss-Legendre in cos(theta) x 48-point trapezoid in phi
+            const int nt = 24, nph = 48;
+            std::vector<double> x(nt), w(nt);
+            for (int i = 0; i < nt; ++i) {  // Newton on P_n
+                double z = std::cos(M_PI * (i + 0.75) / (nt + 0.5));
+                for (int it = 0; it < 100; ++it) {
+                    double p1 = 1, p2 = 0;
+                    for (int j = 1; j <= nt; ++j) {
+                        double p3 = p2;
+                        p2 = p1;
+                        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+                    }
+                    double pp = nt * (z * p1 - p2) / (z * z - 1.0);
+                    double z1 = z;
+                    z = z1 - p1 / pp;
+                    if (std::fabs(z - z1) < 1e-15) {
+                        w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+                        break;
+                    }
+                    w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+                }
+                x[i] = z;
+            }
+            std::vector<double> d, wt;
+            for (int i = 0; i < nt; ++i)
+                for (int j = 0; j < nph; ++j) {
+                    double st_ = std::sqrt(1 - x[i] * x[i]), ph = 2 * M_PI * j / nph;
+                    d.push_back(st_ * std::cos(ph));
+                    d.push_back(st_ * std::sin(ph));
+                    d.push_back(x[i]);
+                    wt.push_back(w[i] * 2 * M_PI / nph);
+                }
+            std::vector<cd> F;
+            far(d, F);
+            // extinction Re(I^H v0), v0 = b / (j k)
+            DevBuf b((size_t)n * nrhs * sizeof(double2)), kh(3 * nrhs * sizeof(double)), pl(6 * nrhs * sizeof(double));
+            VIE_CUDA(cudaMemcpyAsync(kh.p, inc->khat, kh.bytes, cudaMemcpyHostToDevice, s));
+            VIE_CUDA(cudaMemcpyAsync(pl.p, inc->pol, pl.bytes, cudaMemcpyHostToDevice, s));
+            rhs_kernel_launch(o, kh.as<double>(), pl.as<double>(), nrhs, b.p, n, s);
+            std::vector<cd> hb((size_t)n * nrhs);
+            VIE_CUDA(cudaMemcpyAsync(hb.data(), b.p, b.bytes, cudaMemcpyDeviceToHost, s));
+            VIE_CUDA(cudaStreamSynchronize(s));
+            const cd* hI = static_cast<const cd*>(I);
+            for (int c = 0; c < nrhs; ++c) {
+                cd acc = 0;
+                for (int64_t i = 0; i < n; ++i) acc += std::conj(hI[i + c * n]) * hb[i + c * n] / cd(0, o.k);
+                double sca = 0;
+                for (size_t p = 0; p < wt.size(); ++p)
+                    for (int e = 0; e < 3; ++e) sca += wt[p] * std::norm(F[((size_t)c * wt.size() + p) * 3 + e]);
+                sigma_out[2 * c] = acc.real();
+                sigma_out[2 * c + 1] = sca;
+            }
+        }
+    });
+}
+
+int vie_export_block(vie_op* op, int kind, int a, int b, int precision, void* out) {
+    if (!op || !out) return VIE_ERR_INVALID_ARG;
+    return guarded(ctx_of(op), [&] {
+        Op& o = op->o;
+        set_device(*o.ctx);
+        cudaStream_t s = o.ctx->stream;
+        const size_t np2 = (size_t)o.np * o.np;
+        if (kind == 0 || kind == 2) {
+            if (a < 0 || a >= o.T) fail(VIE_ERR_INVALID_ARG, "type out of range");
+            const DevBuf& src = kind == 0 ? o.d_zself64 : o.d_inv64;
+            VIE_CUDA(cudaMemcpyAsync(out, src.as<double2>() + a * np2, np2 * sizeof(double2), cudaMemcpyDeviceToHost, s));
+        } else if (kind == 1) {
+            if (a < 0 || b < 0 || a >= o.N || b >= o.N || a == b) fail(VIE_ERR_INVALID_ARG, "need two different atoms");
+            size_t esz = precision == VIE_C128 ? sizeof(double2) : sizeof(float2);
+            DevBuf blk(np2 * esz);
+            PairJob jb{a, b, 0, 0, 0};
+            std::vector<PairJob> jobs{jb};
+            std::vector<void*> dst{blk.p};
+            std::vector<int64_t> ld{o.np};
+            DevBuf dj, dd, dl;
+            upload(dj, jobs);
+            upload(dd, dst);
+            upload(dl, ld);
+            if (precision == VIE_C128)
+                assemble_pairs<double>(o, dj.as<PairJob>(), 1, dd.as<void* const>(), dl.as<int64_t>(), s);
+            else
+                assemble_pairs<float>(o, dj.as<PairJob>(), 1, dd.as<void* const>(), dl.as<int64_t>(), s);
+            VIE_CUDA(cudaMemcpyAsync(out, blk.p, np2 * esz, cudaMemcpyDeviceToHost, s));
+        } else {
+            fail(VIE_ERR_INVALID_ARG, "unknown block kind");
+        }
+        VIE_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int vie_far_block_info(vie_op* op, int64_t i, int* level, int* n_tatoms, int* n_satoms, int* rank) {
+    if (!op) return VIE_ERR_INVALID_ARG;
+    return guarded(ctx_of(op), [&] {
+        const Op& o = op->o;
+        if (i < 0 || i >= (int64_t)o.blocks.size()) fail(VIE_ERR_INVALID_ARG, "block index out of range");
+        const FarBlock& b = o.blocks[i];
+        if (level) *level = b.level;
+        if (n_tatoms) *n_tatoms = b.nt;
+        if (n_satoms) *n_satoms = b.ns;
+        if (rank) *rank = b.rank;
+    });
+}
+
+int vie_export_far_block(vie_op* op, int64_t i, int* tatoms, int* satoms, void* Q, void* R) {
+    if (!op) return VIE_ERR_INVALID_ARG;
+    return guarded(ctx_of(op), [&] {
+        Op& o = op->o;
+        set_device(*o.ctx);
+        if (i < 0 || i >= (int64_t)o.blocks.size()) fail(VIE_ERR_INVALID_ARG, "block index out of range");
+        const FarBlock& b = o.blocks[i];
+        if (tatoms) std::memcpy(tatoms, &o.block_atoms[b.t_off], b.nt * sizeof(int));
+        if (satoms) std::memcpy(satoms, &o.block_atoms[b.s_off], b.ns * sizeof(int));
+        if (!Q && !R) return;
+        if (o.fprec == 0) fail(VIE_ERR_STATE, "operator is not compressed");
+        const size_t cnt = (size_t)b.rank * (b.m + b.n);
+        std::vector<cd> h(cnt);
+        cudaStream_t s = o.ctx->stream;
+        if (o.fprec == VIE_C128) {
+            VIE_CUDA(cudaMemcpyAsync(h.data(), o.d_factors.as<double2>() + b.q_off, cnt * sizeof(double2),
+                                     cudaMemcpyDeviceToHost, s));
+        } else {
+            std::vector<std::complex<float>> f(cnt);
+            VIE_CUDA(cudaMemcpyAsync(f.data(), o.d_factors.as<float2>() + b.q_off, cnt * sizeof(float2),
+                                     cudaMemcpyDeviceToHost, s));
+            VIE_CUDA(cudaStreamSynchronize(s));
+            for (size_t e = 0; e < cnt; ++e) h[e] = cd(f[e].real(), f[e].imag());
+        }
+        VIE_CUDA(cudaStreamSynchronize(s));
+        cd* q = static_cast<cd*>(Q);
+        cd* r = static_cast<cd*>(R);
+        const size_t mq = (size_t)b.rank * b.m;
+        if (q) std::memcpy(q, h.data(), mq * sizeof(cd));
+        if (r)  // stored R^H (n x r col-major) -> R (r x n col-major)
+            for (int k = 0; k < b.rank; ++k)
+                for (int c = 0; c < b.n; ++c) r[k + (size_t)c * b.rank] = std::conj(h[mq + c + (size_t)k * b.n]);
+    });
+}
+
+int64_t vie_footprint_bytes(int64_t n, int np, int nrhs, int restart, int64_t factor_entries) {
+    // factors (c64) + self/inverse blocks (c128 + c64, two per type upper bound 3 types)
+    // + Krylov basis (restart + 1) n c128 per rhs in flight + solver vectors
+    int64_t m = restart > 0 ? restart : 60;
+    int64_t bytes = 8 * factor_entries;
+    bytes += 3 * (int64_t)np * np * (16 + 16 + 8 + 8);
+    bytes += (m + 1) * n * 16;
+    bytes += n * (int64_t)nrhs * (16 * 3 + 8 * 2) + n * 16 * 6;
+    return bytes;
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// Compressed far-field apply (paper Sec. 5.2, eq. eq_02): for every far block
+// b = (target box I, source box J),  F_I += Q_b (R_b x_J),  evaluated as
+//   phase 1:  t_b = R_b x_J        (r_b values per right-hand side)
+//   phase 2:  F_a = sum_b Q_b[rows of atom a] t_b   for every atom a
+// Both phases are persistent kernels over static work lists that the greedy
+// least-loaded rule of App. C (weights = factor bytes) maps onto the CTAs.
+// Every output element is written once by one thread (no atomics), so the
+// result does not depend on the schedule or on other work on the GPU.
+//
+// Storage: Q_b is m_b x r_b column-major; R_b is kept as R_b^H (n_b x r_b
+// column-major, i.e. conj(R_b) row-major), so both phases stream their
+// factor with unit stride; complex values are interleaved and pairs of
+// complex float32 move as one 16-byte load.
+#include "common.h"
+#include "cplx.cuh"
+
+namespace vie {
+
+namespace {
+
+template <class T2> struct Pair { T2 a, b; };
+
+__device__ __forceinline__ Pair<float2> ldpair(const float2* p) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ Pair<double2> ldpair(const double2* p) {
+    return {__ldg(p), __ldg(p + 1)};
+}
+// streaming (read-once) variant for the factors
+__device__ __forceinline__ Pair<float2> ldpair_stream(const float2* p) {
+    float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ Pair<double2> ldpair_stream(const double2* p) {
+    return {__ldcs(p), __ldcs(p + 1)};
+}
+
+template <class T2> __device__ __forceinline__ T2 shfl_down2(T2 v, int o) {
+    v.x = __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y = __shfl_down_sync(0xffffffffu, v.y, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// phase 1: one warp per group of ROWS rows of R_b, lanes stride over columns
+// ---------------------------------------------------------------------------
+template <class TF, class TX, int ROWS>
+__global__ void __launch_bounds__(256) p1_kernel(const FarBlockDev* __restrict__ blocks,
+                                                 const int* __restrict__ batoms, const int4* __restrict__ items,
+                                                 const int* __restrict__ cta_ptr, const TF* __restrict__ factors,
+                                                 const TX* __restrict__ x, int64_t ldx, int np,
+                                                 TX* __restrict__ t, int64_t ldt, int nrhs) {
+    using TA = TX;  // accumulate in the vector precision
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1]; ++it) {
+        const int4 item = items[it];
+        const FarBlockDev B = blocks[item.x];
+        const TF* RH = factors + B.rh_off;
+        const int* S = batoms + B.s_off;
+        for (int k = item.y + warp * ROWS; k < item.z; k += nwarps * ROWS) {
+            const int nrow = min(ROWS, item.z - k);
+            for (int c0 = 0; c0 < nrhs; ++c0) {
+                TA acc[ROWS];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) acc[r] = mk(decltype(acc[0].x)(0), decltype(acc[0].x)(0));
+                // column c = 2 lane + 64 i; (slot, off) tracked incrementally
+                int c = 2 * lane;
+                int slot = c / np, off = c - slot * np;
+                const TX* xc = x + (int64_t)c0 * ldx;
+                for (; c < B.n; c += 64) {
+                    Pair<TX> xv = ldpair(xc + (int64_t)S[slot] * np + off);
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) {
+                        if (r < nrow) {
+                            Pair<TF> rv = ldpair_stream(RH + c + (int64_t)(k + r) * B.n);
+                            cfmac(acc[r], cvt<TA>(rv.a), xv.a);
+                            cfmac(acc[r], cvt<TA>(rv.b), xv.b);
+                        }
+                    }
+                    off += 64;
+                    while (off >= np) { off -= np; ++slot; }
+                }
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    TA v = acc[r];
+                    for (int o = 16; o > 0; o >>= 1) v += shfl_down2(v, o);
+                    if (lane == 0 && r < nrow) t[B.tvec_off + k + r + (int64_t)c0 * ldt] = v;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// phase 2: item = (atom a, rows p0..p1 of a).  256 threads = 64 row pairs x
+// 4 rank groups; each thread streams Q column segments of 2 rows and the
+// partial sums of the 4 rank groups are added in a fixed order at the end.
+// ---------------------------------------------------------------------------
+template <class TF, class TX>
+__global__ void __launch_bounds__(256) p2_kernel(const FarBlockDev* __restrict__ blocks,
+                                                 const int4* __restrict__ items, const int* __restrict__ cta_ptr,
+                                                 const int* __restrict__ csr, const int2* __restrict__ ent,
+                                                 const TF* __restrict__ factors, const TX* __restrict__ t,
+                                                 int64_t ldt, int np, TX* __restrict__ F, int64_t ldf, int nrhs) {
+    using TA = TX;
+    using R = decltype(TA().x);
+    __shared__ TA red[3][64][2];
+    const int rp = threadIdx.x & 63, kg = threadIdx.x >> 6;
+    for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1]; ++it) {
+        const int4 item = items[it];
+        const int a = item.x;
+        const int row = item.y + 2 * rp;
+        const bool active = row < item.z;
+        for (int c0 = 0; c0 < nrhs; ++c0) {
+            TA acc0 = mk(R(0), R(0)), acc1 = mk(R(0), R(0));
+            if (active) {
+                for (int e = csr[a]; e < csr[a + 1]; ++e) {
+                    const int2 en = ent[e];
+                    const FarBlockDev B = blocks[en.x];
+                    const TF* Q = factors + B.q_off + (int64_t)en.y * np + row;
+                    const TX* tb = t + B.tvec_off + (int64_t)c0 * ldt;
+                    int k = kg;
+                    for (; k + 12 < B.rank; k += 16) {
+                        Pair<TF> q0 = ldpair_stream(Q + (int64_t)k * B.m);
+                        Pair<TF> q1 = ldpair_stream(Q + (int64_t)(k + 4) * B.m);
+                        Pair<TF> q2 = ldpair_stream(Q + (int64_t)(k + 8) * B.m);
+                        Pair<TF> q3 = ldpair_stream(Q + (int64_t)(k + 12) * B.m);
+                        TA t0 = tb[k], t1 = tb[k + 4], t2 = tb[k + 8], t3 = tb[k + 12];
+                        cfma(acc0, cvt<TA>(q0.a), t0); cfma(acc1, cvt<TA>(q0.b), t0);
+                        cfma(acc0, cvt<TA>(q1.a), t1); cfma(acc1, cvt<TA>(q1.b), t1);
+                        cfma(acc0, cvt<TA>(q2.a), t2); cfma(acc1, cvt<TA>(q2.b), t2);
+                        cfma(acc0, cvt<TA>(q3.a), t3); cfma(acc1, cvt<TA>(q3.b), t3);
+                    }
+                    for (; k < B.rank; k += 4) {
+                        Pair<TF> q0 = ldpair_stream(Q + (int64_t)k * B.m);
+                        TA t0 = tb[k];
+                        cfma(acc0, cvt<TA>(q0.a), t0);
+                        cfma(acc1, cvt<TA>(q0.b), t0);
+                    }
+                }
+            }
+            if (kg > 0) {
+                red[kg - 1][rp][0] = acc0;
+                red[kg - 1][rp][1] = acc1;
+            }
+            __syncthreads();
+            if (kg == 0 && active) {
+                for (int g = 0; g < 3; ++g) {
+                    acc0 += red[g][rp][0];
+                    acc1 += red[g][rp][1];
+                }
+                TX* out = F + (int64_t)a * np + row + (int64_t)c0 * ldf;
+                out[0] = acc0;
+                out[1] = acc1;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+
+template <class TF, class TX>
+void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, cudaStream_t s) {
+    size_t need = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(TX);
+    if (op.d_t.bytes < need) op.d_t.alloc(need);
+    const TF* fac = op.d_factors.as<TF>();
+    const int nc = op.n_cta;
+    if (op.n_p1_items > 0) {
+        p1_kernel<TF, TX, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
+                                                op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, x, ldx,
+                                                op.np, op.d_t.as<TX>(), op.t_total, nrhs);
+        VIE_CHECK_LAUNCH();
+    }
+    p2_kernel<TF, TX><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
+                                         op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(),
+                                         fac, op.d_t.as<TX>(), op.t_total, op.np, F, ldf, nrhs);
+    VIE_CHECK_LAUNCH();
+}
+
+template void apply_far<float2, float2>(Op&, const float2*, int64_t, float2*, int64_t, int, cudaStream_t);
+template void apply_far<float2, double2>(Op&, const double2*, int64_t, double2*, int64_t, int, cudaStream_t);
+template void apply_far<double2, double2>(Op&, const double2*, int64_t, double2*, int64_t, int, cudaStream_t);
+
+}  // namespace vie

@@ -1,0 +1,772 @@
+// Galerkin entries of the scaled VIE matrix (paper Sec. 3, eq. matrixeq):
+//   Zs = M / chi - k^2 L + D,
+// M_ij = int w_i.w_j, L_ij = int int w_i g w_j, D_ij = int int q_i g q_j with
+// q = div w (volume charge on the voxels beside a face plus a sheet on a
+// boundary face), g = exp(-j k R) / (4 pi R).
+//
+// Quadrature rule (the paper leaves it to its references; this is the
+// library's definition):
+//   * elements in different atoms: Gauss-Legendre, 2 points per axis on both;
+//   * separated elements of one atom: Gauss-Legendre, 3 points per axis;
+//   * touching elements of one atom: g = 1/(4 pi R) + g_s; the static part
+//     integrates the source element in closed form (uniform box, linear box,
+//     uniform rectangle) and the test element with 6 Gauss points per axis;
+//     g_s = (exp(-j k R) - 1)/(4 pi R) (limit -j k/(4 pi)) uses 3 points.
+//
+// Work is organised in two kernels per atom pair: element-pair tables
+// (U = int int g over voxel pairs, W[d][sa][sb] with the rooftop profiles
+// xi / 1 - xi along d, and the uniform voxel/sheet combinations VS, SV, SS),
+// then one thread per matrix entry gathers its (at most 2 x 2) element pairs.
+#include <cmath>
+
+#include "common.h"
+#include "cplx.cuh"
+
+namespace vie {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kInv4Pi = 1.0 / (4.0 * kPi);
+
+// Gauss-Legendre on [0, 1]
+__constant__ double c_gl3_x[3] = {0.11270166537925831148, 0.5, 0.88729833462074168852};
+__constant__ double c_gl3_w[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+__constant__ double c_gl6_x[6] = {0.03376524289842398609, 0.16939530676686774317, 0.38069040695840154568,
+                                  0.61930959304159845432, 0.83060469323313225683, 0.96623475710157601391};
+__constant__ double c_gl6_w[6] = {0.08566224618958517252, 0.18038078652406930378, 0.23395696728634552369,
+                                  0.23395696728634552369, 0.18038078652406930378, 0.08566224618958517252};
+// 2-point nodes xi = 1/2 -+ 1/(2 sqrt 3); weights 1/2
+constexpr double kGl2Off = 0.28867513459481288225;  // 1/(2 sqrt 3)
+
+// --------------------------------------------------------------------------
+// closed-form inner integrals (source minus field coordinates u, v, w)
+// --------------------------------------------------------------------------
+__device__ double log_a_plus_R(double a, double R, double rest2) {
+    if (R == 0.0) return 0.0;
+    if (a >= 0.0) return log(a + R);
+    if (rest2 <= 0.0) return 0.0;
+    return log(rest2) - log(R - a);   // a + R = rest2 / (R - a) for a < 0
+}
+__device__ double atan_ratio(double num, double den) { return den != 0.0 ? atan(num / den) : 0.0; }
+
+// d^3 F / du dv dw = 1/R
+__device__ double F_box(double u, double v, double w) {
+    double u2 = u * u, v2 = v * v, w2 = w * w;
+    double R = sqrt(u2 + v2 + w2);
+    double t = v * w * log_a_plus_R(u, R, v2 + w2) + u * w * log_a_plus_R(v, R, u2 + w2) +
+               u * v * log_a_plus_R(w, R, u2 + v2);
+    t -= 0.5 * u2 * atan_ratio(v * w, u * R);
+    t -= 0.5 * v2 * atan_ratio(u * w, v * R);
+    t -= 0.5 * w2 * atan_ratio(u * v, w * R);
+    return t;
+}
+// d^2 G / du dv = 1/R
+__device__ double G_rect(double u, double v, double w) {
+    double R = sqrt(u * u + v * v + w * w);
+    return u * log_a_plus_R(v, R, u * u + w * w) + v * log_a_plus_R(u, R, v * v + w * w) -
+           w * atan_ratio(u * v, w * R);
+}
+// d^2 H / du dv = R
+__device__ double H_rectR(double u, double v, double w) {
+    double R = sqrt(u * u + v * v + w * w);
+    return u * v * R / 3.0 + (u * u * u + 3.0 * u * w * w) / 6.0 * log_a_plus_R(v, R, u * u + w * w) +
+           (v * v * v + 3.0 * v * w * w) / 6.0 * log_a_plus_R(u, R, v * v + w * w) -
+           w * w * w / 3.0 * atan_ratio(u * v, w * R);
+}
+
+// int_box dV'/|r - r'|
+__device__ double box_pot(const double r[3], const double lo[3], const double hi[3]) {
+    double acc = 0.0;
+    for (int ix = 0; ix < 2; ++ix)
+        for (int iy = 0; iy < 2; ++iy)
+            for (int iz = 0; iz < 2; ++iz) {
+                double u = (ix ? hi[0] : lo[0]) - r[0];
+                double v = (iy ? hi[1] : lo[1]) - r[1];
+                double w = (iz ? hi[2] : lo[2]) - r[2];
+                // sign = product over axes of (+1 for hi, -1 for lo)
+                double s = (ix ? 1.0 : -1.0) * (iy ? 1.0 : -1.0) * (iz ? 1.0 : -1.0);
+                acc += s * F_box(u, v, w);
+            }
+    return acc;
+}
+
+// rectangle {r'_axis = c, lo <= r'_other <= hi}: kernel K(u, v, w) summed over corners
+template <int KIND>  // 0: 1/R, 1: R
+__device__ double rect_int(const double r[3], int axis, double c, const double lo[3], const double hi[3]) {
+    int a = axis == 0 ? 1 : 0;
+    int b = axis == 2 ? 1 : 2;
+    double w = c - r[axis];
+    double acc = 0.0;
+    for (int iu = 0; iu < 2; ++iu)
+        for (int iv = 0; iv < 2; ++iv) {
+            double u = (iu ? hi[a] : lo[a]) - r[a];
+            double v = (iv ? hi[b] : lo[b]) - r[b];
+            double s = (iu ? 1.0 : -1.0) * (iv ? 1.0 : -1.0);
+            acc += s * (KIND == 0 ? G_rect(u, v, w) : H_rectR(u, v, w));
+        }
+    return acc;
+}
+
+// int_box xi_d(r') / |r - r'| dV',  xi_d = (r'_d - lo_d) / (hi_d - lo_d)
+__device__ double box_lin_pot(const double r[3], const double lo[3], const double hi[3], int d, double phi) {
+    double top = rect_int<1>(r, d, hi[d], lo, hi);
+    double bot = rect_int<1>(r, d, lo[d], lo, hi);
+    return (top - bot + (r[d] - lo[d]) * phi) / (hi[d] - lo[d]);
+}
+
+// full and smooth Green's functions (times 4 pi)
+template <class T>
+__device__ __forceinline__ typename C2<T>::t green4pi(T R, T two_over_lambda) {
+    T s, c;
+    sincospi_t(R * two_over_lambda, &s, &c);
+    T inv = T(1) / R;
+    return mk(c * inv, -s * inv);
+}
+__device__ __forceinline__ double2 green4pi_smooth(double R, double k) {
+    if (R == 0.0) return make_double2(0.0, -k);
+    double s = sin(0.5 * k * R);
+    return make_double2(-2.0 * s * s / R, -sin(k * R) / R);
+}
+
+// --------------------------------------------------------------------------
+// self tables (one atom type, float64, local coordinates)
+// tables layout: plane 0 = U, planes 1 + 4 d + 2 sa + sb = W[d][sa][sb],
+// each nvox x nvox (A * nvox + B); then VS (nvox x nsurf), SV (nsurf x nvox),
+// SS (nsurf x nsurf).
+// --------------------------------------------------------------------------
+__device__ void vox_box(const DevMesh& m, int A, double h, double lo[3], double hi[3]) {
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = h * m.vox_ijk[3 * A + d];
+        hi[d] = lo[d] + h;
+    }
+}
+// surface element: axis, plane coordinate, lo/hi (hi[axis] = lo[axis])
+__device__ int surf_rect(const DevMesh& m, int s, double h, double lo[3], double hi[3], int ext[6]) {
+    int f = m.surf_face[s];
+    int4 fi = m.face[f];
+    int d = fi.x;
+    // recover (i, j, k) of face f from its position in the direction-major numbering
+    int nv = m.nv;
+    int per_dir = (nv + 1) * nv * nv;
+    int g = f - d * per_dir;
+    int ijk[3];
+    if (d == 0) { ijk[0] = g / (nv * nv); ijk[1] = (g / nv) % nv; ijk[2] = g % nv; }
+    else if (d == 1) { ijk[0] = g / (nv * (nv + 1)); ijk[1] = (g / nv) % (nv + 1); ijk[2] = g % nv; }
+    else { ijk[0] = g / (nv * (nv + 1)); ijk[1] = (g / (nv + 1)) % nv; ijk[2] = g % (nv + 1); }
+    for (int e = 0; e < 3; ++e) {
+        lo[e] = h * ijk[e];
+        hi[e] = (e == d) ? lo[e] : lo[e] + h;
+        ext[2 * e] = ijk[e];
+        ext[2 * e + 1] = (e == d) ? ijk[e] : ijk[e] + 1;
+    }
+    return d;
+}
+
+__global__ void self_vv_kernel(DevMesh m, double h, double k, double2* tab) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int nv2 = m.nvox * m.nvox;
+    if (t >= nv2) return;
+    int A = t / m.nvox, B = t % m.nvox;
+    double loA[3], hiA[3], loB[3], hiB[3];
+    vox_box(m, A, h, loA, hiA);
+    vox_box(m, B, h, loB, hiB);
+    bool touch = true;
+    for (int d = 0; d < 3; ++d) touch &= abs(m.vox_ijk[3 * A + d] - m.vox_ijk[3 * B + d]) <= 1;
+    const double two_over_lambda = k / kPi;
+
+    // Gauss-Gauss part (full g if separated, smooth remainder if touching);
+    // G[d][a][b] = sum over point pairs with node a (resp. b) along d
+    double2 G[3][3][3];
+    for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) G[d][a][b] = make_double2(0, 0);
+    for (int pa = 0; pa < 27; ++pa) {
+        int ax = pa / 9, ay = (pa / 3) % 3, az = pa % 3;
+        double ra[3] = {loA[0] + h * c_gl3_x[ax], loA[1] + h * c_gl3_x[ay], loA[2] + h * c_gl3_x[az]};
+        double wa = c_gl3_w[ax] * c_gl3_w[ay] * c_gl3_w[az];
+        for (int pb = 0; pb < 27; ++pb) {
+            int bx = pb / 9, by = (pb / 3) % 3, bz = pb % 3;
+            double dx = ra[0] - (loB[0] + h * c_gl3_x[bx]);
+            double dy = ra[1] - (loB[1] + h * c_gl3_x[by]);
+            double dz = ra[2] - (loB[2] + h * c_gl3_x[bz]);
+            double R = sqrt(dx * dx + dy * dy + dz * dz);
+            double2 g = touch ? green4pi_smooth(R, k) : green4pi<double>(R, two_over_lambda);
+            double wgt = wa * c_gl3_w[bx] * c_gl3_w[by] * c_gl3_w[bz];
+            g = wgt * g;
+            G[0][ax][bx] += g;
+            G[1][ay][by] += g;
+            G[2][az][bz] += g;
+        }
+    }
+    double scale = h * h * h * h * h * h * kInv4Pi;
+    double2 U = make_double2(0, 0);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) U += G[0][a][b];
+    U = scale * U;
+    double2 W[3][2][2];
+    for (int d = 0; d < 3; ++d)
+        for (int sa = 0; sa < 2; ++sa)
+            for (int sb = 0; sb < 2; ++sb) {
+                double2 acc = make_double2(0, 0);
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        double pa = sa ? 1.0 - c_gl3_x[a] : c_gl3_x[a];
+                        double pb = sb ? 1.0 - c_gl3_x[b] : c_gl3_x[b];
+                        acc += (pa * pb) * G[d][a][b];
+                    }
+                W[d][sa][sb] = scale * acc;
+            }
+    if (touch) {
+        // static part: outer 6-point rule on A, closed-form inner over B
+        double h3 = h * h * h;
+        for (int p = 0; p < 216; ++p) {
+            int ix = p / 36, iy = (p / 6) % 6, iz = p % 6;
+            double xi[3] = {c_gl6_x[ix], c_gl6_x[iy], c_gl6_x[iz]};
+            double r[3] = {loA[0] + h * xi[0], loA[1] + h * xi[1], loA[2] + h * xi[2]};
+            double wp = h3 * c_gl6_w[ix] * c_gl6_w[iy] * c_gl6_w[iz] * kInv4Pi;
+            double phi = box_pot(r, loB, hiB);
+            U.x += wp * phi;
+            for (int d = 0; d < 3; ++d) {
+                double lin = box_lin_pot(r, loB, hiB, d, phi);
+                double inner[2] = {lin, phi - lin};
+                double prof[2] = {xi[d], 1.0 - xi[d]};
+                for (int sa = 0; sa < 2; ++sa)
+                    for (int sb = 0; sb < 2; ++sb) W[d][sa][sb].x += wp * prof[sa] * inner[sb];
+            }
+        }
+    }
+    tab[t] = U;
+    for (int d = 0; d < 3; ++d)
+        for (int sa = 0; sa < 2; ++sa)
+            for (int sb = 0; sb < 2; ++sb) tab[(size_t)(1 + 4 * d + 2 * sa + sb) * nv2 + t] = W[d][sa][sb];
+}
+
+// uniform voxel/sheet combinations of one atom with itself
+// mode 0: VS (voxel A, sheet s), 1: SV (sheet s, voxel B), 2: SS
+__global__ void self_surf_kernel(DevMesh m, double h, double k, double2* tab) {
+    int mode = blockIdx.y;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int nA = mode == 2 ? m.nsurf : (mode == 0 ? m.nvox : m.nsurf);
+    int nB = mode == 2 ? m.nsurf : (mode == 0 ? m.nsurf : m.nvox);
+    if (t >= nA * nB) return;
+    int ia = t / nB, ib = t % nB;
+    const double two_over_lambda = k / kPi;
+    // element descriptions
+    double loA[3], hiA[3], loB[3], hiB[3];
+    int extA[6], extB[6];
+    int axA = -1, axB = -1;
+    if (mode == 0 || mode == 1) {
+        int v = mode == 0 ? ia : ib;
+        int s = mode == 0 ? ib : ia;
+        double lo[3], hi[3], slo[3], shi[3];
+        int vext[6], sext[6];
+        vox_box(m, v, h, lo, hi);
+        for (int e = 0; e < 3; ++e) { vext[2 * e] = m.vox_ijk[3 * v + e]; vext[2 * e + 1] = vext[2 * e] + 1; }
+        int ax = surf_rect(m, s, h, slo, shi, sext);
+        if (mode == 0) {
+            for (int e = 0; e < 3; ++e) { loA[e] = lo[e]; hiA[e] = hi[e]; loB[e] = slo[e]; hiB[e] = shi[e]; }
+            for (int e = 0; e < 6; ++e) { extA[e] = vext[e]; extB[e] = sext[e]; }
+            axB = ax;
+        } else {
+            for (int e = 0; e < 3; ++e) { loA[e] = slo[e]; hiA[e] = shi[e]; loB[e] = lo[e]; hiB[e] = hi[e]; }
+            for (int e = 0; e < 6; ++e) { extA[e] = sext[e]; extB[e] = vext[e]; }
+            axA = ax;
+        }
+    } else {
+        axA = surf_rect(m, ia, h, loA, hiA, extA);
+        axB = surf_rect(m, ib, h, loB, hiB, extB);
+    }
+    bool touch = true;
+    for (int e = 0; e < 3; ++e) touch &= max(extA[2 * e], extB[2 * e]) <= min(extA[2 * e + 1], extB[2 * e + 1]);
+
+    // Gauss-Gauss part with 3 points per axis of each element
+    auto npts = [](int ax) { return ax < 0 ? 27 : 9; };
+    auto point = [&](int ax, const double lo[3], int p, double r[3], double& w) {
+        if (ax < 0) {
+            int i0 = p / 9, i1 = (p / 3) % 3, i2 = p % 3;
+            r[0] = lo[0] + h * c_gl3_x[i0];
+            r[1] = lo[1] + h * c_gl3_x[i1];
+            r[2] = lo[2] + h * c_gl3_x[i2];
+            w = h * h * h * c_gl3_w[i0] * c_gl3_w[i1] * c_gl3_w[i2];
+        } else {
+            int a = ax == 0 ? 1 : 0, b = ax == 2 ? 1 : 2;
+            int i0 = p / 3, i1 = p % 3;
+            r[ax] = lo[ax];
+            r[a] = lo[a] + h * c_gl3_x[i0];
+            r[b] = lo[b] + h * c_gl3_x[i1];
+            w = h * h * c_gl3_w[i0] * c_gl3_w[i1];
+        }
+    };
+    double2 acc = make_double2(0, 0);
+    for (int p = 0; p < npts(axA); ++p) {
+        double ra[3], wa;
+        point(axA, loA, p, ra, wa);
+        for (int q = 0; q < npts(axB); ++q) {
+            double rb[3], wb;
+            point(axB, loB, q, rb, wb);
+            double dx = ra[0] - rb[0], dy = ra[1] - rb[1], dz = ra[2] - rb[2];
+            double R = sqrt(dx * dx + dy * dy + dz * dz);
+            double2 g = touch ? green4pi_smooth(R, k) : green4pi<double>(R, two_over_lambda);
+            acc += (wa * wb) * g;
+        }
+    }
+    acc = kInv4Pi * acc;
+    if (touch) {
+        // static part: outer 6-point rule on the test element, closed-form inner
+        int nq = axA < 0 ? 216 : 36;
+        for (int p = 0; p < nq; ++p) {
+            double r[3], wp;
+            if (axA < 0) {
+                int i0 = p / 36, i1 = (p / 6) % 6, i2 = p % 6;
+                r[0] = loA[0] + h * c_gl6_x[i0];
+                r[1] = loA[1] + h * c_gl6_x[i1];
+                r[2] = loA[2] + h * c_gl6_x[i2];
+                wp = h * h * h * c_gl6_w[i0] * c_gl6_w[i1] * c_gl6_w[i2];
+            } else {
+                int a = axA == 0 ? 1 : 0, b = axA == 2 ? 1 : 2;
+                int i0 = p / 6, i1 = p % 6;
+                r[axA] = loA[axA];
+                r[a] = loA[a] + h * c_gl6_x[i0];
+                r[b] = loA[b] + h * c_gl6_x[i1];
+                wp = h * h * c_gl6_w[i0] * c_gl6_w[i1];
+            }
+            double inner = axB < 0 ? box_pot(r, loB, hiB) : rect_int<0>(r, axB, loB[axB], loB, hiB);
+            acc.x += wp * inner * kInv4Pi;
+        }
+    }
+    size_t nv2 = (size_t)m.nvox * m.nvox;
+    size_t base = 13 * nv2;
+    if (mode == 0) tab[base + (size_t)ia * m.nsurf + ib] = acc;
+    else if (mode == 1) tab[base + (size_t)m.nvox * m.nsurf + (size_t)ia * m.nvox + ib] = acc;
+    else tab[base + 2 * (size_t)m.nvox * m.nsurf + (size_t)ia * m.nsurf + ib] = acc;
+}
+
+// --------------------------------------------------------------------------
+// tables between two different atoms (2-point Gauss-Legendre everywhere)
+// --------------------------------------------------------------------------
+struct GeoPtrs {
+    const double* centres;
+    const int* types;
+    const double* sides;
+};
+
+__device__ __forceinline__ void vox_centre(const DevMesh& m, const GeoPtrs& g, int atom, int v, double c[3],
+                                           double& h) {
+    double side = g.sides[g.types[atom]];
+    h = side / m.nv;
+    for (int d = 0; d < 3; ++d) c[d] = g.centres[3 * atom + d] - 0.5 * side + h * (m.vox_ijk[3 * v + d] + 0.5);
+}
+
+// centre of a boundary face (plane coordinate along its axis)
+__device__ __forceinline__ int surf_centre(const DevMesh& m, const GeoPtrs& g, int atom, int s, double c[3],
+                                           double& h) {
+    double side = g.sides[g.types[atom]];
+    h = side / m.nv;
+    double lo[3], hi[3];
+    int ext[6];
+    int ax = surf_rect(m, s, h, lo, hi, ext);
+    for (int d = 0; d < 3; ++d)
+        c[d] = g.centres[3 * atom + d] - 0.5 * side + (d == ax ? lo[d] : lo[d] + 0.5 * h);
+    return ax;
+}
+
+template <class T>
+__global__ void cross_vv_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, T two_over_lambda,
+                                typename C2<T>::t* tab, size_t job_stride) {
+    using T2 = typename C2<T>::t;
+    const int job = blockIdx.y;
+    const int nv2 = m.nvox * m.nvox;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nv2) return;
+    const int A = t / m.nvox, B = t % m.nvox;
+    const PairJob jb = jobs[job];
+    double cA[3], cB[3], hA, hB;
+    vox_centre(m, geo, jb.a, A, cA, hA);
+    vox_centre(m, geo, jb.b, B, cB, hB);
+    // displacement in float64, then the small node offsets in T
+    T D[3] = {T(cA[0] - cB[0]), T(cA[1] - cB[1]), T(cA[2] - cB[2])};
+    const T oA = T(hA * kGl2Off), oB = T(hB * kGl2Off);
+    T dd[3][2][2];
+    for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) dd[d][a][b] = D[d] + (a ? oA : -oA) - (b ? oB : -oB);
+    T2 G[3][2][2];
+    for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) G[d][a][b] = mk(T(0), T(0));
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+        for (int bx = 0; bx < 2; ++bx) {
+            T x2 = dd[0][ax][bx] * dd[0][ax][bx];
+#pragma unroll
+            for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+                for (int by = 0; by < 2; ++by) {
+                    T xy2 = x2 + dd[1][ay][by] * dd[1][ay][by];
+#pragma unroll
+                    for (int az = 0; az < 2; ++az)
+#pragma unroll
+                        for (int bz = 0; bz < 2; ++bz) {
+                            T r2 = xy2 + dd[2][az][bz] * dd[2][az][bz];
+                            T inv = rsqrt_t(r2);
+                            T R = r2 * inv;
+                            T s, c;
+                            sincospi_t(R * two_over_lambda, &s, &c);
+                            T2 g = mk(c * inv, -s * inv);
+                            G[0][ax][bx] += g;
+                            G[1][ay][by] += g;
+                            G[2][az][bz] += g;
+                        }
+                }
+        }
+    const T scale = T(hA * hA * hA * hB * hB * hB / 64.0 * kInv4Pi);
+    const T xn[2] = {T(0.5 - kGl2Off), T(0.5 + kGl2Off)};
+    T2* out = tab + (size_t)job * job_stride;
+    T2 U = G[0][0][0] + G[0][0][1] + G[0][1][0] + G[0][1][1];
+    out[t] = scale * U;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int sa = 0; sa < 2; ++sa)
+#pragma unroll
+            for (int sb = 0; sb < 2; ++sb) {
+                T2 acc = mk(T(0), T(0));
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        T pa = sa ? T(1) - xn[a] : xn[a];
+                        T pb = sb ? T(1) - xn[b] : xn[b];
+                        acc += (pa * pb) * G[d][a][b];
+                    }
+                out[(size_t)(1 + 4 * d + 2 * sa + sb) * nv2 + t] = scale * acc;
+            }
+}
+
+template <class T>
+__global__ void cross_surf_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, T two_over_lambda,
+                                  typename C2<T>::t* tab, size_t job_stride) {
+    using T2 = typename C2<T>::t;
+    const int job = blockIdx.z;
+    const int mode = blockIdx.y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nA = mode == 0 ? m.nvox : m.nsurf;
+    const int nB = mode == 1 ? m.nvox : m.nsurf;
+    if (t >= nA * nB) return;
+    const int ia = t / nB, ib = t % nB;
+    const PairJob jb = jobs[job];
+    double cA[3], cB[3], hA, hB;
+    int axA = -1, axB = -1;
+    if (mode == 0) vox_centre(m, geo, jb.a, ia, cA, hA);
+    else axA = surf_centre(m, geo, jb.a, ia, cA, hA);
+    if (mode == 1) vox_centre(m, geo, jb.b, ib, cB, hB);
+    else axB = surf_centre(m, geo, jb.b, ib, cB, hB);
+    T D[3] = {T(cA[0] - cB[0]), T(cA[1] - cB[1]), T(cA[2] - cB[2])};
+    const T oA = T(hA * kGl2Off), oB = T(hB * kGl2Off);
+    const int na = axA < 0 ? 8 : 4, nb = axB < 0 ? 8 : 4;
+    T2 acc = mk(T(0), T(0));
+    for (int p = 0; p < na; ++p) {
+        T pa[3];
+        int bit = 0;
+        for (int d = 0; d < 3; ++d) {
+            if (d == axA) { pa[d] = T(0); continue; }
+            int sgn = (p >> (na == 8 ? 2 - d : bit)) & 1;
+            if (na == 4) ++bit;
+            pa[d] = sgn ? oA : -oA;
+        }
+        for (int q = 0; q < nb; ++q) {
+            T pb[3];
+            int bitb = 0;
+            for (int d = 0; d < 3; ++d) {
+                if (d == axB) { pb[d] = T(0); continue; }
+                int sgn = (q >> (nb == 8 ? 2 - d : bitb)) & 1;
+                if (nb == 4) ++bitb;
+                pb[d] = sgn ? oB : -oB;
+            }
+            T dx = D[0] + pa[0] - pb[0], dy = D[1] + pa[1] - pb[1], dz = D[2] + pa[2] - pb[2];
+            T r2 = dx * dx + dy * dy + dz * dz;
+            T inv = rsqrt_t(r2);
+            T s, c;
+            sincospi_t(r2 * inv * two_over_lambda, &s, &c);
+            acc += mk(c * inv, -s * inv);
+        }
+    }
+    double wA = axA < 0 ? hA * hA * hA / 8.0 : hA * hA / 4.0;
+    double wB = axB < 0 ? hB * hB * hB / 8.0 : hB * hB / 4.0;
+    acc = T(wA * wB * kInv4Pi) * acc;
+    const size_t nv2 = (size_t)m.nvox * m.nvox;
+    T2* out = tab + (size_t)job * job_stride + 13 * nv2;
+    if (mode == 0) out[(size_t)ia * m.nsurf + ib] = acc;
+    else if (mode == 1) out[(size_t)m.nvox * m.nsurf + (size_t)ia * m.nvox + ib] = acc;
+    else out[2 * (size_t)m.nvox * m.nsurf + (size_t)ia * m.nsurf + ib] = acc;
+}
+
+// --------------------------------------------------------------------------
+// entries from tables: -k^2 L + D (+ M / chi for a self block)
+// --------------------------------------------------------------------------
+template <class T, class TO, bool SELF>
+__global__ void entries_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, double k2,
+                               const typename C2<T>::t* tab, size_t job_stride, TO* const* dst,
+                               const int64_t* ld, const double2* inv_chi) {
+    using T2 = typename C2<T>::t;
+    const int job = blockIdx.y;
+    const int np = m.np;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)np * np) return;
+    const int i = (int)(t % np), j = (int)(t / np);
+    const PairJob jb = jobs[job];
+    const double hA = geo.sides[geo.types[jb.a]] / m.nv;
+    const double hB = geo.sides[geo.types[jb.b]] / m.nv;
+    const T2* tb = tab + (size_t)job * job_stride;
+    const size_t nv2 = (size_t)m.nvox * m.nvox;
+    const int4 fi = m.face[i], fj = m.face[j];
+    const int vi[2] = {fi.y, fi.z}, vj[2] = {fj.y, fj.z};  // voxel below (xi), above (1 - xi)
+    T2 L = mk(T(0), T(0)), D = mk(T(0), T(0));
+    if (fi.x == fj.x) {
+        for (int sa = 0; sa < 2; ++sa) {
+            if (vi[sa] < 0) continue;
+            for (int sb = 0; sb < 2; ++sb) {
+                if (vj[sb] < 0) continue;
+                L += tb[(size_t)(1 + 4 * fi.x + 2 * sa + sb) * nv2 + (size_t)vi[sa] * m.nvox + vj[sb]];
+            }
+        }
+        L = T(1.0 / (hA * hA * hB * hB)) * L;
+    }
+    const T cvA = T(1.0 / (hA * hA * hA)), cvB = T(1.0 / (hB * hB * hB));
+    const int si = fi.w, sj = fj.w;
+    const T csA = si >= 0 ? T(m.sheet_sign[i] / (hA * hA)) : T(0);
+    const T csB = sj >= 0 ? T(m.sheet_sign[j] / (hB * hB)) : T(0);
+    const T2* VS = tb + 13 * nv2;
+    const T2* SV = VS + (size_t)m.nvox * m.nsurf;
+    const T2* SS = SV + (size_t)m.nsurf * m.nvox;
+    for (int sa = 0; sa < 2; ++sa) {
+        if (vi[sa] < 0) continue;
+        T ca = sa ? -cvA : cvA;
+        for (int sb = 0; sb < 2; ++sb) {
+            if (vj[sb] < 0) continue;
+            T cb = sb ? -cvB : cvB;
+            D += (ca * cb) * tb[(size_t)vi[sa] * m.nvox + vj[sb]];
+        }
+        if (sj >= 0) D += (ca * csB) * VS[(size_t)vi[sa] * m.nsurf + sj];
+    }
+    if (si >= 0) {
+        for (int sb = 0; sb < 2; ++sb) {
+            if (vj[sb] < 0) continue;
+            T cb = sb ? -cvB : cvB;
+            D += (csA * cb) * SV[(size_t)si * m.nvox + vj[sb]];
+        }
+        if (sj >= 0) D += (csA * csB) * SS[(size_t)si * m.nsurf + sj];
+    }
+    T2 z = D - T(k2) * L;
+    if (SELF && fi.x == fj.x) {
+        // M_ij = sum over shared voxels of (1/3 equal profiles, 1/6 opposite) / h
+        double Mij = 0.0;
+        for (int sa = 0; sa < 2; ++sa)
+            for (int sb = 0; sb < 2; ++sb)
+                if (vi[sa] >= 0 && vi[sa] == vj[sb]) Mij += (sa == sb ? 1.0 / 3.0 : 1.0 / 6.0) / hA;
+        if (Mij != 0.0) {
+            double2 ic = inv_chi[geo.types[jb.a]];
+            z += mk(T(Mij * ic.x), T(Mij * ic.y));
+        }
+    }
+    TO* out = dst[jb.dst];
+    out[(int64_t)jb.row_off + i + ((int64_t)jb.col_off + j) * ld[jb.dst]] = cvt<TO>(z);
+}
+
+// --------------------------------------------------------------------------
+// right-hand side b = j k v0, v0_i = int w_i . E0, 3-point Gauss per axis
+// --------------------------------------------------------------------------
+__global__ void rhs_kernel(DevMesh m, GeoPtrs geo, int N, double k, const double* khat, const double* pol,
+                           int nrhs, double2* b, int64_t ld) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t n = (int64_t)N * m.np;
+    if (t >= n * nrhs) return;
+    int c = (int)(t / n);
+    int64_t row = t % n;
+    int atom = (int)(row / m.np), f = (int)(row % m.np);
+    double side = geo.sides[geo.types[atom]];
+    double h = side / m.nv;
+    int4 fi = m.face[f];
+    int d = fi.x;
+    const double* kh = khat + 3 * c;
+    double2 pd = make_double2(pol[6 * c + 2 * d], pol[6 * c + 2 * d + 1]);
+    double2 acc = make_double2(0, 0);
+    int vox[2] = {fi.y, fi.z};
+    for (int s = 0; s < 2; ++s) {
+        if (vox[s] < 0) continue;
+        double lo[3];
+        for (int e = 0; e < 3; ++e)
+            lo[e] = geo.centres[3 * atom + e] - 0.5 * side + h * m.vox_ijk[3 * vox[s] + e];
+        for (int p = 0; p < 27; ++p) {
+            int ix[3] = {p / 9, (p / 3) % 3, p % 3};
+            double r[3], w = h * h * h;
+            for (int e = 0; e < 3; ++e) {
+                r[e] = lo[e] + h * c_gl3_x[ix[e]];
+                w *= c_gl3_w[ix[e]];
+            }
+            double xi = c_gl3_x[ix[d]];
+            double prof = s ? 1.0 - xi : xi;
+            double ph = k * (kh[0] * r[0] + kh[1] * r[1] + kh[2] * r[2]);
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            acc += (w * prof) * make_double2(cs, -sn);
+        }
+    }
+    double2 v0 = cmul(acc, pd);
+    v0 = (1.0 / (h * h)) * v0;
+    b[row + (int64_t)c * ld] = make_double2(-k * v0.y, k * v0.x);  // j k v0
+}
+
+// radiation vector N(rhat) = int J exp(j k rhat . r) dV, one block per (direction, rhs)
+__global__ void radiation_kernel(DevMesh m, GeoPtrs geo, int N, double k, const double2* I, int nrhs,
+                                 const double* dirs, int npts, double2* out) {
+    int dir = blockIdx.x, c = blockIdx.y;
+    const double* rh = dirs + 3 * dir;
+    int64_t n = (int64_t)N * m.np;
+    double2 acc[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    for (int64_t row = threadIdx.x; row < n; row += blockDim.x) {
+        int atom = (int)(row / m.np), f = (int)(row % m.np);
+        double side = geo.sides[geo.types[atom]];
+        double h = side / m.nv;
+        int4 fi = m.face[f];
+        int d = fi.x;
+        int vox[2] = {fi.y, fi.z};
+        double2 sum = make_double2(0, 0);
+        for (int s = 0; s < 2; ++s) {
+            if (vox[s] < 0) continue;
+            double lo[3];
+            for (int e = 0; e < 3; ++e)
+                lo[e] = geo.centres[3 * atom + e] - 0.5 * side + h * m.vox_ijk[3 * vox[s] + e];
+            for (int p = 0; p < 27; ++p) {
+                int ix[3] = {p / 9, (p / 3) % 3, p % 3};
+                double r[3], w = h * h * h;
+                for (int e = 0; e < 3; ++e) {
+                    r[e] = lo[e] + h * c_gl3_x[ix[e]];
+                    w *= c_gl3_w[ix[e]];
+                }
+                double xi = c_gl3_x[ix[d]];
+                double prof = s ? 1.0 - xi : xi;
+                double ph = k * (rh[0] * r[0] + rh[1] * r[1] + rh[2] * r[2]);
+                double sn, cs;
+                sincos(ph, &sn, &cs);
+                sum += (w * prof) * make_double2(cs, sn);
+            }
+        }
+        acc[d] += (1.0 / (h * h)) * cmul(I[row + (int64_t)c * n], sum);
+    }
+    __shared__ double2 red[3][256];
+    for (int d = 0; d < 3; ++d) red[d][threadIdx.x] = acc[d];
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+            for (int d = 0; d < 3; ++d) red[d][threadIdx.x] += red[d][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int d = 0; d < 3; ++d) out[((size_t)c * npts + dir) * 3 + d] = red[d][0];
+}
+
+GeoPtrs geo_of(Op& op) {
+    return GeoPtrs{op.d_centres.as<double>(), op.d_types.as<int>(), op.d_sides.as<double>()};
+}
+
+size_t table_stride(const DevMesh& m) {
+    size_t nv2 = (size_t)m.nvox * m.nvox;
+    return 13 * nv2 + 2 * (size_t)m.nvox * m.nsurf + (size_t)m.nsurf * m.nsurf;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// self blocks Zs_ii in float64, one per type
+// ---------------------------------------------------------------------------
+void assemble_self_blocks(Op& op) {
+    const DevMesh& m = op.dmesh;
+    const int np = m.np;
+    size_t stride = table_stride(m);
+    DevBuf tab(stride * sizeof(double2));
+    op.d_zself64.alloc((size_t)op.T * np * np * sizeof(double2));
+    DevBuf jobs(sizeof(PairJob)), dst(sizeof(void*)), ldb(sizeof(int64_t));
+    cudaStream_t s = op.ctx->stream;
+    for (int t = 0; t < op.T; ++t) {
+        double h = op.h[t];
+        int nv2 = m.nvox * m.nvox;
+        self_vv_kernel<<<(nv2 + 63) / 64, 64, 0, s>>>(m, h, op.k, tab.as<double2>());
+        VIE_CHECK_LAUNCH();
+        int ns = std::max(m.nvox, m.nsurf) * m.nsurf;
+        self_surf_kernel<<<dim3((ns + 63) / 64, 3), 64, 0, s>>>(m, h, op.k, tab.as<double2>());
+        VIE_CHECK_LAUNCH();
+        // an atom of this type (entries only need its type)
+        int atom = op.atoms_of_type[t].empty() ? -1 : op.atoms_of_type[t][0];
+        if (atom < 0) continue;
+        PairJob jb{atom, atom, 0, 0, 0};
+        void* dptr = op.d_zself64.as<double2>() + (size_t)t * np * np;
+        int64_t ldv = np;
+        VIE_CUDA(cudaMemcpyAsync(jobs.p, &jb, sizeof(jb), cudaMemcpyHostToDevice, s));
+        VIE_CUDA(cudaMemcpyAsync(dst.p, &dptr, sizeof(dptr), cudaMemcpyHostToDevice, s));
+        VIE_CUDA(cudaMemcpyAsync(ldb.p, &ldv, sizeof(ldv), cudaMemcpyHostToDevice, s));
+        int64_t ne = (int64_t)np * np;
+        entries_kernel<double, double2, true><<<dim3((unsigned)((ne + 255) / 256), 1), 256, 0, s>>>(
+            jobs.as<PairJob>(), m, geo_of(op), op.k * op.k, tab.as<double2>(), stride,
+            dst.as<double2* const>(), ldb.as<int64_t>(), op.d_inv_chi.as<double2>());
+        VIE_CHECK_LAUNCH();
+        VIE_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// interaction blocks of atom pairs (a != b), written into destination matrices
+// ---------------------------------------------------------------------------
+template <class T>
+void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_dst, const int64_t* d_ld,
+                    cudaStream_t s) {
+    using T2 = typename C2<T>::t;
+    const DevMesh& m = op.dmesh;
+    size_t stride = table_stride(m);
+    // scratch for a chunk of jobs (<= 2 GiB)
+    size_t per_job = stride * sizeof(T2);
+    int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_jobs, ((size_t)2 << 30) / per_job));
+    chunk = std::min(chunk, 65535);  // jobs run along grid y / z
+    DevBuf tab((size_t)chunk * per_job);
+    const T tol = T(2.0 / op.wavelength);
+    const int nv2 = m.nvox * m.nvox;
+    const int ns = std::max(m.nvox, m.nsurf) * m.nsurf;
+    const int64_t ne = (int64_t)m.np * m.np;
+    for (int j0 = 0; j0 < n_jobs; j0 += chunk) {
+        int nj = std::min(chunk, n_jobs - j0);
+        cross_vv_kernel<T><<<dim3((nv2 + 127) / 128, nj), 128, 0, s>>>(d_jobs + j0, m, geo_of(op), tol,
+                                                                        tab.as<T2>(), stride);
+        VIE_CHECK_LAUNCH();
+        cross_surf_kernel<T><<<dim3((ns + 127) / 128, 3, nj), 128, 0, s>>>(d_jobs + j0, m, geo_of(op), tol,
+                                                                           tab.as<T2>(), stride);
+        VIE_CHECK_LAUNCH();
+        entries_kernel<T, T2, false><<<dim3((unsigned)((ne + 255) / 256), nj), 256, 0, s>>>(
+            d_jobs + j0, m, geo_of(op), op.k * op.k, tab.as<T2>(), stride, (T2* const*)d_dst, d_ld,
+            op.d_inv_chi.as<double2>());
+        VIE_CHECK_LAUNCH();
+    }
+    // keep the scratch alive until the work is done
+    VIE_CUDA(cudaStreamSynchronize(s));
+}
+
+template void assemble_pairs<float>(Op&, const PairJob*, int, void* const*, const int64_t*, cudaStream_t);
+template void assemble_pairs<double>(Op&, const PairJob*, int, void* const*, const int64_t*, cudaStream_t);
+
+void rhs_kernel_launch(Op& op, const double* d_khat, const double* d_pol, int nrhs, void* b, int64_t ld,
+                       cudaStream_t s) {
+    int64_t total = op.n() * nrhs;
+    rhs_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(op.dmesh, geo_of(op), op.N, op.k, d_khat, d_pol,
+                                                                nrhs, (double2*)b, ld);
+    VIE_CHECK_LAUNCH();
+}
+
+void far_field_launch(Op& op, const void* d_I, int nrhs, const double* d_dirs, int npts, void* d_out,
+                      cudaStream_t s) {
+    radiation_kernel<<<dim3(npts, nrhs), 256, 0, s>>>(op.dmesh, geo_of(op), op.N, op.k, (const double2*)d_I,
+                                                       nrhs, d_dirs, npts, (double2*)d_out);
+    VIE_CHECK_LAUNCH();
+}
+
+}  // namespace vie

@@ -1,0 +1,221 @@
+// Internal declarations of libvie (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cublas_v2.h>
+
+#include <complex>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/vie.h"
+
+namespace vie {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------------------
+// errors: every internal failure throws vie::Error, caught at the C-ABI
+// ---------------------------------------------------------------------------
+struct Error {
+    int status;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int status, const std::string& msg);
+
+#define VIE_CUDA(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            ::vie::fail(e_ == cudaErrorMemoryAllocation ? VIE_ERR_OOM : VIE_ERR_CUDA,         \
+                        std::string(#call " -> ") + cudaGetErrorString(e_) + " at " __FILE__); \
+    } while (0)
+
+#define VIE_BLAS(call)                                                                   \
+    do {                                                                                 \
+        cublasStatus_t s_ = (call);                                                      \
+        if (s_ != CUBLAS_STATUS_SUCCESS)                                                 \
+            ::vie::fail(VIE_ERR_CUDA, std::string(#call " -> cublas status ") +          \
+                                          std::to_string((int)s_) + " at " __FILE__);    \
+    } while (0)
+
+#define VIE_CHECK_LAUNCH() VIE_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// device buffer (RAII)
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t b) { alloc(b); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t b);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+template <class T>
+void upload(DevBuf& d, const std::vector<T>& h) {
+    d.alloc(std::max<size_t>(1, h.size() * sizeof(T)));
+    if (!h.empty()) VIE_CUDA(cudaMemcpy(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+// ---------------------------------------------------------------------------
+// mesh of one atom type (voxels, faces, boundary faces), Sec. 3 basis
+// ---------------------------------------------------------------------------
+struct MeshTables {
+    int nv = 0, np = 0, nvox = 0, nsurf = 0;
+    double side = 0, h = 0;
+    std::vector<int> face_dir, face_lo, face_hi, face_sheet, face_sheet_sign;  // [np]
+    std::vector<int> vox_ijk;   // [3 nvox]
+    std::vector<int> surf_face; // [nsurf]
+};
+MeshTables build_mesh(double side, int nv);
+
+// device copy, packed: for face f: dir, lo voxel, hi voxel, sheet, sign
+struct DevMesh {
+    int nv, np, nvox, nsurf;
+    const int4* face;     // (dir, lo, hi, sheet)
+    const int* sheet_sign;
+    const int* vox_ijk;   // [3 nvox]
+    const int* surf_face; // [nsurf]
+};
+
+// ---------------------------------------------------------------------------
+// far block of the compressed operator (Sec. 5.2)
+// ---------------------------------------------------------------------------
+struct FarBlock {
+    int level = 0;
+    int nt = 0, ns = 0;        // atoms in target / source box
+    int t_off = 0, s_off = 0;  // offsets into Op::block_atoms
+    int m = 0, n = 0;          // unknowns
+    int rank = 0;
+    int64_t q_off = 0;         // element offset of Q (m x r col-major)
+    int64_t rh_off = 0;        // element offset of R^H (n x r col-major) = conj(R) row-major
+    int64_t t_off_vec = 0;     // offset of this block's R x in the t buffer (per RHS column)
+};
+
+struct Ctx;
+
+struct Op {
+    Ctx* ctx = nullptr;
+    // geometry
+    int N = 0, T = 0, np = 0, L = 0;
+    std::vector<double> centres;       // [3N]
+    std::vector<int> types;            // [N]
+    std::vector<double> sides;         // [T]
+    std::vector<int> nvs;              // [T]
+    std::vector<cd> eps;               // [T]
+    double wavelength = 1, k = 0;
+    MeshTables mesh;                   // topology shared by all types (same nv)
+    std::vector<double> h;             // [T] voxel size per type
+    // tree
+    std::vector<FarBlock> blocks;
+    std::vector<int> block_atoms;
+    // device geometry
+    DevBuf d_centres, d_types, d_sides, d_inv_chi;
+    DevBuf d_mesh_face, d_mesh_sign, d_mesh_vox, d_mesh_surf;
+    DevMesh dmesh{};                   // pointers into the buffers above
+    // self blocks (per type, np x np col-major)
+    DevBuf d_zself64, d_inv64, d_zself32, d_inv32;
+    std::vector<std::vector<int>> atoms_of_type;
+    DevBuf d_atoms_by_type;            // atom indices grouped by type
+    std::vector<int> type_atom_off;    // [T+1]
+    // factors
+    int fprec = 0;
+    double tol = 0;
+    DevBuf d_factors;
+    int64_t factor_entries = 0;
+    int64_t t_total = 0;               // sum of ranks
+    // apply work lists (device)
+    DevBuf d_blocks;                   // FarBlockDev[nb]
+    DevBuf d_block_atoms;
+    DevBuf d_p1_items, d_p1_cta;       // phase 1 items and per-CTA ranges
+    DevBuf d_p2_items, d_p2_cta, d_p2_csr, d_p2_ent;
+    int n_p1_items = 0, n_p2_items = 0, n_cta = 0;
+    // scratch
+    DevBuf d_t, d_F;
+    size_t t_cap = 0, F_cap = 0;
+    double t_assemble = 0, t_compress = 0;
+    int64_t n() const { return (int64_t)N * np; }
+};
+
+struct Ctx {
+    int device = 0;
+    int n_sm = 0;
+    cudaStream_t stream = nullptr;
+    cublasHandle_t blas = nullptr;
+    std::string err;
+    size_t budget = 0;
+    int verbose = 0;
+};
+
+// device-side block description used by the apply kernels
+struct FarBlockDev {
+    int m, n, rank, nt, ns, t_off, s_off, pad;
+    long long q_off, rh_off, tvec_off;
+};
+
+// ---------------------------------------------------------------------------
+// host algorithms
+// ---------------------------------------------------------------------------
+void build_tree(Op& op);   // fills op.L, op.blocks, op.block_atoms
+void lpt_assign(const std::vector<double>& w, int nproc, std::vector<int>& owner,
+                std::vector<double>& loads);
+void build_apply_lists(Op& op);
+
+// ---------------------------------------------------------------------------
+// kernel launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+// assemble.cu
+void assemble_self_blocks(Op& op);  // fills d_zself64 (float64)
+// Interaction blocks between atom pairs, written into col-major destination
+// matrices: pair p writes Zs_{a_p, b_p} at dst[p] + row_off + col_off * ld.
+struct PairJob {
+    int a, b;
+    int dst;          // index into the destination pointer table
+    int row_off, col_off;
+};
+template <class T>
+void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_dst, const int64_t* d_ld,
+                    cudaStream_t s);
+void rhs_kernel_launch(Op& op, const double* d_khat, const double* d_pol, int nrhs, void* b, int64_t ld,
+                       cudaStream_t s);
+void far_field_launch(Op& op, const void* d_I, int nrhs, const double* d_dirs, int npts, void* d_out,
+                      cudaStream_t s);
+void v0_dot_launch(Op& op, const void* d_I, const double* d_khat, const double* d_pol, int nrhs,
+                   double* d_out, cudaStream_t s);
+
+// linalg.cu
+void invert_self_blocks(Op& op);   // d_inv64 from d_zself64 (Gauss-Jordan, partial pivoting)
+void convert_c128_to_c64(const void* src, void* dst, int64_t n, cudaStream_t s);
+void convert_c64_to_c128(const void* src, void* dst, int64_t n, cudaStream_t s);
+template <class TM, class TX>
+void self_gemm(Op& op, const TM* M, const TX* X, int64_t ldx, const TX* C, int64_t ldc, TX* Y, int64_t ldy,
+               int nrhs, int mode, cudaStream_t s);
+
+// apply.cu
+template <class TF, class TX>
+void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, cudaStream_t s);
+
+// compress.cu
+void compress_operator(Op& op, double tol, int prec);
+
+// solve.cpp
+int solve(Op& op, const vie_incident* inc, int nrhs, const vie_solve_opts* o, void* I_out,
+          vie_solve_stats* st);
+
+double now_s();
+
+}  // namespace vie

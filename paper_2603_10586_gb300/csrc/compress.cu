@@ -1,0 +1,528 @@
+// QR-recursive compression of the far blocks (paper Sec. 5.2, eq. eq_02;
+// Sec. 5.3): each far block A (m x n) is replaced by Q (m x r, orthonormal
+// columns) and R = Q^H A (r x n) such that ||A - Q R||_F <= tol ||A||_F.
+//
+// The paper does not say how its QR factors are computed for large blocks
+// (it builds them with a cross approximation, Sec. 6.5).  Here a batch of
+// equally sized blocks is formed on the device and compressed together with
+// a blocked adaptive randomised range finder:
+//   Y = A Omega (Gaussian test matrix), project Y against the current basis
+//   twice (classical Gram-Schmidt, two passes), estimate the residual energy
+//   ||(I - Q Q^H) A||_F^2 ~ ||Y||_F^2 / s from the projected block, stop when
+//   the estimate is below (tol / 3)^2 ||A||_F^2, else orthonormalise the block
+//   (Cholesky QR twice, Gram matrix accumulated in float64) and append it.
+// The factor-of-3 margin makes a violation of the bound improbable for the
+// 32-column estimator used here (a chi-square tail below 1/9 of its mean).
+// Plain GEMMs go to cuBLAS; the Gram, Cholesky, triangular product, norms,
+// random numbers and the column compaction are this file's kernels.
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "common.h"
+#include "cplx.cuh"
+
+namespace vie {
+
+namespace {
+
+constexpr int kChunk = 32;    // columns orthonormalised at a time
+constexpr int kRankCap = 1536; // largest rank a block may take (larger: error)
+
+// ------------------------------------------------------------------ kernels
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// complex Gaussian with E|w|^2 = 1 (Box-Muller on two 53-bit uniforms)
+template <class T2>
+__global__ void k_gauss(T2* W, int64_t count, uint64_t seed) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    uint64_t a = splitmix64(seed ^ (uint64_t)(2 * t));
+    uint64_t b = splitmix64(seed ^ (uint64_t)(2 * t + 1));
+    double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740993.0);  // (0, 1]
+    double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+    double r = sqrt(-log(u1));                                    // sqrt(-2 ln u) / sqrt(2)
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    W[t] = mk(decltype(W[0].x)(r * c), decltype(W[0].x)(r * s));
+}
+
+// per-batch-entry sum of |x|^2 over `len` contiguous elements (stride between entries)
+template <class T2>
+__global__ void k_sumsq_partial(const T2* X, int64_t len, int64_t stride, int nchunk, double* part) {
+    int b = blockIdx.y, c = blockIdx.x;
+    int64_t per = (len + nchunk - 1) / nchunk;
+    int64_t lo = c * per, hi = min(len, lo + per);
+    const T2* x = X + b * stride;
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        double re = x[i].x, im = x[i].y;
+        acc += re * re + im * im;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(size_t)b * nchunk + c] = red[0];
+}
+__global__ void k_reduce_rows(const double* part, int nchunk, int nb, double* out) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += part[(size_t)b * nchunk + c];
+    out[b] = s;
+}
+
+// partial Gram matrices G = Y^H Y (kChunk x kChunk, float64) over row chunks
+template <class T2>
+__global__ void k_gram_partial(const T2* Y, int m, int64_t stride, int nchunk, double2* part) {
+    const int b = blockIdx.y, c = blockIdx.x;
+    const int per = (m + nchunk - 1) / nchunk;
+    const int lo = c * per, hi = min(m, lo + per);
+    const T2* y = Y + b * stride;
+    __shared__ double2 rows[64][kChunk + 1];
+    const int i = threadIdx.x % kChunk, j = threadIdx.x / kChunk;  // 1024 threads
+    double2 acc = make_double2(0, 0);
+    for (int r0 = lo; r0 < hi; r0 += 64) {
+        for (int e = threadIdx.x; e < 64 * kChunk; e += blockDim.x) {
+            int rr = e % 64, cc = e / 64;
+            int r = r0 + rr;
+            rows[rr][cc] = r < hi ? cvt<double2>(y[r + (int64_t)cc * m]) : make_double2(0, 0);
+        }
+        __syncthreads();
+        int nr = min(64, hi - r0);
+        for (int rr = 0; rr < nr; ++rr) cfmac(acc, rows[rr][i], rows[rr][j]);
+        __syncthreads();
+    }
+    part[((size_t)b * nchunk + c) * kChunk * kChunk + i + j * kChunk] = acc;
+}
+__global__ void k_gram_reduce(const double2* part, int nchunk, double2* G) {
+    const int b = blockIdx.x;
+    const int e = threadIdx.x;  // kChunk^2 threads
+    double2 s = make_double2(0, 0);
+    for (int c = 0; c < nchunk; ++c) s += part[((size_t)b * nchunk + c) * kChunk * kChunk + e];
+    G[(size_t)b * kChunk * kChunk + e] = s;
+}
+
+// Cholesky G = L L^H (float64, one block per batch entry) and Minv = L^-H
+// (upper triangular) so that Y Minv has orthonormal columns.  A pivot below
+// 1e-10 of the largest diagonal marks the column dead (zero in Minv).
+template <class T2>
+__global__ void k_chol(const double2* G, T2* Minv, const int* active, unsigned char* alive, int rcap,
+                       const int* rbase) {
+    const int b = blockIdx.x;
+    if (!active[b]) return;
+    __shared__ double2 L[kChunk][kChunk + 1];
+    __shared__ double2 X[kChunk][kChunk + 1];
+    __shared__ int dead[kChunk];
+    __shared__ double gmax;
+    const int t = threadIdx.x;  // kChunk threads
+    for (int j = 0; j < kChunk; ++j) L[t][j] = G[(size_t)b * kChunk * kChunk + t + j * kChunk];
+    dead[t] = 0;
+    __syncthreads();
+    if (t == 0) {
+        double mx = 0.0;
+        for (int j = 0; j < kChunk; ++j) mx = fmax(mx, L[j][j].x);
+        gmax = mx;
+    }
+    __syncthreads();
+    // right-looking Cholesky, column by column (thread t owns row t)
+    for (int k = 0; k < kChunk; ++k) {
+        double d = L[k][k].x;
+        bool dk = !(d > 1e-10 * gmax) || gmax <= 0.0;
+        __syncthreads();
+        if (t == 0) dead[k] = dk;
+        double sq = dk ? 0.0 : sqrt(d);
+        if (t > k) {
+            double2 v = L[t][k];
+            L[t][k] = dk ? make_double2(0, 0) : make_double2(v.x / sq, v.y / sq);
+        }
+        if (t == k) L[k][k] = make_double2(dk ? 1.0 : sq, 0.0);
+        __syncthreads();
+        if (t > k)
+            for (int j = k + 1; j <= t; ++j) {
+                // L[t][j] -= L[t][k] conj(L[j][k])
+                double2 a = L[t][k], c = L[j][k];
+                L[t][j].x -= a.x * c.x + a.y * c.y;
+                L[t][j].y -= a.y * c.x - a.x * c.y;
+            }
+        __syncthreads();
+    }
+    // X = L^-1 (lower), column t solved by thread t
+    for (int i = 0; i < kChunk; ++i) X[i][t] = make_double2(0, 0);
+    for (int i = t; i < kChunk; ++i) {
+        double2 s = make_double2(i == t ? 1.0 : 0.0, 0.0);
+        for (int j = t; j < i; ++j) {
+            double2 a = L[i][j], x = X[j][t];
+            s.x -= a.x * x.x - a.y * x.y;
+            s.y -= a.x * x.y + a.y * x.x;
+        }
+        double2 d = L[i][i];
+        X[i][t] = make_double2(s.x / d.x, s.y / d.x);
+    }
+    __syncthreads();
+    // Minv = (L^-1)^H: Minv[i][j] = conj(X[j][i]); dead columns/rows zeroed
+    for (int j = 0; j < kChunk; ++j) {
+        double2 v = X[j][t];
+        bool z = dead[t] || dead[j];
+        Minv[(size_t)b * kChunk * kChunk + t + j * kChunk] =
+            z ? mk(decltype(Minv[0].x)(0), decltype(Minv[0].x)(0))
+              : mk(decltype(Minv[0].x)(v.x), decltype(Minv[0].x)(-v.y));
+    }
+    if (alive && dead[t]) alive[(size_t)b * rcap + rbase[b] + t] = 0;
+}
+
+// OUT[:, j] = sum_i Y[:, i] Minv[i][j] for active entries (row per thread)
+template <class T2>
+__global__ void k_trmul(const T2* Y, int m, int64_t ystride, const T2* Minv, const int* active, T2* OUT,
+                        int64_t ostride, int64_t ld_out, const int* col0) {
+    const int b = blockIdx.y;
+    if (!active[b]) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ T2 M[kChunk][kChunk];
+    for (int e = threadIdx.x; e < kChunk * kChunk; e += blockDim.x) M[e % kChunk][e / kChunk] = Minv[(size_t)b * kChunk * kChunk + e];
+    __syncthreads();
+    if (r >= m) return;
+    using R = decltype(Y[0].x);
+    T2 y[kChunk];
+    for (int i = 0; i < kChunk; ++i) y[i] = Y[b * ystride + r + (int64_t)i * m];
+    T2* o = OUT + b * ostride + (col0 ? (int64_t)col0[b] * ld_out : 0) + r;
+    for (int j = 0; j < kChunk; ++j) {
+        T2 acc = mk(R(0), R(0));
+        for (int i = 0; i <= j; ++i) cfma(acc, y[i], M[i][j]);
+        o[(int64_t)j * ld_out] = acc;
+    }
+}
+
+// copy live columns into the factor store: dst[k] <- src[:, col[k]]
+template <class T2>
+__global__ void k_gather_cols(const T2* src, int64_t rows, const long long* src_off, const long long* dst_off,
+                              T2* dst_base, const T2* src_base) {
+    const int k = blockIdx.y;
+    const T2* s = src_base + src_off[k];
+    T2* d = dst_base + dst_off[k];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = s[i];
+}
+
+// ------------------------------------------------------------------ cuBLAS
+template <class T> struct Blas;
+template <> struct Blas<float> {
+    using T2 = float2;
+    static void gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, T2 alpha,
+                     const T2* A, int lda, long long sa, const T2* B, int ldb, long long sb, T2 beta, T2* C, int ldc,
+                     long long sc, int batch) {
+        VIE_BLAS(cublasCgemmStridedBatched(h, ta, tb, m, n, k, (const cuComplex*)&alpha, (const cuComplex*)A, lda, sa,
+                                           (const cuComplex*)B, ldb, sb, (const cuComplex*)&beta, (cuComplex*)C, ldc,
+                                           sc, batch));
+    }
+};
+template <> struct Blas<double> {
+    using T2 = double2;
+    static void gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, T2 alpha,
+                     const T2* A, int lda, long long sa, const T2* B, int ldb, long long sb, T2 beta, T2* C, int ldc,
+                     long long sc, int batch) {
+        VIE_BLAS(cublasZgemmStridedBatched(h, ta, tb, m, n, k, (const cuDoubleComplex*)&alpha,
+                                           (const cuDoubleComplex*)A, lda, sa, (const cuDoubleComplex*)B, ldb, sb,
+                                           (const cuDoubleComplex*)&beta, (cuDoubleComplex*)C, ldc, sc, batch));
+    }
+};
+
+// ------------------------------------------------------------------ driver
+struct BlockFactors {
+    int rank = 0;
+    int64_t q_off = 0, rh_off = 0;  // into the staging store of its batch
+};
+
+template <class T>
+struct Compressor {
+    using T2 = typename C2<T>::t;
+    Op& op;
+    double tol;
+    cudaStream_t s;
+    cublasHandle_t h;
+    std::vector<DevBuf> stores;          // staging factor stores (one per batch)
+    std::vector<std::pair<int, int64_t>> where;  // per block: (store, offset of Q); R^H follows Q
+    std::map<int, int> level_rank;       // running max rank per level
+    uint64_t seed = 0x5eed0001ull;
+
+    Compressor(Op& o, double t) : op(o), tol(t), s(o.ctx->stream), h(o.ctx->blas) {}
+
+    void sumsq(const T2* X, int64_t len, int64_t stride, int nb, double* out, DevBuf& part) {
+        int nchunk = (int)std::min<int64_t>(256, std::max<int64_t>(1, len / 65536));
+        size_t need = (size_t)nb * nchunk * sizeof(double);
+        if (part.bytes < need) part.alloc(need);
+        k_sumsq_partial<T2><<<dim3(nchunk, nb), 256, 0, s>>>(X, len, stride, nchunk, part.as<double>());
+        VIE_CHECK_LAUNCH();
+        k_reduce_rows<<<(nb + 127) / 128, 128, 0, s>>>(part.as<double>(), nchunk, nb, out);
+        VIE_CHECK_LAUNCH();
+    }
+
+    // compress one batch of equally sized blocks
+    void batch(const std::vector<int>& ids) {
+        const int nb = (int)ids.size();
+        const FarBlock& b0 = op.blocks[ids[0]];
+        const int m = b0.m, n = b0.n, np = op.np;
+        const int rfull = std::min(m, n);
+        const int rcap = std::min(rfull, kRankCap);
+        const int rcap_pad = ((rcap + kChunk - 1) / kChunk) * kChunk;
+        const int64_t mn = (int64_t)m * n;
+
+        // 1. form the blocks (col-major m x n, ld = m)
+        DevBuf A((size_t)nb * mn * sizeof(T2));
+        {
+            std::vector<PairJob> jobs;
+            std::vector<void*> dst(nb);
+            std::vector<int64_t> ld(nb, m);
+            for (int q = 0; q < nb; ++q) {
+                const FarBlock& b = op.blocks[ids[q]];
+                dst[q] = A.as<T2>() + (size_t)q * mn;
+                for (int i = 0; i < b.nt; ++i)
+                    for (int j = 0; j < b.ns; ++j)
+                        jobs.push_back(PairJob{op.block_atoms[b.t_off + i], op.block_atoms[b.s_off + j], q, i * np,
+                                               j * np});
+            }
+            DevBuf dj, dd, dl;
+            upload(dj, jobs);
+            upload(dd, dst);
+            upload(dl, ld);
+            assemble_pairs<T>(op, dj.as<PairJob>(), (int)jobs.size(), dd.as<void* const>(), dl.as<int64_t>(), s);
+        }
+        DevBuf part, normA((size_t)nb * sizeof(double)), est((size_t)nb * sizeof(double));
+        sumsq(A.as<T2>(), mn, mn, nb, normA.as<double>(), part);
+        std::vector<double> hnorm(nb);
+        VIE_CUDA(cudaMemcpyAsync(hnorm.data(), normA.p, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+
+        // 2. adaptive range finder
+        DevBuf Q((size_t)nb * m * rcap_pad * sizeof(T2));
+        VIE_CUDA(cudaMemsetAsync(Q.p, 0, Q.bytes, s));
+        DevBuf alive((size_t)nb * rcap_pad);
+        VIE_CUDA(cudaMemsetAsync(alive.p, 1, alive.bytes, s));
+        DevBuf Cb((size_t)nb * rcap_pad * kChunk * sizeof(T2));
+        DevBuf gpart, G((size_t)nb * kChunk * kChunk * sizeof(double2)), Minv((size_t)nb * kChunk * kChunk * sizeof(T2));
+        DevBuf d_active(nb * sizeof(int)), d_rbase(nb * sizeof(int));
+        std::vector<int> r(nb, 0), conv(nb, 0);
+        int s0 = kChunk;
+        auto it = level_rank.find(b0.level);
+        if (it != level_rank.end()) s0 = std::max(kChunk, ((int)(0.9 * it->second) / kChunk) * kChunk);
+        s0 = std::min(s0, rcap_pad);
+        int step = 0;
+        const double thr = (tol / 3.0) * (tol / 3.0);
+        VIE_CUDA(cudaStreamSynchronize(s));
+        for (int q = 0; q < nb; ++q)
+            if (!(hnorm[q] > 0)) conv[q] = 1;  // an all-zero block has rank 0
+        while (true) {
+            int rmax = *std::max_element(r.begin(), r.end());
+            bool all = std::all_of(conv.begin(), conv.end(), [](int c) { return c; });
+            if (all) break;
+            int scols = step == 0 ? s0 : kChunk;
+            scols = std::min(scols, rcap_pad - rmax);
+            if (scols <= 0) {
+                // every unconverged block has a full basis: exact
+                for (int q = 0; q < nb; ++q) conv[q] = 1;
+                break;
+            }
+            DevBuf W((size_t)n * scols * sizeof(T2)), Y((size_t)nb * m * scols * sizeof(T2));
+            k_gauss<T2><<<(unsigned)(((int64_t)n * scols + 255) / 256), 256, 0, s>>>(W.as<T2>(), (int64_t)n * scols,
+                                                                                     seed + 7919ull * step);
+            VIE_CHECK_LAUNCH();
+            ++step;
+            const T2 one = mk(T(1), T(0)), zero = mk(T(0), T(0)), mone = mk(T(-1), T(0));
+            Blas<T>::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, scols, n, one, A.as<T2>(), m, mn, W.as<T2>(), n, 0, zero,
+                          Y.as<T2>(), m, (long long)m * scols, nb);
+            for (int c0 = 0; c0 < scols; c0 += kChunk) {
+                T2* Yc = Y.as<T2>() + (int64_t)c0 * m;
+                const long long ys = (long long)m * scols;
+                rmax = *std::max_element(r.begin(), r.end());
+                for (int pass = 0; pass < 2 && rmax > 0; ++pass) {
+                    Blas<T>::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, rmax, kChunk, m, one, Q.as<T2>(), m,
+                                  (long long)m * rcap_pad, Yc, m, ys, zero, Cb.as<T2>(), rcap_pad,
+                                  (long long)rcap_pad * kChunk, nb);
+                    Blas<T>::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, kChunk, rmax, mone, Q.as<T2>(), m,
+                                  (long long)m * rcap_pad, Cb.as<T2>(), rcap_pad, (long long)rcap_pad * kChunk, one,
+                                  Yc, m, ys, nb);
+                }
+                sumsq(Yc, (int64_t)m * kChunk, ys, nb, est.as<double>(), part);
+                std::vector<double> he(nb);
+                VIE_CUDA(cudaMemcpyAsync(he.data(), est.p, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+                VIE_CUDA(cudaStreamSynchronize(s));
+                std::vector<int> active(nb, 0), rbase(nb, 0);
+                bool any = false;
+                for (int q = 0; q < nb; ++q) {
+                    if (!conv[q] && he[q] / kChunk <= thr * hnorm[q]) conv[q] = 1;
+                    if (!conv[q] && r[q] + kChunk > rcap_pad) {
+                        if (rcap < rfull)
+                            fail(VIE_ERR_BREAKDOWN, "far block needs a rank above " + std::to_string(kRankCap) +
+                                                        " at this tolerance");
+                        conv[q] = 1;  // full basis of the block's range: exact
+                    }
+                    active[q] = !conv[q];
+                    rbase[q] = r[q];
+                    any |= active[q];
+                }
+                if (!any) break;
+                VIE_CUDA(cudaMemcpyAsync(d_active.p, active.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s));
+                VIE_CUDA(cudaMemcpyAsync(d_rbase.p, rbase.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s));
+                // Cholesky QR, twice
+                int nchunk = std::max(1, std::min(64, m / 256));
+                size_t gneed = (size_t)nb * nchunk * kChunk * kChunk * sizeof(double2);
+                if (gpart.bytes < gneed) gpart.alloc(gneed);
+                for (int pass = 0; pass < 2; ++pass) {
+                    k_gram_partial<T2><<<dim3(nchunk, nb), 1024, 0, s>>>(Yc, m, ys, nchunk, gpart.as<double2>());
+                    VIE_CHECK_LAUNCH();
+                    k_gram_reduce<<<nb, kChunk * kChunk, 0, s>>>(gpart.as<double2>(), nchunk, G.as<double2>());
+                    VIE_CHECK_LAUNCH();
+                    k_chol<T2><<<nb, kChunk, 0, s>>>(G.as<double2>(), Minv.as<T2>(), d_active.as<int>(),
+                                                     alive.as<unsigned char>(), rcap_pad, d_rbase.as<int>());
+                    VIE_CHECK_LAUNCH();
+                    if (pass == 0) {
+                        // in place: Yc <- Yc Minv (rows are independent)
+                        k_trmul<T2><<<dim3((m + 127) / 128, nb), 128, 0, s>>>(Yc, m, ys, Minv.as<T2>(),
+                                                                             d_active.as<int>(), Yc, ys, m, nullptr);
+                    } else {
+                        k_trmul<T2><<<dim3((m + 127) / 128, nb), 128, 0, s>>>(
+                            Yc, m, ys, Minv.as<T2>(), d_active.as<int>(), Q.as<T2>(), (int64_t)m * rcap_pad, m,
+                            d_rbase.as<int>());
+                    }
+                    VIE_CHECK_LAUNCH();
+                }
+                for (int q = 0; q < nb; ++q)
+                    if (active[q]) r[q] += kChunk;
+            }
+        }
+
+        // 3. R^H = A^H Q (n x rmax per block)
+        int rmax = *std::max_element(r.begin(), r.end());
+        std::vector<unsigned char> halive((size_t)nb * rcap_pad);
+        VIE_CUDA(cudaMemcpyAsync(halive.data(), alive.p, halive.size(), cudaMemcpyDeviceToHost, s));
+        DevBuf RH((size_t)nb * n * std::max(rmax, 1) * sizeof(T2));
+        if (rmax > 0) {
+            const T2 one = mk(T(1), T(0)), zero = mk(T(0), T(0));
+            Blas<T>::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, n, rmax, m, one, A.as<T2>(), m, mn, Q.as<T2>(), m,
+                          (long long)m * rcap_pad, zero, RH.as<T2>(), n, (long long)n * rmax, nb);
+        }
+        VIE_CUDA(cudaStreamSynchronize(s));
+        A.release();
+
+        // 4. compact the live columns into a staging store
+        std::vector<int> rank(nb, 0);
+        int64_t total = 0;
+        for (int q = 0; q < nb; ++q) {
+            for (int j = 0; j < r[q]; ++j) rank[q] += halive[(size_t)q * rcap_pad + j] ? 1 : 0;
+            total += (int64_t)rank[q] * (m + n);
+            total = (total + 31) / 32 * 32;
+        }
+        DevBuf store((size_t)std::max<int64_t>(total, 32) * sizeof(T2));
+        std::vector<long long> so, dof;  // Q columns then R^H columns
+        std::vector<long long> so2, dof2;
+        int64_t off = 0;
+        int sidx = (int)stores.size();
+        for (int q = 0; q < nb; ++q) {
+            FarBlock& b = op.blocks[ids[q]];
+            b.rank = rank[q];
+            where[ids[q]] = {sidx, off};
+            int kk = 0;
+            for (int j = 0; j < r[q]; ++j) {
+                if (!halive[(size_t)q * rcap_pad + j]) continue;
+                so.push_back((long long)q * m * rcap_pad + (long long)j * m);
+                dof.push_back(off + (int64_t)kk * m);
+                so2.push_back((long long)q * n * rmax + (long long)j * n);
+                dof2.push_back(off + (int64_t)rank[q] * m + (int64_t)kk * n);
+                ++kk;
+            }
+            off += (int64_t)rank[q] * (m + n);
+            off = (off + 31) / 32 * 32;
+            level_rank[b.level] = std::max(level_rank[b.level], rank[q]);
+        }
+        if (!so.empty()) {
+            DevBuf a1, a2, a3, a4;
+            upload(a1, so);
+            upload(a2, dof);
+            upload(a3, so2);
+            upload(a4, dof2);
+            for (size_t c0 = 0; c0 < so.size(); c0 += 65535) {
+                int cnt = (int)std::min<size_t>(65535, so.size() - c0);
+                k_gather_cols<T2><<<dim3(std::min(64, (m + 255) / 256), cnt), 256, 0, s>>>(
+                    nullptr, m, a1.as<long long>() + c0, a2.as<long long>() + c0, store.as<T2>(), Q.as<T2>());
+                k_gather_cols<T2><<<dim3(std::min(64, (n + 255) / 256), cnt), 256, 0, s>>>(
+                    nullptr, n, a3.as<long long>() + c0, a4.as<long long>() + c0, store.as<T2>(), RH.as<T2>());
+                VIE_CHECK_LAUNCH();
+            }
+            VIE_CUDA(cudaStreamSynchronize(s));
+        }
+        stores.push_back(std::move(store));
+    }
+
+    void run() {
+        where.assign(op.blocks.size(), {-1, 0});
+        // group blocks by (level, m, n), coarse levels first
+        std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+        for (size_t i = 0; i < op.blocks.size(); ++i) {
+            const auto& b = op.blocks[i];
+            groups[{b.level, b.m, b.n}].push_back((int)i);
+        }
+        const size_t budget = std::max<size_t>((size_t)2 << 30, std::min<size_t>(op.ctx->budget / 3, (size_t)48 << 30));
+        for (auto& g : groups) {
+            const auto& ids = g.second;
+            int m = std::get<1>(g.first), n = std::get<2>(g.first);
+            size_t rcap = std::min(std::min(m, n), kRankCap + kChunk);
+            size_t per = ((size_t)m * n + (size_t)m * rcap + (size_t)n * rcap + (size_t)m * 2 * kChunk) * sizeof(T2);
+            int bs = (int)std::max<size_t>(1, std::min<size_t>(4096, budget / per));  // blocks run along grid y
+            for (size_t i0 = 0; i0 < ids.size(); i0 += bs) {
+                std::vector<int> sub(ids.begin() + i0, ids.begin() + std::min(ids.size(), i0 + bs));
+                batch(sub);
+            }
+        }
+        // consolidate into one factor store
+        int64_t total = 0;
+        std::vector<int64_t> qoff(op.blocks.size());
+        for (size_t i = 0; i < op.blocks.size(); ++i) {
+            auto& b = op.blocks[i];
+            qoff[i] = total;
+            total += (int64_t)b.rank * (b.m + b.n);
+            total = (total + 31) / 32 * 32;
+        }
+        op.d_factors.alloc((size_t)std::max<int64_t>(total, 32) * sizeof(T2));
+        op.factor_entries = 0;
+        for (size_t i = 0; i < op.blocks.size(); ++i) {
+            auto& b = op.blocks[i];
+            b.q_off = qoff[i];
+            b.rh_off = qoff[i] + (int64_t)b.rank * b.m;
+            op.factor_entries += (int64_t)b.rank * (b.m + b.n);
+            if (b.rank == 0) continue;
+            const T2* src = stores[where[i].first].template as<T2>() + where[i].second;
+            VIE_CUDA(cudaMemcpyAsync(op.d_factors.as<T2>() + b.q_off, src,
+                                     (size_t)b.rank * (b.m + b.n) * sizeof(T2), cudaMemcpyDeviceToDevice, s));
+        }
+        VIE_CUDA(cudaStreamSynchronize(s));
+        stores.clear();
+    }
+};
+
+}  // namespace
+
+void compress_operator(Op& op, double tol, int prec) {
+    VIE_BLAS(cublasSetStream(op.ctx->blas, op.ctx->stream));
+    op.d_factors.release();
+    for (auto& b : op.blocks) b.rank = 0;
+    if (prec == VIE_C128) {
+        Compressor<double> c(op, tol);
+        c.run();
+    } else {
+        Compressor<float> c(op, tol);
+        c.run();
+    }
+    op.fprec = prec == VIE_C128 ? VIE_C128 : VIE_C64;
+    op.tol = tol;
+    build_apply_lists(op);
+}
+
+}  // namespace vie

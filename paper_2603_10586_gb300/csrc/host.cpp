@@ -1,0 +1,286 @@
+// Host-side algorithms of libvie: voxel/face mesh of an atom type, grid
+// hierarchy and far-block lists, the greedy least-loaded work map and the
+// work lists of the compressed apply.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <limits>
+#include <map>
+#include <numeric>
+#include <queue>
+
+#include "common.h"
+
+namespace vie {
+
+void fail(int status, const std::string& msg) { throw Error{status, msg}; }
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+void DevBuf::alloc(size_t b) {
+    release();
+    if (b == 0) b = 1;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        fail(VIE_ERR_OOM, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    bytes = b;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3 basis on a voxelised cube: one rooftop per voxel face.  Faces are
+// numbered x-faces, y-faces, z-faces; inside a direction lexicographically in
+// (i, j, k) with the normal index running 0..nv.
+// ---------------------------------------------------------------------------
+MeshTables build_mesh(double side, int nv) {
+    MeshTables m;
+    m.nv = nv;
+    m.side = side;
+    m.h = side / nv;
+    m.nvox = nv * nv * nv;
+    auto vnum = [nv](int i, int j, int k) { return (i * nv + j) * nv + k; };
+    for (int i = 0; i < nv; ++i)
+        for (int j = 0; j < nv; ++j)
+            for (int k = 0; k < nv; ++k) {
+                m.vox_ijk.push_back(i);
+                m.vox_ijk.push_back(j);
+                m.vox_ijk.push_back(k);
+            }
+    for (int d = 0; d < 3; ++d) {
+        int ext[3] = {nv, nv, nv};
+        ext[d] = nv + 1;
+        for (int i = 0; i < ext[0]; ++i)
+            for (int j = 0; j < ext[1]; ++j)
+                for (int k = 0; k < ext[2]; ++k) {
+                    int ijk[3] = {i, j, k};
+                    int mm = ijk[d];
+                    int f = (int)m.face_dir.size();
+                    m.face_dir.push_back(d);
+                    int below[3] = {i, j, k};
+                    below[d] = mm - 1;
+                    m.face_lo.push_back(mm >= 1 ? vnum(below[0], below[1], below[2]) : -1);
+                    m.face_hi.push_back(mm <= nv - 1 ? vnum(i, j, k) : -1);
+                    if (mm == 0 || mm == nv) {
+                        m.face_sheet.push_back((int)m.surf_face.size());
+                        m.face_sheet_sign.push_back(mm == 0 ? +1 : -1);
+                        m.surf_face.push_back(f);
+                    } else {
+                        m.face_sheet.push_back(-1);
+                        m.face_sheet_sign.push_back(0);
+                    }
+                }
+    }
+    m.np = (int)m.face_dir.size();
+    m.nsurf = (int)m.surf_face.size();
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// Grid hierarchy (Sec. 5.1 Definition, Sec. 5.3 eq. eq_rec01, Sec. 5.4).
+// Power-of-two quadtree over a root square of side s 2^L whose finest boxes
+// (side s = smallest infinity-norm centre separation) hold at most one atom.
+// Blocks are listed by level, then target box (y, x), then source box (y, x).
+// ---------------------------------------------------------------------------
+void build_tree(Op& op) {
+    const int N = op.N;
+    op.blocks.clear();
+    op.block_atoms.clear();
+    if (N == 1) {
+        op.L = 0;
+        return;
+    }
+    std::vector<double> x(N), y(N);
+    for (int a = 0; a < N; ++a) {
+        x[a] = op.centres[3 * a];
+        y[a] = op.centres[3 * a + 1];
+    }
+    double s = std::numeric_limits<double>::infinity();
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b) s = std::min(s, std::max(std::fabs(x[a] - x[b]), std::fabs(y[a] - y[b])));
+    if (!(s > 0)) fail(VIE_ERR_INVALID_ARG, "two atoms share the same (x, y) position");
+    double xmin = *std::min_element(x.begin(), x.end()), xmax = *std::max_element(x.begin(), x.end());
+    double ymin = *std::min_element(y.begin(), y.end()), ymax = *std::max_element(y.begin(), y.end());
+    double ext = std::max(xmax - xmin, ymax - ymin);
+    int L = 0;
+    while (std::ldexp(1.0, L) < ext / s + 1.0 - 1e-9) ++L;
+    if (L > 20) fail(VIE_ERR_INVALID_ARG, "atom layout needs more than 20 grid levels");
+    op.L = L;
+    const long long side_boxes = 1LL << L;
+    std::vector<long long> fx(N), fy(N);
+    for (int a = 0; a < N; ++a) {
+        fx[a] = std::min(side_boxes - 1, std::max(0LL, (long long)std::floor((x[a] - (xmin - 0.5 * s)) / s)));
+        fy[a] = std::min(side_boxes - 1, std::max(0LL, (long long)std::floor((y[a] - (ymin - 0.5 * s)) / s)));
+    }
+    for (int lev = 1; lev <= L; ++lev) {
+        int shift = L - lev;
+        std::map<std::pair<long long, long long>, std::vector<int>> boxes;  // key (y, x), sorted
+        for (int a = 0; a < N; ++a) boxes[{fy[a] >> shift, fx[a] >> shift}].push_back(a);
+        for (auto& tb : boxes) {
+            long long ty = tb.first.first, tx = tb.first.second;
+            // candidate source boxes: children of the 3x3 parent neighbourhood
+            std::vector<std::pair<long long, long long>> cand;
+            for (long long py = (ty >> 1) - 1; py <= (ty >> 1) + 1; ++py)
+                for (long long px = (tx >> 1) - 1; px <= (tx >> 1) + 1; ++px)
+                    for (int cy = 0; cy < 2; ++cy)
+                        for (int cx = 0; cx < 2; ++cx) {
+                            std::pair<long long, long long> key{2 * py + cy, 2 * px + cx};
+                            if (py >= 0 && px >= 0 && boxes.count(key)) cand.push_back(key);
+                        }
+            std::sort(cand.begin(), cand.end());
+            for (auto& key : cand) {
+                long long dist = std::max(std::llabs(key.first - ty), std::llabs(key.second - tx));
+                bool far = (lev == L) ? (dist != 0) : (dist > 1);
+                if (!far) continue;
+                const auto& ta = tb.second;
+                const auto& sa = boxes[key];
+                FarBlock b;
+                b.level = lev;
+                b.nt = (int)ta.size();
+                b.ns = (int)sa.size();
+                b.t_off = (int)op.block_atoms.size();
+                op.block_atoms.insert(op.block_atoms.end(), ta.begin(), ta.end());
+                b.s_off = (int)op.block_atoms.size();
+                op.block_atoms.insert(op.block_atoms.end(), sa.begin(), sa.end());
+                b.m = b.nt * op.np;
+                b.n = b.ns * op.np;
+                op.blocks.push_back(b);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// App. C: greedy least-loaded assignment.  Interactions sorted by decreasing
+// weight are given one by one to the currently least-loaded process (lowest
+// index on ties).
+// ---------------------------------------------------------------------------
+void lpt_assign(const std::vector<double>& w, int nproc, std::vector<int>& owner, std::vector<double>& loads) {
+    std::vector<int> order(w.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
+    using E = std::pair<double, int>;
+    std::priority_queue<E, std::vector<E>, std::greater<E>> heap;
+    for (int k = 0; k < nproc; ++k) heap.push({0.0, k});
+    owner.assign(w.size(), 0);
+    loads.assign(nproc, 0.0);
+    for (int i : order) {
+        E top = heap.top();
+        heap.pop();
+        owner[i] = top.second;
+        loads[top.second] += w[i];
+        heap.push({loads[top.second], top.second});
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Work lists of the compressed apply (see apply.cu for the item layouts).
+//  phase 1 (t = R x): item (block, k0, k1): rows k0..k1 of R_b
+//  phase 2 (F = sum Q t): item (atom, p0, p1): rows p0..p1 of that atom,
+//          looping over the blocks whose target box holds the atom
+// Items are mapped to persistent CTAs with the greedy least-loaded rule,
+// weighted by their factor bytes.
+// ---------------------------------------------------------------------------
+static void pack_lpt(const std::vector<int4>& items, const std::vector<double>& w, int ncta,
+                     std::vector<int4>& out_items, std::vector<int>& cta_ptr) {
+    std::vector<int> owner;
+    std::vector<double> loads;
+    lpt_assign(w, ncta, owner, loads);
+    std::vector<std::vector<int>> per(ncta);
+    // within a CTA keep the heaviest items first
+    std::vector<int> order(items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
+    for (int i : order) per[owner[i]].push_back(i);
+    out_items.clear();
+    cta_ptr.assign(ncta + 1, 0);
+    for (int c = 0; c < ncta; ++c) {
+        for (int i : per[c]) out_items.push_back(items[i]);
+        cta_ptr[c + 1] = (int)out_items.size();
+    }
+}
+
+void build_apply_lists(Op& op) {
+    const int nb = (int)op.blocks.size();
+    std::vector<FarBlockDev> hb(std::max(nb, 1));
+    int64_t toff = 0;
+    for (int i = 0; i < nb; ++i) {
+        auto& b = op.blocks[i];
+        b.t_off_vec = toff;
+        toff += b.rank;
+        hb[i] = FarBlockDev{b.m, b.n, b.rank, b.nt, b.ns, b.t_off, b.s_off, 0, (long long)b.q_off,
+                            (long long)b.rh_off, (long long)b.t_off_vec};
+    }
+    op.t_total = toff;
+    upload(op.d_blocks, hb);
+    upload(op.d_block_atoms, op.block_atoms.empty() ? std::vector<int>{0} : op.block_atoms);
+    op.n_cta = op.ctx->n_sm * 2;
+
+    // phase 1
+    std::vector<int4> it1;
+    std::vector<double> w1;
+    const double target = 192.0 * 1024;  // bytes of factor per item
+    for (int i = 0; i < nb; ++i) {
+        const auto& b = op.blocks[i];
+        if (b.rank == 0) continue;
+        int rc = std::max(1, (int)(target / (8.0 * b.n)));
+        for (int k0 = 0; k0 < b.rank; k0 += rc) {
+            int k1 = std::min(b.rank, k0 + rc);
+            it1.push_back(make_int4(i, k0, k1, 0));
+            w1.push_back((double)(k1 - k0) * b.n);
+        }
+    }
+    std::vector<int4> p1;
+    std::vector<int> c1;
+    pack_lpt(it1, w1, op.n_cta, p1, c1);
+    op.n_p1_items = (int)p1.size();
+    upload(op.d_p1_items, p1.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : p1);
+    upload(op.d_p1_cta, c1);
+
+    // phase 2: per atom the (block, slot) entries, then row chunks
+    std::vector<std::vector<int2>> ent(op.N);
+    for (int i = 0; i < nb; ++i) {
+        const auto& b = op.blocks[i];
+        if (b.rank == 0) continue;
+        for (int s = 0; s < b.nt; ++s) ent[op.block_atoms[b.t_off + s]].push_back(make_int2(i, s));
+    }
+    std::vector<int> csr(op.N + 1, 0);
+    std::vector<int2> flat;
+    std::vector<double> rsum(op.N, 0.0);
+    for (int a = 0; a < op.N; ++a) {
+        for (auto e : ent[a]) {
+            flat.push_back(e);
+            rsum[a] += op.blocks[e.x].rank;
+        }
+        csr[a + 1] = (int)flat.size();
+    }
+    std::vector<int4> it2;
+    std::vector<double> w2;
+    const int rows_per_item = 128;
+    for (int a = 0; a < op.N; ++a)
+        for (int p0 = 0; p0 < op.np; p0 += rows_per_item) {
+            int p1e = std::min(op.np, p0 + rows_per_item);
+            it2.push_back(make_int4(a, p0, p1e, 0));
+            w2.push_back((double)(p1e - p0) * (rsum[a] + 1.0));
+        }
+    std::vector<int4> p2;
+    std::vector<int> c2;
+    pack_lpt(it2, w2, op.n_cta, p2, c2);
+    op.n_p2_items = (int)p2.size();
+    upload(op.d_p2_items, p2);
+    upload(op.d_p2_cta, c2);
+    upload(op.d_p2_csr, csr);
+    upload(op.d_p2_ent, flat.empty() ? std::vector<int2>{make_int2(0, 0)} : flat);
+}
+
+}  // namespace vie

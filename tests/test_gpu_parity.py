@@ -1,0 +1,208 @@
+"""GPU parity tests: the CUDA path (through the C-ABI) against the CPU oracle
+on the same seeded inputs."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import problem_from_geometry, assembly as A, tree as T, compress as C, krylov as K
+from oracle import fields as OF
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2603_10586_gb300 import vie  # noqa: E402
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = vie.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def tiny_op(ctx, tiny_dense):
+    g, _, _ = workloads.config("tiny")
+    op = vie.Operator(ctx, g)
+    op.compress(1e-4, vie.C64)
+    return op
+
+
+# ------------------------------------------------------------------ assembly
+@pytest.mark.parametrize("nv,side", [(1, 0.2), (2, 0.2), (3, 0.2), (3, 0.05)])
+def test_self_block_float64(ctx, nv, side):
+    g = workloads.square_array(1, nv, side=side)
+    P = problem_from_geometry(g)
+    op = vie.Operator(ctx, g)
+    Zg = op.export_block(0, 0)
+    Zo = A.self_block(P, 0)
+    assert rel(Zg, Zo) < 1e-12
+    inv = op.export_block(2, 0)
+    assert np.linalg.norm(inv @ Zo - np.eye(P.n)) < 1e-10
+
+
+def test_graded_types_self_blocks(ctx):
+    g = workloads.graded_array(4, 2, seed=1)
+    P = problem_from_geometry(g)
+    op = vie.Operator(ctx, g)
+    for t in sorted(set(g.types.tolist())):
+        assert rel(op.export_block(0, t), A.self_block(P, t)) < 1e-12
+
+
+@pytest.mark.parametrize("pair", [(0, 1), (5, 0), (3, 12), (15, 6)])
+def test_cross_block(ctx, tiny_dense, pair):
+    P, Z, _, _, _ = tiny_dense
+    g, _, _ = workloads.config("tiny")
+    op = vie.Operator(ctx, g)
+    a, b = pair
+    ref = Z[P.offsets[a]:P.offsets[a + 1], P.offsets[b]:P.offsets[b + 1]]
+    assert rel(op.export_block(1, a, b, vie.C128), ref) < 1e-12
+    assert rel(op.export_block(1, a, b, vie.C64), ref) < 1e-5
+
+
+def test_cross_block_graded_and_large_atoms(ctx):
+    g = workloads.graded_array(3, 4, seed=2)
+    P = problem_from_geometry(g)
+    op = vie.Operator(ctx, g)
+    for a, b in ((0, 4), (8, 1)):
+        ref = A.cross_block(P, a, b)
+        assert rel(op.export_block(1, a, b, vie.C128), ref) < 1e-12
+        assert rel(op.export_block(1, a, b, vie.C64), ref) < 1e-5
+
+
+def test_rhs(ctx, tiny_dense):
+    import torch as th
+    P, _, b, _, _ = tiny_dense
+    g, kh, pol = workloads.config("tiny")
+    op = vie.Operator(ctx, g)
+    kh2, pol2 = workloads.angle_sweep(3, 60.0)
+    bd = th.zeros((len(kh2), op.n), dtype=th.complex128, device="cuda")
+    op.rhs(kh2, pol2, bd.data_ptr())
+    bg = bd.cpu().numpy()
+    for c in range(len(kh2)):
+        assert rel(bg[c], A.rhs(P, kh2[c], pol2[c])) < 1e-12
+
+
+# ---------------------------------------------------------------------- tree
+@pytest.mark.parametrize("ns", [2, 4, 5, 8])
+def test_far_block_lists_match_oracle(ctx, ns):
+    g = workloads.square_array(ns, 1)
+    op = vie.Operator(ctx, g)
+    mine = [(b["level"], list(b["tatoms"]), list(b["satoms"])) for b in op.far_blocks(with_factors=False)]
+    _, ref = T.build_tree(g.centres)
+    assert mine == [(l, list(t), list(s)) for l, t, s in ref]
+
+
+# ---------------------------------------------------------------- compression
+def test_compression_error_bound(tiny_op, tiny_dense):
+    P, Z, _, _, _ = tiny_dense
+    blocks = tiny_op.far_blocks()
+    for blk in blocks:
+        rows = C.atom_rows(P, blk["tatoms"])
+        cols = C.atom_rows(P, blk["satoms"])
+        Ab = Z[np.ix_(rows, cols)]
+        Q, R = blk["Q"], blk["R"]
+        assert np.linalg.norm(Ab - Q @ R) <= 1e-4 * np.linalg.norm(Ab)
+        assert np.linalg.norm(Q.conj().T @ Q - np.eye(blk["rank"])) < 1e-5
+
+
+# ---------------------------------------------------------------------- apply
+def _oracle_op_from_gpu(op, P, Z):
+    blocks = op.far_blocks()
+    sb = {t: A.self_block(P, t) for t in sorted(set(P.types.tolist()))}
+    return C.operator_from_factors(P, sb, [(b["tatoms"], b["satoms"], b["Q"], b["R"]) for b in blocks]), sb
+
+
+def test_apply_parity_c64_and_acc64(tiny_op, tiny_dense):
+    import torch as th
+    P, Z, _, _, _ = tiny_dense
+    orc, sb = _oracle_op_from_gpu(tiny_op, P, Z)
+    xs = workloads.random_complex(P.n, 1234, cols=3).T.copy()   # 3 RHS, rows contiguous
+    ref = np.stack([orc.apply(x) for x in xs])
+    x32 = th.from_numpy(xs.astype(np.complex64)).cuda()
+    y32 = th.zeros_like(x32)
+    tiny_op.apply(x32.data_ptr(), y32.data_ptr(), 3, vie.C64, 0)
+    assert rel(y32.cpu().numpy(), ref) < 1e-5
+    x64 = th.from_numpy(xs).cuda()
+    y64 = th.zeros_like(x64)
+    tiny_op.apply(x64.data_ptr(), y64.data_ptr(), 3, vie.C64_ACC64, 0)
+    # float32 factors read exactly, float64 arithmetic: rounding-level agreement
+    assert rel(y64.cpu().numpy(), ref) < 1e-12
+
+
+def test_fused_precond_apply(tiny_op, tiny_dense):
+    import torch as th
+    P, Z, _, _, _ = tiny_dense
+    orc, sb = _oracle_op_from_gpu(tiny_op, P, Z)
+    M = K.BlockJacobi(P, sb)
+    x = workloads.random_complex(P.n, 99)
+    ref = M.apply(orc.apply(x))
+    xd = th.from_numpy(x.astype(np.complex64)).cuda()
+    yd = th.zeros_like(xd)
+    tiny_op.apply(xd.data_ptr(), yd.data_ptr(), 1, vie.C64, vie.FUSE_PRECOND)
+    assert rel(yd.cpu().numpy(), ref) < 1e-5
+    xd = th.from_numpy(x).cuda()
+    yd = th.zeros_like(xd)
+    tiny_op.precond(xd.data_ptr(), yd.data_ptr(), 1, vie.C128)
+    assert rel(yd.cpu().numpy(), M.apply(x)) < 1e-12
+
+
+def test_c128_factors_apply(ctx, tiny_dense):
+    import torch as th
+    P, Z, _, _, _ = tiny_dense
+    g, _, _ = workloads.config("tiny")
+    op = vie.Operator(ctx, g)
+    op.compress(1e-4, vie.C128)
+    orc, _ = _oracle_op_from_gpu(op, P, Z)
+    x = workloads.random_complex(P.n, 5)
+    xd = th.from_numpy(x).cuda()
+    yd = th.zeros_like(xd)
+    op.apply(xd.data_ptr(), yd.data_ptr(), 1, vie.C128, 0)
+    assert rel(yd.cpu().numpy(), orc.apply(x)) < 1e-12
+    for blk in op.far_blocks():
+        rows = C.atom_rows(P, blk["tatoms"])
+        cols = C.atom_rows(P, blk["satoms"])
+        Ab = Z[np.ix_(rows, cols)]
+        assert np.linalg.norm(Ab - blk["Q"] @ blk["R"]) <= 1e-4 * np.linalg.norm(Ab)
+        assert np.linalg.norm(blk["Q"].conj().T @ blk["Q"] - np.eye(blk["rank"])) < 1e-12
+
+
+# ---------------------------------------------------------------------- solve
+def test_solve_matches_dense_direct(tiny_op, tiny_dense):
+    P, Z, b, kh, pol = tiny_dense
+    I, st, status = tiny_op.solve(kh[None], pol[None], tol=1e-6)
+    assert status == vie.VIE_OK
+    ref = np.linalg.solve(Z, b)
+    assert rel(I[:, 0], ref) <= 5e-4
+    assert st["residual"] <= 1e-6
+    # the oracle's GMRES on the GPU's factors needs about as many iterations
+    orc, sb = _oracle_op_from_gpu(tiny_op, P, Z)
+    _, info = K.gmres(orc.apply, b, K.BlockJacobi(P, sb).apply, tol=1e-6, restart=60)
+    assert abs(st["iterations"] - info["iterations"]) <= max(2, 0.1 * info["iterations"])
+
+
+def test_solve_all_float64(ctx, tiny_dense):
+    P, Z, b, kh, pol = tiny_dense
+    g, _, _ = workloads.config("tiny")
+    op = vie.Operator(ctx, g)
+    op.compress(1e-4, vie.C128)
+    I, st, status = op.solve(kh[None], pol[None], tol=1e-6, precision=vie.C128)
+    assert status == vie.VIE_OK
+    assert rel(I[:, 0], np.linalg.solve(Z, b)) <= 5e-4
+
+
+def test_cross_sections(tiny_op, tiny_dense):
+    P, Z, b, kh, pol = tiny_dense
+    I, _, _ = tiny_op.solve(kh[None], pol[None], tol=1e-8)
+    sig = tiny_op.sigma(I, kh[None], pol[None])[0]
+    v0 = A.rhs_v0(P, kh, pol)
+    assert abs(sig[0] - OF.sigma_ext(I[:, 0], v0)) < 1e-10 * abs(sig[0])
+    assert abs(sig[1] - OF.sigma_sca(P, I[:, 0])) < 1e-10 * abs(sig[1])
+    assert abs(sig[0] - sig[1]) < 1e-3 * sig[0]   # optical theorem (lossless)
