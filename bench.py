@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""Benchmark: solves/s of the QR-compressed VIE solver on one GB300.
+
+A step is one solve from geometry: vie_assemble (grid hierarchy, float64 self
+blocks and their inverses), vie_compress (every far block formed on the device
+and compressed at tolerance 1e-4, complex float32 factors) and vie_solve
+(mixed-precision GMRES to a relative residual of 1e-6) of the 16 x 16 array of
+6^3-voxel cubes (193,536 unknowns, normal incidence).  `value` keeps the solution
+on the device; `e2e` goes through the same C-ABI with host buffers (geometry
+in, current out).  `roofline` is the compressed apply (the GMRES hot loop)
+timed with CUDA events on the same operator; factors are far larger than L2,
+so no flush is needed between applies.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+Multi-GPU: one process per GPU (torchrun); the solves are independent
+replicas (no collective), value = all ranks' solves / max rank time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = "scale"
+DESC = "16x16 array of eps=12 cubes (side 0.2, pitch 0.4, lambda 1), 6^3 voxels, 193536 unknowns, 1 RHS"
+TOL_COMPRESS = 1e-4
+TOL_SOLVE = 1e-6
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(budget_s=20.0):
+    """The CPU float64 oracle, as it stands, on a bounded sample of the same
+    workload, extrapolated to one full solve (seconds per solve)."""
+    from oracle import problem_from_geometry, assembly as A, compress as OC, tree as OT
+    g, kh, pol = workloads.config(WORKLOAD)
+    P = problem_from_geometry(g)
+    L, blocks = OT.build_tree(P.centres)
+    n_pairs = sum(len(t) * len(s) for _, t, s in blocks)
+    t0 = time.perf_counter()
+    blk = A.cross_block(P, 0, 17)                  # a neighbouring pair at the finest level
+    t_pair = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Q, R, err = OC.householder_qr_truncated(blk, TOL_COMPRESS)
+    t_qr = time.perf_counter() - t0
+    r = R.shape[0]
+    # compression cost modelled as proportional to m n r (unpivoted Householder)
+    work_qr = sum((len(t) * P.meshes[0].n_faces) * (len(s) * P.meshes[0].n_faces) for _, t, s in blocks) * r
+    t_comp = t_qr / (blk.shape[0] * blk.shape[1] * r) * work_qr
+    # apply: the sampled factors applied repeatedly
+    x = workloads.random_complex(blk.shape[1], 1234)
+    t0 = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t0 < 0.5:
+        Q @ (R @ x)
+        reps += 1
+    t_fac = (time.perf_counter() - t0) / reps / ((blk.shape[0] + blk.shape[1]) * r)
+    factor_entries = sum((len(t) + len(s)) * P.meshes[0].n_faces for _, t, s in blocks) * r
+    iters = 60
+    t_apply = t_fac * factor_entries
+    total = n_pairs * t_pair + t_comp + iters * t_apply
+    sample = (f"oracle on host cores: 1 atom-pair block assembly ({t_pair:.2f} s) x {n_pairs} pairs, "
+              f"1 Householder QR of a {blk.shape[0]}x{blk.shape[1]} block (rank {r}, {t_qr:.2f} s) scaled by m n r "
+              f"over all far blocks, {iters} compressed applies at the sampled per-entry rate")
+    return total, sample
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    """--impl reference: the oracle as it stands (CPU), on rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    times = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        total, sample = oracle_sample()
+        if i >= args.warmup:
+            times.append(total)
+    v = 1.0 / statistics.mean(times)
+    line = {"metric": "solves/s", "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "description": DESC}, "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--applies", type=int, default=40)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2603_10586_gb300 import vie
+
+    g, kh, pol = workloads.config(WORKLOAD)
+    ctx = vie.Context(local)
+    n = g.unknowns()
+    out = torch.empty(n, dtype=torch.complex128, device="cuda")
+    h2d = (g.centres.nbytes + g.types.nbytes + g.sides.nbytes + g.nvs.nbytes + 16 * len(g.eps)
+           + kh.nbytes + 2 * pol.real.nbytes)
+    state = {}
+
+    def step(host):
+        op = vie.Operator(ctx, g)
+        op.compress(TOL_COMPRESS, vie.C64)
+        I, stats, status = op.solve(kh, pol, tol=TOL_SOLVE, restart=60,
+                                    out_ptr=None if host else out.data_ptr())
+        if status != vie.VIE_OK:
+            raise RuntimeError(f"solve did not converge: {stats['residual']}")
+        state["stats"], state["info"] = stats, op.info()
+        if "keep" in state:
+            state["keep"].close()
+        state["keep"] = op
+        return I
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(False)
+    clocks = Clocks(local)
+    barrier()
+    l0 = vie.kernel_launches()
+    clocks.start()
+    lat = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(False)
+        e1.record()
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    ev1.record()
+    barrier()
+    clk = clocks.stop()
+    launches = vie.kernel_launches() - l0
+    total_ms = ev0.elapsed_time(ev1)
+    stats, info = state["stats"], state["info"]
+
+    # end to end through the C-ABI with host buffers
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        I = step(True)
+    e1.record()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+
+    # roofline of the compressed apply on the last operator
+    op = state["keep"]
+    x = torch.randn(n, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        op.apply(x.data_ptr(), y.data_ptr(), 1, vie.C64, vie.FUSE_PRECOND)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record()
+    for _ in range(args.applies):
+        op.apply(x.data_ptr(), y.data_ptr(), 1, vie.C64, vie.FUSE_PRECOND)
+    a1.record()
+    torch.cuda.synchronize()
+    apply_ms = a0.elapsed_time(a1) / args.applies
+    peak, peak_kind = peaks()
+    achieved = info["apply_bytes"] / (apply_ms * 1e-3) / 1e9
+
+    def maxr(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    total_ms = maxr(total_ms)
+    e2e_ms = maxr(e2e_ms)
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            t_cpu, sample = oracle_sample()
+            cpu = {"value": 1.0 / t_cpu, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample}
+        lat_sorted = sorted(lat)
+        line = {
+            "metric": "solves/s", "value": world * args.steps / (total_ms * 1e-3), "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "description": DESC, "tol_compress": TOL_COMPRESS,
+                       "tol_solve": TOL_SOLVE, "parallelism": f"replicas{world}",
+                       "l2_flush": "none: factors (GBs) exceed L2"},
+            "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
+            "breakdown_s": {"assemble": info["t_assemble_s"], "compress": info["t_compress_s"],
+                            "solve": stats["t_solve_s"]},
+            "solver": {"iterations": stats["iterations"], "refinements": stats["refinements"],
+                       "residual": stats["residual"], "true_residual": stats["true_residual"]},
+            "operator": {"n": info["n"], "levels": info["levels"], "far_blocks": info["n_far_blocks"],
+                         "factor_entries": info["factor_entries"], "gain": info["gain"],
+                         "rank_min": info["rank_min"], "rank_max": info["rank_max"],
+                         "rank_mean": info["rank_mean"]},
+            "roofline": {"kernel": "compressed apply P^-1 Zs x (c64, 1 RHS)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "algorithmic_bytes": info["apply_bytes"],
+                         "apply_ms": apply_ms, "traffic": None},
+            "e2e": {"value": world * args.steps / (e2e_ms * 1e-3), "unit": "solves/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(16 * n)},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if "keep" in state:
+        state["keep"].close()
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -71,6 +71,9 @@ enum vie_precision {
 
 /* vie_apply flags */
 #define VIE_APPLY_FUSE_PRECOND 1 /* y = x + Z_D^-1 (far part of Zs x) = P^-1 Zs x */
+#define VIE_APPLY_DENSE 2        /* y = Zs x with the uncompressed operator: every
+                                    block regenerated on the device and never stored
+                                    (accuracy reference; 1 RHS; C64 or C128) */
 
 typedef struct vie_ctx_opts {
     int device;            /* CUDA device ordinal */
@@ -139,6 +142,8 @@ typedef struct vie_solve_stats {
 
 /* ---- context ---------------------------------------------------------------- */
 int vie_create(vie_ctx** out, const vie_ctx_opts* opts);
+/* Releases the context; if operators made from it still exist it is freed
+ * when the last of them is destroyed. */
 void vie_destroy(vie_ctx* ctx);
 const char* vie_last_error(vie_ctx* ctx);
 
@@ -165,7 +170,8 @@ int vie_op_get_info(const vie_op* op, vie_op_info* info);
  * x, y: device pointers, n x nrhs, leading dimension ld (elements).
  * precision VIE_C64 (x, y c64), VIE_C128 (c128, needs C128 factors),
  * VIE_C64_ACC64 (x, y c128, c64 factors), VIE_BF16X3 (c64).
- * flags: VIE_APPLY_FUSE_PRECOND returns P^-1 Zs x instead of Zs x.
+ * flags: VIE_APPLY_FUSE_PRECOND returns P^-1 Zs x instead of Zs x;
+ * VIE_APPLY_DENSE applies the uncompressed matrix (works before vie_compress).
  * x and y must not overlap.  Asynchronous on `stream`. */
 int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int precision,
               int flags, vie_stream stream);
@@ -247,6 +253,10 @@ int vie_server_stop(vie_server* s); /* drains in-flight work, then frees the ser
 /* Modelled footprint (bytes) of a request of n unknowns, nrhs right-hand sides,
  * restart m and the given factor-entry estimate: the admission rule. */
 int64_t vie_footprint_bytes(int64_t n, int np, int nrhs, int restart, int64_t factor_entries);
+
+/* Number of libvie kernels launched by this process so far (all contexts);
+ * cuBLAS kernels are not counted.  Diagnostic, thread-safe. */
+int64_t vie_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -4,13 +4,18 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <memory>
 
 #include "common.h"
 #include "krylov.h"
 
+// A context stays alive while operators made from it exist: vie_destroy only
+// marks it closed when operators remain, the last vie_op_destroy frees it.
 struct vie_ctx {
     vie::Ctx c;
+    std::atomic<int> ops{0};
+    std::atomic<bool> closed{false};
 };
 struct vie_op {
     vie::Op o;
@@ -62,6 +67,7 @@ namespace {
 
 template <class F>
 int guarded(vie_ctx* ctx, F&& f) {
+    cudaGetLastError();  // an earlier failure elsewhere is not this call's error
     try {
         f();
         if (ctx) ctx->c.err.clear();
@@ -78,7 +84,7 @@ int guarded(vie_ctx* ctx, F&& f) {
     }
 }
 
-vie_ctx* ctx_of(vie_op* op) { return op ? reinterpret_cast<vie_ctx*>(op->o.ctx) : nullptr; }
+vie_ctx* ctx_of(vie_op* op) { return op ? static_cast<vie_ctx*>(op->o.ctx->owner) : nullptr; }
 
 void set_device(Ctx& c) { VIE_CUDA(cudaSetDevice(c.device)); }
 
@@ -92,6 +98,7 @@ int vie_create(vie_ctx** out, const vie_ctx_opts* opts) {
     auto ctx = std::make_unique<vie_ctx>();
     int st = guarded(ctx.get(), [&] {
         Ctx& c = ctx->c;
+        c.owner = ctx.get();
         c.device = opts ? opts->device : 0;
         c.verbose = opts ? opts->verbose : 0;
         int ndev = 0;
@@ -119,12 +126,17 @@ int vie_create(vie_ctx** out, const vie_ctx_opts* opts) {
     return VIE_OK;
 }
 
-void vie_destroy(vie_ctx* ctx) {
-    if (!ctx) return;
+static void free_ctx(vie_ctx* ctx) {
     cudaSetDevice(ctx->c.device);
     if (ctx->c.blas) cublasDestroy(ctx->c.blas);
     if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
     delete ctx;
+}
+
+void vie_destroy(vie_ctx* ctx) {
+    if (!ctx) return;
+    ctx->closed = true;
+    if (ctx->ops.load() == 0) free_ctx(ctx);
 }
 
 const char* vie_last_error(vie_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "no context"; }
@@ -216,7 +228,10 @@ int vie_assemble(vie_ctx* ctx, const vie_geometry* g, double wavelength, vie_op*
             fprintf(stderr, "[vie] assemble: N=%d np=%d levels=%d far blocks=%zu  %.3f s\n", o.N, o.np, o.L,
                     o.blocks.size(), o.t_assemble);
     });
-    if (st == VIE_OK) *out = op.release();
+    if (st == VIE_OK) {
+        ctx->ops.fetch_add(1);
+        *out = op.release();
+    }
     return st;
 }
 
@@ -238,9 +253,11 @@ int vie_compress(vie_op* op, double tol, int factor_precision) {
 
 void vie_op_destroy(vie_op* op) {
     if (!op) return;
+    vie_ctx* ctx = ctx_of(op);
     cudaSetDevice(op->o.ctx->device);
     cudaStreamSynchronize(op->o.ctx->stream);
     delete op;
+    if (ctx->ops.fetch_sub(1) == 1 && ctx->closed.load()) free_ctx(ctx);
 }
 
 int vie_op_get_info(const vie_op* op, vie_op_info* info) {
@@ -284,9 +301,17 @@ int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int prec
         Op& o = op->o;
         set_device(*o.ctx);
         if (!x || !y || nrhs < 1 || ld != o.n()) fail(VIE_ERR_INVALID_ARG, "vie_apply: bad vectors (ld must be n)");
-        if (o.fprec == 0) fail(VIE_ERR_STATE, "operator is not compressed");
+        if (o.fprec == 0 && !(flags & VIE_APPLY_DENSE)) fail(VIE_ERR_STATE, "operator is not compressed");
         cudaStream_t s = stream ? (cudaStream_t)stream : o.ctx->stream;
         const bool fuse = flags & VIE_APPLY_FUSE_PRECOND;
+        if (flags & VIE_APPLY_DENSE) {
+            if (fuse) fail(VIE_ERR_INVALID_ARG, "VIE_APPLY_DENSE cannot be combined with the preconditioner");
+            if (precision == VIE_C64) dense_apply_c64(o, (const float2*)x, (float2*)y, s);
+            else if (precision == VIE_C128) dense_apply_c128(o, (const double2*)x, (double2*)y, s);
+            else fail(VIE_ERR_INVALID_ARG, "VIE_APPLY_DENSE needs VIE_C64 or VIE_C128");
+            if (nrhs != 1) fail(VIE_ERR_INVALID_ARG, "VIE_APPLY_DENSE takes one right-hand side");
+            return;
+        }
         if (precision == VIE_C64) {
             if (fuse) op_apply_fused32(o, (const float2*)x, (float2*)y, nrhs, s);
             else {
@@ -529,6 +554,8 @@ int vie_export_far_block(vie_op* op, int64_t i, int* tatoms, int* satoms, void* 
                 for (int c = 0; c < b.n; ++c) r[k + (size_t)c * b.rank] = std::conj(h[mq + c + (size_t)k * b.n]);
     });
 }
+
+int64_t vie_kernel_launches(void) { return g_kernel_launches.load(); }
 
 int64_t vie_footprint_bytes(int64_t n, int np, int nrhs, int restart, int64_t factor_entries) {
     // factors (c64) + self/inverse blocks (c128 + c64, two per type upper bound 3 types)

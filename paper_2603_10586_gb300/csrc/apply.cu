@@ -46,12 +46,13 @@ template <class T2> __device__ __forceinline__ T2 shfl_down2(T2 v, int o) {
 // phase 1: one warp per group of ROWS rows of R_b, lanes stride over columns
 // ---------------------------------------------------------------------------
 template <class TF, class TX, int ROWS>
-__global__ void __launch_bounds__(256) p1_kernel(const FarBlockDev* __restrict__ blocks,
+__global__ void __launch_bounds__(256, 3) p1_kernel(const FarBlockDev* __restrict__ blocks,
                                                  const int* __restrict__ batoms, const int4* __restrict__ items,
                                                  const int* __restrict__ cta_ptr, const TF* __restrict__ factors,
                                                  const TX* __restrict__ x, int64_t ldx, int np,
                                                  TX* __restrict__ t, int64_t ldt, int nrhs) {
     using TA = TX;  // accumulate in the vector precision
+    using R = decltype(TA().x);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1]; ++it) {
@@ -61,26 +62,48 @@ __global__ void __launch_bounds__(256) p1_kernel(const FarBlockDev* __restrict__
         const int* S = batoms + B.s_off;
         for (int k = item.y + warp * ROWS; k < item.z; k += nwarps * ROWS) {
             const int nrow = min(ROWS, item.z - k);
+            const TF* rows[ROWS];
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) rows[r] = RH + (int64_t)(k + min(r, nrow - 1)) * B.n;
             for (int c0 = 0; c0 < nrhs; ++c0) {
                 TA acc[ROWS];
 #pragma unroll
-                for (int r = 0; r < ROWS; ++r) acc[r] = mk(decltype(acc[0].x)(0), decltype(acc[0].x)(0));
-                // column c = 2 lane + 64 i; (slot, off) tracked incrementally
+                for (int r = 0; r < ROWS; ++r) acc[r] = mk(R(0), R(0));
+                const TX* xc = x + (int64_t)c0 * ldx;
+                // column c = 2 lane + 64 i; two positions (c, c + 64) per iteration;
+                // (slot, off) of each tracked incrementally
                 int c = 2 * lane;
                 int slot = c / np, off = c - slot * np;
-                const TX* xc = x + (int64_t)c0 * ldx;
-                for (; c < B.n; c += 64) {
-                    Pair<TX> xv = ldpair(xc + (int64_t)S[slot] * np + off);
+                for (; c + 64 < B.n; c += 128) {
+                    int off2 = off + 64, slot2 = slot;
+                    while (off2 >= np) { off2 -= np; ++slot2; }
+                    Pair<TX> xa = ldpair(xc + (int64_t)S[slot] * np + off);
+                    Pair<TX> xb = ldpair(xc + (int64_t)S[slot2] * np + off2);
+                    Pair<TF> ra[ROWS], rb[ROWS];
 #pragma unroll
                     for (int r = 0; r < ROWS; ++r) {
-                        if (r < nrow) {
-                            Pair<TF> rv = ldpair_stream(RH + c + (int64_t)(k + r) * B.n);
-                            cfmac(acc[r], cvt<TA>(rv.a), xv.a);
-                            cfmac(acc[r], cvt<TA>(rv.b), xv.b);
-                        }
+                        ra[r] = ldpair_stream(rows[r] + c);
+                        rb[r] = ldpair_stream(rows[r] + c + 64);
                     }
-                    off += 64;
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) {
+                        cfmac(acc[r], cvt<TA>(ra[r].a), xa.a);
+                        cfmac(acc[r], cvt<TA>(ra[r].b), xa.b);
+                        cfmac(acc[r], cvt<TA>(rb[r].a), xb.a);
+                        cfmac(acc[r], cvt<TA>(rb[r].b), xb.b);
+                    }
+                    off = off2 + 64;
+                    slot = slot2;
                     while (off >= np) { off -= np; ++slot; }
+                }
+                if (c < B.n) {
+                    Pair<TX> xa = ldpair(xc + (int64_t)S[slot] * np + off);
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) {
+                        Pair<TF> ra = ldpair_stream(rows[r] + c);
+                        cfmac(acc[r], cvt<TA>(ra.a), xa.a);
+                        cfmac(acc[r], cvt<TA>(ra.b), xa.b);
+                    }
                 }
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
@@ -122,16 +145,18 @@ __global__ void __launch_bounds__(256) p2_kernel(const FarBlockDev* __restrict__
                     const TF* Q = factors + B.q_off + (int64_t)en.y * np + row;
                     const TX* tb = t + B.tvec_off + (int64_t)c0 * ldt;
                     int k = kg;
-                    for (; k + 12 < B.rank; k += 16) {
-                        Pair<TF> q0 = ldpair_stream(Q + (int64_t)k * B.m);
-                        Pair<TF> q1 = ldpair_stream(Q + (int64_t)(k + 4) * B.m);
-                        Pair<TF> q2 = ldpair_stream(Q + (int64_t)(k + 8) * B.m);
-                        Pair<TF> q3 = ldpair_stream(Q + (int64_t)(k + 12) * B.m);
-                        TA t0 = tb[k], t1 = tb[k + 4], t2 = tb[k + 8], t3 = tb[k + 12];
-                        cfma(acc0, cvt<TA>(q0.a), t0); cfma(acc1, cvt<TA>(q0.b), t0);
-                        cfma(acc0, cvt<TA>(q1.a), t1); cfma(acc1, cvt<TA>(q1.b), t1);
-                        cfma(acc0, cvt<TA>(q2.a), t2); cfma(acc1, cvt<TA>(q2.b), t2);
-                        cfma(acc0, cvt<TA>(q3.a), t3); cfma(acc1, cvt<TA>(q3.b), t3);
+                    for (; k + 28 < B.rank; k += 32) {
+                        Pair<TF> q[8];
+                        TA tv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) q[u] = ldpair_stream(Q + (int64_t)(k + 4 * u) * B.m);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) tv[u] = tb[k + 4 * u];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            cfma(acc0, cvt<TA>(q[u].a), tv[u]);
+                            cfma(acc1, cvt<TA>(q[u].b), tv[u]);
+                        }
                     }
                     for (; k < B.rank; k += 4) {
                         Pair<TF> q0 = ldpair_stream(Q + (int64_t)k * B.m);

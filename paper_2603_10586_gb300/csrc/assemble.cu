@@ -698,9 +698,17 @@ void assemble_self_blocks(Op& op) {
         int ns = std::max(m.nvox, m.nsurf) * m.nsurf;
         self_surf_kernel<<<dim3((ns + 63) / 64, 3), 64, 0, s>>>(m, h, op.k, tab.as<double2>());
         VIE_CHECK_LAUNCH();
-        // an atom of this type (entries only need its type)
+        // an atom of this type (entries only need its type); a type without
+        // atoms gets an identity block so that its inverse stays defined
         int atom = op.atoms_of_type[t].empty() ? -1 : op.atoms_of_type[t][0];
-        if (atom < 0) continue;
+        if (atom < 0) {
+            std::vector<double2> eye((size_t)np * np, make_double2(0, 0));
+            for (int i = 0; i < np; ++i) eye[(size_t)i * np + i] = make_double2(1, 0);
+            VIE_CUDA(cudaMemcpyAsync(op.d_zself64.as<double2>() + (size_t)t * np * np, eye.data(),
+                                     eye.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+            VIE_CUDA(cudaStreamSynchronize(s));
+            continue;
+        }
         PairJob jb{atom, atom, 0, 0, 0};
         void* dptr = op.d_zself64.as<double2>() + (size_t)t * np * np;
         int64_t ldv = np;
@@ -752,6 +760,69 @@ void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_ds
 }
 
 template void assemble_pairs<float>(Op&, const PairJob*, int, void* const*, const int64_t*, cudaStream_t);
+
+namespace {
+// y[a] = sum_b Z_ab x_b for the atoms of a chunk; blocks of atom a_local are
+// stored at blk + (a_local * N + b) * np^2 (self block pointer for b == a)
+template <class T2>
+__global__ void dense_rows_kernel(const T2* blk, const T2* zself, const int* types, int N, int np, int a0,
+                                  const T2* x, T2* y) {
+    const int al = blockIdx.y;
+    const int a = a0 + al;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    using R = decltype(x[0].x);
+    T2 acc = mk(R(0), R(0));
+    const size_t np2 = (size_t)np * np;
+    for (int b = 0; b < N; ++b) {
+        const T2* Zb = b == a ? zself + (size_t)types[a] * np2 : blk + ((size_t)al * N + b) * np2;
+        const T2* xb = x + (size_t)b * np;
+        for (int j = 0; j < np; ++j) cfma(acc, Zb[i + (size_t)j * np], xb[j]);
+    }
+    y[(size_t)a * np + i] = acc;
+}
+}  // namespace
+
+// y = Zs x with every interaction block regenerated on the fly (never stored):
+// the uncompressed operator, for accuracy checks of the compressed one and as
+// the plain dense product it replaces.
+template <class T>
+void dense_apply(Op& op, const typename C2<T>::t* x, typename C2<T>::t* y, cudaStream_t s) {
+    using T2 = typename C2<T>::t;
+    const int N = op.N, np = op.np;
+    const size_t np2 = (size_t)np * np;
+    const T2* zself;
+    DevBuf z32;
+    if (sizeof(T) == 8) zself = (const T2*)op.d_zself64.p;
+    else zself = (const T2*)op.d_zself32.p;
+    int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)N, ((size_t)4 << 30) / (N * np2 * sizeof(T2))));
+    DevBuf blk((size_t)chunk * N * np2 * sizeof(T2));
+    std::vector<void*> dst{blk.p};
+    std::vector<int64_t> ld{np};
+    DevBuf dd, dl;
+    upload(dd, dst);
+    upload(dl, ld);
+    for (int a0 = 0; a0 < N; a0 += chunk) {
+        int na = std::min(chunk, N - a0);
+        std::vector<PairJob> jobs;
+        for (int al = 0; al < na; ++al)
+            for (int b = 0; b < N; ++b)
+                if (b != a0 + al) {
+                    // block (al, b) at column offset (al * N + b) * np of an np-row matrix
+                    jobs.push_back(PairJob{a0 + al, b, 0, 0, (al * N + b) * np});
+                }
+        DevBuf dj;
+        upload(dj, jobs);
+        if (!jobs.empty())
+            assemble_pairs<T>(op, dj.as<PairJob>(), (int)jobs.size(), dd.as<void* const>(), dl.as<int64_t>(), s);
+        dense_rows_kernel<T2><<<dim3((np + 127) / 128, na), 128, 0, s>>>(blk.as<T2>(), zself, op.d_types.as<int>(),
+                                                                         N, np, a0, x, y);
+        VIE_CHECK_LAUNCH();
+        VIE_CUDA(cudaStreamSynchronize(s));
+    }
+}
+void dense_apply_c64(Op& op, const float2* x, float2* y, cudaStream_t s) { dense_apply<float>(op, x, y, s); }
+void dense_apply_c128(Op& op, const double2* x, double2* y, cudaStream_t s) { dense_apply<double>(op, x, y, s); }
 template void assemble_pairs<double>(Op&, const PairJob*, int, void* const*, const int64_t*, cudaStream_t);
 
 void rhs_kernel_launch(Op& op, const double* d_khat, const double* d_pol, int nrhs, void* b, int64_t ld,

@@ -4,10 +4,12 @@
 #include <cuda_runtime.h>
 #include <cublas_v2.h>
 
+#include <atomic>
 #include <complex>
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/vie.h"
@@ -42,7 +44,14 @@ struct Error {
                                           std::to_string((int)s_) + " at " __FILE__);    \
     } while (0)
 
-#define VIE_CHECK_LAUNCH() VIE_CUDA(cudaGetLastError())
+// every launch site of a libvie kernel calls VIE_CHECK_LAUNCH (or VIE_COUNT_LAUNCH)
+extern std::atomic<long long> g_kernel_launches;
+#define VIE_COUNT_LAUNCH(k) (::vie::g_kernel_launches.fetch_add((k), std::memory_order_relaxed))
+#define VIE_CHECK_LAUNCH()          \
+    do {                            \
+        VIE_COUNT_LAUNCH(1);        \
+        VIE_CUDA(cudaGetLastError()); \
+    } while (0)
 
 // ---------------------------------------------------------------------------
 // device buffer (RAII)
@@ -159,6 +168,7 @@ struct Ctx {
     std::string err;
     size_t budget = 0;
     int verbose = 0;
+    void* owner = nullptr;  // the C-ABI handle holding this context
 };
 
 // device-side block description used by the apply kernels
@@ -190,6 +200,8 @@ struct PairJob {
 template <class T>
 void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_dst, const int64_t* d_ld,
                     cudaStream_t s);
+void dense_apply_c64(Op& op, const float2* x, float2* y, cudaStream_t s);
+void dense_apply_c128(Op& op, const double2* x, double2* y, cudaStream_t s);
 void rhs_kernel_launch(Op& op, const double* d_khat, const double* d_pol, int nrhs, void* b, int64_t ld,
                        cudaStream_t s);
 void far_field_launch(Op& op, const void* d_I, int nrhs, const double* d_dirs, int npts, void* d_out,

@@ -17,6 +17,7 @@
 // random numbers and the column compaction are this file's kernels.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <map>
 
 #include "common.h"
@@ -114,7 +115,9 @@ __global__ void k_gram_reduce(const double2* part, int nchunk, double2* G) {
 
 // Cholesky G = L L^H (float64, one block per batch entry) and Minv = L^-H
 // (upper triangular) so that Y Minv has orthonormal columns.  A pivot below
-// 1e-10 of the largest diagonal marks the column dead (zero in Minv).
+// 1e-8 of the largest diagonal (a column norm below 1e-4 of the largest after
+// the earlier ones are removed) marks the column dead (zero in Minv); what it
+// held stays in the residual and is picked up by a later sketch.
 template <class T2>
 __global__ void k_chol(const double2* G, T2* Minv, const int* active, unsigned char* alive, int rcap,
                        const int* rbase) {
@@ -137,7 +140,7 @@ __global__ void k_chol(const double2* G, T2* Minv, const int* active, unsigned c
     // right-looking Cholesky, column by column (thread t owns row t)
     for (int k = 0; k < kChunk; ++k) {
         double d = L[k][k].x;
-        bool dk = !(d > 1e-10 * gmax) || gmax <= 0.0;
+        bool dk = !(d > 1e-8 * gmax) || gmax <= 0.0;
         __syncthreads();
         if (t == 0) dead[k] = dk;
         double sq = dk ? 0.0 : sqrt(d);
@@ -217,6 +220,18 @@ __global__ void k_gather_cols(const T2* src, int64_t rows, const long long* src_
 template <class T> struct Blas;
 template <> struct Blas<float> {
     using T2 = float2;
+    static void gemm_ptr(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, T2 alpha,
+                         const T2* const* A, int lda, const T2* const* B, int ldb, T2 beta, T2* const* C, int ldc,
+                         int batch) {
+        VIE_BLAS(cublasCgemmBatched(h, ta, tb, m, n, k, (const cuComplex*)&alpha, (const cuComplex* const*)A, lda,
+                                    (const cuComplex* const*)B, ldb, (const cuComplex*)&beta, (cuComplex* const*)C,
+                                    ldc, batch));
+    }
+    static void gemm1(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, T2 alpha,
+                      const T2* A, int lda, const T2* B, int ldb, T2 beta, T2* C, int ldc) {
+        VIE_BLAS(cublasCgemm(h, ta, tb, m, n, k, (const cuComplex*)&alpha, (const cuComplex*)A, lda,
+                             (const cuComplex*)B, ldb, (const cuComplex*)&beta, (cuComplex*)C, ldc));
+    }
     static void gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, T2 alpha,
                      const T2* A, int lda, long long sa, const T2* B, int ldb, long long sb, T2 beta, T2* C, int ldc,
                      long long sc, int batch) {
@@ -227,6 +242,18 @@ template <> struct Blas<float> {
 };
 template <> struct Blas<double> {
     using T2 = double2;
+    static void gemm_ptr(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, T2 alpha,
+                         const T2* const* A, int lda, const T2* const* B, int ldb, T2 beta, T2* const* C, int ldc,
+                         int batch) {
+        VIE_BLAS(cublasZgemmBatched(h, ta, tb, m, n, k, (const cuDoubleComplex*)&alpha,
+                                    (const cuDoubleComplex* const*)A, lda, (const cuDoubleComplex* const*)B, ldb,
+                                    (const cuDoubleComplex*)&beta, (cuDoubleComplex* const*)C, ldc, batch));
+    }
+    static void gemm1(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, T2 alpha,
+                      const T2* A, int lda, const T2* B, int ldb, T2 beta, T2* C, int ldc) {
+        VIE_BLAS(cublasZgemm(h, ta, tb, m, n, k, (const cuDoubleComplex*)&alpha, (const cuDoubleComplex*)A, lda,
+                             (const cuDoubleComplex*)B, ldb, (const cuDoubleComplex*)&beta, (cuDoubleComplex*)C, ldc));
+    }
     static void gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, T2 alpha,
                      const T2* A, int lda, long long sa, const T2* B, int ldb, long long sb, T2 beta, T2* C, int ldc,
                      long long sc, int batch) {
@@ -251,7 +278,7 @@ struct Compressor {
     cublasHandle_t h;
     std::vector<DevBuf> stores;          // staging factor stores (one per batch)
     std::vector<std::pair<int, int64_t>> where;  // per block: (store, offset of Q); R^H follows Q
-    std::map<int, int> level_rank;       // running max rank per level
+    std::map<int, std::pair<double, int>> level_rank;  // per level: (sum of ranks, blocks)
     uint64_t seed = 0x5eed0001ull;
 
     Compressor(Op& o, double t) : op(o), tol(t), s(o.ctx->stream), h(o.ctx->blas) {}
@@ -310,9 +337,12 @@ struct Compressor {
         DevBuf gpart, G((size_t)nb * kChunk * kChunk * sizeof(double2)), Minv((size_t)nb * kChunk * kChunk * sizeof(T2));
         DevBuf d_active(nb * sizeof(int)), d_rbase(nb * sizeof(int));
         std::vector<int> r(nb, 0), conv(nb, 0);
+        // first sketch: the mean rank already seen at this level (one pass over A),
+        // then 32-column passes for the blocks that still need more
         int s0 = kChunk;
         auto it = level_rank.find(b0.level);
-        if (it != level_rank.end()) s0 = std::max(kChunk, ((int)(0.9 * it->second) / kChunk) * kChunk);
+        if (it != level_rank.end() && it->second.second > 0)
+            s0 = std::max(kChunk, ((int)(it->second.first / it->second.second + kChunk - 1) / kChunk) * kChunk);
         s0 = std::min(s0, rcap_pad);
         int step = 0;
         const double thr = (tol / 3.0) * (tol / 3.0);
@@ -336,8 +366,26 @@ struct Compressor {
             VIE_CHECK_LAUNCH();
             ++step;
             const T2 one = mk(T(1), T(0)), zero = mk(T(0), T(0)), mone = mk(T(-1), T(0));
-            Blas<T>::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, scols, n, one, A.as<T2>(), m, mn, W.as<T2>(), n, 0, zero,
-                          Y.as<T2>(), m, (long long)m * scols, nb);
+            if (step == 1) {
+                Blas<T>::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, scols, n, one, A.as<T2>(), m, mn, W.as<T2>(), n, 0, zero,
+                              Y.as<T2>(), m, (long long)m * scols, nb);
+            } else {
+                std::vector<const T2*> pa, pb;
+                std::vector<T2*> pc;
+                for (int q = 0; q < nb; ++q)
+                    if (!conv[q]) {
+                        pa.push_back(A.as<T2>() + (size_t)q * mn);
+                        pb.push_back(W.as<T2>());
+                        pc.push_back(Y.as<T2>() + (size_t)q * m * scols);
+                    }
+                DevBuf da, db, dc;
+                upload(da, pa);
+                upload(db, pb);
+                upload(dc, pc);
+                Blas<T>::gemm_ptr(h, CUBLAS_OP_N, CUBLAS_OP_N, m, scols, n, one, da.as<const T2* const>(), m,
+                                  db.as<const T2* const>(), n, zero, dc.as<T2* const>(), m, (int)pa.size());
+                VIE_CUDA(cudaStreamSynchronize(s));
+            }
             for (int c0 = 0; c0 < scols; c0 += kChunk) {
                 T2* Yc = Y.as<T2>() + (int64_t)c0 * m;
                 const long long ys = (long long)m * scols;
@@ -376,6 +424,16 @@ struct Compressor {
                 size_t gneed = (size_t)nb * nchunk * kChunk * kChunk * sizeof(double2);
                 if (gpart.bytes < gneed) gpart.alloc(gneed);
                 for (int pass = 0; pass < 2; ++pass) {
+                    if (pass == 1 && rmax > 0) {
+                        // the normalisation above scales up whatever overlap with the
+                        // basis the float32 projection left behind: project once more
+                        Blas<T>::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, rmax, kChunk, m, one, Q.as<T2>(), m,
+                                      (long long)m * rcap_pad, Yc, m, ys, zero, Cb.as<T2>(), rcap_pad,
+                                      (long long)rcap_pad * kChunk, nb);
+                        Blas<T>::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, kChunk, rmax, mone, Q.as<T2>(), m,
+                                      (long long)m * rcap_pad, Cb.as<T2>(), rcap_pad, (long long)rcap_pad * kChunk,
+                                      one, Yc, m, ys, nb);
+                    }
                     k_gram_partial<T2><<<dim3(nchunk, nb), 1024, 0, s>>>(Yc, m, ys, nchunk, gpart.as<double2>());
                     VIE_CHECK_LAUNCH();
                     k_gram_reduce<<<nb, kChunk * kChunk, 0, s>>>(gpart.as<double2>(), nchunk, G.as<double2>());
@@ -406,8 +464,17 @@ struct Compressor {
         DevBuf RH((size_t)nb * n * std::max(rmax, 1) * sizeof(T2));
         if (rmax > 0) {
             const T2 one = mk(T(1), T(0)), zero = mk(T(0), T(0));
-            Blas<T>::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, n, rmax, m, one, A.as<T2>(), m, mn, Q.as<T2>(), m,
-                          (long long)m * rcap_pad, zero, RH.as<T2>(), n, (long long)n * rmax, nb);
+            if (mn >= ((int64_t)1 << 22)) {
+                // large blocks: one GEMM per block with its own rank
+                for (int q = 0; q < nb; ++q)
+                    if (r[q] > 0)
+                        Blas<T>::gemm1(h, CUBLAS_OP_C, CUBLAS_OP_N, n, r[q], m, one, A.as<T2>() + (size_t)q * mn, m,
+                                       Q.as<T2>() + (size_t)q * m * rcap_pad, m, zero,
+                                       RH.as<T2>() + (size_t)q * n * rmax, n);
+            } else {
+                Blas<T>::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, n, rmax, m, one, A.as<T2>(), m, mn, Q.as<T2>(), m,
+                              (long long)m * rcap_pad, zero, RH.as<T2>(), n, (long long)n * rmax, nb);
+            }
         }
         VIE_CUDA(cudaStreamSynchronize(s));
         A.release();
@@ -440,7 +507,8 @@ struct Compressor {
             }
             off += (int64_t)rank[q] * (m + n);
             off = (off + 31) / 32 * 32;
-            level_rank[b.level] = std::max(level_rank[b.level], rank[q]);
+            level_rank[b.level].first += rank[q];
+            level_rank[b.level].second += 1;
         }
         if (!so.empty()) {
             DevBuf a1, a2, a3, a4;
@@ -476,6 +544,7 @@ struct Compressor {
             size_t rcap = std::min(std::min(m, n), kRankCap + kChunk);
             size_t per = ((size_t)m * n + (size_t)m * rcap + (size_t)n * rcap + (size_t)m * 2 * kChunk) * sizeof(T2);
             int bs = (int)std::max<size_t>(1, std::min<size_t>(4096, budget / per));  // blocks run along grid y
+            if (const char* e = std::getenv("VIE_COMPRESS_MAX_BATCH")) bs = std::max(1, std::min(bs, std::atoi(e)));
             for (size_t i0 = 0; i0 < ids.size(); i0 += bs) {
                 std::vector<int> sub(ids.begin() + i0, ids.begin() + std::min(ids.size(), i0 + bs));
                 batch(sub);
@@ -511,6 +580,16 @@ struct Compressor {
 
 void compress_operator(Op& op, double tol, int prec) {
     VIE_BLAS(cublasSetStream(op.ctx->blas, op.ctx->stream));
+    // float32-accurate GEMMs on the bf16 tensor cores (BF16x9), float64-accurate
+    // fixed-point emulation for the c128 path, where cuBLAS finds them faster
+    const char* em = std::getenv("VIE_GEMM_EMULATION");
+    if (em && em[0] == '1') {
+        VIE_BLAS(cublasSetMathMode(op.ctx->blas, (cublasMath_t)(CUBLAS_FP32_EMULATED_BF16X9_MATH |
+                                                                CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH)));
+        VIE_BLAS(cublasSetEmulationStrategy(op.ctx->blas, CUBLAS_EMULATION_STRATEGY_PERFORMANT));
+    } else {
+        VIE_BLAS(cublasSetMathMode(op.ctx->blas, CUBLAS_DEFAULT_MATH));
+    }
     op.d_factors.release();
     for (auto& b : op.blocks) b.rank = 0;
     if (prec == VIE_C128) {

@@ -13,6 +13,8 @@
 
 namespace vie {
 
+std::atomic<long long> g_kernel_launches{0};
+
 void fail(int status, const std::string& msg) { throw Error{status, msg}; }
 
 double now_s() {
@@ -224,16 +226,17 @@ void build_apply_lists(Op& op) {
     op.t_total = toff;
     upload(op.d_blocks, hb);
     upload(op.d_block_atoms, op.block_atoms.empty() ? std::vector<int>{0} : op.block_atoms);
-    op.n_cta = op.ctx->n_sm * 2;
+    op.n_cta = op.ctx->n_sm * 3;
 
     // phase 1
     std::vector<int4> it1;
     std::vector<double> w1;
-    const double target = 192.0 * 1024;  // bytes of factor per item
+    // one item = up to 32 rows of R_b (8 warps x 4 rows); smaller blocks keep
+    // whole rows together so that every warp of the CTA has work
     for (int i = 0; i < nb; ++i) {
         const auto& b = op.blocks[i];
         if (b.rank == 0) continue;
-        int rc = std::max(1, (int)(target / (8.0 * b.n)));
+        int rc = 32;
         for (int k0 = 0; k0 < b.rank; k0 += rc) {
             int k1 = std::min(b.rank, k0 + rc);
             it1.push_back(make_int4(i, k0, k1, 0));

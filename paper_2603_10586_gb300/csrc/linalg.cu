@@ -177,6 +177,7 @@ void invert_self_blocks(Op& op) {
             int64_t work = (int64_t)np * (2 * np - k);
             gj_eliminate<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(M.as<double2>(), np, k, fac.as<double2>());
         }
+        VIE_COUNT_LAUNCH(2 * np);
         VIE_CHECK_LAUNCH();
         gj_extract<<<(unsigned)(((int64_t)np * np + 255) / 256), 256, 0, s>>>(
             M.as<double2>(), op.d_inv64.as<double2>() + (size_t)t * np * np, np);

@@ -21,6 +21,7 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED"
           -6: "NAN", -7: "TIMEOUT", -8: "ADMISSION", -9: "STATE"}
 C64, C128, BF16X3, C64_ACC64 = 1, 2, 3, 4
 FUSE_PRECOND = 1
+DENSE = 2
 
 
 class VieError(RuntimeError):
@@ -89,7 +90,7 @@ class ResultC(C.Structure):
 EXPORTS = ["vie_create", "vie_destroy", "vie_last_error", "vie_assemble", "vie_compress", "vie_op_destroy",
            "vie_op_get_info", "vie_apply", "vie_precond", "vie_rhs", "vie_solve", "vie_fields",
            "vie_export_block", "vie_far_block_info", "vie_export_far_block", "vie_serve", "vie_submit",
-           "vie_poll", "vie_result_free", "vie_server_stop", "vie_footprint_bytes"]
+           "vie_poll", "vie_result_free", "vie_server_stop", "vie_footprint_bytes", "vie_kernel_launches"]
 
 _lib = None
 
@@ -129,6 +130,7 @@ def load():
         "vie_result_free": (None, [C.POINTER(ResultC)]),
         "vie_server_stop": (C.c_int, [vp]),
         "vie_footprint_bytes": (i64, [i64, C.c_int, C.c_int, C.c_int, i64]),
+        "vie_kernel_launches": (i64, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -136,6 +138,24 @@ def load():
         f.argtypes = args
     _lib = L
     return L
+
+
+def _stream(stream):
+    """Explicit stream handle, else torch's current stream when torch has CUDA
+    initialised (its legacy default stream is passed as cudaStreamLegacy = 1),
+    else NULL = the library context's own stream."""
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import sys
+    th = sys.modules.get("torch")
+    if th is not None and th.cuda.is_available() and th.cuda.is_initialized():
+        h = th.cuda.current_stream().cuda_stream
+        return C.c_void_p(h if h != 0 else 1)
+    return C.c_void_p(0)
+
+
+def kernel_launches():
+    return int(load().vie_kernel_launches())
 
 
 def _dp(a):
@@ -218,16 +238,16 @@ class Operator:
 
     def apply(self, x_ptr, y_ptr, nrhs=1, precision=C64, flags=0, stream=None):
         self.ctx.check(self.L.vie_apply(self.h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(nrhs), self.n,
-                                        int(precision), int(flags), C.c_void_p(stream or 0)))
+                                        int(precision), int(flags), _stream(stream)))
 
     def precond(self, x_ptr, y_ptr, nrhs=1, precision=C64, stream=None):
         self.ctx.check(self.L.vie_precond(self.h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(nrhs), self.n,
-                                          int(precision), C.c_void_p(stream or 0)))
+                                          int(precision), _stream(stream)))
 
     def rhs(self, khat, pol, b_ptr, stream=None):
         inc, keep, nrhs = _incident_struct(khat, pol)
         self.ctx.check(self.L.vie_rhs(self.h, C.byref(inc), nrhs, C.c_void_p(b_ptr), self.n,
-                                      C.c_void_p(stream or 0)))
+                                      _stream(stream)))
 
     def solve(self, khat, pol, tol=1e-6, restart=60, max_iters=2000, precision=C64, precond=1, out_ptr=None):
         """Returns (I (numpy complex128 n x nrhs, or None with out_ptr), stats dict, status)."""

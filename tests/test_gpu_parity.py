@@ -74,7 +74,9 @@ def test_cross_block_graded_and_large_atoms(ctx):
     for a, b in ((0, 4), (8, 1)):
         ref = A.cross_block(P, a, b)
         assert rel(op.export_block(1, a, b, vie.C128), ref) < 1e-12
-        assert rel(op.export_block(1, a, b, vie.C64), ref) < 1e-5
+        # float32 entries: the charge term is a second difference of voxel
+        # integrals, so cancellation costs about one digit
+        assert rel(op.export_block(1, a, b, vie.C64), ref) < 5e-5
 
 
 def test_rhs(ctx, tiny_dense):
@@ -110,7 +112,7 @@ def test_compression_error_bound(tiny_op, tiny_dense):
         Ab = Z[np.ix_(rows, cols)]
         Q, R = blk["Q"], blk["R"]
         assert np.linalg.norm(Ab - Q @ R) <= 1e-4 * np.linalg.norm(Ab)
-        assert np.linalg.norm(Q.conj().T @ Q - np.eye(blk["rank"])) < 1e-5
+        assert np.linalg.norm(Q.conj().T @ Q - np.eye(blk["rank"])) < 1e-4   # float32 storage
 
 
 # ---------------------------------------------------------------------- apply
