@@ -131,9 +131,11 @@ __device__ __forceinline__ double2 green4pi_smooth(double R, double k) {
 
 // --------------------------------------------------------------------------
 // self tables (one atom type, float64, local coordinates)
-// tables layout: plane 0 = U, planes 1 + 4 d + 2 sa + sb = W[d][sa][sb],
-// each nvox x nvox (A * nvox + B); then VS (nvox x nsurf), SV (nsurf x nvox),
-// SS (nsurf x nsurf).
+// tables layout (test element index fastest, so that the entry kernel's
+// neighbouring threads, which differ in the test face, read neighbouring
+// words): plane 0 = U, planes 1 + 4 d + 2 sa + sb = W[d][sa][sb], each
+// nvox x nvox at B * nvox + A; then VS at t * nvox + A, SV at B * nsurf + s,
+// SS at t * nsurf + s (A, s: test voxel / sheet; B, t: source voxel / sheet).
 // --------------------------------------------------------------------------
 __device__ void vox_box(const DevMesh& m, int A, double h, double lo[3], double hi[3]) {
     for (int d = 0; d < 3; ++d) {
@@ -236,10 +238,11 @@ __global__ void self_vv_kernel(DevMesh m, double h, double k, double2* tab) {
             }
         }
     }
-    tab[t] = U;
+    const int tt = B * m.nvox + A;
+    tab[tt] = U;
     for (int d = 0; d < 3; ++d)
         for (int sa = 0; sa < 2; ++sa)
-            for (int sb = 0; sb < 2; ++sb) tab[(size_t)(1 + 4 * d + 2 * sa + sb) * nv2 + t] = W[d][sa][sb];
+            for (int sb = 0; sb < 2; ++sb) tab[(size_t)(1 + 4 * d + 2 * sa + sb) * nv2 + tt] = W[d][sa][sb];
 }
 
 // uniform voxel/sheet combinations of one atom with itself
@@ -337,9 +340,9 @@ __global__ void self_surf_kernel(DevMesh m, double h, double k, double2* tab) {
     }
     size_t nv2 = (size_t)m.nvox * m.nvox;
     size_t base = 13 * nv2;
-    if (mode == 0) tab[base + (size_t)ia * m.nsurf + ib] = acc;
-    else if (mode == 1) tab[base + (size_t)m.nvox * m.nsurf + (size_t)ia * m.nvox + ib] = acc;
-    else tab[base + 2 * (size_t)m.nvox * m.nsurf + (size_t)ia * m.nsurf + ib] = acc;
+    if (mode == 0) tab[base + (size_t)ib * m.nvox + ia] = acc;
+    else if (mode == 1) tab[base + (size_t)m.nvox * m.nsurf + (size_t)ib * m.nsurf + ia] = acc;
+    else tab[base + 2 * (size_t)m.nvox * m.nsurf + (size_t)ib * m.nsurf + ia] = acc;
 }
 
 // --------------------------------------------------------------------------
@@ -379,7 +382,7 @@ __global__ void cross_vv_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, T t
     const int nv2 = m.nvox * m.nvox;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nv2) return;
-    const int A = t / m.nvox, B = t % m.nvox;
+    const int B = t / m.nvox, A = t % m.nvox;  // table index t = B * nvox + A
     const PairJob jb = jobs[job];
     double cA[3], cB[3], hA, hB;
     vox_centre(m, geo, jb.a, A, cA, hA);
@@ -445,6 +448,48 @@ __global__ void cross_vv_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, T t
             }
 }
 
+// uniform voxel/sheet integrals between two atoms, 2 points per axis:
+// mode 0: VS (test voxel, source sheet), 1: SV (test sheet, source voxel), 2: SS
+template <class T, int NA, int NB>
+__device__ __forceinline__ typename C2<T>::t surf_pair(const T D[3], const T (*pa)[3], const T (*pb)[3],
+                                                       T two_over_lambda) {
+    using T2 = typename C2<T>::t;
+    T2 acc = mk(T(0), T(0));
+#pragma unroll
+    for (int p = 0; p < NA; ++p) {
+        T ra[3] = {D[0] + pa[p][0], D[1] + pa[p][1], D[2] + pa[p][2]};
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            T dx = ra[0] - pb[q][0], dy = ra[1] - pb[q][1], dz = ra[2] - pb[q][2];
+            T r2 = dx * dx + dy * dy + dz * dz;
+            T inv = rsqrt_t(r2);
+            T sn, cs;
+            sincospi_t(r2 * inv * two_over_lambda, &sn, &cs);
+            acc += mk(cs * inv, -sn * inv);
+        }
+    }
+    return acc;
+}
+
+// node offsets of the 2-point rule on a voxel (8) or on a sheet normal to `ax` (4)
+template <class T>
+__device__ __forceinline__ void rule_points(int ax, T o, T (*pts)[3]) {
+    if (ax < 0) {
+        for (int p = 0; p < 8; ++p) {
+            pts[p][0] = (p & 4) ? o : -o;
+            pts[p][1] = (p & 2) ? o : -o;
+            pts[p][2] = (p & 1) ? o : -o;
+        }
+    } else {
+        int a = ax == 0 ? 1 : 0, b = ax == 2 ? 1 : 2;
+        for (int p = 0; p < 4; ++p) {
+            pts[p][ax] = T(0);
+            pts[p][a] = (p & 2) ? o : -o;
+            pts[p][b] = (p & 1) ? o : -o;
+        }
+    }
+}
+
 template <class T>
 __global__ void cross_surf_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, T two_over_lambda,
                                   typename C2<T>::t* tab, size_t job_stride) {
@@ -452,10 +497,10 @@ __global__ void cross_surf_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, T
     const int job = blockIdx.z;
     const int mode = blockIdx.y;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nA = mode == 0 ? m.nvox : m.nsurf;
-    const int nB = mode == 1 ? m.nvox : m.nsurf;
+    const int nA = mode == 0 ? m.nvox : m.nsurf;  // test elements (fastest)
+    const int nB = mode == 1 ? m.nvox : m.nsurf;  // source elements
     if (t >= nA * nB) return;
-    const int ia = t / nB, ib = t % nB;
+    const int ib = t / nA, ia = t % nA;
     const PairJob jb = jobs[job];
     double cA[3], cB[3], hA, hB;
     int axA = -1, axB = -1;
@@ -463,44 +508,22 @@ __global__ void cross_surf_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, T
     else axA = surf_centre(m, geo, jb.a, ia, cA, hA);
     if (mode == 1) vox_centre(m, geo, jb.b, ib, cB, hB);
     else axB = surf_centre(m, geo, jb.b, ib, cB, hB);
-    T D[3] = {T(cA[0] - cB[0]), T(cA[1] - cB[1]), T(cA[2] - cB[2])};
-    const T oA = T(hA * kGl2Off), oB = T(hB * kGl2Off);
-    const int na = axA < 0 ? 8 : 4, nb = axB < 0 ? 8 : 4;
-    T2 acc = mk(T(0), T(0));
-    for (int p = 0; p < na; ++p) {
-        T pa[3];
-        int bit = 0;
-        for (int d = 0; d < 3; ++d) {
-            if (d == axA) { pa[d] = T(0); continue; }
-            int sgn = (p >> (na == 8 ? 2 - d : bit)) & 1;
-            if (na == 4) ++bit;
-            pa[d] = sgn ? oA : -oA;
-        }
-        for (int q = 0; q < nb; ++q) {
-            T pb[3];
-            int bitb = 0;
-            for (int d = 0; d < 3; ++d) {
-                if (d == axB) { pb[d] = T(0); continue; }
-                int sgn = (q >> (nb == 8 ? 2 - d : bitb)) & 1;
-                if (nb == 4) ++bitb;
-                pb[d] = sgn ? oB : -oB;
-            }
-            T dx = D[0] + pa[0] - pb[0], dy = D[1] + pa[1] - pb[1], dz = D[2] + pa[2] - pb[2];
-            T r2 = dx * dx + dy * dy + dz * dz;
-            T inv = rsqrt_t(r2);
-            T s, c;
-            sincospi_t(r2 * inv * two_over_lambda, &s, &c);
-            acc += mk(c * inv, -s * inv);
-        }
-    }
-    double wA = axA < 0 ? hA * hA * hA / 8.0 : hA * hA / 4.0;
-    double wB = axB < 0 ? hB * hB * hB / 8.0 : hB * hB / 4.0;
+    const T D[3] = {T(cA[0] - cB[0]), T(cA[1] - cB[1]), T(cA[2] - cB[2])};
+    T pa[8][3], pb[8][3];
+    rule_points<T>(axA, T(hA * kGl2Off), pa);
+    rule_points<T>(axB, T(hB * kGl2Off), pb);
+    T2 acc;
+    if (mode == 0) acc = surf_pair<T, 8, 4>(D, pa, pb, two_over_lambda);
+    else if (mode == 1) acc = surf_pair<T, 4, 8>(D, pa, pb, two_over_lambda);
+    else acc = surf_pair<T, 4, 4>(D, pa, pb, two_over_lambda);
+    const double wA = axA < 0 ? hA * hA * hA / 8.0 : hA * hA / 4.0;
+    const double wB = axB < 0 ? hB * hB * hB / 8.0 : hB * hB / 4.0;
     acc = T(wA * wB * kInv4Pi) * acc;
     const size_t nv2 = (size_t)m.nvox * m.nvox;
     T2* out = tab + (size_t)job * job_stride + 13 * nv2;
-    if (mode == 0) out[(size_t)ia * m.nsurf + ib] = acc;
-    else if (mode == 1) out[(size_t)m.nvox * m.nsurf + (size_t)ia * m.nvox + ib] = acc;
-    else out[2 * (size_t)m.nvox * m.nsurf + (size_t)ia * m.nsurf + ib] = acc;
+    if (mode == 0) out[(size_t)ib * m.nvox + ia] = acc;
+    else if (mode == 1) out[(size_t)m.nvox * m.nsurf + (size_t)ib * m.nsurf + ia] = acc;
+    else out[2 * (size_t)m.nvox * m.nsurf + (size_t)ib * m.nsurf + ia] = acc;
 }
 
 // --------------------------------------------------------------------------
@@ -529,7 +552,7 @@ __global__ void entries_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, doub
             if (vi[sa] < 0) continue;
             for (int sb = 0; sb < 2; ++sb) {
                 if (vj[sb] < 0) continue;
-                L += tb[(size_t)(1 + 4 * fi.x + 2 * sa + sb) * nv2 + (size_t)vi[sa] * m.nvox + vj[sb]];
+                L += tb[(size_t)(1 + 4 * fi.x + 2 * sa + sb) * nv2 + (size_t)vj[sb] * m.nvox + vi[sa]];
             }
         }
         L = T(1.0 / (hA * hA * hB * hB)) * L;
@@ -547,17 +570,17 @@ __global__ void entries_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, doub
         for (int sb = 0; sb < 2; ++sb) {
             if (vj[sb] < 0) continue;
             T cb = sb ? -cvB : cvB;
-            D += (ca * cb) * tb[(size_t)vi[sa] * m.nvox + vj[sb]];
+            D += (ca * cb) * tb[(size_t)vj[sb] * m.nvox + vi[sa]];
         }
-        if (sj >= 0) D += (ca * csB) * VS[(size_t)vi[sa] * m.nsurf + sj];
+        if (sj >= 0) D += (ca * csB) * VS[(size_t)sj * m.nvox + vi[sa]];
     }
     if (si >= 0) {
         for (int sb = 0; sb < 2; ++sb) {
             if (vj[sb] < 0) continue;
             T cb = sb ? -cvB : cvB;
-            D += (csA * cb) * SV[(size_t)si * m.nvox + vj[sb]];
+            D += (csA * cb) * SV[(size_t)vj[sb] * m.nsurf + si];
         }
-        if (sj >= 0) D += (csA * csB) * SS[(size_t)si * m.nsurf + sj];
+        if (sj >= 0) D += (csA * csB) * SS[(size_t)sj * m.nsurf + si];
     }
     T2 z = D - T(k2) * L;
     if (SELF && fi.x == fj.x) {

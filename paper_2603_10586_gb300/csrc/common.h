@@ -113,6 +113,10 @@ struct FarBlock {
     int64_t q_off = 0;         // element offset of Q (m x r col-major)
     int64_t rh_off = 0;        // element offset of R^H (n x r col-major) = conj(R) row-major
     int64_t t_off_vec = 0;     // offset of this block's R x in the t buffer (per RHS column)
+    int dist = 0;              // Chebyshev distance of the two boxes at this level
+    int dmin = 0;              // the smaller of the two box-offset components
+    int mirror = -1;           // index of the block (source box, target box)
+    bool derived = false;      // factors taken from the mirror's (transposed)
 };
 
 struct Ctx;

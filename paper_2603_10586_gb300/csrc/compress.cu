@@ -15,6 +15,12 @@
 // 32-column estimator used here (a chi-square tail below 1/9 of its mean).
 // Plain GEMMs go to cuBLAS; the Gram, Cholesky, triangular product, norms,
 // random numbers and the column compaction are this file's kernels.
+//
+// Reciprocity: between two different atoms the quadrature rule is symmetric,
+// so the block (J, I) is the transpose of the block (I, J).  Only one block of
+// each mirror pair is formed and compressed; its mirror stores the transposed
+// factors, Q' = R^T (n x r) and R' = Q^T (r x m), whose product carries exactly
+// the same error.  (Q' is then not orthonormal; the apply does not need it.)
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -82,28 +88,31 @@ __global__ void k_reduce_rows(const double* part, int nchunk, int nb, double* ou
     out[b] = s;
 }
 
-// partial Gram matrices G = Y^H Y (kChunk x kChunk, float64) over row chunks
-template <class T2>
+// partial Gram matrices G = Y^H Y (kChunk x kChunk) over row chunks,
+// accumulated in ACC (double2 for a general block; float2 is enough once the
+// block is close to orthonormal), stored as double2
+template <class T2, class ACC>
 __global__ void k_gram_partial(const T2* Y, int m, int64_t stride, int nchunk, double2* part) {
     const int b = blockIdx.y, c = blockIdx.x;
     const int per = (m + nchunk - 1) / nchunk;
     const int lo = c * per, hi = min(m, lo + per);
     const T2* y = Y + b * stride;
-    __shared__ double2 rows[64][kChunk + 1];
+    using R = decltype(ACC().x);
+    __shared__ ACC rows[64][kChunk + 1];
     const int i = threadIdx.x % kChunk, j = threadIdx.x / kChunk;  // 1024 threads
-    double2 acc = make_double2(0, 0);
+    ACC acc = mk(R(0), R(0));
     for (int r0 = lo; r0 < hi; r0 += 64) {
         for (int e = threadIdx.x; e < 64 * kChunk; e += blockDim.x) {
             int rr = e % 64, cc = e / 64;
             int r = r0 + rr;
-            rows[rr][cc] = r < hi ? cvt<double2>(y[r + (int64_t)cc * m]) : make_double2(0, 0);
+            rows[rr][cc] = r < hi ? cvt<ACC>(y[r + (int64_t)cc * m]) : mk(R(0), R(0));
         }
         __syncthreads();
         int nr = min(64, hi - r0);
         for (int rr = 0; rr < nr; ++rr) cfmac(acc, rows[rr][i], rows[rr][j]);
         __syncthreads();
     }
-    part[((size_t)b * nchunk + c) * kChunk * kChunk + i + j * kChunk] = acc;
+    part[((size_t)b * nchunk + c) * kChunk * kChunk + i + j * kChunk] = cvt<double2>(acc);
 }
 __global__ void k_gram_reduce(const double2* part, int nchunk, double2* G) {
     const int b = blockIdx.x;
@@ -205,6 +214,16 @@ __global__ void k_trmul(const T2* Y, int m, int64_t ystride, const T2* Minv, con
     }
 }
 
+// dst = conj(src)
+template <class T2>
+__global__ void k_conj_copy(const T2* src, T2* dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T2 v = src[i];
+        v.y = -v.y;
+        dst[i] = v;
+    }
+}
+
 // copy live columns into the factor store: dst[k] <- src[:, col[k]]
 template <class T2>
 __global__ void k_gather_cols(const T2* src, int64_t rows, const long long* src_off, const long long* dst_off,
@@ -278,7 +297,7 @@ struct Compressor {
     cublasHandle_t h;
     std::vector<DevBuf> stores;          // staging factor stores (one per batch)
     std::vector<std::pair<int, int64_t>> where;  // per block: (store, offset of Q); R^H follows Q
-    std::map<int, std::pair<double, int>> level_rank;  // per level: (sum of ranks, blocks)
+    std::map<std::tuple<int, int, int>, int> class_rank;  // (level, offsets) -> largest rank seen
     uint64_t seed = 0x5eed0001ull;
 
     Compressor(Op& o, double t) : op(o), tol(t), s(o.ctx->stream), h(o.ctx->blas) {}
@@ -293,8 +312,16 @@ struct Compressor {
         VIE_CHECK_LAUNCH();
     }
 
+    double tim[5] = {0, 0, 0, 0, 0};  // form, sketch loop, R, compaction, total
+    double mark() {
+        if (!op.ctx->verbose) return 0.0;
+        VIE_CUDA(cudaStreamSynchronize(s));
+        return now_s();
+    }
+
     // compress one batch of equally sized blocks
-    void batch(const std::vector<int>& ids) {
+    void batch(const std::vector<int>& ids, int s0_hint) {
+        double t0 = mark();
         const int nb = (int)ids.size();
         const FarBlock& b0 = op.blocks[ids[0]];
         const int m = b0.m, n = b0.n, np = op.np;
@@ -323,6 +350,8 @@ struct Compressor {
             upload(dl, ld);
             assemble_pairs<T>(op, dj.as<PairJob>(), (int)jobs.size(), dd.as<void* const>(), dl.as<int64_t>(), s);
         }
+        double t1 = mark();
+        tim[0] += t1 - t0;
         DevBuf part, normA((size_t)nb * sizeof(double)), est((size_t)nb * sizeof(double));
         sumsq(A.as<T2>(), mn, mn, nb, normA.as<double>(), part);
         std::vector<double> hnorm(nb);
@@ -337,13 +366,9 @@ struct Compressor {
         DevBuf gpart, G((size_t)nb * kChunk * kChunk * sizeof(double2)), Minv((size_t)nb * kChunk * kChunk * sizeof(T2));
         DevBuf d_active(nb * sizeof(int)), d_rbase(nb * sizeof(int));
         std::vector<int> r(nb, 0), conv(nb, 0);
-        // first sketch: the mean rank already seen at this level (one pass over A),
-        // then 32-column passes for the blocks that still need more
-        int s0 = kChunk;
-        auto it = level_rank.find(b0.level);
-        if (it != level_rank.end() && it->second.second > 0)
-            s0 = std::max(kChunk, ((int)(it->second.first / it->second.second + kChunk - 1) / kChunk) * kChunk);
-        s0 = std::min(s0, rcap_pad);
+        // first sketch: the rank prior of this block class (one pass over A), then
+        // 32-column passes for the blocks that still need more
+        int s0 = std::min(std::max(kChunk, s0_hint), rcap_pad);
         int step = 0;
         const double thr = (tol / 3.0) * (tol / 3.0);
         VIE_CUDA(cudaStreamSynchronize(s));
@@ -434,7 +459,12 @@ struct Compressor {
                                       (long long)m * rcap_pad, Cb.as<T2>(), rcap_pad, (long long)rcap_pad * kChunk,
                                       one, Yc, m, ys, nb);
                     }
-                    k_gram_partial<T2><<<dim3(nchunk, nb), 1024, 0, s>>>(Yc, m, ys, nchunk, gpart.as<double2>());
+                    if (pass == 0)
+                        k_gram_partial<T2, double2><<<dim3(nchunk, nb), 1024, 0, s>>>(Yc, m, ys, nchunk,
+                                                                                    gpart.as<double2>());
+                    else
+                        k_gram_partial<T2, T2><<<dim3(nchunk, nb), 1024, 0, s>>>(Yc, m, ys, nchunk,
+                                                                               gpart.as<double2>());
                     VIE_CHECK_LAUNCH();
                     k_gram_reduce<<<nb, kChunk * kChunk, 0, s>>>(gpart.as<double2>(), nchunk, G.as<double2>());
                     VIE_CHECK_LAUNCH();
@@ -457,6 +487,8 @@ struct Compressor {
             }
         }
 
+        double t2 = mark();
+        tim[1] += t2 - t1;
         // 3. R^H = A^H Q (n x rmax per block)
         int rmax = *std::max_element(r.begin(), r.end());
         std::vector<unsigned char> halive((size_t)nb * rcap_pad);
@@ -477,6 +509,8 @@ struct Compressor {
             }
         }
         VIE_CUDA(cudaStreamSynchronize(s));
+        double t3 = mark();
+        tim[2] += t3 - t2;
         A.release();
 
         // 4. compact the live columns into a staging store
@@ -507,8 +541,8 @@ struct Compressor {
             }
             off += (int64_t)rank[q] * (m + n);
             off = (off + 31) / 32 * 32;
-            level_rank[b.level].first += rank[q];
-            level_rank[b.level].second += 1;
+            int& cr = class_rank[{b.level, b.dist, b.dmin}];
+            cr = std::max(cr, rank[q]);
         }
         if (!so.empty()) {
             DevBuf a1, a2, a3, a4;
@@ -527,30 +561,56 @@ struct Compressor {
             VIE_CUDA(cudaStreamSynchronize(s));
         }
         stores.push_back(std::move(store));
+        double t4 = mark();
+        tim[3] += t4 - t3;
+        if (op.ctx->verbose) {
+            int rsum = 0, rmx = 0;
+            for (int q = 0; q < nb; ++q) { rsum += rank[q]; rmx = std::max(rmx, rank[q]); }
+            fprintf(stderr, "[vie]   level %d batch %d x (%d x %d): s0 %d steps %d mean rank %.1f max %d | form %.3f "
+                    "sketch %.3f R %.3f pack %.3f s\n", b0.level, nb, m, n, s0, step, (double)rsum / nb, rmx,
+                    t1 - t0, t2 - t1, t3 - t2, t4 - t3);
+        }
     }
 
     void run() {
         where.assign(op.blocks.size(), {-1, 0});
-        // group blocks by (level, m, n), coarse levels first
-        std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+        // group blocks by (level, m, n, box distance), coarse levels first; blocks
+        // of one class have similar ranks: one pilot block learns the rank, the
+        // rest start from a sketch of that size plus a margin
+        std::map<std::tuple<int, int, int, int, int>, std::vector<int>> groups;
         for (size_t i = 0; i < op.blocks.size(); ++i) {
-            const auto& b = op.blocks[i];
-            groups[{b.level, b.m, b.n}].push_back((int)i);
+            auto& b = op.blocks[i];
+            b.derived = b.mirror >= 0 && b.mirror < (int)i;
+            if (b.derived) continue;
+            groups[{b.level, b.m, b.n, b.dist, b.dmin}].push_back((int)i);
         }
         const size_t budget = std::max<size_t>((size_t)2 << 30, std::min<size_t>(op.ctx->budget / 3, (size_t)48 << 30));
         for (auto& g : groups) {
-            const auto& ids = g.second;
-            int m = std::get<1>(g.first), n = std::get<2>(g.first);
+            std::vector<int> ids = g.second;
+            int lev = std::get<0>(g.first), m = std::get<1>(g.first), n = std::get<2>(g.first);
+            std::tuple<int, int, int> cls{lev, std::get<3>(g.first), std::get<4>(g.first)};
             size_t rcap = std::min(std::min(m, n), kRankCap + kChunk);
             size_t per = ((size_t)m * n + (size_t)m * rcap + (size_t)n * rcap + (size_t)m * 2 * kChunk) * sizeof(T2);
             int bs = (int)std::max<size_t>(1, std::min<size_t>(4096, budget / per));  // blocks run along grid y
             if (const char* e = std::getenv("VIE_COMPRESS_MAX_BATCH")) bs = std::max(1, std::min(bs, std::atoi(e)));
-            for (size_t i0 = 0; i0 < ids.size(); i0 += bs) {
+            size_t i0 = 0;
+            if (!class_rank.count(cls) && ids.size() > 1 && (size_t)m * n >= ((size_t)1 << 20)) {
+                batch({ids[0]}, kChunk);  // pilot
+                i0 = 1;
+            }
+            for (; i0 < ids.size(); i0 += bs) {
                 std::vector<int> sub(ids.begin() + i0, ids.begin() + std::min(ids.size(), i0 + bs));
-                batch(sub);
+                auto it = class_rank.find(cls);
+                int hint = it == class_rank.end() ? kChunk : ((it->second + kChunk + kChunk - 1) / kChunk) * kChunk;
+                batch(sub, hint);
             }
         }
-        // consolidate into one factor store
+        // consolidate into one factor store (mirrors take their partner's rank)
+        op.factor_entries = 0;
+        for (size_t i = 0; i < op.blocks.size(); ++i) {
+            auto& b = op.blocks[i];
+            if (b.derived) b.rank = op.blocks[b.mirror].rank;
+        }
         int64_t total = 0;
         std::vector<int64_t> qoff(op.blocks.size());
         for (size_t i = 0; i < op.blocks.size(); ++i) {
@@ -560,16 +620,27 @@ struct Compressor {
             total = (total + 31) / 32 * 32;
         }
         op.d_factors.alloc((size_t)std::max<int64_t>(total, 32) * sizeof(T2));
-        op.factor_entries = 0;
         for (size_t i = 0; i < op.blocks.size(); ++i) {
             auto& b = op.blocks[i];
             b.q_off = qoff[i];
             b.rh_off = qoff[i] + (int64_t)b.rank * b.m;
             op.factor_entries += (int64_t)b.rank * (b.m + b.n);
             if (b.rank == 0) continue;
-            const T2* src = stores[where[i].first].template as<T2>() + where[i].second;
-            VIE_CUDA(cudaMemcpyAsync(op.d_factors.as<T2>() + b.q_off, src,
-                                     (size_t)b.rank * (b.m + b.n) * sizeof(T2), cudaMemcpyDeviceToDevice, s));
+            if (!b.derived) {
+                const T2* src = stores[where[i].first].template as<T2>() + where[i].second;
+                VIE_CUDA(cudaMemcpyAsync(op.d_factors.as<T2>() + b.q_off, src,
+                                         (size_t)b.rank * (b.m + b.n) * sizeof(T2), cudaMemcpyDeviceToDevice, s));
+            } else {
+                // mirror of block p (A' = A_p^T): Q' = conj(R_p^H), R'^H = conj(Q_p)
+                const FarBlock& p = op.blocks[b.mirror];
+                const T2* src = stores[where[b.mirror].first].template as<T2>() + where[b.mirror].second;
+                const int64_t nq = (int64_t)p.rank * p.m, nr = (int64_t)p.rank * p.n;
+                k_conj_copy<T2><<<(unsigned)std::min<int64_t>(4096, (nr + 255) / 256), 256, 0, s>>>(
+                    src + nq, op.d_factors.as<T2>() + b.q_off, nr);
+                k_conj_copy<T2><<<(unsigned)std::min<int64_t>(4096, (nq + 255) / 256), 256, 0, s>>>(
+                    src, op.d_factors.as<T2>() + b.rh_off, nq);
+                VIE_CHECK_LAUNCH();
+            }
         }
         VIE_CUDA(cudaStreamSynchronize(s));
         stores.clear();
@@ -582,8 +653,9 @@ void compress_operator(Op& op, double tol, int prec) {
     VIE_BLAS(cublasSetStream(op.ctx->blas, op.ctx->stream));
     // float32-accurate GEMMs on the bf16 tensor cores (BF16x9), float64-accurate
     // fixed-point emulation for the c128 path, where cuBLAS finds them faster
+    // (VIE_GEMM_EMULATION=0 keeps plain float32/float64 arithmetic)
     const char* em = std::getenv("VIE_GEMM_EMULATION");
-    if (em && em[0] == '1') {
+    if (!(em && em[0] == '0')) {
         VIE_BLAS(cublasSetMathMode(op.ctx->blas, (cublasMath_t)(CUBLAS_FP32_EMULATED_BF16X9_MATH |
                                                                 CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH)));
         VIE_BLAS(cublasSetEmulationStrategy(op.ctx->blas, CUBLAS_EMULATION_STRATEGY_PERFORMANT));

@@ -156,9 +156,23 @@ void build_tree(Op& op) {
                 op.block_atoms.insert(op.block_atoms.end(), sa.begin(), sa.end());
                 b.m = b.nt * op.np;
                 b.n = b.ns * op.np;
+                b.dist = (int)dist;
+                b.dmin = (int)std::min(std::llabs(key.first - ty), std::llabs(key.second - tx));
                 op.blocks.push_back(b);
             }
         }
+    }
+    // pair every block with its mirror (the far relation is symmetric)
+    std::map<std::tuple<int, int, int>, int> idx;
+    for (size_t i = 0; i < op.blocks.size(); ++i) {
+        const auto& b = op.blocks[i];
+        idx[{b.level, op.block_atoms[b.t_off], op.block_atoms[b.s_off]}] = (int)i;
+    }
+    for (size_t i = 0; i < op.blocks.size(); ++i) {
+        auto& b = op.blocks[i];
+        auto it = idx.find({b.level, op.block_atoms[b.s_off], op.block_atoms[b.t_off]});
+        if (it == idx.end()) fail(VIE_ERR_STATE, "far block without a mirror");
+        b.mirror = it->second;
     }
 }
 

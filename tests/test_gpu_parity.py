@@ -103,6 +103,28 @@ def test_far_block_lists_match_oracle(ctx, ns):
 
 
 # ---------------------------------------------------------------- compression
+def mirrors(blocks):
+    """index of the block (source box, target box) for every block"""
+    key = {(b["level"], int(b["tatoms"][0]), int(b["satoms"][0])): i for i, b in enumerate(blocks)}
+    return [key[(b["level"], int(b["satoms"][0]), int(b["tatoms"][0]))] for b in blocks]
+
+
+def check_factors(blocks, ortho_tol):
+    """Of each mirror pair the first block is compressed (orthonormal Q); the
+    second holds the transposed factors (reciprocity of the rule between atoms)."""
+    mir = mirrors(blocks)
+    for i, blk in enumerate(blocks):
+        j = mir[i]
+        assert j != i
+        if i < j:
+            Q = blk["Q"]
+            assert np.linalg.norm(Q.conj().T @ Q - np.eye(blk["rank"])) < ortho_tol
+        else:
+            p = blocks[j]
+            assert blk["rank"] == p["rank"]
+            assert np.array_equal(blk["Q"], p["R"].T) and np.array_equal(blk["R"], p["Q"].T)
+
+
 def test_compression_error_bound(tiny_op, tiny_dense):
     P, Z, _, _, _ = tiny_dense
     blocks = tiny_op.far_blocks()
@@ -110,9 +132,8 @@ def test_compression_error_bound(tiny_op, tiny_dense):
         rows = C.atom_rows(P, blk["tatoms"])
         cols = C.atom_rows(P, blk["satoms"])
         Ab = Z[np.ix_(rows, cols)]
-        Q, R = blk["Q"], blk["R"]
-        assert np.linalg.norm(Ab - Q @ R) <= 1e-4 * np.linalg.norm(Ab)
-        assert np.linalg.norm(Q.conj().T @ Q - np.eye(blk["rank"])) < 1e-4   # float32 storage
+        assert np.linalg.norm(Ab - blk["Q"] @ blk["R"]) <= 1e-4 * np.linalg.norm(Ab)
+    check_factors(blocks, 1e-4)   # float32 storage
 
 
 # ---------------------------------------------------------------------- apply
@@ -168,12 +189,13 @@ def test_c128_factors_apply(ctx, tiny_dense):
     yd = th.zeros_like(xd)
     op.apply(xd.data_ptr(), yd.data_ptr(), 1, vie.C128, 0)
     assert rel(yd.cpu().numpy(), orc.apply(x)) < 1e-12
-    for blk in op.far_blocks():
+    blocks = op.far_blocks()
+    for blk in blocks:
         rows = C.atom_rows(P, blk["tatoms"])
         cols = C.atom_rows(P, blk["satoms"])
         Ab = Z[np.ix_(rows, cols)]
         assert np.linalg.norm(Ab - blk["Q"] @ blk["R"]) <= 1e-4 * np.linalg.norm(Ab)
-        assert np.linalg.norm(blk["Q"].conj().T @ blk["Q"] - np.eye(blk["rank"])) < 1e-12
+    check_factors(blocks, 1e-12)
 
 
 # ---------------------------------------------------------------------- solve

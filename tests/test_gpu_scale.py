@@ -38,11 +38,13 @@ def test_multibatch_compression_matches_oracle_bound(ctx, monkeypatch):
     op = vie.Operator(ctx, g)
     op.compress(1e-4, vie.C64)
     blocks = op.far_blocks(with_factors=False)
+    key = {(b["level"], int(b["tatoms"][0]), int(b["satoms"][0])): i for i, b in enumerate(blocks)}
     sample = list(range(0, len(blocks), 37))
-    for blk in op.far_blocks(indices=sample):
+    for i, blk in zip(sample, op.far_blocks(indices=sample)):
         Ab = np.block([[A.cross_block(P, int(a), int(b)) for b in blk["satoms"]] for a in blk["tatoms"]])
         assert np.linalg.norm(Ab - blk["Q"] @ blk["R"]) <= 1e-4 * np.linalg.norm(Ab)
-        assert np.linalg.norm(blk["Q"].conj().T @ blk["Q"] - np.eye(blk["rank"])) < 1e-4
+        if i < key[(blk["level"], int(blk["satoms"][0]), int(blk["tatoms"][0]))]:
+            assert np.linalg.norm(blk["Q"].conj().T @ blk["Q"] - np.eye(blk["rank"])) < 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -85,8 +87,11 @@ def test_scale_sampled_blocks_error_bound(scale_op):
             R = torch.from_numpy(b["R"]).cuda()
             err = (torch.linalg.norm(Ab - Q @ R) / torch.linalg.norm(Ab)).item()
             assert err <= 1.05e-4, (lev, i, err)   # entries in float32 (relative 1e-6)
-            eye = torch.eye(b["rank"], dtype=Q.dtype, device="cuda")
-            assert torch.linalg.norm(Q.conj().T @ Q - eye).item() < 1e-4
+            mate = [j for j, c in enumerate(blocks) if c["level"] == lev and
+                    list(c["tatoms"]) == list(b["satoms"]) and list(c["satoms"]) == list(b["tatoms"])][0]
+            if i < mate:   # compressed block of its mirror pair: orthonormal Q
+                eye = torch.eye(b["rank"], dtype=Q.dtype, device="cuda")
+                assert torch.linalg.norm(Q.conj().T @ Q - eye).item() < 1e-4
 
 
 def test_scale_apply_parity_sampled_atoms(scale_op):
