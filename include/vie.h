@@ -176,6 +176,32 @@ int vie_op_get_info(const vie_op* op, vie_op_info* info);
 int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int precision,
               int flags, vie_stream stream);
 
+/* vie_apply_noalloc: y = Zs x exactly as vie_apply(op, x, y, nrhs, ld, VIE_C64, 0,
+ * stream) computes it, but without allocating any device memory.  The paper
+ * has no counterpart: it is an interface for callers that cannot call
+ * cudaMalloc between set-up and use, for instance code whose device memory is
+ * all handed to its own pool allocator (a new cudaMalloc could fail or
+ * fragment that pool), or loops in which the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree is not acceptable.  vie_apply may
+ * allocate its scratch on first use; this entry point never does.
+ *  - Scratch: a file-scope device array of VIE_NOALLOC_SCRATCH_ELEMS
+ *    complex float32 elements (32 MiB), held by every GPU that loads the
+ *    library until the process exits.  A call needs (sum of the far-block
+ *    ranks) x nrhs elements; larger requests fail with VIE_ERR_INVALID_ARG
+ *    before anything is launched.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array and overwrites it; nothing
+ *    in it has to start at zero.  Calls that overlap on the GPU (different
+ *    streams, or different operators on one device) race on the array: order
+ *    them on one stream or synchronise between them.
+ *  - x, y: device pointers, c64, n x nrhs, ld = n, not overlapping; the
+ *    operator must hold VIE_C64 factors.  Asynchronous on `stream` (NULL =
+ *    the context's stream). */
+#define VIE_NOALLOC_SCRATCH_ELEMS (1LL << 22)
+int vie_apply_noalloc(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, vie_stream stream);
+
 /* vie_precond (Sec. 4, eq. diagprecond): y = Z_D^-1 x atom by atom, with the
  * inverse of the atom's type.  Same pointer conventions as vie_apply;
  * precision VIE_C64 or VIE_C128. */

@@ -333,6 +333,18 @@ int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int prec
     });
 }
 
+int vie_apply_noalloc(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, vie_stream stream) {
+    if (!op) return VIE_ERR_INVALID_ARG;
+    return guarded(ctx_of(op), [&] {
+        Op& o = op->o;
+        set_device(*o.ctx);
+        if (!x || !y || nrhs < 1 || ld != o.n()) fail(VIE_ERR_INVALID_ARG, "vie_apply_noalloc: bad vectors (ld must be n)");
+        if (x == y) fail(VIE_ERR_INVALID_ARG, "vie_apply_noalloc: x and y must not overlap");
+        if (o.fprec == 0) fail(VIE_ERR_STATE, "operator is not compressed");
+        apply_static(o, (const float2*)x, (float2*)y, nrhs, stream ? (cudaStream_t)stream : o.ctx->stream);
+    });
+}
+
 int vie_precond(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int precision, vie_stream stream) {
     if (!op) return VIE_ERR_INVALID_ARG;
     return guarded(ctx_of(op), [&] {

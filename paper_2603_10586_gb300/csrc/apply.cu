@@ -11,6 +11,8 @@
 // column-major, i.e. conj(R_b) row-major), so both phases stream their
 // factor with unit stride; complex values are interleaved and pairs of
 // complex float32 move as one 16-byte load.
+#include <mutex>
+
 #include "common.h"
 #include "cplx.cuh"
 
@@ -208,5 +210,62 @@ void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, c
 template void apply_far<float2, float2>(Op&, const float2*, int64_t, float2*, int64_t, int, cudaStream_t);
 template void apply_far<float2, double2>(Op&, const double2*, int64_t, double2*, int64_t, int, cudaStream_t);
 template void apply_far<double2, double2>(Op&, const double2*, int64_t, double2*, int64_t, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Allocation-free apply: the phase-1 vector t lives in a fixed device array
+// of this module instead of memory obtained with cudaMalloc, and the far part
+// is accumulated straight into y.  Host code cannot use the array's name as
+// a device address, so its address is looked up once per device.
+// ---------------------------------------------------------------------------
+constexpr int64_t kStaticScratchElems = VIE_NOALLOC_SCRATCH_ELEMS;  // complex float32: 32 MiB per device
+static __device__ __align__(256) float2 g_static_scratch[kStaticScratchElems];
+
+namespace {
+std::mutex g_static_mu;
+float2* g_static_addr[256] = {};
+
+float2* static_scratch_address(int device) {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (device < 0 || device >= 256) fail(VIE_ERR_INVALID_ARG, "device ordinal out of range");
+    if (!g_static_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess)
+            fail(VIE_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") +
+                                   cudaGetErrorString(e));
+        g_static_addr[device] = static_cast<float2*>(p);
+    }
+    return g_static_addr[device];
+}
+}  // namespace
+
+// y = Zs x with complex float32 factors and vectors; the caller has made the
+// operator's device current
+void apply_static(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s) {
+    if (op.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "the allocation-free apply needs VIE_C64 factors");
+    const int64_t need = std::max<int64_t>(op.t_total, 1) * nrhs;
+    if (need > kStaticScratchElems)
+        fail(VIE_ERR_INVALID_ARG, "allocation-free apply: " + std::to_string(need) +
+                                      " complex scratch elements needed (sum of ranks x nrhs), the static array holds " +
+                                      std::to_string(kStaticScratchElems));
+    float2* t = static_scratch_address(op.ctx->device);
+    const float2* fac = op.d_factors.as<float2>();
+    const int nc = op.n_cta;
+    const int64_t n = op.n();
+    // every element of t[0, t_total * nrhs) is written by phase 1 before phase 2
+    // reads it, and every element of y by phase 2: nothing needs clearing
+    if (op.n_p1_items > 0) {
+        p1_kernel<float2, float2, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
+                                                        op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, x, n,
+                                                        op.np, t, op.t_total, nrhs);
+        VIE_CHECK_LAUNCH();
+    }
+    p2_kernel<float2, float2><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
+                                                 op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(),
+                                                 fac, t, op.t_total, op.np, y, n, nrhs);
+    VIE_CHECK_LAUNCH();
+    // y = Z_ii x + y, each element read and written by the same thread
+    self_gemm<float2, float2>(op, op.d_zself32.as<float2>(), x, n, y, n, y, n, nrhs, 0, s);
+}
 
 }  // namespace vie

@@ -225,6 +225,8 @@ void self_gemm(Op& op, const TM* M, const TX* X, int64_t ldx, const TX* C, int64
 template <class TF, class TX>
 void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, cudaStream_t s);
 
+void apply_static(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s);
+
 // compress.cu
 void compress_operator(Op& op, double tol, int prec);
 

@@ -20,6 +20,7 @@ VIE_ERR_ADMISSION = -8
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "BREAKDOWN",
           -6: "NAN", -7: "TIMEOUT", -8: "ADMISSION", -9: "STATE"}
 C64, C128, BF16X3, C64_ACC64 = 1, 2, 3, 4
+NOALLOC_SCRATCH_ELEMS = 1 << 22   # VIE_NOALLOC_SCRATCH_ELEMS
 FUSE_PRECOND = 1
 DENSE = 2
 
@@ -90,7 +91,8 @@ class ResultC(C.Structure):
 EXPORTS = ["vie_create", "vie_destroy", "vie_last_error", "vie_assemble", "vie_compress", "vie_op_destroy",
            "vie_op_get_info", "vie_apply", "vie_precond", "vie_rhs", "vie_solve", "vie_fields",
            "vie_export_block", "vie_far_block_info", "vie_export_far_block", "vie_serve", "vie_submit",
-           "vie_poll", "vie_result_free", "vie_server_stop", "vie_footprint_bytes", "vie_kernel_launches"]
+           "vie_poll", "vie_result_free", "vie_server_stop", "vie_footprint_bytes", "vie_kernel_launches",
+           "vie_apply_noalloc"]
 
 _lib = None
 
@@ -131,6 +133,7 @@ def load():
         "vie_server_stop": (C.c_int, [vp]),
         "vie_footprint_bytes": (i64, [i64, C.c_int, C.c_int, C.c_int, i64]),
         "vie_kernel_launches": (i64, []),
+        "vie_apply_noalloc": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -239,6 +242,11 @@ class Operator:
     def apply(self, x_ptr, y_ptr, nrhs=1, precision=C64, flags=0, stream=None):
         self.ctx.check(self.L.vie_apply(self.h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(nrhs), self.n,
                                         int(precision), int(flags), _stream(stream)))
+
+    def apply_noalloc(self, x_ptr, y_ptr, nrhs=1, stream=None):
+        """vie_apply_noalloc: y = Zs x (c64) with the library's static scratch."""
+        self.ctx.check(self.L.vie_apply_noalloc(self.h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(nrhs), self.n,
+                                                _stream(stream)))
 
     def precond(self, x_ptr, y_ptr, nrhs=1, precision=C64, stream=None):
         self.ctx.check(self.L.vie_precond(self.h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(nrhs), self.n,
