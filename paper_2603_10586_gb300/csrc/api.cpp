@@ -201,8 +201,30 @@ int vie_assemble(vie_ctx* ctx, const vie_geometry* g, double wavelength, vie_op*
         upload(o.d_mesh_sign, o.mesh.face_sheet_sign);
         upload(o.d_mesh_vox, o.mesh.vox_ijk);
         upload(o.d_mesh_surf, o.mesh.surf_face);
+        std::vector<float4> voxc(o.mesh.nvox), surfc(o.mesh.nsurf);
+        for (int v = 0; v < o.mesh.nvox; ++v)
+            voxc[v] = make_float4(o.mesh.vox_ijk[3 * v] + 0.5f, o.mesh.vox_ijk[3 * v + 1] + 0.5f,
+                                  o.mesh.vox_ijk[3 * v + 2] + 0.5f, 0.f);
+        {
+            // face (d, i, j, k) in its direction-major numbering
+            const int nv = o.mesh.nv;
+            for (int sidx = 0; sidx < o.mesh.nsurf; ++sidx) {
+                int f = o.mesh.surf_face[sidx], d = o.mesh.face_dir[f];
+                int g = f - d * (nv + 1) * nv * nv;
+                int ijk[3];
+                if (d == 0) { ijk[0] = g / (nv * nv); ijk[1] = (g / nv) % nv; ijk[2] = g % nv; }
+                else if (d == 1) { ijk[0] = g / (nv * (nv + 1)); ijk[1] = (g / nv) % (nv + 1); ijk[2] = g % nv; }
+                else { ijk[0] = g / (nv * (nv + 1)); ijk[1] = (g / (nv + 1)) % nv; ijk[2] = g % (nv + 1); }
+                float c[3];
+                for (int e = 0; e < 3; ++e) c[e] = e == d ? (float)ijk[e] : ijk[e] + 0.5f;
+                surfc[sidx] = make_float4(c[0], c[1], c[2], (float)d);
+            }
+        }
+        upload(o.d_mesh_voxc, voxc);
+        upload(o.d_mesh_surfc, surfc);
         o.dmesh = DevMesh{o.mesh.nv, o.mesh.np, o.mesh.nvox, o.mesh.nsurf, o.d_mesh_face.as<int4>(),
-                          o.d_mesh_sign.as<int>(), o.d_mesh_vox.as<int>(), o.d_mesh_surf.as<int>()};
+                          o.d_mesh_sign.as<int>(), o.d_mesh_vox.as<int>(), o.d_mesh_surf.as<int>(),
+                          o.d_mesh_voxc.as<float4>(), o.d_mesh_surfc.as<float4>()};
         o.atoms_of_type.assign(o.T, {});
         for (int a = 0; a < o.N; ++a) o.atoms_of_type[o.types[a]].push_back(a);
         std::vector<int> flat;

@@ -356,22 +356,24 @@ struct GeoPtrs {
 
 __device__ __forceinline__ void vox_centre(const DevMesh& m, const GeoPtrs& g, int atom, int v, double c[3],
                                            double& h) {
-    double side = g.sides[g.types[atom]];
+    const double side = g.sides[g.types[atom]];
     h = side / m.nv;
-    for (int d = 0; d < 3; ++d) c[d] = g.centres[3 * atom + d] - 0.5 * side + h * (m.vox_ijk[3 * v + d] + 0.5);
+    const float4 l = m.vox_c[v];
+    c[0] = g.centres[3 * atom] - 0.5 * side + h * l.x;
+    c[1] = g.centres[3 * atom + 1] - 0.5 * side + h * l.y;
+    c[2] = g.centres[3 * atom + 2] - 0.5 * side + h * l.z;
 }
 
-// centre of a boundary face (plane coordinate along its axis)
+// centre of a boundary face (its plane coordinate along the normal axis)
 __device__ __forceinline__ int surf_centre(const DevMesh& m, const GeoPtrs& g, int atom, int s, double c[3],
                                            double& h) {
-    double side = g.sides[g.types[atom]];
+    const double side = g.sides[g.types[atom]];
     h = side / m.nv;
-    double lo[3], hi[3];
-    int ext[6];
-    int ax = surf_rect(m, s, h, lo, hi, ext);
-    for (int d = 0; d < 3; ++d)
-        c[d] = g.centres[3 * atom + d] - 0.5 * side + (d == ax ? lo[d] : lo[d] + 0.5 * h);
-    return ax;
+    const float4 l = m.surf_c[s];
+    c[0] = g.centres[3 * atom] - 0.5 * side + h * l.x;
+    c[1] = g.centres[3 * atom + 1] - 0.5 * side + h * l.y;
+    c[2] = g.centres[3 * atom + 2] - 0.5 * side + h * l.z;
+    return (int)l.w;
 }
 
 template <class T>
@@ -475,18 +477,20 @@ __device__ __forceinline__ typename C2<T>::t surf_pair(const T D[3], const T (*p
 template <class T>
 __device__ __forceinline__ void rule_points(int ax, T o, T (*pts)[3]) {
     if (ax < 0) {
+#pragma unroll
         for (int p = 0; p < 8; ++p) {
             pts[p][0] = (p & 4) ? o : -o;
             pts[p][1] = (p & 2) ? o : -o;
             pts[p][2] = (p & 1) ? o : -o;
         }
     } else {
-        int a = ax == 0 ? 1 : 0, b = ax == 2 ? 1 : 2;
-        for (int p = 0; p < 4; ++p) {
-            pts[p][ax] = T(0);
-            pts[p][a] = (p & 2) ? o : -o;
-            pts[p][b] = (p & 1) ? o : -o;
-        }
+        // the normal axis is a runtime value: select per (compile-time) component
+        const int a = ax == 0 ? 1 : 0;
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                pts[p][d] = d == ax ? T(0) : (d == a ? ((p & 2) ? o : -o) : ((p & 1) ? o : -o));
     }
 }
 
@@ -529,73 +533,106 @@ __global__ void cross_surf_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, T
 // --------------------------------------------------------------------------
 // entries from tables: -k^2 L + D (+ M / chi for a self block)
 // --------------------------------------------------------------------------
+// One CTA: 128 test faces i (threads) x kEntCols source faces j (loop), so the
+// source-face data are loaded once per column and the index arithmetic stays
+// 32-bit.  Optionally accumulates the squared norm of the written entries per
+// CTA (fixed reduction order) into norm_part.
+constexpr int kEntRows = 128, kEntCols = 8;
+
 template <class T, class TO, bool SELF>
-__global__ void entries_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, double k2,
-                               const typename C2<T>::t* tab, size_t job_stride, TO* const* dst,
-                               const int64_t* ld, const double2* inv_chi) {
+__global__ void __launch_bounds__(kEntRows) entries_kernel(const PairJob* jobs, DevMesh m, GeoPtrs geo, double k2,
+                                                           const typename C2<T>::t* __restrict__ tab,
+                                                           size_t job_stride, TO* const* dst, const int64_t* ld,
+                                                           const double2* inv_chi, double* norm_part) {
     using T2 = typename C2<T>::t;
     const int job = blockIdx.y;
-    const int np = m.np;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)np * np) return;
-    const int i = (int)(t % np), j = (int)(t / np);
+    const int np = m.np, nvox = m.nvox, nsurf = m.nsurf;
+    const int nv2 = nvox * nvox;
+    const int i = blockIdx.x * kEntRows + threadIdx.x;
     const PairJob jb = jobs[job];
     const double hA = geo.sides[geo.types[jb.a]] / m.nv;
     const double hB = geo.sides[geo.types[jb.b]] / m.nv;
-    const T2* tb = tab + (size_t)job * job_stride;
-    const size_t nv2 = (size_t)m.nvox * m.nvox;
-    const int4 fi = m.face[i], fj = m.face[j];
-    const int vi[2] = {fi.y, fi.z}, vj[2] = {fj.y, fj.z};  // voxel below (xi), above (1 - xi)
-    T2 L = mk(T(0), T(0)), D = mk(T(0), T(0));
-    if (fi.x == fj.x) {
-        for (int sa = 0; sa < 2; ++sa) {
-            if (vi[sa] < 0) continue;
-            for (int sb = 0; sb < 2; ++sb) {
-                if (vj[sb] < 0) continue;
-                L += tb[(size_t)(1 + 4 * fi.x + 2 * sa + sb) * nv2 + (size_t)vj[sb] * m.nvox + vi[sa]];
+    const T2* __restrict__ tb = tab + (size_t)job * job_stride;
+    const T2* __restrict__ VS = tb + 13 * (size_t)nv2;
+    const T2* __restrict__ SV = VS + (size_t)nvox * nsurf;
+    const T2* __restrict__ SS = SV + (size_t)nsurf * nvox;
+    const T cvA = T(1.0 / (hA * hA * hA)), cvB = T(1.0 / (hB * hB * hB));
+    const T lscale = T(1.0 / (hA * hA * hB * hB)), tk2 = T(k2);
+    TO* out = dst[jb.dst];
+    const int64_t ldo = ld[jb.dst];
+    const bool active = i < np;
+    int4 fi = make_int4(0, -1, -1, -1);
+    T csA = T(0);
+    if (active) {
+        fi = m.face[i];
+        if (fi.w >= 0) csA = T(m.sheet_sign[i] / (hA * hA));
+    }
+    const int vi0 = fi.y, vi1 = fi.z, si = fi.w;
+    double nrm = 0.0;
+    const int j0 = blockIdx.z * kEntCols;
+    for (int jj = 0; jj < kEntCols; ++jj) {
+        const int j = j0 + jj;
+        if (j >= np || !active) continue;
+        const int4 fj = m.face[j];
+        const int vj0 = fj.y, vj1 = fj.z, sj = fj.w;
+        const T csB = sj >= 0 ? T(m.sheet_sign[j] / (hB * hB)) : T(0);
+        T2 L = mk(T(0), T(0)), D = mk(T(0), T(0));
+        // volume charges (+h^-3 below the face, -h^-3 above) and profiles (xi, 1 - xi)
+        if (fi.x == fj.x) {
+            const T2* W = tb + (size_t)(1 + 4 * fi.x) * nv2;
+            if (vi0 >= 0 && vj0 >= 0) L += W[0 * nv2 + vj0 * nvox + vi0];
+            if (vi0 >= 0 && vj1 >= 0) L += W[1 * (size_t)nv2 + vj1 * nvox + vi0];
+            if (vi1 >= 0 && vj0 >= 0) L += W[2 * (size_t)nv2 + vj0 * nvox + vi1];
+            if (vi1 >= 0 && vj1 >= 0) L += W[3 * (size_t)nv2 + vj1 * nvox + vi1];
+        }
+        T2 Uc = mk(T(0), T(0));
+        if (vi0 >= 0) {
+            if (vj0 >= 0) Uc += tb[vj0 * nvox + vi0];
+            if (vj1 >= 0) Uc -= tb[vj1 * nvox + vi0];
+            if (sj >= 0) D += (cvA * csB) * VS[sj * nvox + vi0];
+        }
+        if (vi1 >= 0) {
+            if (vj0 >= 0) Uc -= tb[vj0 * nvox + vi1];
+            if (vj1 >= 0) Uc += tb[vj1 * nvox + vi1];
+            if (sj >= 0) D -= (cvA * csB) * VS[sj * nvox + vi1];
+        }
+        D += (cvA * cvB) * Uc;
+        if (si >= 0) {
+            T2 Sv = mk(T(0), T(0));
+            if (vj0 >= 0) Sv += SV[vj0 * nsurf + si];
+            if (vj1 >= 0) Sv -= SV[vj1 * nsurf + si];
+            D += (csA * cvB) * Sv;
+            if (sj >= 0) D += (csA * csB) * SS[sj * nsurf + si];
+        }
+        T2 z = D - (tk2 * lscale) * L;
+        if (SELF && fi.x == fj.x) {
+            // M_ij = sum over shared voxels of (1/3 equal profiles, 1/6 opposite) / h
+            double Mij = 0.0;
+            if (vi0 >= 0 && vi0 == vj0) Mij += 1.0 / 3.0;
+            if (vi0 >= 0 && vi0 == vj1) Mij += 1.0 / 6.0;
+            if (vi1 >= 0 && vi1 == vj0) Mij += 1.0 / 6.0;
+            if (vi1 >= 0 && vi1 == vj1) Mij += 1.0 / 3.0;
+            if (Mij != 0.0) {
+                Mij /= hA;
+                double2 ic = inv_chi[geo.types[jb.a]];
+                z += mk(T(Mij * ic.x), T(Mij * ic.y));
             }
         }
-        L = T(1.0 / (hA * hA * hB * hB)) * L;
+        const TO zo = cvt<TO>(z);
+        out[(int64_t)jb.row_off + i + ((int64_t)jb.col_off + j) * ldo] = zo;
+        nrm += (double)zo.x * zo.x + (double)zo.y * zo.y;
     }
-    const T cvA = T(1.0 / (hA * hA * hA)), cvB = T(1.0 / (hB * hB * hB));
-    const int si = fi.w, sj = fj.w;
-    const T csA = si >= 0 ? T(m.sheet_sign[i] / (hA * hA)) : T(0);
-    const T csB = sj >= 0 ? T(m.sheet_sign[j] / (hB * hB)) : T(0);
-    const T2* VS = tb + 13 * nv2;
-    const T2* SV = VS + (size_t)m.nvox * m.nsurf;
-    const T2* SS = SV + (size_t)m.nsurf * m.nvox;
-    for (int sa = 0; sa < 2; ++sa) {
-        if (vi[sa] < 0) continue;
-        T ca = sa ? -cvA : cvA;
-        for (int sb = 0; sb < 2; ++sb) {
-            if (vj[sb] < 0) continue;
-            T cb = sb ? -cvB : cvB;
-            D += (ca * cb) * tb[(size_t)vj[sb] * m.nvox + vi[sa]];
+    if (norm_part) {
+        __shared__ double red[kEntRows];
+        red[threadIdx.x] = nrm;
+        __syncthreads();
+        for (int st = kEntRows / 2; st > 0; st >>= 1) {
+            if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+            __syncthreads();
         }
-        if (sj >= 0) D += (ca * csB) * VS[(size_t)sj * m.nvox + vi[sa]];
+        if (threadIdx.x == 0)
+            norm_part[((size_t)job * gridDim.z + blockIdx.z) * gridDim.x + blockIdx.x] = red[0];
     }
-    if (si >= 0) {
-        for (int sb = 0; sb < 2; ++sb) {
-            if (vj[sb] < 0) continue;
-            T cb = sb ? -cvB : cvB;
-            D += (csA * cb) * SV[(size_t)vj[sb] * m.nsurf + si];
-        }
-        if (sj >= 0) D += (csA * csB) * SS[(size_t)sj * m.nsurf + si];
-    }
-    T2 z = D - T(k2) * L;
-    if (SELF && fi.x == fj.x) {
-        // M_ij = sum over shared voxels of (1/3 equal profiles, 1/6 opposite) / h
-        double Mij = 0.0;
-        for (int sa = 0; sa < 2; ++sa)
-            for (int sb = 0; sb < 2; ++sb)
-                if (vi[sa] >= 0 && vi[sa] == vj[sb]) Mij += (sa == sb ? 1.0 / 3.0 : 1.0 / 6.0) / hA;
-        if (Mij != 0.0) {
-            double2 ic = inv_chi[geo.types[jb.a]];
-            z += mk(T(Mij * ic.x), T(Mij * ic.y));
-        }
-    }
-    TO* out = dst[jb.dst];
-    out[(int64_t)jb.row_off + i + ((int64_t)jb.col_off + j) * ld[jb.dst]] = cvt<TO>(z);
 }
 
 // --------------------------------------------------------------------------
@@ -738,10 +775,10 @@ void assemble_self_blocks(Op& op) {
         VIE_CUDA(cudaMemcpyAsync(jobs.p, &jb, sizeof(jb), cudaMemcpyHostToDevice, s));
         VIE_CUDA(cudaMemcpyAsync(dst.p, &dptr, sizeof(dptr), cudaMemcpyHostToDevice, s));
         VIE_CUDA(cudaMemcpyAsync(ldb.p, &ldv, sizeof(ldv), cudaMemcpyHostToDevice, s));
-        int64_t ne = (int64_t)np * np;
-        entries_kernel<double, double2, true><<<dim3((unsigned)((ne + 255) / 256), 1), 256, 0, s>>>(
-            jobs.as<PairJob>(), m, geo_of(op), op.k * op.k, tab.as<double2>(), stride,
-            dst.as<double2* const>(), ldb.as<int64_t>(), op.d_inv_chi.as<double2>());
+        entries_kernel<double, double2, true>
+            <<<dim3((np + kEntRows - 1) / kEntRows, 1, (np + kEntCols - 1) / kEntCols), kEntRows, 0, s>>>(
+                jobs.as<PairJob>(), m, geo_of(op), op.k * op.k, tab.as<double2>(), stride,
+                dst.as<double2* const>(), ldb.as<int64_t>(), op.d_inv_chi.as<double2>(), nullptr);
         VIE_CHECK_LAUNCH();
         VIE_CUDA(cudaStreamSynchronize(s));
     }
@@ -750,9 +787,17 @@ void assemble_self_blocks(Op& op) {
 // ---------------------------------------------------------------------------
 // interaction blocks of atom pairs (a != b), written into destination matrices
 // ---------------------------------------------------------------------------
+__global__ void k_sum_rows(const double* part, int per, int nrows, double* out) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    double acc = 0.0;
+    for (int c = 0; c < per; ++c) acc += part[(size_t)r * per + c];
+    out[r] = acc;
+}
+
 template <class T>
 void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_dst, const int64_t* d_ld,
-                    cudaStream_t s) {
+                    cudaStream_t s, double* norm_out) {
     using T2 = typename C2<T>::t;
     const DevMesh& m = op.dmesh;
     size_t stride = table_stride(m);
@@ -764,7 +809,10 @@ void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_ds
     const T tol = T(2.0 / op.wavelength);
     const int nv2 = m.nvox * m.nvox;
     const int ns = std::max(m.nvox, m.nsurf) * m.nsurf;
-    const int64_t ne = (int64_t)m.np * m.np;
+    DevBuf npart;
+    if (norm_out)
+        npart.alloc((size_t)chunk * ((m.np + kEntRows - 1) / kEntRows) * ((m.np + kEntCols - 1) / kEntCols) *
+                    sizeof(double));
     for (int j0 = 0; j0 < n_jobs; j0 += chunk) {
         int nj = std::min(chunk, n_jobs - j0);
         cross_vv_kernel<T><<<dim3((nv2 + 127) / 128, nj), 128, 0, s>>>(d_jobs + j0, m, geo_of(op), tol,
@@ -773,16 +821,21 @@ void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_ds
         cross_surf_kernel<T><<<dim3((ns + 127) / 128, 3, nj), 128, 0, s>>>(d_jobs + j0, m, geo_of(op), tol,
                                                                            tab.as<T2>(), stride);
         VIE_CHECK_LAUNCH();
-        entries_kernel<T, T2, false><<<dim3((unsigned)((ne + 255) / 256), nj), 256, 0, s>>>(
+        const dim3 eg((m.np + kEntRows - 1) / kEntRows, nj, (m.np + kEntCols - 1) / kEntCols);
+        entries_kernel<T, T2, false><<<eg, kEntRows, 0, s>>>(
             d_jobs + j0, m, geo_of(op), op.k * op.k, tab.as<T2>(), stride, (T2* const*)d_dst, d_ld,
-            op.d_inv_chi.as<double2>());
+            op.d_inv_chi.as<double2>(), norm_out ? npart.as<double>() : nullptr);
         VIE_CHECK_LAUNCH();
+        if (norm_out) {
+            k_sum_rows<<<(nj + 127) / 128, 128, 0, s>>>(npart.as<double>(), (int)(eg.x * eg.z), nj, norm_out + j0);
+            VIE_CHECK_LAUNCH();
+        }
     }
     // keep the scratch alive until the work is done
     VIE_CUDA(cudaStreamSynchronize(s));
 }
 
-template void assemble_pairs<float>(Op&, const PairJob*, int, void* const*, const int64_t*, cudaStream_t);
+template void assemble_pairs<float>(Op&, const PairJob*, int, void* const*, const int64_t*, cudaStream_t, double*);
 
 namespace {
 // y[a] = sum_b Z_ab x_b for the atoms of a chunk; blocks of atom a_local are
@@ -846,7 +899,7 @@ void dense_apply(Op& op, const typename C2<T>::t* x, typename C2<T>::t* y, cudaS
 }
 void dense_apply_c64(Op& op, const float2* x, float2* y, cudaStream_t s) { dense_apply<float>(op, x, y, s); }
 void dense_apply_c128(Op& op, const double2* x, double2* y, cudaStream_t s) { dense_apply<double>(op, x, y, s); }
-template void assemble_pairs<double>(Op&, const PairJob*, int, void* const*, const int64_t*, cudaStream_t);
+template void assemble_pairs<double>(Op&, const PairJob*, int, void* const*, const int64_t*, cudaStream_t, double*);
 
 void rhs_kernel_launch(Op& op, const double* d_khat, const double* d_pol, int nrhs, void* b, int64_t ld,
                        cudaStream_t s) {

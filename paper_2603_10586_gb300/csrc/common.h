@@ -99,6 +99,8 @@ struct DevMesh {
     const int* sheet_sign;
     const int* vox_ijk;   // [3 nvox]
     const int* surf_face; // [nsurf]
+    const float4* vox_c;  // voxel centres in units of h from the cube corner
+    const float4* surf_c; // boundary-face centres in units of h, w = normal axis
 };
 
 // ---------------------------------------------------------------------------
@@ -138,7 +140,7 @@ struct Op {
     std::vector<int> block_atoms;
     // device geometry
     DevBuf d_centres, d_types, d_sides, d_inv_chi;
-    DevBuf d_mesh_face, d_mesh_sign, d_mesh_vox, d_mesh_surf;
+    DevBuf d_mesh_face, d_mesh_sign, d_mesh_vox, d_mesh_surf, d_mesh_voxc, d_mesh_surfc;
     DevMesh dmesh{};                   // pointers into the buffers above
     // self blocks (per type, np x np col-major)
     DevBuf d_zself64, d_inv64, d_zself32, d_inv32;
@@ -201,9 +203,10 @@ struct PairJob {
     int dst;          // index into the destination pointer table
     int row_off, col_off;
 };
+// norm_out (optional, device): per job, the squared Frobenius norm of its block
 template <class T>
 void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_dst, const int64_t* d_ld,
-                    cudaStream_t s);
+                    cudaStream_t s, double* norm_out = nullptr);
 void dense_apply_c64(Op& op, const float2* x, float2* y, cudaStream_t s);
 void dense_apply_c128(Op& op, const double2* x, double2* y, cudaStream_t s);
 void rhs_kernel_launch(Op& op, const double* d_khat, const double* d_pol, int nrhs, void* b, int64_t ld,

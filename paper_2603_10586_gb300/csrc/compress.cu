@@ -330,8 +330,8 @@ struct Compressor {
         const int rcap_pad = ((rcap + kChunk - 1) / kChunk) * kChunk;
         const int64_t mn = (int64_t)m * n;
 
-        // 1. form the blocks (col-major m x n, ld = m)
-        DevBuf A((size_t)nb * mn * sizeof(T2));
+        // 1. form the blocks (col-major m x n, ld = m) and their squared norms
+        DevBuf A((size_t)nb * mn * sizeof(T2)), jobnorm;
         {
             std::vector<PairJob> jobs;
             std::vector<void*> dst(nb);
@@ -348,12 +348,16 @@ struct Compressor {
             upload(dj, jobs);
             upload(dd, dst);
             upload(dl, ld);
-            assemble_pairs<T>(op, dj.as<PairJob>(), (int)jobs.size(), dd.as<void* const>(), dl.as<int64_t>(), s);
+            jobnorm.alloc(jobs.size() * sizeof(double));
+            assemble_pairs<T>(op, dj.as<PairJob>(), (int)jobs.size(), dd.as<void* const>(), dl.as<int64_t>(), s,
+                              jobnorm.as<double>());
         }
         double t1 = mark();
         tim[0] += t1 - t0;
         DevBuf part, normA((size_t)nb * sizeof(double)), est((size_t)nb * sizeof(double));
-        sumsq(A.as<T2>(), mn, mn, nb, normA.as<double>(), part);
+        // ||A||_F^2 of each block: the sum over its (contiguous) atom-pair jobs
+        k_reduce_rows<<<(nb + 127) / 128, 128, 0, s>>>(jobnorm.as<double>(), b0.nt * b0.ns, nb, normA.as<double>());
+        VIE_CHECK_LAUNCH();
         std::vector<double> hnorm(nb);
         VIE_CUDA(cudaMemcpyAsync(hnorm.data(), normA.p, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
 
@@ -658,7 +662,9 @@ void compress_operator(Op& op, double tol, int prec) {
     if (!(em && em[0] == '0')) {
         VIE_BLAS(cublasSetMathMode(op.ctx->blas, (cublasMath_t)(CUBLAS_FP32_EMULATED_BF16X9_MATH |
                                                                 CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH)));
-        VIE_BLAS(cublasSetEmulationStrategy(op.ctx->blas, CUBLAS_EMULATION_STRATEGY_PERFORMANT));
+        const char* es = std::getenv("VIE_GEMM_EMULATION_STRATEGY");
+        VIE_BLAS(cublasSetEmulationStrategy(op.ctx->blas, (es && es[0] == 'p') ? CUBLAS_EMULATION_STRATEGY_PERFORMANT
+                                                                                 : CUBLAS_EMULATION_STRATEGY_EAGER));
     } else {
         VIE_BLAS(cublasSetMathMode(op.ctx->blas, CUBLAS_DEFAULT_MATH));
     }
