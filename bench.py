@@ -15,9 +15,14 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|referenc
 Multi-GPU: one process per GPU (torchrun); the solves are independent
 replicas (no collective), value = all ranks' solves / max rank time.
 """
+import os
+
+# the CPU oracle baseline is timed single-threaded (reported as 1 core)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import argparse
 import json
-import os
 import statistics
 import subprocess
 import sys
@@ -119,6 +124,21 @@ def oracle_sample(budget_s=20.0):
               f"1 Householder QR of a {blk.shape[0]}x{blk.shape[1]} block (rank {r}, {t_qr:.2f} s) scaled by m n r "
               f"over all far blocks, {iters} compressed applies at the sampled per-entry rate")
     return total, sample
+
+
+def reduce_max(v, dist=None, device="cpu"):
+    """Max over ranks of a per-rank time (identity without a process group)."""
+    if dist is None:
+        return float(v)
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, steps, max_ms):
+    """Solves/s of the whole job: every rank solves `steps` problems (replicas)."""
+    return world * steps / (max_ms * 1e-3)
 
 
 def cores():
@@ -254,15 +274,8 @@ def main():
     peak, peak_kind = peaks()
     achieved = info["apply_bytes"] / (apply_ms * 1e-3) / 1e9
 
-    def maxr(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    total_ms = maxr(total_ms)
-    e2e_ms = maxr(e2e_ms)
+    total_ms = reduce_max(total_ms, dist, "cuda")
+    e2e_ms = reduce_max(e2e_ms, dist, "cuda")
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -270,7 +283,7 @@ def main():
             cpu = {"value": 1.0 / t_cpu, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample}
         lat_sorted = sorted(lat)
         line = {
-            "metric": "solves/s", "value": world * args.steps / (total_ms * 1e-3), "unit": "solves/s",
+            "metric": "solves/s", "value": whole_job_value(world, args.steps, total_ms), "unit": "solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
             "data": "synthetic",
@@ -290,7 +303,7 @@ def main():
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "algorithmic_bytes": info["apply_bytes"],
                          "apply_ms": apply_ms, "traffic": None},
-            "e2e": {"value": world * args.steps / (e2e_ms * 1e-3), "unit": "solves/s",
+            "e2e": {"value": whole_job_value(world, args.steps, e2e_ms), "unit": "solves/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(16 * n)},
             "gpu_launches": int(launches),
             "clocks": clk,

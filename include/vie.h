@@ -241,6 +241,21 @@ int vie_export_block(vie_op* op, int kind, int a, int b, int precision, void* ou
 int vie_far_block_info(vie_op* op, int64_t i, int* level, int* n_tatoms, int* n_satoms, int* rank);
 int vie_export_far_block(vie_op* op, int64_t i, int* tatoms, int* satoms, void* Q, void* R);
 
+/* ---- host-only planning (no GPU needed) --------------------------------------
+ * vie_plan_far_blocks: the grid hierarchy and far-block list that vie_assemble
+ * builds (Sec. 5.1 Definition, eq. eq_rec01, Sec. 5.4), for atom centres
+ * xy[2 n_atoms] (host).  Writes *levels and *n_blocks; if `out` is not NULL and
+ * out_len is large enough it receives, per block in order, the record
+ * (level, nt, ns, nt target atoms, ns source atoms) as ints; *out_needed
+ * receives the length required.  VIE_ERR_INVALID_ARG for coincident atoms. */
+int vie_plan_far_blocks(const double* xy, int n_atoms, int* levels, int64_t* n_blocks, int* out, int64_t out_len,
+                        int64_t* out_needed);
+
+/* vie_lpt_assign (App. C): greedy least-loaded assignment of n weights w[n] to
+ * n_proc processes; owner[n] receives each weight's process, loads[n_proc]
+ * the process totals (both host memory). */
+int vie_lpt_assign(const double* w, int64_t n, int n_proc, int* owner, double* loads);
+
 /* ---- serving (continuous batching) ------------------------------------------
  * Requests (geometry + plane waves) are admitted while the modelled HBM
  * footprint of their compressed operator, inverses and Krylov state fits

@@ -591,6 +591,57 @@ int vie_export_far_block(vie_op* op, int64_t i, int* tatoms, int* satoms, void* 
 
 int64_t vie_kernel_launches(void) { return g_kernel_launches.load(); }
 
+int vie_plan_far_blocks(const double* xy, int n_atoms, int* levels, int64_t* n_blocks, int* out, int64_t out_len,
+                        int64_t* out_needed) {
+    if (!xy || n_atoms < 1 || !levels || !n_blocks) return VIE_ERR_INVALID_ARG;
+    try {
+        Op o;
+        o.N = n_atoms;
+        o.np = 1;
+        o.centres.resize(3 * (size_t)n_atoms);
+        for (int a = 0; a < n_atoms; ++a) {
+            o.centres[3 * a] = xy[2 * a];
+            o.centres[3 * a + 1] = xy[2 * a + 1];
+            o.centres[3 * a + 2] = 0.0;
+        }
+        build_tree(o);
+        *levels = o.L;
+        *n_blocks = (int64_t)o.blocks.size();
+        int64_t need = 0;
+        for (const auto& b : o.blocks) need += 3 + b.nt + b.ns;
+        if (out_needed) *out_needed = need;
+        if (out && out_len >= need) {
+            int64_t k = 0;
+            for (const auto& b : o.blocks) {
+                out[k++] = b.level;
+                out[k++] = b.nt;
+                out[k++] = b.ns;
+                for (int i = 0; i < b.nt; ++i) out[k++] = o.block_atoms[b.t_off + i];
+                for (int i = 0; i < b.ns; ++i) out[k++] = o.block_atoms[b.s_off + i];
+            }
+        }
+        return VIE_OK;
+    } catch (const Error& e) {
+        return e.status;
+    } catch (...) {
+        return VIE_ERR_INVALID_ARG;
+    }
+}
+
+int vie_lpt_assign(const double* w, int64_t n, int n_proc, int* owner, double* loads) {
+    if (!w || n < 0 || n_proc < 1 || !owner || !loads) return VIE_ERR_INVALID_ARG;
+    try {
+        std::vector<double> wv(w, w + n), ld;
+        std::vector<int> ow;
+        lpt_assign(wv, n_proc, ow, ld);
+        std::copy(ow.begin(), ow.end(), owner);
+        std::copy(ld.begin(), ld.end(), loads);
+        return VIE_OK;
+    } catch (...) {
+        return VIE_ERR_INVALID_ARG;
+    }
+}
+
 int64_t vie_footprint_bytes(int64_t n, int np, int nrhs, int restart, int64_t factor_entries) {
     // factors (c64) + self/inverse blocks (c128 + c64, two per type upper bound 3 types)
     // + Krylov basis (restart + 1) n c128 per rhs in flight + solver vectors

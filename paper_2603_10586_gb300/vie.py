@@ -92,7 +92,7 @@ EXPORTS = ["vie_create", "vie_destroy", "vie_last_error", "vie_assemble", "vie_c
            "vie_op_get_info", "vie_apply", "vie_precond", "vie_rhs", "vie_solve", "vie_fields",
            "vie_export_block", "vie_far_block_info", "vie_export_far_block", "vie_serve", "vie_submit",
            "vie_poll", "vie_result_free", "vie_server_stop", "vie_footprint_bytes", "vie_kernel_launches",
-           "vie_apply_noalloc"]
+           "vie_apply_noalloc", "vie_plan_far_blocks", "vie_lpt_assign"]
 
 _lib = None
 
@@ -134,6 +134,9 @@ def load():
         "vie_footprint_bytes": (i64, [i64, C.c_int, C.c_int, C.c_int, i64]),
         "vie_kernel_launches": (i64, []),
         "vie_apply_noalloc": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
+        "vie_plan_far_blocks": (C.c_int, [C.POINTER(dbl), C.c_int, C.POINTER(C.c_int), C.POINTER(i64),
+                                          C.POINTER(C.c_int), i64, C.POINTER(i64)]),
+        "vie_lpt_assign": (C.c_int, [C.POINTER(dbl), i64, C.c_int, C.POINTER(C.c_int), C.POINTER(dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -328,6 +331,39 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+def plan_far_blocks(centres):
+    """Host-only: (levels, [(level, target atoms, source atoms)]) as vie_assemble builds them."""
+    L = load()
+    xy = np.ascontiguousarray(np.asarray(centres, np.float64)[:, :2]).ravel()
+    n = len(xy) // 2
+    lev, nb, need = C.c_int(), C.c_int64(), C.c_int64()
+    st = L.vie_plan_far_blocks(_dp(xy), n, C.byref(lev), C.byref(nb), None, 0, C.byref(need))
+    if st != VIE_OK:
+        raise VieError(st, "vie_plan_far_blocks")
+    buf = np.zeros(max(1, need.value), np.int32)
+    st = L.vie_plan_far_blocks(_dp(xy), n, C.byref(lev), C.byref(nb), _ip(buf), need.value, C.byref(need))
+    if st != VIE_OK:
+        raise VieError(st, "vie_plan_far_blocks")
+    out, k = [], 0
+    for _ in range(nb.value):
+        l, nt, ns = buf[k:k + 3]
+        k += 3
+        out.append((int(l), buf[k:k + nt].tolist(), buf[k + nt:k + nt + ns].tolist()))
+        k += nt + ns
+    return lev.value, out
+
+
+def lpt_assign(weights, n_proc):
+    """Host-only greedy least-loaded map: (owner, loads)."""
+    w = np.ascontiguousarray(np.asarray(weights, np.float64))
+    owner = np.zeros(len(w), np.int32)
+    loads = np.zeros(n_proc, np.float64)
+    st = load().vie_lpt_assign(_dp(w), len(w), int(n_proc), _ip(owner), _dp(loads))
+    if st != VIE_OK:
+        raise VieError(st, "vie_lpt_assign")
+    return owner, loads
 
 
 def footprint_bytes(n, np_, nrhs, restart, factor_entries):
