@@ -171,6 +171,57 @@ def run_reference(args):
     return 0
 
 
+def run_serving(args):
+    """--serving: the Poisson request stream (20 req/s; arrays of 8x8..48x48 cubes of
+    3^3 voxels; lambda ~ U[0.9, 1.1], eps ~ U[8, 14]; 1-8 RHS) through vie_serve with
+    continuous batching; reports solves/s (right-hand sides per second) and the
+    p50/p99 latency from submit to result."""
+    import threading
+    import torch
+    from paper_2603_10586_gb300 import vie
+    torch.cuda.set_device(0)
+    ctx = vie.Context(0)
+    warm = workloads.serving_stream(args.warmup, seed=99)
+    reqs = workloads.serving_stream(args.requests, seed=0)
+    srv = vie.Server(ctx, max_inflight=args.slots, tol=TOL_COMPRESS)
+    for r in warm:                                   # warm-up, not timed
+        srv.poll(srv.submit(r.geometry, r.khat, r.pol), timeout_ms=600000)
+    tickets = [None] * len(reqs)
+    t_start = time.perf_counter()
+
+    def feeder():
+        for i, r in enumerate(reqs):
+            delay = r.arrival_s - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = srv.submit(r.geometry, r.khat, r.pol)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    res = []
+    for t in tickets:
+        out = None
+        while out is None:
+            out = srv.poll(t, timeout_ms=1000)
+        res.append(out)
+    srv.stop()
+    lat = sorted(r["t_done"] - r["t_submit"] for r in res)
+    span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    rhs = sum(r["nrhs"] for r in res)
+    ok = sum(1 for r in res if r["status"] == 0)
+    line = {"metric": "serving solves/s", "value": rhs / span, "unit": "solves/s", "n_gpus": 1,
+            "requests": len(res), "completed_ok": ok, "requests_per_s": len(res) / span,
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "higher_is_better": True, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "serving", "slots": args.slots, "rate_hz": 20.0,
+                       "arrays": "8x8..48x48 cubes of 3^3 voxels", "tol_compress": TOL_COMPRESS,
+                       "tol_solve": TOL_SOLVE}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -179,9 +230,14 @@ def main():
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--applies", type=int, default=40)
+    ap.add_argument("--serving", action="store_true", help="the request-stream workload instead")
+    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--slots", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -123,15 +123,14 @@ typedef struct vie_solve_opts {
     int restart;               /* GMRES restart length m (e.g. 60) */
     int max_iters;             /* iteration cap (e.g. 2000) */
     int precision;             /* VIE_C64: FP32 inner applies with FP64 Krylov and FP64
-                                  residual refinement; VIE_C128: all-FP64 (needs C128 factors);
-                                  VIE_BF16X3: block GMRES with tensor-core far applies */
+                                  residual refinement; VIE_C128: all-FP64 (needs C128 factors) */
     int out_on_device;         /* 1: I_out is a device pointer, 0: host pointer */
     int precond;               /* 1: block-diagonal preconditioner (default), 0: none */
 } vie_solve_opts;
 
 typedef struct vie_solve_stats {
-    int iterations;            /* Arnoldi steps (block steps for block GMRES) */
-    int applies;               /* compressed operator applications */
+    int iterations;            /* Arnoldi steps of the slowest right-hand side */
+    int applies;               /* operator applications (each on all right-hand sides still iterating) */
     int refinements;           /* FP64 residual recomputations */
     double residual;           /* final true preconditioned relative residual (max over RHS) */
     double true_residual;      /* ||b - Zs I|| / ||b|| with the compressed operator (max over RHS) */
@@ -169,7 +168,8 @@ int vie_op_get_info(const vie_op* op, vie_op_info* info);
 /* vie_apply (Sec. 5.2: y = Z_D x + sum_far Q (R x)):
  * x, y: device pointers, n x nrhs, leading dimension ld (elements).
  * precision VIE_C64 (x, y c64), VIE_C128 (c128, needs C128 factors),
- * VIE_C64_ACC64 (x, y c128, c64 factors), VIE_BF16X3 (c64).
+ * VIE_C64_ACC64 (x, y c128, c64 factors).  (VIE_BF16X3 is reserved: refused
+ * with VIE_ERR_INVALID_ARG in this version.)
  * flags: VIE_APPLY_FUSE_PRECOND returns P^-1 Zs x instead of Zs x;
  * VIE_APPLY_DENSE applies the uncompressed matrix (works before vie_compress).
  * x and y must not overlap.  Asynchronous on `stream`. */
@@ -215,6 +215,9 @@ int vie_rhs(vie_op* op, const vie_incident* inc, int nrhs, void* b, int64_t ld, 
 /* vie_solve (Sec. 6: left-preconditioned GMRES, Sec. 4 preconditioner):
  * solves Zs I = b for the plane waves in `inc`; writes I (c128, n x nrhs,
  * column-major, ld = n) to I_out (host or device per opts->out_on_device).
+ * The right-hand sides iterate in lockstep: every Arnoldi step applies the
+ * operator once to all of them still iterating (each keeps its own Krylov
+ * space); the solve returns when all have converged or max_iters is hit.
  * Returns VIE_ERR_NOT_CONVERGED (I and stats still written) if max_iters is hit. */
 int vie_solve(vie_op* op, const vie_incident* inc, int nrhs, const vie_solve_opts* opts,
               void* I_out, vie_solve_stats* stats);

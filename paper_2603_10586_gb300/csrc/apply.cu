@@ -187,6 +187,135 @@ __global__ void __launch_bounds__(256) p2_kernel(const FarBlockDev* __restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// several right-hand sides: every factor element is read once per group of NR
+// right-hand sides (the single-RHS kernels above re-read it per column)
+// ---------------------------------------------------------------------------
+template <class TF, class TX, int NR>
+__global__ void __launch_bounds__(256, 2) p1m_kernel(const FarBlockDev* __restrict__ blocks,
+                                                  const int* __restrict__ batoms, const int4* __restrict__ items,
+                                                  const int* __restrict__ cta_ptr, const TF* __restrict__ factors,
+                                                  const TX* __restrict__ x, int64_t ldx, int np,
+                                                  TX* __restrict__ t, int64_t ldt, int nrhs) {
+    using TA = TX;
+    using R = decltype(TA().x);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1]; ++it) {
+        const int4 item = items[it];
+        const FarBlockDev B = blocks[item.x];
+        const TF* RH = factors + B.rh_off;
+        const int* S = batoms + B.s_off;
+        for (int k = item.y + warp * 2; k < item.z; k += nwarps * 2) {
+            const bool two = k + 1 < item.z;
+            const TF* row0 = RH + (int64_t)k * B.n;
+            const TF* row1 = RH + (int64_t)(two ? k + 1 : k) * B.n;
+            for (int c0 = 0; c0 < nrhs; c0 += NR) {
+                const int nr = min(NR, nrhs - c0);
+                TA a0[NR], a1[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) a0[r] = a1[r] = mk(R(0), R(0));
+                int c = 2 * lane;
+                int slot = c / np, off = c - slot * np;
+                for (; c < B.n; c += 64) {
+                    Pair<TF> ra = ldpair_stream(row0 + c);
+                    Pair<TF> rb = ldpair_stream(row1 + c);
+                    const TX* xb = x + (int64_t)S[slot] * np + off + (int64_t)c0 * ldx;
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        if (r < nr) {
+                            Pair<TX> xv = ldpair(xb + (int64_t)r * ldx);
+                            cfmac(a0[r], cvt<TA>(ra.a), xv.a);
+                            cfmac(a0[r], cvt<TA>(ra.b), xv.b);
+                            cfmac(a1[r], cvt<TA>(rb.a), xv.a);
+                            cfmac(a1[r], cvt<TA>(rb.b), xv.b);
+                        }
+                    }
+                    off += 64;
+                    while (off >= np) { off -= np; ++slot; }
+                }
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    TA v0 = a0[r], v1 = a1[r];
+                    for (int o = 16; o > 0; o >>= 1) {
+                        v0 += shfl_down2(v0, o);
+                        v1 += shfl_down2(v1, o);
+                    }
+                    if (lane == 0 && r < nr) {
+                        t[B.tvec_off + k + (int64_t)(c0 + r) * ldt] = v0;
+                        if (two) t[B.tvec_off + k + 1 + (int64_t)(c0 + r) * ldt] = v1;
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <class TF, class TX, int NR>
+__global__ void __launch_bounds__(256, 2) p2m_kernel(const FarBlockDev* __restrict__ blocks,
+                                                  const int4* __restrict__ items, const int* __restrict__ cta_ptr,
+                                                  const int* __restrict__ csr, const int2* __restrict__ ent,
+                                                  const TF* __restrict__ factors, const TX* __restrict__ t,
+                                                  int64_t ldt, int np, TX* __restrict__ F, int64_t ldf, int nrhs) {
+    using TA = TX;
+    using R = decltype(TA().x);
+    __shared__ TA red[3][64][2][NR];
+    const int rp = threadIdx.x & 63, kg = threadIdx.x >> 6;
+    for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1]; ++it) {
+        const int4 item = items[it];
+        const int a = item.x;
+        const int row = item.y + 2 * rp;
+        const bool active = row < item.z;
+        for (int c0 = 0; c0 < nrhs; c0 += NR) {
+            const int nr = min(NR, nrhs - c0);
+            TA a0[NR], a1[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) a0[r] = a1[r] = mk(R(0), R(0));
+            if (active) {
+                for (int e = csr[a]; e < csr[a + 1]; ++e) {
+                    const int2 en = ent[e];
+                    const FarBlockDev B = blocks[en.x];
+                    const TF* Q = factors + B.q_off + (int64_t)en.y * np + row;
+                    const TX* tb = t + B.tvec_off + (int64_t)c0 * ldt;
+                    for (int k = kg; k < B.rank; k += 4) {
+                        Pair<TF> q = ldpair_stream(Q + (int64_t)k * B.m);
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            if (r < nr) {
+                                TA tv = tb[k + (int64_t)r * ldt];
+                                cfma(a0[r], cvt<TA>(q.a), tv);
+                                cfma(a1[r], cvt<TA>(q.b), tv);
+                            }
+                        }
+                    }
+                }
+            }
+            if (kg > 0)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    red[kg - 1][rp][0][r] = a0[r];
+                    red[kg - 1][rp][1][r] = a1[r];
+                }
+            __syncthreads();
+            if (kg == 0 && active) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    if (r >= nr) continue;
+                    TA v0 = a0[r], v1 = a1[r];
+                    for (int g = 0; g < 3; ++g) {
+                        v0 += red[g][rp][0][r];
+                        v1 += red[g][rp][1][r];
+                    }
+                    TX* out = F + (int64_t)a * np + row + (int64_t)(c0 + r) * ldf;
+                    out[0] = v0;
+                    out[1] = v1;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 }  // namespace
 
 template <class TF, class TX>
@@ -195,6 +324,19 @@ void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, c
     if (op.d_t.bytes < need) op.d_t.alloc(need);
     const TF* fac = op.d_factors.as<TF>();
     const int nc = op.n_cta;
+    if (nrhs > 1) {
+        if (op.n_p1_items > 0) {
+            p1m_kernel<TF, TX, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
+                                                     op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, x, ldx,
+                                                     op.np, op.d_t.as<TX>(), op.t_total, nrhs);
+            VIE_CHECK_LAUNCH();
+        }
+        p2m_kernel<TF, TX, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
+                                                 op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(),
+                                                 fac, op.d_t.as<TX>(), op.t_total, op.np, F, ldf, nrhs);
+        VIE_CHECK_LAUNCH();
+        return;
+    }
     if (op.n_p1_items > 0) {
         p1_kernel<TF, TX, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
                                                 op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, x, ldx,

@@ -101,6 +101,7 @@ __global__ void k_gram_partial(const T2* Y, int m, int64_t stride, int nchunk, d
     __shared__ ACC rows[64][kChunk + 1];
     const int i = threadIdx.x % kChunk, j = threadIdx.x / kChunk;  // 1024 threads
     ACC acc = mk(R(0), R(0));
+    const bool upper = i <= j;  // Hermitian: the reduce mirrors the lower triangle
     for (int r0 = lo; r0 < hi; r0 += 64) {
         for (int e = threadIdx.x; e < 64 * kChunk; e += blockDim.x) {
             int rr = e % 64, cc = e / 64;
@@ -109,7 +110,8 @@ __global__ void k_gram_partial(const T2* Y, int m, int64_t stride, int nchunk, d
         }
         __syncthreads();
         int nr = min(64, hi - r0);
-        for (int rr = 0; rr < nr; ++rr) cfmac(acc, rows[rr][i], rows[rr][j]);
+        if (upper)
+            for (int rr = 0; rr < nr; ++rr) cfmac(acc, rows[rr][i], rows[rr][j]);
         __syncthreads();
     }
     part[((size_t)b * nchunk + c) * kChunk * kChunk + i + j * kChunk] = cvt<double2>(acc);
@@ -117,9 +119,12 @@ __global__ void k_gram_partial(const T2* Y, int m, int64_t stride, int nchunk, d
 __global__ void k_gram_reduce(const double2* part, int nchunk, double2* G) {
     const int b = blockIdx.x;
     const int e = threadIdx.x;  // kChunk^2 threads
+    const int i = e % kChunk, j = e / kChunk;
+    if (i > j) return;
     double2 s = make_double2(0, 0);
     for (int c = 0; c < nchunk; ++c) s += part[((size_t)b * nchunk + c) * kChunk * kChunk + e];
     G[(size_t)b * kChunk * kChunk + e] = s;
+    G[(size_t)b * kChunk * kChunk + j + i * kChunk] = make_double2(s.x, -s.y);
 }
 
 // Cholesky G = L L^H (float64, one block per batch entry) and Minv = L^-H
@@ -128,68 +133,69 @@ __global__ void k_gram_reduce(const double2* part, int nchunk, double2* G) {
 // the earlier ones are removed) marks the column dead (zero in Minv); what it
 // held stays in the residual and is picked up by a later sketch.
 template <class T2>
-__global__ void k_chol(const double2* G, T2* Minv, const int* active, unsigned char* alive, int rcap,
-                       const int* rbase) {
+__global__ void __launch_bounds__(kChunk * kChunk) k_chol(const double2* G, T2* Minv, const int* active,
+                                                          unsigned char* alive, int rcap, const int* rbase) {
     const int b = blockIdx.x;
     if (!active[b]) return;
     __shared__ double2 L[kChunk][kChunk + 1];
     __shared__ double2 X[kChunk][kChunk + 1];
     __shared__ int dead[kChunk];
     __shared__ double gmax;
-    const int t = threadIdx.x;  // kChunk threads
-    for (int j = 0; j < kChunk; ++j) L[t][j] = G[(size_t)b * kChunk * kChunk + t + j * kChunk];
-    dead[t] = 0;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // column, row
+    L[ty][tx] = G[(size_t)b * kChunk * kChunk + ty + tx * kChunk];
+    X[ty][tx] = make_double2(ty == tx ? 1.0 : 0.0, 0.0);
+    if (ty == 0) dead[tx] = 0;
     __syncthreads();
-    if (t == 0) {
-        double mx = 0.0;
-        for (int j = 0; j < kChunk; ++j) mx = fmax(mx, L[j][j].x);
-        gmax = mx;
+    if (ty == 0) {
+        double v = L[tx][tx].x;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+        if (tx == 0) gmax = v;
     }
     __syncthreads();
-    // right-looking Cholesky, column by column (thread t owns row t)
+    // right-looking Cholesky: one column per step, the trailing update in parallel
     for (int k = 0; k < kChunk; ++k) {
-        double d = L[k][k].x;
-        bool dk = !(d > 1e-8 * gmax) || gmax <= 0.0;
+        const double d = L[k][k].x;
+        const bool dk = !(d > 1e-8 * gmax) || gmax <= 0.0;
         __syncthreads();
-        if (t == 0) dead[k] = dk;
-        double sq = dk ? 0.0 : sqrt(d);
-        if (t > k) {
-            double2 v = L[t][k];
-            L[t][k] = dk ? make_double2(0, 0) : make_double2(v.x / sq, v.y / sq);
-        }
-        if (t == k) L[k][k] = make_double2(dk ? 1.0 : sq, 0.0);
-        __syncthreads();
-        if (t > k)
-            for (int j = k + 1; j <= t; ++j) {
-                // L[t][j] -= L[t][k] conj(L[j][k])
-                double2 a = L[t][k], c = L[j][k];
-                L[t][j].x -= a.x * c.x + a.y * c.y;
-                L[t][j].y -= a.y * c.x - a.x * c.y;
+        if (tx == k) {
+            if (ty > k) {
+                double2 v = L[ty][k];
+                double sq = dk ? 0.0 : sqrt(d);
+                L[ty][k] = dk ? make_double2(0, 0) : make_double2(v.x / sq, v.y / sq);
+            } else if (ty == k) {
+                L[k][k] = make_double2(dk ? 1.0 : sqrt(d), 0.0);
+                dead[k] = dk;
             }
+        }
+        __syncthreads();
+        if (ty > k && tx > k && tx <= ty) {
+            // L[i][j] -= L[i][k] conj(L[j][k])
+            double2 a = L[ty][k], c = L[tx][k];
+            L[ty][tx].x -= a.x * c.x + a.y * c.y;
+            L[ty][tx].y -= a.y * c.x - a.x * c.y;
+        }
         __syncthreads();
     }
-    // X = L^-1 (lower), column t solved by thread t
-    for (int i = 0; i < kChunk; ++i) X[i][t] = make_double2(0, 0);
-    for (int i = t; i < kChunk; ++i) {
-        double2 s = make_double2(i == t ? 1.0 : 0.0, 0.0);
-        for (int j = t; j < i; ++j) {
-            double2 a = L[i][j], x = X[j][t];
-            s.x -= a.x * x.x - a.y * x.y;
-            s.y -= a.x * x.y + a.y * x.x;
-        }
-        double2 d = L[i][i];
-        X[i][t] = make_double2(s.x / d.x, s.y / d.x);
-    }
-    __syncthreads();
-    // Minv = (L^-1)^H: Minv[i][j] = conj(X[j][i]); dead columns/rows zeroed
+    // X = L^-1 by forward substitution, all columns at once
     for (int j = 0; j < kChunk; ++j) {
-        double2 v = X[j][t];
-        bool z = dead[t] || dead[j];
-        Minv[(size_t)b * kChunk * kChunk + t + j * kChunk] =
-            z ? mk(decltype(Minv[0].x)(0), decltype(Minv[0].x)(0))
-              : mk(decltype(Minv[0].x)(v.x), decltype(Minv[0].x)(-v.y));
+        if (ty == j) {
+            const double dj = L[j][j].x;
+            X[j][tx] = make_double2(X[j][tx].x / dj, X[j][tx].y / dj);
+        }
+        __syncthreads();
+        if (ty > j) {
+            double2 a = L[ty][j], x = X[j][tx];
+            X[ty][tx].x -= a.x * x.x - a.y * x.y;
+            X[ty][tx].y -= a.x * x.y + a.y * x.x;
+        }
+        __syncthreads();
     }
-    if (alive && dead[t]) alive[(size_t)b * rcap + rbase[b] + t] = 0;
+    // Minv = (L^-1)^H: Minv[i][j] = conj(X[j][i]); dead columns and rows zeroed
+    using R = decltype(Minv[0].x);
+    const double2 v = X[tx][ty];
+    const bool z = dead[ty] || dead[tx];
+    Minv[(size_t)b * kChunk * kChunk + ty + tx * kChunk] = z ? mk(R(0), R(0)) : mk(R(v.x), R(-v.y));
+    if (tx == 0 && alive && dead[ty]) alive[(size_t)b * rcap + rbase[b] + ty] = 0;
 }
 
 // OUT[:, j] = sum_i Y[:, i] Minv[i][j] for active entries (row per thread)
@@ -472,8 +478,9 @@ struct Compressor {
                     VIE_CHECK_LAUNCH();
                     k_gram_reduce<<<nb, kChunk * kChunk, 0, s>>>(gpart.as<double2>(), nchunk, G.as<double2>());
                     VIE_CHECK_LAUNCH();
-                    k_chol<T2><<<nb, kChunk, 0, s>>>(G.as<double2>(), Minv.as<T2>(), d_active.as<int>(),
-                                                     alive.as<unsigned char>(), rcap_pad, d_rbase.as<int>());
+                    k_chol<T2><<<nb, dim3(kChunk, kChunk), 0, s>>>(G.as<double2>(), Minv.as<T2>(),
+                                                                    d_active.as<int>(), alive.as<unsigned char>(),
+                                                                    rcap_pad, d_rbase.as<int>());
                     VIE_CHECK_LAUNCH();
                     if (pass == 0) {
                         // in place: Yc <- Yc Minv (rows are independent)
@@ -662,6 +669,9 @@ void compress_operator(Op& op, double tol, int prec) {
     if (!(em && em[0] == '0')) {
         VIE_BLAS(cublasSetMathMode(op.ctx->blas, (cublasMath_t)(CUBLAS_FP32_EMULATED_BF16X9_MATH |
                                                                 CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH)));
+        // the formed blocks and sketches are finite: skip the emulation's
+        // inf/NaN scans of every operand
+        VIE_BLAS(cublasSetEmulationSpecialValuesSupport(op.ctx->blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE));
         const char* es = std::getenv("VIE_GEMM_EMULATION_STRATEGY");
         VIE_BLAS(cublasSetEmulationStrategy(op.ctx->blas, (es && es[0] == 'p') ? CUBLAS_EMULATION_STRATEGY_PERFORMANT
                                                                                  : CUBLAS_EMULATION_STRATEGY_EAGER));

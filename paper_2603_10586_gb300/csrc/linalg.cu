@@ -99,8 +99,9 @@ __global__ void c64_to_c128(const float2* s, double2* d, int64_t n) {
 // ---------------------------------------------------------------------------
 // Y[:, col] = M B[:, col] (+ ADD[:, col]) for the columns col = (atom of the
 // type, rhs).  M: np x np column-major.  Vector element (row r of atom a, rhs c)
-// lives at a * np + r + c * ld.  64 x 64 output tile per CTA, 256 threads,
-// each thread a 4 x 4 sub-tile; K staged through shared memory 16 at a time.
+// lives at a * np + r + c * ld.  32 x 32 output tile per CTA (enough CTAs for a
+// few hundred atoms), 256 threads, each a 2 x 2 sub-tile; K staged through
+// shared memory 32 at a time.
 // ---------------------------------------------------------------------------
 template <class TM, class TX>
 __global__ void __launch_bounds__(256) type_gemm(const TM* __restrict__ M, int np, const int* __restrict__ atoms,
@@ -109,15 +110,15 @@ __global__ void __launch_bounds__(256) type_gemm(const TM* __restrict__ M, int n
                                                  int64_t ldy) {
     using R = decltype(TM().x);
     using TA = typename C2<R>::t;
-    constexpr int BM = 64, BN = 64, BK = 16;
+    constexpr int BM = 32, BN = 32, BK = 32;
     __shared__ TA sM[BK][BM + 1];
     __shared__ TA sB[BK][BN + 1];
     const int ncols = n_atoms * nrhs;
     const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
-    const int tr = threadIdx.x % 16, tc = threadIdx.x / 16;  // 16 x 16 threads, 4 x 4 each
-    TA acc[4][4];
-    for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) acc[a][b] = mk(R(0), R(0));
+    const int tr = threadIdx.x % 16, tc = threadIdx.x / 16;  // 16 x 16 threads, 2 x 2 each
+    TA acc[2][2];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) acc[a][b] = mk(R(0), R(0));
     // column -> (atom, rhs) base offsets for the B loads of this tile
     for (int k0 = 0; k0 < np; k0 += BK) {
         for (int e = threadIdx.x; e < BK * BM; e += 256) {
@@ -138,19 +139,19 @@ __global__ void __launch_bounds__(256) type_gemm(const TM* __restrict__ M, int n
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            TA mv[4], bv[4];
-            for (int a = 0; a < 4; ++a) mv[a] = sM[kk][tr + 16 * a];
-            for (int b = 0; b < 4; ++b) bv[b] = sB[kk][tc + 16 * b];
-            for (int a = 0; a < 4; ++a)
-                for (int b = 0; b < 4; ++b) cfma(acc[a][b], mv[a], bv[b]);
+            TA mv[2], bv[2];
+            for (int a = 0; a < 2; ++a) mv[a] = sM[kk][tr + 16 * a];
+            for (int b = 0; b < 2; ++b) bv[b] = sB[kk][tc + 16 * b];
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) cfma(acc[a][b], mv[a], bv[b]);
         }
         __syncthreads();
     }
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < 2; ++b) {
         int gc = col0 + tc + 16 * b;
         if (gc >= ncols) continue;
         int a_ = atoms[gc % n_atoms], rhs = gc / n_atoms;
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < 2; ++a) {
             int gr = row0 + tr + 16 * a;
             if (gr >= np) continue;
             TA v = acc[a][b];
@@ -212,7 +213,7 @@ void self_gemm(Op& op, const TM* M, const TX* X, int64_t ldx, const TX* C, int64
         if (na == 0) continue;
         const int* atoms = op.d_atoms_by_type.as<int>() + op.type_atom_off[t];
         const TM* Mt = M + (size_t)t * np * np;
-        dim3 grid((np + 63) / 64, (na * nrhs + 63) / 64);
+        dim3 grid((np + 31) / 32, (na * nrhs + 31) / 32);
         const TX* Bop = mode == 1 ? C : X;
         int64_t ldb = mode == 1 ? ldc : ldx;
         const TX* ADD = mode == 0 ? C : (mode == 1 ? X : nullptr);
