@@ -222,6 +222,36 @@ def run_serving(args):
     return 0
 
 
+def run_profile(args):
+    """--profile: one untimed solve from geometry followed by 20 fused applies, for
+    ncu captures (no warm-up, no timing, no baseline).  --profile-case small uses
+    the 8x8 array of 6^3-voxel cubes (48,384 unknowns; factors ~1.6 GB, above L2)
+    and skips the solve."""
+    import torch
+    from paper_2603_10586_gb300 import vie
+    torch.cuda.set_device(0)
+    ctx = vie.Context(0)
+    if args.profile_case == "small":
+        g, kh, pol = workloads.square_array(8, 6), *workloads.normal_incidence()
+    else:
+        g, kh, pol = workloads.config(WORKLOAD)
+    op = vie.Operator(ctx, g)
+    info = op.compress(TOL_COMPRESS, vie.C64)
+    if args.profile_case != "small":
+        out = torch.empty(op.n, dtype=torch.complex128, device="cuda")
+        op.solve(kh, pol, tol=TOL_SOLVE, out_ptr=out.data_ptr())
+    x = torch.randn(op.n, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(20 if args.profile_case != "small" else 3):
+        op.apply(x.data_ptr(), y.data_ptr(), 1, vie.C64, vie.FUSE_PRECOND)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "n": op.n, "factor_entries": info["factor_entries"],
+                      "apply_bytes": info["apply_bytes"]}), flush=True)
+    op.close()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -233,7 +263,11 @@ def main():
     ap.add_argument("--serving", action="store_true", help="the request-stream workload instead")
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--profile", action="store_true", help="one untimed step for ncu captures")
+    ap.add_argument("--profile-case", default="scale", choices=["scale", "small"])
     args = ap.parse_args()
+    if args.profile:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.serving:

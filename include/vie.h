@@ -123,7 +123,9 @@ typedef struct vie_solve_opts {
     int restart;               /* GMRES restart length m (e.g. 60) */
     int max_iters;             /* iteration cap (e.g. 2000) */
     int precision;             /* VIE_C64: FP32 inner applies with FP64 Krylov and FP64
-                                  residual refinement; VIE_C128: all-FP64 (needs C128 factors) */
+                                  residual refinement; VIE_BF16X3: as VIE_C64 but the far part of
+                                  the inner applies on the tensor cores (split bf16, FP32 accumulation);
+                                  VIE_C128: all-FP64 (needs C128 factors) */
     int out_on_device;         /* 1: I_out is a device pointer, 0: host pointer */
     int precond;               /* 1: block-diagonal preconditioner (default), 0: none */
 } vie_solve_opts;
@@ -168,8 +170,8 @@ int vie_op_get_info(const vie_op* op, vie_op_info* info);
 /* vie_apply (Sec. 5.2: y = Z_D x + sum_far Q (R x)):
  * x, y: device pointers, n x nrhs, leading dimension ld (elements).
  * precision VIE_C64 (x, y c64), VIE_C128 (c128, needs C128 factors),
- * VIE_C64_ACC64 (x, y c128, c64 factors).  (VIE_BF16X3 is reserved: refused
- * with VIE_ERR_INVALID_ARG in this version.)
+ * VIE_C64_ACC64 (x, y c128, c64 factors), VIE_BF16X3 (x, y c64, c64 factors;
+ * the far part on the tensor cores, relative error ~1e-5).
  * flags: VIE_APPLY_FUSE_PRECOND returns P^-1 Zs x instead of Zs x;
  * VIE_APPLY_DENSE applies the uncompressed matrix (works before vie_compress).
  * x and y must not overlap.  Asynchronous on `stream`. */

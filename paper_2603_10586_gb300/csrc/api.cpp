@@ -37,6 +37,15 @@ void op_apply_fused32(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t
     self_gemm<float2, float2>(op, op.d_inv32.as<float2>(), x, n, F, n, y, n, nrhs, 1, s);
 }
 
+void op_apply_fused_bf16x3(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s) {
+    if (op.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "VIE_BF16X3 applies need VIE_C64 factors");
+    const int64_t n = op.n();
+    ensure_F(op, (size_t)n * nrhs * sizeof(float2));
+    float2* F = op.d_F.as<float2>();
+    apply_far_bf16x3(op, x, n, F, n, nrhs, s);
+    self_gemm<float2, float2>(op, op.d_inv32.as<float2>(), x, n, F, n, y, n, nrhs, 1, s);
+}
+
 void op_apply64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s) {
     const int64_t n = op.n();
     ensure_F(op, (size_t)n * nrhs * sizeof(double2));
@@ -341,6 +350,16 @@ int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int prec
                 ensure_F(o, (size_t)o.n() * nrhs * sizeof(float2));
                 float2* F = o.d_F.as<float2>();
                 apply_far<float2, float2>(o, (const float2*)x, o.n(), F, o.n(), nrhs, s);
+                self_gemm<float2, float2>(o, o.d_zself32.as<float2>(), (const float2*)x, o.n(), F, o.n(),
+                                          (float2*)y, o.n(), nrhs, 0, s);
+            }
+        } else if (precision == VIE_BF16X3) {
+            if (fuse) op_apply_fused_bf16x3(o, (const float2*)x, (float2*)y, nrhs, s);
+            else {
+                if (o.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "VIE_BF16X3 applies need VIE_C64 factors");
+                ensure_F(o, (size_t)o.n() * nrhs * sizeof(float2));
+                float2* F = o.d_F.as<float2>();
+                apply_far_bf16x3(o, (const float2*)x, o.n(), F, o.n(), nrhs, s);
                 self_gemm<float2, float2>(o, o.d_zself32.as<float2>(), (const float2*)x, o.n(), F, o.n(),
                                           (float2*)y, o.n(), nrhs, 0, s);
             }

@@ -159,6 +159,8 @@ struct Op {
     DevBuf d_p1_items, d_p1_cta;       // phase 1 items and per-CTA ranges
     DevBuf d_p2_items, d_p2_cta, d_p2_csr, d_p2_ent;
     int n_p1_items = 0, n_p2_items = 0, n_cta = 0;
+    DevBuf d_t1_items, d_t1_cta, d_t2_items, d_t2_cta;  // tensor-core path (64-row items)
+    int n_t1_items = 0, n_t2_items = 0, n_cta_tc = 0;
     // scratch
     DevBuf d_t, d_F;
     size_t t_cap = 0, F_cap = 0;
@@ -229,6 +231,8 @@ template <class TF, class TX>
 void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, cudaStream_t s);
 
 void apply_static(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s);
+// apply_tc.cu: several right-hand sides on the tensor cores (BF16x3)
+void apply_far_bf16x3(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
 
 // compress.cu
 void compress_operator(Op& op, double tol, int prec);

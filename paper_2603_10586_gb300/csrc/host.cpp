@@ -296,6 +296,33 @@ void build_apply_lists(Op& op) {
     op.n_p2_items = (int)p2.size();
     upload(op.d_p2_items, p2);
     upload(op.d_p2_cta, c2);
+
+    // tensor-core path: 64-row output tiles (rows of R_b, rows of an atom)
+    op.n_cta_tc = op.ctx->n_sm * 4;
+    std::vector<int4> t1, t2;
+    std::vector<double> wt1, wt2;
+    for (int i = 0; i < nb; ++i) {
+        const auto& b = op.blocks[i];
+        for (int k0 = 0; k0 < b.rank; k0 += 64) {
+            t1.push_back(make_int4(i, k0, std::min(b.rank, k0 + 64), 0));
+            wt1.push_back(64.0 * b.n);
+        }
+    }
+    for (int a = 0; a < op.N; ++a)
+        for (int p0 = 0; p0 < op.np; p0 += 64) {
+            t2.push_back(make_int4(a, p0, std::min(op.np, p0 + 64), 0));
+            wt2.push_back(64.0 * (rsum[a] + 1.0));
+        }
+    std::vector<int4> q1, q2;
+    std::vector<int> e1, e2;
+    pack_lpt(t1, wt1, op.n_cta_tc, q1, e1);
+    pack_lpt(t2, wt2, op.n_cta_tc, q2, e2);
+    op.n_t1_items = (int)q1.size();
+    op.n_t2_items = (int)q2.size();
+    upload(op.d_t1_items, q1.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : q1);
+    upload(op.d_t1_cta, e1);
+    upload(op.d_t2_items, q2);
+    upload(op.d_t2_cta, e2);
     upload(op.d_p2_csr, csr);
     upload(op.d_p2_ent, flat.empty() ? std::vector<int2>{make_int2(0, 0)} : flat);
 }

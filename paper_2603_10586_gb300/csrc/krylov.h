@@ -20,6 +20,8 @@ void ksub(const double2* a, const double2* b, double2* y, int64_t n, cudaStream_
 // operator applications used by the solver (solve.cpp / api.cpp)
 // y = P^-1 Zs x in complex float32 (fused preconditioner), x, y: n x nrhs, ld = n
 void op_apply_fused32(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s);
+// y = P^-1 Zs x with the far part on the tensor cores (BF16x3), float32 vectors
+void op_apply_fused_bf16x3(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s);
 // y = Zs x with float64 vectors; factors in their stored precision (float64 accumulation)
 void op_apply64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s);
 // y = P^-1 Zs x in float64 (needs C128 factors for an all-float64 solve)

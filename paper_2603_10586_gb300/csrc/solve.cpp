@@ -7,7 +7,9 @@
 // Givens rotations are float64.  At the end of every cycle the residual
 // P^-1 (b - Zs x) is recomputed in float64 (c64 factors read exactly, float64
 // accumulation): this is the iterative refinement step, and the stopping test
-// uses that true residual.  With VIE_C128 every apply is float64.
+// uses that true residual.  With VIE_C128 every apply is float64; with
+// VIE_BF16X3 the far part of the inner applies runs on the tensor cores in
+// split-precision bf16 (the refinement residual stays float64).
 //
 // Several right-hand sides advance in lockstep: each Arnoldi step gathers the
 // current basis vector of every right-hand side still iterating into one
@@ -77,7 +79,8 @@ struct Gmres {
             return;
         }
         convert_c128_to_c64(in, X32.p, n * k, s);
-        op_apply_fused32(op, X32.as<float2>(), Y32.as<float2>(), k, s);
+        if (o.precision == VIE_BF16X3) op_apply_fused_bf16x3(op, X32.as<float2>(), Y32.as<float2>(), k, s);
+        else op_apply_fused32(op, X32.as<float2>(), Y32.as<float2>(), k, s);
         convert_c64_to_c128(Y32.p, out, n * k, s);
     }
 
@@ -207,8 +210,8 @@ int solve(Op& op, const vie_incident* inc, int nrhs, const vie_solve_opts* o, vo
     if (op.fprec == 0) fail(VIE_ERR_STATE, "operator is not compressed");
     if (o->precision == VIE_C128 && op.fprec != VIE_C128)
         fail(VIE_ERR_INVALID_ARG, "an all-float64 solve needs VIE_C128 factors");
-    if (o->precision != VIE_C128 && o->precision != VIE_C64 && o->precision != 0)
-        fail(VIE_ERR_INVALID_ARG, "solve precision must be VIE_C64 or VIE_C128");
+    if (o->precision != VIE_C128 && o->precision != VIE_C64 && o->precision != VIE_BF16X3 && o->precision != 0)
+        fail(VIE_ERR_INVALID_ARG, "solve precision must be VIE_C64, VIE_BF16X3 or VIE_C128");
     cudaStream_t s = op.ctx->stream;
     const int64_t n = op.n();
     double t0 = now_s();

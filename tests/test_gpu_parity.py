@@ -259,3 +259,29 @@ def test_multi_rhs_apply_reads_factors_once(ctx, tiny_op, tiny_dense):
         tiny_op.apply(X[c].data_ptr(), y1.data_ptr(), 1, vie.C64, vie.FUSE_PRECOND)
         th.cuda.synchronize()
         assert rel(Y[c].cpu().numpy(), y1.cpu().numpy()) < 1e-6
+
+
+# ------------------------------------------------- BF16x3 tensor-core far apply
+@pytest.mark.parametrize("nrhs", [1, 5, 64, 70])
+def test_bf16x3_apply_against_c64(tiny_op, tiny_dense, nrhs):
+    # split-precision bf16 (hi.hi + hi.lo + lo.hi, float32 accumulation): the
+    # dropped lo.lo term and the bf16 remainders give ~1e-5 relative
+    import torch as th
+    P, Z, _, _, _ = tiny_dense
+    orc, sb = _oracle_op_from_gpu(tiny_op, P, Z)
+    xs = workloads.random_complex(P.n, 31, cols=nrhs).T.copy()
+    X = th.from_numpy(xs.astype(np.complex64)).cuda()
+    Y = th.zeros_like(X)
+    tiny_op.apply(X.data_ptr(), Y.data_ptr(), nrhs, vie.BF16X3, 0)
+    th.cuda.synchronize()
+    ref = np.stack([orc.apply(x) for x in xs])
+    assert rel(Y.cpu().numpy(), ref) < 5e-5
+
+
+def test_bf16x3_multi_rhs_solve(tiny_op, tiny_dense):
+    P, Z, _, _, _ = tiny_dense
+    kh, pol = workloads.angle_sweep(4, 60.0)           # 8 right-hand sides
+    I, st, status = tiny_op.solve(kh, pol, tol=1e-6, precision=vie.BF16X3)
+    assert status == vie.VIE_OK and st["residual"] <= 1e-6
+    for c in range(len(kh)):
+        assert rel(I[:, c], np.linalg.solve(Z, A.rhs(P, kh[c], pol[c]))) <= 5e-4
