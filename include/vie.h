@@ -128,6 +128,9 @@ typedef struct vie_solve_opts {
                                   VIE_C128: all-FP64 (needs C128 factors) */
     int out_on_device;         /* 1: I_out is a device pointer, 0: host pointer */
     int precond;               /* 1: block-diagonal preconditioner (default), 0: none */
+    int launch;                /* 0: each restart cycle is one CUDA graph (Arnoldi steps in a
+                                  conditional while-node, no host round trip inside a cycle);
+                                  1: the host launches every step and reads the continue flag */
 } vie_solve_opts;
 
 typedef struct vie_solve_stats {

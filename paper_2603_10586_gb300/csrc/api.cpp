@@ -51,7 +51,7 @@ void op_apply64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s) 
     ensure_F(op, (size_t)n * nrhs * sizeof(double2));
     double2* F = op.d_F.as<double2>();
     if (op.fprec == VIE_C128) apply_far<double2, double2>(op, x, n, F, n, nrhs, s);
-    else apply_far<float2, double2>(op, x, n, F, n, nrhs, s);
+    else apply_far_df(op, x, n, F, n, nrhs, s);
     self_gemm<double2, double2>(op, op.d_zself64.as<double2>(), x, n, F, n, y, n, nrhs, 0, s);
 }
 
@@ -60,8 +60,16 @@ void op_apply_fused64(Op& op, const double2* x, double2* y, int nrhs, cudaStream
     ensure_F(op, (size_t)n * nrhs * sizeof(double2));
     double2* F = op.d_F.as<double2>();
     if (op.fprec == VIE_C128) apply_far<double2, double2>(op, x, n, F, n, nrhs, s);
-    else apply_far<float2, double2>(op, x, n, F, n, nrhs, s);
+    else apply_far_df(op, x, n, F, n, nrhs, s);
     self_gemm<double2, double2>(op, op.d_inv64.as<double2>(), x, n, F, n, y, n, nrhs, 1, s);
+}
+
+void op_reserve(Op& op, int nrhs) {
+    ensure_F(op, (size_t)op.n() * nrhs * sizeof(double2));
+    const size_t need = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(double2);
+    if (op.d_t.bytes < need) op.d_t.alloc(need);
+    const size_t need_x = (size_t)op.n() * nrhs * sizeof(float4);
+    if (op.fprec == VIE_C64 && op.d_xs.bytes < need_x) op.d_xs.alloc(need_x);
 }
 
 void op_precond64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s) {

@@ -45,6 +45,94 @@ template <class T2> __device__ __forceinline__ T2 shfl_down2(T2 v, int o) {
 }
 
 // ---------------------------------------------------------------------------
+// Accumulation.  Float32 and float64 vectors accumulate in their own
+// precision.  For the float64 refinement residual the vectors come split into
+// float32 head + tail (float4: re_h, im_h, re_l, im_l) and the products with
+// the exact float32 factors are summed in double-float arithmetic: each
+// product is formed exactly with an FMA (Dekker's two-product), each addition
+// keeps its rounding error (Knuth's two-sum), so a sum carries about 48
+// significant bits while every operation runs on the float32 pipes (the
+// float64 pipe of this GPU is a small fraction of the float32 one).
+// ---------------------------------------------------------------------------
+struct Dfc { float rh, rl, ih, il; };  // (rh + rl) + j (ih + il)
+
+template <class TX> struct AccOf { using t = TX; };
+template <> struct AccOf<float4> { using t = Dfc; };
+
+template <class TA> __device__ __forceinline__ TA acc_zero();
+template <> __device__ __forceinline__ float2 acc_zero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 acc_zero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ Dfc acc_zero<Dfc>() { return {0.f, 0.f, 0.f, 0.f}; }
+
+// acc += conj(a) x  and  acc += a x
+__device__ __forceinline__ void mac_conj(float2& acc, float2 a, float2 x) { cfmac(acc, a, x); }
+__device__ __forceinline__ void mac_conj(double2& acc, float2 a, double2 x) { cfmac(acc, cvt<double2>(a), x); }
+__device__ __forceinline__ void mac_conj(double2& acc, double2 a, double2 x) { cfmac(acc, a, x); }
+__device__ __forceinline__ void mac(float2& acc, float2 a, float2 x) { cfma(acc, a, x); }
+__device__ __forceinline__ void mac(double2& acc, float2 a, double2 x) { cfma(acc, cvt<double2>(a), x); }
+__device__ __forceinline__ void mac(double2& acc, double2 a, double2 x) { cfma(acc, a, x); }
+
+// (h, l) += a (bh + bl): the product a bh exactly as p + e, the tail a bl
+// folded into e, then h + p by two-sum with its error and e added to l.
+// The _rn intrinsics keep the compiler from fusing these steps.
+__device__ __forceinline__ void df_acc(float& h, float& l, float a, float bh, float bl) {
+    const float p = __fmul_rn(a, bh);
+    float e = fmaf(a, bh, -p);
+    e = fmaf(a, bl, e);
+    const float sum = __fadd_rn(h, p);
+    const float bv = __fsub_rn(sum, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(sum, bv)), __fsub_rn(p, bv));
+    h = sum;
+    l = __fadd_rn(l, __fadd_rn(err, e));
+}
+__device__ __forceinline__ void mac_conj(Dfc& acc, float2 a, float4 x) {
+    df_acc(acc.rh, acc.rl, a.x, x.x, x.z);
+    df_acc(acc.rh, acc.rl, a.y, x.y, x.w);
+    df_acc(acc.ih, acc.il, a.x, x.y, x.w);
+    df_acc(acc.ih, acc.il, -a.y, x.x, x.z);
+}
+__device__ __forceinline__ void mac(Dfc& acc, float2 a, float4 x) {
+    df_acc(acc.rh, acc.rl, a.x, x.x, x.z);
+    df_acc(acc.rh, acc.rl, -a.y, x.y, x.w);
+    df_acc(acc.ih, acc.il, a.x, x.y, x.w);
+    df_acc(acc.ih, acc.il, a.y, x.x, x.z);
+}
+
+__device__ __forceinline__ void acc_add(float2& a, float2 b) { a += b; }
+__device__ __forceinline__ void acc_add(double2& a, double2 b) { a += b; }
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
+    const float sum = __fadd_rn(h, bh);
+    const float bv = __fsub_rn(sum, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(sum, bv)), __fsub_rn(bh, bv));
+    h = sum;
+    l = __fadd_rn(__fadd_rn(l, bl), err);
+}
+__device__ __forceinline__ void acc_add(Dfc& a, const Dfc& b) {
+    df_add(a.rh, a.rl, b.rh, b.rl);
+    df_add(a.ih, a.il, b.ih, b.il);
+}
+
+__device__ __forceinline__ float2 acc_shfl_down(float2 v, int o) { return shfl_down2(v, o); }
+__device__ __forceinline__ double2 acc_shfl_down(double2 v, int o) { return shfl_down2(v, o); }
+__device__ __forceinline__ Dfc acc_shfl_down(Dfc v, int o) {
+    return {__shfl_down_sync(0xffffffffu, v.rh, o), __shfl_down_sync(0xffffffffu, v.rl, o),
+            __shfl_down_sync(0xffffffffu, v.ih, o), __shfl_down_sync(0xffffffffu, v.il, o)};
+}
+
+__device__ __forceinline__ void store(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void store(double2* p, double2 v) { *p = v; }
+__device__ __forceinline__ void store(double2* p, const Dfc& v) {
+    *p = make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
+}
+// renormalised head + tail (fast two-sum, the head dominates)
+__device__ __forceinline__ void store(float4* p, const Dfc& v) {
+    const float sr = __fadd_rn(v.rh, v.rl), si = __fadd_rn(v.ih, v.il);
+    *p = make_float4(sr, si, __fsub_rn(v.rl, __fsub_rn(sr, v.rh)), __fsub_rn(v.il, __fsub_rn(si, v.ih)));
+}
+
+__device__ __forceinline__ Pair<float4> ldpair(const float4* p) { return {__ldg(p), __ldg(p + 1)}; }
+
+// ---------------------------------------------------------------------------
 // phase 1: one warp per group of ROWS rows of R_b, lanes stride over columns
 // ---------------------------------------------------------------------------
 template <class TF, class TX, int ROWS>
@@ -53,8 +141,7 @@ __global__ void __launch_bounds__(256, 3) p1_kernel(const FarBlockDev* __restric
                                                  const int* __restrict__ cta_ptr, const TF* __restrict__ factors,
                                                  const TX* __restrict__ x, int64_t ldx, int np,
                                                  TX* __restrict__ t, int64_t ldt, int nrhs) {
-    using TA = TX;  // accumulate in the vector precision
-    using R = decltype(TA().x);
+    using TA = typename AccOf<TX>::t;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1]; ++it) {
@@ -70,7 +157,7 @@ __global__ void __launch_bounds__(256, 3) p1_kernel(const FarBlockDev* __restric
             for (int c0 = 0; c0 < nrhs; ++c0) {
                 TA acc[ROWS];
 #pragma unroll
-                for (int r = 0; r < ROWS; ++r) acc[r] = mk(R(0), R(0));
+                for (int r = 0; r < ROWS; ++r) acc[r] = acc_zero<TA>();
                 const TX* xc = x + (int64_t)c0 * ldx;
                 // column c = 2 lane + 64 i; two positions (c, c + 64) per iteration;
                 // (slot, off) of each tracked incrementally
@@ -89,10 +176,10 @@ __global__ void __launch_bounds__(256, 3) p1_kernel(const FarBlockDev* __restric
                     }
 #pragma unroll
                     for (int r = 0; r < ROWS; ++r) {
-                        cfmac(acc[r], cvt<TA>(ra[r].a), xa.a);
-                        cfmac(acc[r], cvt<TA>(ra[r].b), xa.b);
-                        cfmac(acc[r], cvt<TA>(rb[r].a), xb.a);
-                        cfmac(acc[r], cvt<TA>(rb[r].b), xb.b);
+                        mac_conj(acc[r], ra[r].a, xa.a);
+                        mac_conj(acc[r], ra[r].b, xa.b);
+                        mac_conj(acc[r], rb[r].a, xb.a);
+                        mac_conj(acc[r], rb[r].b, xb.b);
                     }
                     off = off2 + 64;
                     slot = slot2;
@@ -103,15 +190,15 @@ __global__ void __launch_bounds__(256, 3) p1_kernel(const FarBlockDev* __restric
 #pragma unroll
                     for (int r = 0; r < ROWS; ++r) {
                         Pair<TF> ra = ldpair_stream(rows[r] + c);
-                        cfmac(acc[r], cvt<TA>(ra.a), xa.a);
-                        cfmac(acc[r], cvt<TA>(ra.b), xa.b);
+                        mac_conj(acc[r], ra.a, xa.a);
+                        mac_conj(acc[r], ra.b, xa.b);
                     }
                 }
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
                     TA v = acc[r];
-                    for (int o = 16; o > 0; o >>= 1) v += shfl_down2(v, o);
-                    if (lane == 0 && r < nrow) t[B.tvec_off + k + r + (int64_t)c0 * ldt] = v;
+                    for (int o = 16; o > 0; o >>= 1) acc_add(v, acc_shfl_down(v, o));
+                    if (lane == 0 && r < nrow) store(&t[B.tvec_off + k + r + (int64_t)c0 * ldt], v);
                 }
             }
         }
@@ -123,14 +210,13 @@ __global__ void __launch_bounds__(256, 3) p1_kernel(const FarBlockDev* __restric
 // 4 rank groups; each thread streams Q column segments of 2 rows and the
 // partial sums of the 4 rank groups are added in a fixed order at the end.
 // ---------------------------------------------------------------------------
-template <class TF, class TX>
+template <class TF, class TX, class TO>
 __global__ void __launch_bounds__(256) p2_kernel(const FarBlockDev* __restrict__ blocks,
                                                  const int4* __restrict__ items, const int* __restrict__ cta_ptr,
                                                  const int* __restrict__ csr, const int2* __restrict__ ent,
                                                  const TF* __restrict__ factors, const TX* __restrict__ t,
-                                                 int64_t ldt, int np, TX* __restrict__ F, int64_t ldf, int nrhs) {
-    using TA = TX;
-    using R = decltype(TA().x);
+                                                 int64_t ldt, int np, TO* __restrict__ F, int64_t ldf, int nrhs) {
+    using TA = typename AccOf<TX>::t;
     __shared__ TA red[3][64][2];
     const int rp = threadIdx.x & 63, kg = threadIdx.x >> 6;
     for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1]; ++it) {
@@ -139,7 +225,7 @@ __global__ void __launch_bounds__(256) p2_kernel(const FarBlockDev* __restrict__
         const int row = item.y + 2 * rp;
         const bool active = row < item.z;
         for (int c0 = 0; c0 < nrhs; ++c0) {
-            TA acc0 = mk(R(0), R(0)), acc1 = mk(R(0), R(0));
+            TA acc0 = acc_zero<TA>(), acc1 = acc_zero<TA>();
             if (active) {
                 for (int e = csr[a]; e < csr[a + 1]; ++e) {
                     const int2 en = ent[e];
@@ -149,22 +235,22 @@ __global__ void __launch_bounds__(256) p2_kernel(const FarBlockDev* __restrict__
                     int k = kg;
                     for (; k + 28 < B.rank; k += 32) {
                         Pair<TF> q[8];
-                        TA tv[8];
+                        TX tv[8];
 #pragma unroll
                         for (int u = 0; u < 8; ++u) q[u] = ldpair_stream(Q + (int64_t)(k + 4 * u) * B.m);
 #pragma unroll
                         for (int u = 0; u < 8; ++u) tv[u] = tb[k + 4 * u];
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
-                            cfma(acc0, cvt<TA>(q[u].a), tv[u]);
-                            cfma(acc1, cvt<TA>(q[u].b), tv[u]);
+                            mac(acc0, q[u].a, tv[u]);
+                            mac(acc1, q[u].b, tv[u]);
                         }
                     }
                     for (; k < B.rank; k += 4) {
                         Pair<TF> q0 = ldpair_stream(Q + (int64_t)k * B.m);
-                        TA t0 = tb[k];
-                        cfma(acc0, cvt<TA>(q0.a), t0);
-                        cfma(acc1, cvt<TA>(q0.b), t0);
+                        const TX t0 = tb[k];
+                        mac(acc0, q0.a, t0);
+                        mac(acc1, q0.b, t0);
                     }
                 }
             }
@@ -175,12 +261,12 @@ __global__ void __launch_bounds__(256) p2_kernel(const FarBlockDev* __restrict__
             __syncthreads();
             if (kg == 0 && active) {
                 for (int g = 0; g < 3; ++g) {
-                    acc0 += red[g][rp][0];
-                    acc1 += red[g][rp][1];
+                    acc_add(acc0, red[g][rp][0]);
+                    acc_add(acc1, red[g][rp][1]);
                 }
-                TX* out = F + (int64_t)a * np + row + (int64_t)c0 * ldf;
-                out[0] = acc0;
-                out[1] = acc1;
+                TO* out = F + (int64_t)a * np + row + (int64_t)c0 * ldf;
+                store(out, acc0);
+                store(out + 1, acc1);
             }
             __syncthreads();
         }
@@ -197,8 +283,7 @@ __global__ void __launch_bounds__(256, 2) p1m_kernel(const FarBlockDev* __restri
                                                   const int* __restrict__ cta_ptr, const TF* __restrict__ factors,
                                                   const TX* __restrict__ x, int64_t ldx, int np,
                                                   TX* __restrict__ t, int64_t ldt, int nrhs) {
-    using TA = TX;
-    using R = decltype(TA().x);
+    using TA = typename AccOf<TX>::t;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1]; ++it) {
@@ -214,7 +299,7 @@ __global__ void __launch_bounds__(256, 2) p1m_kernel(const FarBlockDev* __restri
                 const int nr = min(NR, nrhs - c0);
                 TA a0[NR], a1[NR];
 #pragma unroll
-                for (int r = 0; r < NR; ++r) a0[r] = a1[r] = mk(R(0), R(0));
+                for (int r = 0; r < NR; ++r) a0[r] = a1[r] = acc_zero<TA>();
                 int c = 2 * lane;
                 int slot = c / np, off = c - slot * np;
                 for (; c < B.n; c += 64) {
@@ -225,10 +310,10 @@ __global__ void __launch_bounds__(256, 2) p1m_kernel(const FarBlockDev* __restri
                     for (int r = 0; r < NR; ++r) {
                         if (r < nr) {
                             Pair<TX> xv = ldpair(xb + (int64_t)r * ldx);
-                            cfmac(a0[r], cvt<TA>(ra.a), xv.a);
-                            cfmac(a0[r], cvt<TA>(ra.b), xv.b);
-                            cfmac(a1[r], cvt<TA>(rb.a), xv.a);
-                            cfmac(a1[r], cvt<TA>(rb.b), xv.b);
+                            mac_conj(a0[r], ra.a, xv.a);
+                            mac_conj(a0[r], ra.b, xv.b);
+                            mac_conj(a1[r], rb.a, xv.a);
+                            mac_conj(a1[r], rb.b, xv.b);
                         }
                     }
                     off += 64;
@@ -238,12 +323,12 @@ __global__ void __launch_bounds__(256, 2) p1m_kernel(const FarBlockDev* __restri
                 for (int r = 0; r < NR; ++r) {
                     TA v0 = a0[r], v1 = a1[r];
                     for (int o = 16; o > 0; o >>= 1) {
-                        v0 += shfl_down2(v0, o);
-                        v1 += shfl_down2(v1, o);
+                        acc_add(v0, acc_shfl_down(v0, o));
+                        acc_add(v1, acc_shfl_down(v1, o));
                     }
                     if (lane == 0 && r < nr) {
-                        t[B.tvec_off + k + (int64_t)(c0 + r) * ldt] = v0;
-                        if (two) t[B.tvec_off + k + 1 + (int64_t)(c0 + r) * ldt] = v1;
+                        store(&t[B.tvec_off + k + (int64_t)(c0 + r) * ldt], v0);
+                        if (two) store(&t[B.tvec_off + k + 1 + (int64_t)(c0 + r) * ldt], v1);
                     }
                 }
             }
@@ -251,14 +336,13 @@ __global__ void __launch_bounds__(256, 2) p1m_kernel(const FarBlockDev* __restri
     }
 }
 
-template <class TF, class TX, int NR>
+template <class TF, class TX, class TO, int NR>
 __global__ void __launch_bounds__(256, 2) p2m_kernel(const FarBlockDev* __restrict__ blocks,
                                                   const int4* __restrict__ items, const int* __restrict__ cta_ptr,
                                                   const int* __restrict__ csr, const int2* __restrict__ ent,
                                                   const TF* __restrict__ factors, const TX* __restrict__ t,
-                                                  int64_t ldt, int np, TX* __restrict__ F, int64_t ldf, int nrhs) {
-    using TA = TX;
-    using R = decltype(TA().x);
+                                                  int64_t ldt, int np, TO* __restrict__ F, int64_t ldf, int nrhs) {
+    using TA = typename AccOf<TX>::t;
     __shared__ TA red[3][64][2][NR];
     const int rp = threadIdx.x & 63, kg = threadIdx.x >> 6;
     for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1]; ++it) {
@@ -270,7 +354,7 @@ __global__ void __launch_bounds__(256, 2) p2m_kernel(const FarBlockDev* __restri
             const int nr = min(NR, nrhs - c0);
             TA a0[NR], a1[NR];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) a0[r] = a1[r] = mk(R(0), R(0));
+            for (int r = 0; r < NR; ++r) a0[r] = a1[r] = acc_zero<TA>();
             if (active) {
                 for (int e = csr[a]; e < csr[a + 1]; ++e) {
                     const int2 en = ent[e];
@@ -282,9 +366,9 @@ __global__ void __launch_bounds__(256, 2) p2m_kernel(const FarBlockDev* __restri
 #pragma unroll
                         for (int r = 0; r < NR; ++r) {
                             if (r < nr) {
-                                TA tv = tb[k + (int64_t)r * ldt];
-                                cfma(a0[r], cvt<TA>(q.a), tv);
-                                cfma(a1[r], cvt<TA>(q.b), tv);
+                                const TX tv = tb[k + (int64_t)r * ldt];
+                                mac(a0[r], q.a, tv);
+                                mac(a1[r], q.b, tv);
                             }
                         }
                     }
@@ -303,12 +387,12 @@ __global__ void __launch_bounds__(256, 2) p2m_kernel(const FarBlockDev* __restri
                     if (r >= nr) continue;
                     TA v0 = a0[r], v1 = a1[r];
                     for (int g = 0; g < 3; ++g) {
-                        v0 += red[g][rp][0][r];
-                        v1 += red[g][rp][1][r];
+                        acc_add(v0, red[g][rp][0][r]);
+                        acc_add(v1, red[g][rp][1][r]);
                     }
-                    TX* out = F + (int64_t)a * np + row + (int64_t)(c0 + r) * ldf;
-                    out[0] = v0;
-                    out[1] = v1;
+                    TO* out = F + (int64_t)a * np + row + (int64_t)(c0 + r) * ldf;
+                    store(out, v0);
+                    store(out + 1, v1);
                 }
             }
             __syncthreads();
@@ -331,7 +415,7 @@ void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, c
                                                      op.np, op.d_t.as<TX>(), op.t_total, nrhs);
             VIE_CHECK_LAUNCH();
         }
-        p2m_kernel<TF, TX, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
+        p2m_kernel<TF, TX, TX, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
                                                  op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(),
                                                  fac, op.d_t.as<TX>(), op.t_total, op.np, F, ldf, nrhs);
         VIE_CHECK_LAUNCH();
@@ -343,15 +427,68 @@ void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, c
                                                 op.np, op.d_t.as<TX>(), op.t_total, nrhs);
         VIE_CHECK_LAUNCH();
     }
-    p2_kernel<TF, TX><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
+    p2_kernel<TF, TX, TX><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
                                          op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(),
                                          fac, op.d_t.as<TX>(), op.t_total, op.np, F, ldf, nrhs);
     VIE_CHECK_LAUNCH();
 }
 
 template void apply_far<float2, float2>(Op&, const float2*, int64_t, float2*, int64_t, int, cudaStream_t);
-template void apply_far<float2, double2>(Op&, const double2*, int64_t, double2*, int64_t, int, cudaStream_t);
 template void apply_far<double2, double2>(Op&, const double2*, int64_t, double2*, int64_t, int, cudaStream_t);
+
+namespace {
+// x (complex float64, n x nrhs, leading dimension ldx) -> float32 head + tail
+__global__ void k_split_hl(const double2* __restrict__ x, int64_t ldx, int64_t n, int nrhs, float4* __restrict__ xs) {
+    const int64_t total = n * nrhs;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / n, r = i - c * n;
+        const double2 v = x[r + c * ldx];
+        const float hr = (float)v.x, hi = (float)v.y;
+        xs[i] = make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
+    }
+}
+}  // namespace
+
+// F = far part of Zs x for complex float32 factors and complex float64 vectors,
+// summed in double-float arithmetic (the float64 refinement residual)
+void apply_far_df(Op& op, const double2* x, int64_t ldx, double2* F, int64_t ldf, int nrhs, cudaStream_t s) {
+    if (op.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "the double-float apply needs VIE_C64 factors");
+    const int64_t n = op.n();
+    const size_t need_t = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(float4);
+    const size_t need_x = (size_t)n * nrhs * sizeof(float4);
+    if (op.d_t.bytes < need_t) op.d_t.alloc(need_t);
+    if (op.d_xs.bytes < need_x) op.d_xs.alloc(need_x);
+    float4* xs = op.d_xs.as<float4>();
+    float4* t = op.d_t.as<float4>();
+    const float2* fac = op.d_factors.as<float2>();
+    const int nc = op.n_cta;
+    k_split_hl<<<op.ctx->n_sm * 8, 256, 0, s>>>(x, ldx, n, nrhs, xs);
+    VIE_CHECK_LAUNCH();
+    if (nrhs > 1) {
+        if (op.n_p1_items > 0) {
+            p1m_kernel<float2, float4, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
+                                                             op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, xs,
+                                                             n, op.np, t, op.t_total, nrhs);
+            VIE_CHECK_LAUNCH();
+        }
+        p2m_kernel<float2, float4, double2, 4><<<nc, 256, 0, s>>>(
+            op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(), op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(),
+            op.d_p2_ent.as<int2>(), fac, t, op.t_total, op.np, F, ldf, nrhs);
+        VIE_CHECK_LAUNCH();
+        return;
+    }
+    if (op.n_p1_items > 0) {
+        p1_kernel<float2, float4, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
+                                                        op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, xs, n,
+                                                        op.np, t, op.t_total, nrhs);
+        VIE_CHECK_LAUNCH();
+    }
+    p2_kernel<float2, float4, double2><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
+                                                          op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(),
+                                                          op.d_p2_ent.as<int2>(), fac, t, op.t_total, op.np, F, ldf,
+                                                          nrhs);
+    VIE_CHECK_LAUNCH();
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free apply: the phase-1 vector t lives in a fixed device array
@@ -402,7 +539,7 @@ void apply_static(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s) 
                                                         op.np, t, op.t_total, nrhs);
         VIE_CHECK_LAUNCH();
     }
-    p2_kernel<float2, float2><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
+    p2_kernel<float2, float2, float2><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
                                                  op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(),
                                                  fac, t, op.t_total, op.np, y, n, nrhs);
     VIE_CHECK_LAUNCH();

@@ -163,6 +163,7 @@ struct Op {
     int n_t1_items = 0, n_t2_items = 0, n_cta_tc = 0;
     // scratch
     DevBuf d_t, d_F;
+    DevBuf d_xs;  // float64 vectors split into float32 head + tail (double-float apply)
     size_t t_cap = 0, F_cap = 0;
     double t_assemble = 0, t_compress = 0;
     int64_t n() const { return (int64_t)N * np; }
@@ -231,6 +232,8 @@ template <class TF, class TX>
 void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, cudaStream_t s);
 
 void apply_static(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s);
+// far part with c64 factors and c128 vectors in double-float arithmetic
+void apply_far_df(Op& op, const double2* x, int64_t ldx, double2* F, int64_t ldf, int nrhs, cudaStream_t s);
 // apply_tc.cu: several right-hand sides on the tensor cores (BF16x3)
 void apply_far_bf16x3(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
 

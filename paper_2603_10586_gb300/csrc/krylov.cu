@@ -1,7 +1,13 @@
-// Float64 vector kernels of the Krylov solver (paper Sec. 6: GMRES with the
-// Arnoldi process): norms, the multi-vector dot products and updates of
-// classical Gram-Schmidt, scaling and residual formation.  Reductions are
-// two-stage with a fixed chunking, so results are reproducible run to run.
+// Device-resident kernels of the lockstep GMRES (paper Sec. 6: restarted
+// GMRES with the Arnoldi process, left-preconditioned by the block diagonal of
+// Sec. 4).  Every kernel works on all right-hand sides of a restart cycle at
+// once (grid dimension y or z = slot) and reads the Arnoldi step j and the
+// per-slot "still iterating" flags from device memory, so a whole cycle runs
+// without the host: the Hessenberg matrix, the Givens rotations and the
+// residual estimates live on the device too.
+//
+// Reductions are two-stage with a fixed partition of the rows, so every
+// result is the same from run to run.
 #include "common.h"
 #include "cplx.cuh"
 #include "krylov.h"
@@ -10,141 +16,469 @@ namespace vie {
 
 namespace {
 
-constexpr int kRed = 256;   // CTAs in the first reduction stage
-constexpr int kMaxCols = 64;
+constexpr int kT = 256;  // threads of the row kernels
+constexpr int kCG = 8;   // basis columns per CTA in the projections
 
-__global__ void k_norm2_partial(const double2* x, int64_t n, double* part) {
+__device__ __forceinline__ double2 ld64(const float2* p, int64_t i) {
+    const float2 v = p[i];
+    return make_double2(v.x, v.y);
+}
+__device__ __forceinline__ double2 ld64(const double2* p, int64_t i) { return p[i]; }
+__device__ __forceinline__ void st(float2* p, int64_t i, double2 v) { p[i] = make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ void st(double2* p, int64_t i, double2 v) { p[i] = v; }
+
+// sum of v over the CTA (kT threads), valid in thread 0
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kT / 32; ++w) s += sh[w];
+    return s;
+}
+
+__device__ __forceinline__ double2* basis(const KrylovArgs& a, int slot, int col) {
+    return a.V + ((int64_t)slot * (a.m + 1) + col) * a.n;
+}
+
+__global__ void k_cycle_start(KrylovArgs a, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) a.ctr[KR_J] = 0;
+    if (i >= k) return;
+    const int c = a.cols[i];
+    double2* g = a.g + (int64_t)i * (a.m + 1);
+    g[0] = make_double2(a.beta[c], 0.0);
+    for (int l = 1; l <= a.m; ++l) g[l] = make_double2(0.0, 0.0);
+    a.inv[i] = a.beta[c] > 0.0 ? 1.0 / a.beta[c] : 0.0;
+    a.cycling[i] = a.beta[c] > 0.0 && a.iters[c] < a.maxit;
+    a.jdone[i] = 0;
+}
+
+template <class TX>
+__global__ void __launch_bounds__(kT) k_gather(KrylovArgs a, const double2* __restrict__ W, TX* __restrict__ Xg) {
+    const int i = blockIdx.y;
+    const int64_t n = a.n, stride = (int64_t)gridDim.x * kT;
+    TX* x = Xg + (int64_t)i * n;
+    if (!a.cycling[i]) {
+        for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += stride) st(x, r, make_double2(0.0, 0.0));
+        return;
+    }
+    const int j = a.ctr[KR_J];
+    double2* v = basis(a, i, j);
+    const double2* src = j == 0 ? W + (int64_t)a.cols[i] * n : v;
+    const double sc = a.inv[i];
+    for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += stride) {
+        const double2 e = sc * src[r];
+        v[r] = e;
+        st(x, r, e);
+    }
+}
+
+// partial h[col] = sum_r conj(V[r, col]) w[r] over one row chunk, 8 columns per CTA.
+// Pass 1 takes w from the operator output and stores it as basis column j+1.
+template <class TW, bool kFirst>
+__global__ void __launch_bounds__(kT) k_mdot(KrylovArgs a, const TW* __restrict__ Y, int64_t rows_per) {
+    const int i = blockIdx.z, cg = blockIdx.y;
+    if (!a.cycling[i]) return;
+    const int j = a.ctr[KR_J];
+    const int ncols = j + 1;
+    if (cg * kCG >= ncols) return;
+    const int64_t n = a.n;
+    const double2* V = basis(a, i, 0);
+    double2* w = basis(a, i, j + 1);
+    const TW* y = Y + (int64_t)i * n;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
+    double2 acc[kCG];
+#pragma unroll
+    for (int c = 0; c < kCG; ++c) acc[c] = make_double2(0.0, 0.0);
+    // two rows per iteration keep more loads in flight
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += 2 * kT) {
+        const bool second = r + kT < r1;
+        double2 wv, wv2 = make_double2(0.0, 0.0);
+        if (kFirst) {
+            wv = ld64(y, r);
+            if (second) wv2 = ld64(y, r + kT);
+            if (cg == 0) {
+                w[r] = wv;
+                if (second) w[r + kT] = wv2;
+            }
+        } else {
+            wv = w[r];
+            if (second) wv2 = w[r + kT];
+        }
+        double2 v1[kCG], v2[kCG];
+#pragma unroll
+        for (int c = 0; c < kCG; ++c) {
+            const int col = cg * kCG + c;
+            v1[c] = col < ncols ? V[(int64_t)col * n + r] : make_double2(0.0, 0.0);
+            v2[c] = (col < ncols && second) ? V[(int64_t)col * n + r + kT] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int c = 0; c < kCG; ++c) {
+            cfmac(acc[c], v1[c], wv);
+            cfmac(acc[c], v2[c], wv2);
+        }
+    }
+    __shared__ double2 sh[kT / 32][kCG];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < kCG; ++c) {
+        double re = acc[c].x, im = acc[c].y;
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_down_sync(0xffffffffu, re, o);
+            im += __shfl_down_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) sh[wid][c] = make_double2(re, im);
+    }
+    __syncthreads();
+    if (threadIdx.x < kCG) {
+        const int col = cg * kCG + threadIdx.x;
+        if (col < ncols) {
+            double2 s = make_double2(0.0, 0.0);
+            for (int w2 = 0; w2 < kT / 32; ++w2) s += sh[w2][threadIdx.x];
+            a.part[((int64_t)i * 64 + col) * gridDim.x + blockIdx.x] = s;
+        }
+    }
+}
+
+// h = sum of the chunk partials (one warp per basis column); the Hessenberg
+// column accumulates both passes
+template <bool kFirst>
+__global__ void __launch_bounds__(kT) k_reduce(KrylovArgs a, int nchunk) {
+    const int i = blockIdx.x;
+    if (!a.cycling[i]) return;
+    const int j = a.ctr[KR_J];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int col = wid; col <= j; col += kT / 32) {
+        const double2* p = a.part + ((int64_t)i * 64 + col) * nchunk;
+        double re = 0.0, im = 0.0;
+        for (int x = lane; x < nchunk; x += 32) {
+            re += p[x].x;
+            im += p[x].y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_down_sync(0xffffffffu, re, o);
+            im += __shfl_down_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) {
+            const double2 s = make_double2(re, im);
+            a.h[i * 64 + col] = s;
+            double2* Hc = a.H + ((int64_t)i * a.m + j) * (a.m + 1);
+            if (kFirst) Hc[col] = s;
+            else Hc[col] += s;
+        }
+    }
+}
+
+// nsq[slot] = sum of the slot's squared-norm partials (one CTA per slot)
+__global__ void __launch_bounds__(kT) k_nsq(KrylovArgs a, int nblk, int check_cycling) {
+    const int i = blockIdx.x;
+    if (check_cycling && !a.cycling[i]) return;
+    __shared__ double sh[kT / 32];
     double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 v = x[i];
+    for (int b = threadIdx.x; b < nblk; b += kT) acc += a.npart[(int64_t)i * a.nblk_max + b];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) a.nsq[i] = s;
+}
+
+// w -= V h (columns 0..j); pass 2 also forms the squared-norm partials of w
+template <bool kSecond>
+__global__ void __launch_bounds__(kT) k_maxpy(KrylovArgs a) {
+    const int i = blockIdx.y;
+    if (!a.cycling[i]) return;
+    const int j = a.ctr[KR_J];
+    __shared__ double2 hs[64];
+    __shared__ double sh[kT / 32];
+    if ((int)threadIdx.x <= j) hs[threadIdx.x] = a.h[i * 64 + threadIdx.x];
+    __syncthreads();
+    const int64_t n = a.n;
+    const double2* V = basis(a, i, 0);
+    double2* w = basis(a, i, j + 1);
+    double nacc = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) {
+        double2 acc = w[r];
+        for (int c = 0; c <= j; ++c) {
+            const double2 v = V[(int64_t)c * n + r], hc = hs[c];
+            acc.x -= v.x * hc.x - v.y * hc.y;
+            acc.y -= v.x * hc.y + v.y * hc.x;
+        }
+        w[r] = acc;
+        if (kSecond) nacc += acc.x * acc.x + acc.y * acc.y;
+    }
+    if (kSecond) {
+        const double s = block_sum(nacc, sh);
+        if (threadIdx.x == 0) a.npart[(int64_t)i * a.nblk_max + blockIdx.x] = s;
+    }
+}
+
+// one thread per slot: new Hessenberg column, Givens rotations
+// G = [[conj c, conj s], [-s, c]], residual estimate |g_{j+1}| / ||M^-1 b||
+__global__ void k_givens(KrylovArgs a, int k, int nblk, cudaGraphConditionalHandle hnd, int use_handle) {
+    const int i = threadIdx.x;
+    const int j = a.ctr[KR_J];
+    const int m = a.m;
+    bool cyc = i < k && a.cycling[i] != 0;
+    double est = 0.0;
+    if (cyc) {
+        const int c = a.cols[i];
+        const double hn = sqrt(a.nsq[i]);
+        double2* Hc = a.H + ((int64_t)i * m + j) * (m + 1);
+        double2* cs = a.cs + (int64_t)i * m;
+        double2* sn = a.sn + (int64_t)i * m;
+        double2* g = a.g + (int64_t)i * (m + 1);
+        Hc[j + 1] = make_double2(hn, 0.0);
+        for (int l = 0; l < j; ++l) {
+            const double2 x = Hc[l], y = Hc[l + 1];
+            Hc[l] = cmulc(cs[l], x) + cmulc(sn[l], y);
+            Hc[l + 1] = cmul(cs[l], y) - cmul(sn[l], x);
+        }
+        const double2 x = Hc[j], y = Hc[j + 1];
+        const double den = sqrt(x.x * x.x + x.y * x.y + y.x * y.x + y.y * y.y);
+        const double2 cj = den > 0.0 ? (1.0 / den) * x : make_double2(1.0, 0.0);
+        const double2 sj = den > 0.0 ? (1.0 / den) * y : make_double2(0.0, 0.0);
+        cs[j] = cj;
+        sn[j] = sj;
+        Hc[j] = make_double2(den, 0.0);
+        Hc[j + 1] = make_double2(0.0, 0.0);
+        const double2 gj = g[j];
+        g[j + 1] = -1.0 * cmul(sj, gj);
+        g[j] = cmulc(cj, gj);
+        const int it = a.iters[c] + 1;
+        a.iters[c] = it;
+        a.jdone[i] = j + 1;
+        est = hypot(g[j + 1].x, g[j + 1].y) / a.beta0[c];
+        if (!isfinite(est)) {
+            a.ctr[KR_NAN] = 1;
+            cyc = false;
+            est = 0.0;
+        } else if (est <= a.tol || hn == 0.0 || it >= a.maxit) {
+            cyc = false;
+        }
+        a.inv[i] = hn > 0.0 ? 1.0 / hn : 0.0;
+        a.cycling[i] = cyc ? 1 : 0;
+    }
+    __shared__ double se[1024];
+    se[i] = est;
+    const int any = __syncthreads_or(cyc ? 1 : 0);
+    if (i == 0) {
+        double mx = 0.0;
+        for (int t = 0; t < (int)blockDim.x; ++t) mx = fmax(mx, se[t]);
+        const int it = a.ctr[KR_IT];
+        if (it < 512) a.hist[it] = mx;
+        a.ctr[KR_IT] = it + 1;
+        a.ctr[KR_APPLIES] += 1;
+        const int cont = (any && j + 1 < m) ? 1 : 0;
+        if (cont) a.ctr[KR_J] = j + 1;
+        a.ctr[KR_CONT] = cont;
+        if (use_handle) cudaGraphSetConditional(hnd, (unsigned)cont);
+    }
+}
+
+// back substitution y = H^-1 g on the rotated (upper triangular) Hessenberg matrix
+__global__ void k_backsub(KrylovArgs a, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    const int jd = a.jdone[i], m = a.m;
+    const double2* H = a.H + (int64_t)i * m * (m + 1);
+    const double2* g = a.g + (int64_t)i * (m + 1);
+    double2* y = a.y + (int64_t)i * 64;
+    for (int r = jd - 1; r >= 0; --r) {
+        double2 acc = g[r];
+        for (int l = r + 1; l < jd; ++l) acc -= cmul(H[r + (int64_t)l * (m + 1)], y[l]);
+        const double2 d = H[r + (int64_t)r * (m + 1)];
+        const double dd = d.x * d.x + d.y * d.y;
+        y[r] = dd > 0.0 ? (1.0 / dd) * cmulc(d, acc) : make_double2(0.0, 0.0);
+    }
+}
+
+__global__ void __launch_bounds__(kT) k_xupdate(KrylovArgs a, double2* __restrict__ X) {
+    const int i = blockIdx.y;
+    const int jd = a.jdone[i];
+    if (jd == 0) return;
+    __shared__ double2 ys[64];
+    if ((int)threadIdx.x < jd) ys[threadIdx.x] = a.y[(int64_t)i * 64 + threadIdx.x];
+    __syncthreads();
+    const int64_t n = a.n;
+    const double2* V = basis(a, i, 0);
+    double2* x = X + (int64_t)a.cols[i] * n;
+    for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) {
+        double2 acc = x[r];
+        for (int l = 0; l < jd; ++l) cfma(acc, V[(int64_t)l * n + r], ys[l]);
+        x[r] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(kT) k_gather_cols(const double2* __restrict__ src, const int* __restrict__ cols,
+                                                   double2* __restrict__ dst, int64_t n) {
+    const int i = blockIdx.y;
+    const double2* s = src + (int64_t)cols[i] * n;
+    double2* d = dst + (int64_t)i * n;
+    for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) d[r] = s[r];
+}
+
+__global__ void __launch_bounds__(kT) k_sub_cols(const double2* __restrict__ b, const int* __restrict__ cols,
+                                                const double2* __restrict__ T, double2* __restrict__ R, int64_t n) {
+    const int i = blockIdx.y;
+    const double2* bc = b + (int64_t)cols[i] * n;
+    const double2* t = T + (int64_t)i * n;
+    double2* rr = R + (int64_t)i * n;
+    for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) rr[r] = bc[r] - t[r];
+}
+
+__global__ void __launch_bounds__(kT) k_scatter_norm(KrylovArgs a, const double2* Wl, double2* W) {
+    const int i = blockIdx.y;
+    const int64_t n = a.n;
+    const double2* src = Wl + (int64_t)i * n;
+    double2* dst = W + (int64_t)a.cols[i] * n;
+    __shared__ double sh[kT / 32];
+    double acc = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) {
+        const double2 v = src[r];
+        if (dst != src) dst[r] = v;
         acc += v.x * v.x + v.y * v.y;
     }
-    __shared__ double red[256];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) a.npart[(int64_t)i * a.nblk_max + blockIdx.x] = s;
 }
-__global__ void k_sum(const double* part, int n, double* out) {
-    __shared__ double red[256];
+
+__global__ void k_cycle_end(KrylovArgs a, int k, int nblk, int init) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && !init) a.ctr[KR_REFIN] += 1;
+    if (i >= k) return;
+    const int c = a.cols[i];
+    const double bn = sqrt(a.nsq[i]);
+    if (!isfinite(bn)) a.ctr[KR_NAN] = 1;
+    a.beta[c] = bn;
+    if (init) {
+        a.beta0[c] = bn;
+        a.res[c] = bn > 0.0 ? 1.0 : 0.0;
+        a.done[c] = bn > 0.0 ? 0 : 1;
+        a.iters[c] = 0;
+    } else {
+        const double r = a.beta0[c] > 0.0 ? bn / a.beta0[c] : 0.0;
+        a.res[c] = r;
+        a.done[c] = (r <= a.tol || a.iters[c] >= a.maxit || bn == 0.0) ? 1 : 0;
+    }
+}
+
+__global__ void __launch_bounds__(kT) k_colnorm_partial(const double2* __restrict__ A, int64_t n, double* part) {
+    const int i = blockIdx.y;
+    const double2* x = A + (int64_t)i * n;
+    __shared__ double sh[kT / 32];
     double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
+    for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) {
+        const double2 v = x[r];
+        acc += v.x * v.x + v.y * v.y;
     }
-    if (threadIdx.x == 0) *out = red[0];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(int64_t)i * gridDim.x + blockIdx.x] = s;
 }
 
-// h[j] = sum_i conj(V[i, j]) w[i], j < ncols; partial sums per CTA
-__global__ void k_mdot_partial(const double2* V, int64_t ldv, int ncols, const double2* w, int64_t n,
-                               double2* part) {
-    double2 acc[kMaxCols];
-    for (int j = 0; j < ncols; ++j) acc[j] = make_double2(0, 0);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 wv = w[i];
-        for (int j = 0; j < ncols; ++j) cfmac(acc[j], V[i + j * ldv], wv);
-    }
-    __shared__ double2 red[256];
-    for (int j = 0; j < ncols; ++j) {
-        red[threadIdx.x] = acc[j];
-        __syncthreads();
-        for (int s = 128; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) part[(size_t)j * gridDim.x + blockIdx.x] = red[0];
-        __syncthreads();
-    }
-}
-__global__ void k_mdot_reduce(const double2* part, int nchunk, double2* h) {
-    int j = blockIdx.x;
-    __shared__ double2 red[256];
-    double2 acc = make_double2(0, 0);
-    for (int c = threadIdx.x; c < nchunk; c += blockDim.x) acc += part[(size_t)j * nchunk + c];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) h[j] = red[0];
+__global__ void k_colnorm_final(const double* part, int nblk, int k, const int* cols, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)i * nblk + b];
+    out[cols ? cols[i] : i] = sqrt(s);
 }
 
-// w += sign * V h
-__global__ void k_maxpy(const double2* V, int64_t ldv, int ncols, const double2* h, double sign, double2* w,
-                        int64_t n) {
-    __shared__ double2 hs[kMaxCols];
-    if ((int)threadIdx.x < ncols) hs[threadIdx.x] = h[threadIdx.x];
-    __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 acc = w[i];
-        for (int j = 0; j < ncols; ++j) {
-            double2 p = cmul(V[i + j * ldv], hs[j]);
-            acc.x += sign * p.x;
-            acc.y += sign * p.y;
-        }
-        w[i] = acc;
-    }
-}
-
-__global__ void k_scale(const double2* x, double a, double2* y, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = a * x[i];
-}
-// y = a - b
-__global__ void k_sub(const double2* a, const double2* b, double2* y, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = a[i] - b[i];
-}
-
-int grid_for(int64_t n) { return (int)std::min<int64_t>(kRed * 4, (n + 255) / 256); }
+int slot_threads(int k) { return std::max(32, (k + 31) / 32 * 32); }
 
 }  // namespace
 
-double knorm2(const double2* x, int64_t n, KrylovScratch& ks, cudaStream_t s) {
-    k_norm2_partial<<<kRed, 256, 0, s>>>(x, n, ks.part.as<double>());
-    k_sum<<<1, 256, 0, s>>>(ks.part.as<double>(), kRed, ks.scalar.as<double>());
-    VIE_CHECK_LAUNCH();
-    double v = 0;
-    VIE_CUDA(cudaMemcpyAsync(&v, ks.scalar.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-    VIE_CUDA(cudaStreamSynchronize(s));
-    return v;
+int kr_nblk(int64_t n, int k, int n_sm) {
+    const int64_t want = ((int64_t)n_sm * 8 + k - 1) / k;       // ~8 CTAs per SM in total
+    const int64_t cap = (n + kT - 1) / kT;
+    return (int)std::max<int64_t>(1, std::min(want, cap));
 }
 
-void kmdot(const double2* V, int64_t ldv, int ncols, const double2* w, int64_t n, double2* d_h, KrylovScratch& ks,
-           cudaStream_t s) {
-    if (ncols > kMaxCols) fail(VIE_ERR_INVALID_ARG, "restart length above 63");
-    k_mdot_partial<<<kRed, 256, 0, s>>>(V, ldv, ncols, w, n, ks.part2.as<double2>());
-    k_mdot_reduce<<<ncols, 256, 0, s>>>(ks.part2.as<double2>(), kRed, d_h);
-    VIE_CHECK_LAUNCH();
+int kr_nchunk(int64_t n, int k, int m, int n_sm) {
+    const int groups = std::max(1, std::min(4, (m + kCG - 1) / kCG));  // column groups live on average
+    const int64_t want = ((int64_t)n_sm * 8 + (int64_t)k * groups - 1) / ((int64_t)k * groups);
+    const int64_t cap = (n + 4 * kT - 1) / (4 * kT);
+    return (int)std::max<int64_t>(1, std::min(want, cap));
 }
 
-void kmaxpy(const double2* V, int64_t ldv, int ncols, const double2* d_h, double sign, double2* w, int64_t n,
-            cudaStream_t s) {
-    k_maxpy<<<grid_for(n), 256, 0, s>>>(V, ldv, ncols, d_h, sign, w, n);
+void kr_cycle_start(const KrylovArgs& a, int k, cudaStream_t s) {
+    k_cycle_start<<<(k + 255) / 256, 256, 0, s>>>(a, k);
     VIE_CHECK_LAUNCH();
 }
 
-void kscale(const double2* x, double a, double2* y, int64_t n, cudaStream_t s) {
-    k_scale<<<grid_for(n), 256, 0, s>>>(x, a, y, n);
+void kr_gather(const KrylovArgs& a, const double2* W, void* Xg, bool c64, int k, int nblk, cudaStream_t s) {
+    dim3 grid(nblk, k);
+    if (c64) k_gather<float2><<<grid, kT, 0, s>>>(a, W, static_cast<float2*>(Xg));
+    else k_gather<double2><<<grid, kT, 0, s>>>(a, W, static_cast<double2*>(Xg));
     VIE_CHECK_LAUNCH();
 }
 
-void ksub(const double2* a, const double2* b, double2* y, int64_t n, cudaStream_t s) {
-    k_sub<<<grid_for(n), 256, 0, s>>>(a, b, y, n);
+void kr_project(const KrylovArgs& a, const void* Y, bool c64, int pass, int k, int nchunk, int nblk, cudaStream_t s) {
+    const int ncg = (a.m + kCG - 1) / kCG;
+    const int64_t rows_per = (a.n + nchunk - 1) / nchunk;
+    dim3 gd(nchunk, ncg, k);
+    if (pass == 1) {
+        if (c64) k_mdot<float2, true><<<gd, kT, 0, s>>>(a, static_cast<const float2*>(Y), rows_per);
+        else k_mdot<double2, true><<<gd, kT, 0, s>>>(a, static_cast<const double2*>(Y), rows_per);
+        VIE_CHECK_LAUNCH();
+        k_reduce<true><<<k, kT, 0, s>>>(a, nchunk);
+        VIE_CHECK_LAUNCH();
+        k_maxpy<false><<<dim3(nblk, k), kT, 0, s>>>(a);
+        VIE_CHECK_LAUNCH();
+    } else {
+        k_mdot<double2, false><<<gd, kT, 0, s>>>(a, nullptr, rows_per);
+        VIE_CHECK_LAUNCH();
+        k_reduce<false><<<k, kT, 0, s>>>(a, nchunk);
+        VIE_CHECK_LAUNCH();
+        k_maxpy<true><<<dim3(nblk, k), kT, 0, s>>>(a);
+        VIE_CHECK_LAUNCH();
+        k_nsq<<<k, kT, 0, s>>>(a, nblk, 1);
+        VIE_CHECK_LAUNCH();
+    }
+}
+
+void kr_givens(const KrylovArgs& a, int k, int nblk, cudaGraphConditionalHandle hnd, int use_handle, cudaStream_t s) {
+    if (k > 1024) fail(VIE_ERR_INVALID_ARG, "more than 1024 right-hand sides in one solve");
+    k_givens<<<1, slot_threads(k), 0, s>>>(a, k, nblk, hnd, use_handle);
     VIE_CHECK_LAUNCH();
 }
 
-void KrylovScratch::init() {
-    part.alloc(kRed * sizeof(double));
-    part2.alloc((size_t)kRed * kMaxCols * sizeof(double2));
-    scalar.alloc(sizeof(double));
+void kr_update(const KrylovArgs& a, double2* X, int k, int nblk, cudaStream_t s) {
+    k_backsub<<<(k + 63) / 64, 64, 0, s>>>(a, k);
+    VIE_CHECK_LAUNCH();
+    k_xupdate<<<dim3(nblk, k), kT, 0, s>>>(a, X);
+    VIE_CHECK_LAUNCH();
+}
+
+void kr_gather_cols(const double2* src, const int* cols, double2* dst, int64_t n, int k, int nblk, cudaStream_t s) {
+    k_gather_cols<<<dim3(nblk, k), kT, 0, s>>>(src, cols, dst, n);
+    VIE_CHECK_LAUNCH();
+}
+
+void kr_sub_cols(const double2* b, const int* cols, const double2* T, double2* R, int64_t n, int k, int nblk,
+                 cudaStream_t s) {
+    k_sub_cols<<<dim3(nblk, k), kT, 0, s>>>(b, cols, T, R, n);
+    VIE_CHECK_LAUNCH();
+}
+
+void kr_scatter_norm(const KrylovArgs& a, const double2* Wl, double2* W, int k, int nblk, cudaStream_t s) {
+    if (nblk > a.nblk_max) fail(VIE_ERR_STATE, "norm partials exceed their buffer");
+    k_scatter_norm<<<dim3(nblk, k), kT, 0, s>>>(a, Wl, W);
+    VIE_CHECK_LAUNCH();
+}
+
+void kr_cycle_end(const KrylovArgs& a, int k, int nblk, int init, cudaStream_t s) {
+    k_nsq<<<k, kT, 0, s>>>(a, nblk, 0);
+    VIE_CHECK_LAUNCH();
+    k_cycle_end<<<(k + 255) / 256, 256, 0, s>>>(a, k, nblk, init);
+    VIE_CHECK_LAUNCH();
+}
+
+void kr_colnorms(const double2* A, int64_t n, int k, int nblk, const int* cols, double* d_part, double* d_out,
+                 cudaStream_t s) {
+    k_colnorm_partial<<<dim3(nblk, k), kT, 0, s>>>(A, n, d_part);
+    VIE_CHECK_LAUNCH();
+    k_colnorm_final<<<(k + 255) / 256, 256, 0, s>>>(d_part, nblk, k, cols, d_out);
+    VIE_CHECK_LAUNCH();
 }
 
 }  // namespace vie

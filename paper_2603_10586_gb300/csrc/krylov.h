@@ -1,21 +1,81 @@
-// Float64 Krylov vector kernels (see krylov.cu).
+// Device-resident lockstep GMRES state and kernels (see krylov.cu), and the
+// operator applications the solver uses (api.cpp).
 #pragma once
 #include "common.h"
 
 namespace vie {
 
-struct KrylovScratch {
-    DevBuf part, part2, scalar;
-    void init();
+// Counters kept on the device.
+enum : int {
+    KR_J = 0,        // Arnoldi step within the current restart cycle
+    KR_IT = 1,       // lockstep iterations so far (all cycles)
+    KR_APPLIES = 2,  // operator applications
+    KR_REFIN = 3,    // float64 refinement residuals
+    KR_NAN = 4,      // a non-finite residual was seen
+    KR_CONT = 5,     // another Arnoldi step follows in this cycle
+    KR_NCTR = 8
 };
 
-double knorm2(const double2* x, int64_t n, KrylovScratch& ks, cudaStream_t s);  // sum |x|^2 (synchronises)
-void kmdot(const double2* V, int64_t ldv, int ncols, const double2* w, int64_t n, double2* d_h, KrylovScratch& ks,
-           cudaStream_t s);
-void kmaxpy(const double2* V, int64_t ldv, int ncols, const double2* d_h, double sign, double2* w, int64_t n,
-            cudaStream_t s);
-void kscale(const double2* x, double a, double2* y, int64_t n, cudaStream_t s);
-void ksub(const double2* a, const double2* b, double2* y, int64_t n, cudaStream_t s);
+// Pointers into the solver's device state, passed by value to every kernel.
+// Slot i (< k) of a restart cycle works on column cols[i] of the n x nrhs
+// right-hand side, solution and residual arrays.
+struct KrylovArgs {
+    int64_t n;
+    int m;            // restart length (<= 63)
+    int nblk_max;     // row blocks the norm partials are laid out for
+    double tol;
+    int maxit;
+    double2* V;       // [slot][m+1][n] float64 basis
+    double2* H;       // [slot][m][m+1] Hessenberg columns (rotated in place)
+    double2* g;       // [slot][m+1] rotated right-hand side of the least-squares problem
+    double2* cs;      // [slot][m] Givens cosines
+    double2* sn;      // [slot][m] Givens sines
+    double2* h;       // [slot][64] coefficients of the current Gram-Schmidt pass
+    double2* y;       // [slot][64] least-squares solution of the cycle
+    double2* part;    // [slot][64][nchunk] projection partial sums
+    double* npart;    // [slot][nblk_max] squared-norm partial sums
+    double* nsq;      // [slot] their total
+    double* inv;      // [slot] scale the next gather applies to its basis column
+    int* cycling;     // [slot] still iterating in this cycle
+    int* jdone;       // [slot] Arnoldi steps done in this cycle
+    int* cols;        // [slot] right-hand-side column of the slot
+    int* iters;       // [nrhs] Arnoldi steps per column (all cycles)
+    int* done;        // [nrhs] converged or out of iterations
+    double* beta0;    // [nrhs] ||M^-1 b||
+    double* beta;     // [nrhs] norm of the latest refinement residual
+    double* res;      // [nrhs] beta / beta0
+    double* rnorm;    // [nrhs] ||b - Zs x|| at the latest refinement
+    double* hist;     // [512] largest estimated residual per lockstep iteration
+    int* ctr;         // [KR_NCTR]
+};
+
+// launch shapes: row blocks of the (rows, slot) kernels and row chunks of the
+// projections, chosen so that one launch covers the GPU a few times over
+int kr_nblk(int64_t n, int k, int n_sm);
+int kr_nchunk(int64_t n, int k, int m, int n_sm);
+
+void kr_cycle_start(const KrylovArgs& a, int k, cudaStream_t s);
+// Xg[:, i] = basis column j of slot i, scaled to unit norm (column 0 comes from W)
+void kr_gather(const KrylovArgs& a, const double2* W, void* Xg, bool c64, int k, int nblk, cudaStream_t s);
+// classical Gram-Schmidt pass 1 (w from the operator output Y) or pass 2 (w = basis column j+1)
+void kr_project(const KrylovArgs& a, const void* Y, bool c64, int pass, int k, int nchunk, int nblk, cudaStream_t s);
+// Givens update of the Hessenberg column, residual estimate, end-of-step test;
+// with use_handle the continue flag also drives the enclosing graph loop
+void kr_givens(const KrylovArgs& a, int k, int nblk, cudaGraphConditionalHandle hnd, int use_handle, cudaStream_t s);
+// X[:, cols[i]] += V_i y_i with y_i = H_i^-1 g_i
+void kr_update(const KrylovArgs& a, double2* X, int k, int nblk, cudaStream_t s);
+// dst[:, i] = src[:, cols[i]]
+void kr_gather_cols(const double2* src, const int* cols, double2* dst, int64_t n, int k, int nblk, cudaStream_t s);
+// R[:, i] = b[:, cols[i]] - T[:, i]
+void kr_sub_cols(const double2* b, const int* cols, const double2* T, double2* R, int64_t n, int k, int nblk,
+                 cudaStream_t s);
+// W[:, cols[i]] = Wl[:, i] (W may equal Wl with cols the identity) and its squared-norm partials
+void kr_scatter_norm(const KrylovArgs& a, const double2* Wl, double2* W, int k, int nblk, cudaStream_t s);
+// beta, res and done of the slots' columns from the norm partials; init also sets beta0
+void kr_cycle_end(const KrylovArgs& a, int k, int nblk, int init, cudaStream_t s);
+// norms of the k columns of A (n x k) into d_out[cols ? cols[i] : i]; d_part holds k * nblk doubles
+void kr_colnorms(const double2* A, int64_t n, int k, int nblk, const int* cols, double* d_part, double* d_out,
+                 cudaStream_t s);
 
 // operator applications used by the solver (solve.cpp / api.cpp)
 // y = P^-1 Zs x in complex float32 (fused preconditioner), x, y: n x nrhs, ld = n
@@ -28,5 +88,8 @@ void op_apply64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s);
 void op_apply_fused64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s);
 // y = Z_D^-1 x in float64
 void op_precond64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s);
+// size the operator's apply workspaces for nrhs float64 columns (no allocation
+// may happen while a CUDA graph is being captured)
+void op_reserve(Op& op, int nrhs);
 
 }  // namespace vie

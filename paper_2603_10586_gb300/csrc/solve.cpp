@@ -11,15 +11,21 @@
 // VIE_BF16X3 the far part of the inner applies runs on the tensor cores in
 // split-precision bf16 (the refinement residual stays float64).
 //
-// Several right-hand sides advance in lockstep: each Arnoldi step gathers the
-// current basis vector of every right-hand side still iterating into one
-// n x s block and applies the operator once to all of them, so the factors
-// are streamed once per step instead of once per right-hand side.  Each
-// right-hand side keeps its own Krylov space, Hessenberg matrix and rotations
-// and leaves the lockstep when it has converged.
+// Several right-hand sides advance in lockstep: each Arnoldi step applies the
+// operator once to the current basis vectors of all of them (one n x k
+// block), so the factors are streamed once per step instead of once per
+// right-hand side.  Each right-hand side keeps its own Krylov space,
+// Hessenberg matrix and rotations and leaves the lockstep when it converges.
+//
+// The whole restart cycle runs on the device: the Arnoldi step, the
+// orthogonalisation, the Givens updates and the end-of-step test are kernels
+// (krylov.cu), and by default one cycle is one CUDA graph whose Arnoldi steps
+// sit in a conditional while-node driven by the Givens kernel.  The host only
+// reads the per-column convergence flags between cycles.
 #include <algorithm>
 #include <cmath>
-#include <complex>
+#include <cstring>
+#include <map>
 
 #include "common.h"
 #include "krylov.h"
@@ -28,179 +34,246 @@ namespace vie {
 
 namespace {
 
-struct Rhs {
-    DevBuf V;                // n x (m+1) float64 complex basis
-    std::vector<cd> H, g, cs, sn;
-    double beta0 = 0, beta = 0, res = 1;
-    bool done = false;       // converged (true residual) or out of iterations
-    bool cycling = false;    // still iterating in the current restart cycle
-    int jdone = 0, iters = 0;
+struct CycleGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long pre = 0, body = 0, post = 0;  // kernels per launch of each part
 };
 
 struct Gmres {
     Op& op;
     const vie_solve_opts& o;
-    cudaStream_t s;
+    cudaStream_t s, s_body = nullptr;
     int64_t n;
-    int m, nrhs;
-    KrylovScratch ks;
-    std::vector<Rhs> R;
-    DevBuf X32, Y32, Xg, Yg, h, tmp, r0, W;
+    int m, nrhs, n_sm;
+    bool c64;  // inner applies on float32 vectors
+    DevBuf V, H, g, cs, sn, h, y, part, npart, nsq, rpart, inv, cycling, jdone, cols, iters, done, beta0, beta, res, rnorm,
+        bnorm, hist, ctr;
+    DevBuf Xg, Yg, Xl, T, Rl, Wl, W;
+    KrylovArgs a{};
+    std::map<int, CycleGraph> graphs;
+    int* h_pinned = nullptr;  // [KR_NCTR + nrhs] host-visible copy of counters and done flags
 
     Gmres(Op& op_, const vie_solve_opts& o_, int nrhs_)
-        : op(op_), o(o_), s(op_.ctx->stream), n(op_.n()), nrhs(nrhs_) {
+        : op(op_), o(o_), s(op_.ctx->stream), n(op_.n()), nrhs(nrhs_), n_sm(op_.ctx->n_sm) {
         m = std::max(1, std::min(o.restart > 0 ? o.restart : 60, 63));
-        ks.init();
-        R.resize(nrhs);
-        for (auto& r : R) {
-            r.V.alloc((size_t)n * (m + 1) * sizeof(double2));
-            r.H.assign((size_t)(m + 1) * m, cd(0));
-            r.g.assign(m + 1, cd(0));
-            r.cs.assign(m, cd(0));
-            r.sn.assign(m, cd(0));
-        }
-        h.alloc(64 * sizeof(double2));
-        tmp.alloc((size_t)n * nrhs * sizeof(double2));
-        r0.alloc((size_t)n * nrhs * sizeof(double2));
-        W.alloc((size_t)n * nrhs * sizeof(double2));
-        Xg.alloc((size_t)n * nrhs * sizeof(double2));
-        Yg.alloc((size_t)n * nrhs * sizeof(double2));
-        if (o.precision != VIE_C128) {
-            X32.alloc((size_t)n * nrhs * sizeof(float2));
-            Y32.alloc((size_t)n * nrhs * sizeof(float2));
+        c64 = !(o.precision == VIE_C128 || !o.precond);
+        const int S = nrhs;
+        const int nblk_max = kr_nblk(n, 1, n_sm);
+        const int nchunk_max = kr_nchunk(n, 1, m, n_sm);
+        V.alloc((size_t)S * (m + 1) * n * sizeof(double2));
+        H.alloc((size_t)S * m * (m + 1) * sizeof(double2));
+        g.alloc((size_t)S * (m + 1) * sizeof(double2));
+        cs.alloc((size_t)S * m * sizeof(double2));
+        sn.alloc((size_t)S * m * sizeof(double2));
+        h.alloc((size_t)S * 64 * sizeof(double2));
+        y.alloc((size_t)S * 64 * sizeof(double2));
+        part.alloc((size_t)S * 64 * nchunk_max * sizeof(double2));
+        npart.alloc((size_t)S * nblk_max * sizeof(double));
+        rpart.alloc((size_t)S * nblk_max * sizeof(double));
+        nsq.alloc(S * sizeof(double));
+        inv.alloc(S * sizeof(double));
+        cycling.alloc(S * sizeof(int));
+        jdone.alloc(S * sizeof(int));
+        cols.alloc(S * sizeof(int));
+        iters.alloc(nrhs * sizeof(int));
+        done.alloc(nrhs * sizeof(int));
+        beta0.alloc(nrhs * sizeof(double));
+        beta.alloc(nrhs * sizeof(double));
+        res.alloc(nrhs * sizeof(double));
+        rnorm.alloc(nrhs * sizeof(double));
+        bnorm.alloc(nrhs * sizeof(double));
+        hist.alloc(512 * sizeof(double));
+        ctr.alloc(KR_NCTR * sizeof(int));
+        const size_t vec = (size_t)n * nrhs * sizeof(double2);
+        Xg.alloc(vec);
+        Yg.alloc(vec);
+        Xl.alloc(vec);
+        T.alloc(vec);
+        Rl.alloc(vec);
+        Wl.alloc(vec);
+        W.alloc(vec);
+        op_reserve(op, nrhs);
+        VIE_CUDA(cudaMemsetAsync(ctr.p, 0, KR_NCTR * sizeof(int), s));
+        VIE_CUDA(cudaMemsetAsync(hist.p, 0, 512 * sizeof(double), s));
+        a.n = n;
+        a.m = m;
+        a.nblk_max = nblk_max;
+        a.tol = o.tol > 0 ? o.tol : 1e-6;
+        a.maxit = o.max_iters > 0 ? o.max_iters : 2000;
+        a.V = V.as<double2>();
+        a.H = H.as<double2>();
+        a.g = g.as<double2>();
+        a.cs = cs.as<double2>();
+        a.sn = sn.as<double2>();
+        a.h = h.as<double2>();
+        a.y = y.as<double2>();
+        a.part = part.as<double2>();
+        a.npart = npart.as<double>();
+        a.nsq = nsq.as<double>();
+        a.inv = inv.as<double>();
+        a.cycling = cycling.as<int>();
+        a.jdone = jdone.as<int>();
+        a.cols = cols.as<int>();
+        a.iters = iters.as<int>();
+        a.done = done.as<int>();
+        a.beta0 = beta0.as<double>();
+        a.beta = beta.as<double>();
+        a.res = res.as<double>();
+        a.rnorm = rnorm.as<double>();
+        a.hist = hist.as<double>();
+        a.ctr = ctr.as<int>();
+        VIE_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h_pinned), (KR_NCTR + nrhs) * sizeof(int)));
+    }
+
+    ~Gmres() {
+        for (auto& kv : graphs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (s_body) cudaStreamDestroy(s_body);
+        if (h_pinned) cudaFreeHost(h_pinned);
+    }
+
+    // Yg = M^-1 Zs Xg for k columns (M = Z_D or the identity)
+    void apply_inner(int k, cudaStream_t st) {
+        if (!c64) {
+            if (o.precond) op_apply_fused64(op, Xg.as<double2>(), Yg.as<double2>(), k, st);
+            else op_apply64(op, Xg.as<double2>(), Yg.as<double2>(), k, st);
+        } else if (o.precision == VIE_BF16X3) {
+            op_apply_fused_bf16x3(op, Xg.as<float2>(), Yg.as<float2>(), k, st);
+        } else {
+            op_apply_fused32(op, Xg.as<float2>(), Yg.as<float2>(), k, st);
         }
     }
 
-    // out[:, i] = M^-1 Zs in[:, i] for the k gathered columns (M = Z_D or identity)
-    void apply_inner(const double2* in, double2* out, int k) {
-        if (o.precision == VIE_C128 || !o.precond) {
-            if (o.precond) op_apply_fused64(op, in, out, k, s);
-            else op_apply64(op, in, out, k, s);
-            return;
+    void launch_pre(int k, cudaStream_t st) { kr_cycle_start(a, k, st); }
+
+    void launch_body(int k, cudaStream_t st, cudaGraphConditionalHandle hnd, int use_handle) {
+        const int nblk = kr_nblk(n, k, n_sm), nchunk = kr_nchunk(n, k, m, n_sm);
+        kr_gather(a, W.as<double2>(), Xg.p, c64, k, nblk, st);
+        apply_inner(k, st);
+        kr_project(a, Yg.p, c64, 1, k, nchunk, nblk, st);
+        kr_project(a, nullptr, c64, 2, k, nchunk, nblk, st);
+        kr_givens(a, k, nblk, hnd, use_handle, st);
+    }
+
+    // x += V y, then the float64 refinement residual W = M^-1 (b - Zs x) of the slots' columns
+    void launch_post(int k, const double2* b, double2* X, cudaStream_t st) {
+        const int nblk = kr_nblk(n, k, n_sm);
+        kr_update(a, X, k, nblk, st);
+        kr_gather_cols(X, a.cols, Xl.as<double2>(), n, k, nblk, st);
+        op_apply64(op, Xl.as<double2>(), T.as<double2>(), k, st);
+        kr_sub_cols(b, a.cols, T.as<double2>(), Rl.as<double2>(), n, k, nblk, st);
+        kr_colnorms(Rl.as<double2>(), n, k, nblk, a.cols, rpart.as<double>(), a.rnorm, st);
+        if (o.precond) op_precond64(op, Rl.as<double2>(), Wl.as<double2>(), k, st);
+        else VIE_CUDA(cudaMemcpyAsync(Wl.p, Rl.p, (size_t)n * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        kr_scatter_norm(a, Wl.as<double2>(), W.as<double2>(), k, nblk, st);
+        kr_cycle_end(a, k, nblk, 0, st);
+    }
+
+    // one restart cycle as a CUDA graph: pre -> while (continue) { Arnoldi step } -> post
+    CycleGraph& graph_for(int k, const double2* b, double2* X) {
+        auto it = graphs.find(k);
+        if (it != graphs.end()) return it->second;
+        if (!s_body) VIE_CUDA(cudaStreamCreateWithFlags(&s_body, cudaStreamNonBlocking));
+        CycleGraph cg;
+        const long long c0 = g_kernel_launches.load();
+        VIE_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t graph = nullptr;
+        try {
+            launch_pre(k, s);
+            const long long c1 = g_kernel_launches.load();
+            cudaStreamCaptureStatus cst;
+            cudaGraph_t cap = nullptr;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t ndeps = 0;
+            VIE_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cap, &deps, nullptr, &ndeps));
+            std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+            cudaGraphConditionalHandle hnd;
+            VIE_CUDA(cudaGraphConditionalHandleCreate(&hnd, cap, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};  // the rest zero
+            p.conditional.handle = hnd;
+            p.conditional.type = cudaGraphCondTypeWhile;
+            p.conditional.size = 1;
+            cudaGraphNode_t wnode;
+            VIE_CUDA(cudaGraphAddNode(&wnode, cap, dv.data(), nullptr, dv.size(), &p));
+            cudaGraph_t body = p.conditional.phGraph_out[0];
+            VIE_CUDA(cudaStreamBeginCaptureToGraph(s_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            try {
+                launch_body(k, s_body, hnd, 1);
+            } catch (...) {
+                cudaGraph_t tmp = nullptr;
+                cudaStreamEndCapture(s_body, &tmp);
+                throw;
+            }
+            VIE_CUDA(cudaStreamEndCapture(s_body, &body));
+            const long long c2 = g_kernel_launches.load();
+            VIE_CUDA(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+            launch_post(k, b, X, s);
+            const long long c3 = g_kernel_launches.load();
+            VIE_CUDA(cudaStreamEndCapture(s, &graph));
+            cg.pre = c1 - c0;
+            cg.body = c2 - c1;
+            cg.post = c3 - c2;
+            VIE_COUNT_LAUNCH(-(c3 - c0));  // counted again per executed launch
+        } catch (...) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(s, &tmp);
+            if (tmp) cudaGraphDestroy(tmp);
+            cudaGetLastError();
+            throw;
         }
-        convert_c128_to_c64(in, X32.p, n * k, s);
-        if (o.precision == VIE_BF16X3) op_apply_fused_bf16x3(op, X32.as<float2>(), Y32.as<float2>(), k, s);
-        else op_apply_fused32(op, X32.as<float2>(), Y32.as<float2>(), k, s);
-        convert_c64_to_c128(Y32.p, out, n * k, s);
+        cudaError_t e = cudaGraphInstantiate(&cg.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) fail(VIE_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        return graphs.emplace(k, cg).first->second;
     }
 
-    // out = M^-1 (b - Zs x) in float64 for all right-hand sides
-    void residual(const double2* b, const double2* x, double2* out) {
-        op_apply64(op, x, tmp.as<double2>(), nrhs, s);
-        ksub(b, tmp.as<double2>(), r0.as<double2>(), n * nrhs, s);
-        if (o.precond) op_precond64(op, r0.as<double2>(), out, nrhs, s);
-        else VIE_CUDA(cudaMemcpyAsync(out, r0.p, n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    void read_state() {
+        VIE_CUDA(cudaMemcpyAsync(h_pinned, ctr.p, KR_NCTR * sizeof(int), cudaMemcpyDeviceToHost, s));
+        VIE_CUDA(cudaMemcpyAsync(h_pinned + KR_NCTR, done.p, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+        VIE_CUDA(cudaStreamSynchronize(s));
+        if (h_pinned[KR_NAN]) fail(VIE_ERR_NAN, "non-finite residual in GMRES");
     }
 
-    int run(const double2* b, double2* X, vie_solve_stats* st, int& applies, int& refin) {
-        const double tol = o.tol > 0 ? o.tol : 1e-6;
-        const int maxit = o.max_iters > 0 ? o.max_iters : 2000;
+    void run(const double2* b, double2* X) {
         VIE_CUDA(cudaMemsetAsync(X, 0, (size_t)n * nrhs * sizeof(double2), s));
-        // r = M^-1 b
+        // W = M^-1 b, beta0 = ||W|| per column
         if (o.precond) op_precond64(op, b, W.as<double2>(), nrhs, s);
-        else VIE_CUDA(cudaMemcpyAsync(W.p, b, n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-        for (int c = 0; c < nrhs; ++c) {
-            Rhs& r = R[c];
-            r.beta0 = r.beta = std::sqrt(knorm2(W.as<double2>() + (size_t)c * n, n, ks, s));
-            r.done = r.beta0 == 0.0;
-            r.res = r.done ? 0.0 : 1.0;
-        }
-        std::vector<cd> hv(m + 1);
+        else VIE_CUDA(cudaMemcpyAsync(W.p, b, (size_t)n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        std::vector<int> ident(nrhs);
+        for (int c = 0; c < nrhs; ++c) ident[c] = c;
+        VIE_CUDA(cudaMemcpyAsync(cols.p, ident.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+        const int nb1 = kr_nblk(n, nrhs, n_sm);
+        // x = 0: the unpreconditioned residual is b
+        kr_colnorms(b, n, nrhs, nb1, nullptr, rpart.as<double>(), bnorm.as<double>(), s);
+        VIE_CUDA(cudaMemcpyAsync(rnorm.p, bnorm.p, nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        kr_scatter_norm(a, W.as<double2>(), W.as<double2>(), nrhs, nb1, s);
+        kr_cycle_end(a, nrhs, nb1, 1, s);
+        read_state();
+        std::vector<int> live;
         while (true) {
-            std::vector<int> live;
+            live.clear();
             for (int c = 0; c < nrhs; ++c)
-                if (!R[c].done) live.push_back(c);
+                if (!h_pinned[KR_NCTR + c]) live.push_back(c);
             if (live.empty()) break;
-            for (int c : live) {
-                Rhs& r = R[c];
-                kscale(W.as<double2>() + (size_t)c * n, 1.0 / r.beta, r.V.as<double2>(), n, s);
-                std::fill(r.g.begin(), r.g.end(), cd(0));
-                r.g[0] = r.beta;
-                r.jdone = 0;
-                r.cycling = true;
-            }
-            for (int j = 0; j < m; ++j) {
-                std::vector<int> act;
-                for (int c : live)
-                    if (R[c].cycling && R[c].iters < maxit) act.push_back(c);
-                if (act.empty()) break;
-                const int k = (int)act.size();
-                for (int i = 0; i < k; ++i)
-                    VIE_CUDA(cudaMemcpyAsync(Xg.as<double2>() + (size_t)i * n, R[act[i]].V.as<double2>() + (size_t)j * n,
-                                             n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-                apply_inner(Xg.as<double2>(), Yg.as<double2>(), k);
-                ++applies;
-                double est_max = 0.0;
-                for (int i = 0; i < k; ++i) {
-                    Rhs& r = R[act[i]];
-                    double2* V0 = r.V.as<double2>();
-                    double2* vj1 = V0 + (size_t)(j + 1) * n;
-                    VIE_CUDA(cudaMemcpyAsync(vj1, Yg.as<double2>() + (size_t)i * n, n * sizeof(double2),
-                                             cudaMemcpyDeviceToDevice, s));
-                    // two-pass classical Gram-Schmidt in float64
-                    std::vector<cd> hsum(j + 1, cd(0));
-                    for (int pass = 0; pass < 2; ++pass) {
-                        kmdot(V0, n, j + 1, vj1, n, h.as<double2>(), ks, s);
-                        kmaxpy(V0, n, j + 1, h.as<double2>(), -1.0, vj1, n, s);
-                        VIE_CUDA(cudaMemcpyAsync(hv.data(), h.p, (j + 1) * sizeof(double2), cudaMemcpyDeviceToHost, s));
-                        VIE_CUDA(cudaStreamSynchronize(s));
-                        for (int l = 0; l <= j; ++l) hsum[l] += hv[l];
-                    }
-                    double hn = std::sqrt(knorm2(vj1, n, ks, s));
-                    if (hn > 0) kscale(vj1, 1.0 / hn, vj1, n, s);
-                    auto H = [&](int row, int col) -> cd& { return r.H[row + (size_t)col * (m + 1)]; };
-                    for (int l = 0; l <= j; ++l) H(l, j) = hsum[l];
-                    H(j + 1, j) = hn;
-                    // Givens rotations G = [[conj c, conj s], [-s, c]]
-                    for (int l = 0; l < j; ++l) {
-                        cd a = H(l, j), c2 = H(l + 1, j);
-                        H(l, j) = std::conj(r.cs[l]) * a + std::conj(r.sn[l]) * c2;
-                        H(l + 1, j) = -r.sn[l] * a + r.cs[l] * c2;
-                    }
-                    cd a = H(j, j), c2 = H(j + 1, j);
-                    double den = std::sqrt(std::norm(a) + std::norm(c2));
-                    r.cs[j] = den > 0 ? a / den : cd(1);
-                    r.sn[j] = den > 0 ? c2 / den : cd(0);
-                    H(j, j) = den;
-                    H(j + 1, j) = 0;
-                    r.g[j + 1] = -r.sn[j] * r.g[j];
-                    r.g[j] = std::conj(r.cs[j]) * r.g[j];
-                    ++r.iters;
-                    r.jdone = j + 1;
-                    double est = std::abs(r.g[j + 1]) / r.beta0;
-                    if (!std::isfinite(est)) fail(VIE_ERR_NAN, "non-finite residual in GMRES");
-                    est_max = std::max(est_max, est);
-                    if (est <= tol || hn == 0.0) r.cycling = false;
-                }
-                if (st && st->n_history < 512) st->history[st->n_history++] = est_max;
-            }
-            // x += V y with y = H^-1 g (upper triangular), per right-hand side
-            for (int c : live) {
-                Rhs& r = R[c];
-                if (r.jdone == 0) continue;
-                std::vector<cd> y(r.jdone);
-                for (int i = r.jdone - 1; i >= 0; --i) {
-                    cd acc = r.g[i];
-                    for (int l = i + 1; l < r.jdone; ++l) acc -= r.H[i + (size_t)l * (m + 1)] * y[l];
-                    y[i] = acc / r.H[i + (size_t)i * (m + 1)];
-                }
-                VIE_CUDA(cudaMemcpyAsync(h.p, y.data(), r.jdone * sizeof(double2), cudaMemcpyHostToDevice, s));
-                kmaxpy(r.V.as<double2>(), n, r.jdone, h.as<double2>(), 1.0, X + (size_t)c * n, n, s);
-            }
-            // float64 refinement residual for every right-hand side
-            residual(b, X, W.as<double2>());
-            ++refin;
-            for (int c : live) {
-                Rhs& r = R[c];
-                r.beta = std::sqrt(knorm2(W.as<double2>() + (size_t)c * n, n, ks, s));
-                r.res = r.beta / r.beta0;
-                if (r.res <= tol || r.iters >= maxit || r.beta == 0.0) r.done = true;
+            const int k = (int)live.size();
+            VIE_CUDA(cudaMemcpyAsync(cols.p, live.data(), k * sizeof(int), cudaMemcpyHostToDevice, s));
+            const int it0 = h_pinned[KR_IT];
+            if (o.launch == 1) {
+                launch_pre(k, s);
+                do {
+                    launch_body(k, s, 0, 0);
+                    VIE_CUDA(cudaMemcpyAsync(h_pinned, ctr.p, KR_NCTR * sizeof(int), cudaMemcpyDeviceToHost, s));
+                    VIE_CUDA(cudaStreamSynchronize(s));
+                } while (h_pinned[KR_CONT] && !h_pinned[KR_NAN]);
+                launch_post(k, b, X, s);
+                read_state();
+            } else {
+                CycleGraph& cg = graph_for(k, b, X);
+                VIE_CUDA(cudaGraphLaunch(cg.exec, s));
+                read_state();
+                VIE_COUNT_LAUNCH(cg.pre + cg.post + cg.body * (long long)(h_pinned[KR_IT] - it0));
             }
         }
-        int status = VIE_OK;
-        for (auto& r : R)
-            if (r.res > tol) status = VIE_ERR_NOT_CONVERGED;
-        return status;
     }
 };
 
@@ -212,6 +285,8 @@ int solve(Op& op, const vie_incident* inc, int nrhs, const vie_solve_opts* o, vo
         fail(VIE_ERR_INVALID_ARG, "an all-float64 solve needs VIE_C128 factors");
     if (o->precision != VIE_C128 && o->precision != VIE_C64 && o->precision != VIE_BF16X3 && o->precision != 0)
         fail(VIE_ERR_INVALID_ARG, "solve precision must be VIE_C64, VIE_BF16X3 or VIE_C128");
+    if (o->launch != 0 && o->launch != 1) fail(VIE_ERR_INVALID_ARG, "solve launch must be 0 (graph) or 1 (host loop)");
+    if (nrhs < 1 || nrhs > 1024) fail(VIE_ERR_INVALID_ARG, "vie_solve takes 1 to 1024 right-hand sides");
     cudaStream_t s = op.ctx->stream;
     const int64_t n = op.n();
     double t0 = now_s();
@@ -227,35 +302,39 @@ int solve(Op& op, const vie_incident* inc, int nrhs, const vie_solve_opts* o, vo
         xdev.alloc((size_t)n * nrhs * sizeof(double2));
         X = xdev.as<double2>();
     }
-    if (st) st->n_history = 0;
-    int applies = 0, refin = 0;
     Gmres G(op, *o, nrhs);
-    int status = G.run(b.as<double2>(), X, st, applies, refin);
-    // unpreconditioned relative residual with the compressed operator
-    KrylovScratch ks;
-    ks.init();
-    DevBuf zx((size_t)n * nrhs * sizeof(double2)), rr((size_t)n * nrhs * sizeof(double2));
-    op_apply64(op, X, zx.as<double2>(), nrhs, s);
-    ksub(b.as<double2>(), zx.as<double2>(), rr.as<double2>(), n * nrhs, s);
-    double worst = 0.0, worst_true = 0.0;
-    int iters = 0;
-    for (int c = 0; c < nrhs; ++c) {
-        double rn = std::sqrt(knorm2(rr.as<double2>() + (size_t)c * n, n, ks, s));
-        double bn = std::sqrt(knorm2(b.as<double2>() + (size_t)c * n, n, ks, s));
-        worst_true = std::max(worst_true, bn > 0 ? rn / bn : 0.0);
-        worst = std::max(worst, G.R[c].res);
-        iters = std::max(iters, G.R[c].iters);
-    }
+    G.run(b.as<double2>(), X);
+    // unpreconditioned relative residual ||b - Zs x|| / ||b|| with the compressed
+    // operator, from each column's last refinement (x has not changed since)
+    std::vector<double> hn(2 * nrhs), hres(nrhs), hh(512);
+    std::vector<int> hit(nrhs), hc(KR_NCTR);
+    VIE_CUDA(cudaMemcpyAsync(hn.data(), G.rnorm.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaMemcpyAsync(hn.data() + nrhs, G.bnorm.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaMemcpyAsync(hres.data(), G.res.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaMemcpyAsync(hit.data(), G.iters.p, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaMemcpyAsync(hh.data(), G.hist.p, 512 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaMemcpyAsync(hc.data(), G.ctr.p, KR_NCTR * sizeof(int), cudaMemcpyDeviceToHost, s));
     if (!o->out_on_device)
         VIE_CUDA(cudaMemcpyAsync(I_out, X, (size_t)n * nrhs * sizeof(double2), cudaMemcpyDeviceToHost, s));
     VIE_CUDA(cudaStreamSynchronize(s));
+    const double tol = o->tol > 0 ? o->tol : 1e-6;
+    double worst = 0.0, worst_true = 0.0;
+    int iters = 0, status = VIE_OK;
+    for (int c = 0; c < nrhs; ++c) {
+        worst_true = std::max(worst_true, hn[nrhs + c] > 0 ? hn[c] / hn[nrhs + c] : 0.0);
+        worst = std::max(worst, hres[c]);
+        iters = std::max(iters, hit[c]);
+        if (hres[c] > tol) status = VIE_ERR_NOT_CONVERGED;
+    }
     if (st) {
         st->iterations = iters;
-        st->applies = applies;
-        st->refinements = refin;
+        st->applies = hc[KR_APPLIES];
+        st->refinements = hc[KR_REFIN];
         st->residual = worst;
         st->true_residual = worst_true;
         st->t_solve_s = now_s() - t0;
+        st->n_history = std::min(512, hc[KR_IT]);
+        for (int i = 0; i < st->n_history; ++i) st->history[i] = hh[i];
     }
     return status;
 }

@@ -59,7 +59,7 @@ class IncidentC(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_iters", C.c_int), ("precision", C.c_int),
-                ("out_on_device", C.c_int), ("precond", C.c_int)]
+                ("out_on_device", C.c_int), ("precond", C.c_int), ("launch", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -260,10 +260,11 @@ class Operator:
         self.ctx.check(self.L.vie_rhs(self.h, C.byref(inc), nrhs, C.c_void_p(b_ptr), self.n,
                                       _stream(stream)))
 
-    def solve(self, khat, pol, tol=1e-6, restart=60, max_iters=2000, precision=C64, precond=1, out_ptr=None):
+    def solve(self, khat, pol, tol=1e-6, restart=60, max_iters=2000, precision=C64, precond=1, out_ptr=None,
+              launch=0):
         """Returns (I (numpy complex128 n x nrhs, or None with out_ptr), stats dict, status)."""
         inc, keep, nrhs = _incident_struct(khat, pol)
-        o = SolveOpts(tol, restart, max_iters, precision, 1 if out_ptr else 0, precond)
+        o = SolveOpts(tol, restart, max_iters, precision, 1 if out_ptr else 0, precond, launch)
         st = SolveStats()
         out = None
         if out_ptr is None:

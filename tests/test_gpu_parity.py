@@ -285,3 +285,31 @@ def test_bf16x3_multi_rhs_solve(tiny_op, tiny_dense):
     assert status == vie.VIE_OK and st["residual"] <= 1e-6
     for c in range(len(kh)):
         assert rel(I[:, c], np.linalg.solve(Z, A.rhs(P, kh[c], pol[c]))) <= 5e-4
+
+
+# ------------------------------------------------ graph-captured restart cycles
+def test_graph_cycle_equals_host_loop(tiny_op, tiny_dense):
+    # the same kernels in the same order: one CUDA graph per restart cycle
+    # (Arnoldi steps in a conditional while-node) against host-launched steps
+    P, Z, _, _, _ = tiny_dense
+    kh, pol = workloads.angle_sweep(2, 40.0)           # 4 right-hand sides
+    Ig, stg, sg = tiny_op.solve(kh, pol, tol=1e-6, restart=8, launch=0)
+    Ih, sth, sh = tiny_op.solve(kh, pol, tol=1e-6, restart=8, launch=1)
+    assert sg == sh == vie.VIE_OK
+    assert stg["iterations"] == sth["iterations"] and stg["refinements"] == sth["refinements"] > 1
+    assert np.array_equal(Ig, Ih)
+    assert stg["history"] == sth["history"]
+    for c in range(len(kh)):
+        assert rel(Ig[:, c], np.linalg.solve(Z, A.rhs(P, kh[c], pol[c]))) <= 5e-4
+
+
+def test_solver_history_and_limits(tiny_op, tiny_dense):
+    P, Z, b, kh, pol = tiny_dense
+    I, st, status = tiny_op.solve(kh[None], pol[None], tol=1e-6)
+    h = st["history"]
+    assert len(h) == st["applies"] and h[-1] <= 1e-6 < h[0]
+    # an iteration cap that stops the solve early reports NOT_CONVERGED with the stats written
+    I2, st2, status2 = tiny_op.solve(kh[None], pol[None], tol=1e-12, max_iters=3)
+    assert status2 == vie.VIE_ERR_NOT_CONVERGED and st2["iterations"] == 3 and st2["residual"] > 1e-12
+    with pytest.raises(vie.VieError):
+        tiny_op.solve(np.tile(kh, (1025, 1)), np.tile(pol, (1025, 1)))
