@@ -42,7 +42,7 @@ void op_apply_fused_bf16x3(Op& op, const float2* x, float2* y, int nrhs, cudaStr
     const int64_t n = op.n();
     ensure_F(op, (size_t)n * nrhs * sizeof(float2));
     float2* F = op.d_F.as<float2>();
-    apply_far_bf16x3(op, x, n, F, n, nrhs, s);
+    apply_far_umma(op, x, n, F, n, nrhs, s);
     self_gemm<float2, float2>(op, op.d_inv32.as<float2>(), x, n, F, n, y, n, nrhs, 1, s);
 }
 
@@ -64,7 +64,8 @@ void op_apply_fused64(Op& op, const double2* x, double2* y, int nrhs, cudaStream
     self_gemm<double2, double2>(op, op.d_inv64.as<double2>(), x, n, F, n, y, n, nrhs, 1, s);
 }
 
-void op_reserve(Op& op, int nrhs) {
+void op_reserve(Op& op, int nrhs, int precision, cudaStream_t s) {
+    if (precision == VIE_BF16X3) umma_prepare(op, s);
     ensure_F(op, (size_t)op.n() * nrhs * sizeof(double2));
     const size_t need = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(double2);
     if (op.d_t.bytes < need) op.d_t.alloc(need);
@@ -367,7 +368,7 @@ int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int prec
                 if (o.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "VIE_BF16X3 applies need VIE_C64 factors");
                 ensure_F(o, (size_t)o.n() * nrhs * sizeof(float2));
                 float2* F = o.d_F.as<float2>();
-                apply_far_bf16x3(o, (const float2*)x, o.n(), F, o.n(), nrhs, s);
+                apply_far_umma(o, (const float2*)x, o.n(), F, o.n(), nrhs, s);
                 self_gemm<float2, float2>(o, o.d_zself32.as<float2>(), (const float2*)x, o.n(), F, o.n(),
                                           (float2*)y, o.n(), nrhs, 0, s);
             }

@@ -1,0 +1,519 @@
+// Multi-right-hand-side far apply on the 5th-generation tensor cores
+// (tcgen05.mma, accumulators in tensor memory), split precision BF16x3.
+//
+// With s right-hand sides the far apply is two sets of dense contractions,
+//   phase 1:  t_b = R_b X_J           (paper Sec. 5.2, the inner product R x)
+//   phase 2:  F_a = sum_b Q_b[a] t_b  (the outer product Q t, per atom a)
+// Each complex float32 operand value v is split into bfloat16 hi = bf16(v)
+// and lo = bf16(v - hi) for its real and imaginary parts; a real product is
+// hi.hi + hi.lo + lo.hi (the lo.lo term, ~2^-16 relative, is dropped), so a
+// complex product is twelve bf16 MMAs accumulated in float32:
+//   D_r += Ar Br - Ai Bi,   D_i += Ar Bi + Ai Br,
+// the minus sign taken by the MMA's negate-A bit.
+//
+// Tile: 128 output rows (tensor-memory lanes) x up to 64 right-hand sides;
+// D_r occupies tensor-memory columns [0, 64) and D_i columns [64, 128).
+// The K dimension is staged 32 complex values at a time: the four warps load
+// the operands from global memory, split them into bf16 planes and store the
+// planes in shared memory in the canonical no-swizzle K-major layout (8x8
+// core matrices of 128 contiguous bytes); one thread then issues the 24 MMAs
+// of the stage and commits them to an mbarrier, and while the tensor core
+// works on one stage the warps fill the other.
+//
+// Phase 1 stacks the R rows of all blocks that share one source atom list,
+// so one gathered x_J feeds up to 128 rows; phase 2 walks one virtual K axis
+// made of every (block, rank index) that touches the atom, so short ranks do
+// not pad the K stages.
+//
+// Every wait on an mbarrier gives up after about a second of clock cycles,
+// records the failure in an error word and leaves the kernel after freeing
+// its tensor memory.
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "common.h"
+#include "cplx.cuh"
+
+namespace vie {
+
+namespace {
+
+constexpr int kM = 128;                 // output rows per tile
+constexpr int kN = 64;                  // right-hand sides per pass
+constexpr int kKS = 32;                 // complex K values per stage
+constexpr int kThr = 128;               // four warps
+constexpr int kTmemCols = 128;          // D_r: [0, 64), D_i: [64, 128)
+constexpr int kChunksA = kM * kKS / 8;  // 16-byte chunks per A plane (512)
+constexpr int kChunksB = kN * kKS / 8;  // 16-byte chunks per B plane (256)
+constexpr uint32_t kLboA = kM * 16;     // bytes between K-adjacent core matrices of A
+constexpr uint32_t kLboB = kN * 16;
+constexpr uint32_t kSbo = 128;          // bytes between 8-row groups
+
+// one stage: planes (re hi, re lo, im hi, im lo) of A (128 x 32) and B (64 x 32);
+// chunk (row, q) of a plane holds K values 8q .. 8q+7 of that row and sits at
+// index q * rows + row, i.e. core matrix (row / 8, q) at q * LBO + (row / 8) * 128
+struct Stage {
+    uint4 a[4][kChunksA];
+    uint4 b[4][kChunksB];
+};
+constexpr size_t kStageBytes = sizeof(Stage);  // 48 KiB
+// two stages plus a guard band, so that no descriptor reach can leave the
+// allocation whatever the stride interpretation
+constexpr size_t kSmemBytes = 2 * kStageBytes + 12 * 1024;
+
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor, canonical layout without swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((kSbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of this architecture
+    return d;                // base offset 0, relative LBO, no swizzle
+}
+
+// instruction descriptor of kind::f16: bf16 x bf16 -> f32, both K-major,
+// M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc(int n, bool neg_a) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (neg_a ? (1u << 13) : 0u) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(kM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+}
+
+// bounded wait for the completion of the phase with the given parity
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// split 8 complex values into the 16-byte chunk of each plane
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+__device__ __forceinline__ void split1(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(v);
+    l = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+template <int CHUNKS>
+__device__ __forceinline__ void put8(uint4 (*planes)[CHUNKS], int chunk, const float2 (&v)[8]) {
+    uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        __nv_bfloat16 h0, l0, h1, l1;
+        split1(v[2 * e].x, h0, l0);
+        split1(v[2 * e + 1].x, h1, l1);
+        rh[e] = pack2(h0, h1);
+        rl[e] = pack2(l0, l1);
+        split1(v[2 * e].y, h0, l0);
+        split1(v[2 * e + 1].y, h1, l1);
+        ih[e] = pack2(h0, h1);
+        il[e] = pack2(l0, l1);
+    }
+    planes[0][chunk] = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+    planes[1][chunk] = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+    planes[2][chunk] = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+    planes[3][chunk] = make_uint4(il[0], il[1], il[2], il[3]);
+}
+
+__device__ __forceinline__ void zero8(float2 (&v)[8]) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = make_float2(0.f, 0.f);
+}
+
+// the 24 MMAs of one stage (two K steps of 16)
+__device__ __forceinline__ void issue_stage(const Stage& st, uint32_t tm, int nmma, bool first) {
+    const uint32_t id = idesc(nmma, false), idn = idesc(nmma, true);
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+        uint64_t A[4], B[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            A[p] = sdesc(smem_u32(&st.a[p][0]) + ks * 2 * kLboA, kLboA);
+            B[p] = sdesc(smem_u32(&st.b[p][0]) + ks * 2 * kLboB, kLboB);
+        }
+        const uint32_t acc0 = (first && ks == 0) ? 0u : 1u;
+        // planes: 0 re hi, 1 re lo, 2 im hi, 3 im lo
+        umma(tm, A[0], B[0], id, acc0);
+        umma(tm, A[0], B[1], id, 1u);
+        umma(tm, A[1], B[0], id, 1u);
+        umma(tm, A[2], B[2], idn, 1u);
+        umma(tm, A[2], B[3], idn, 1u);
+        umma(tm, A[3], B[2], idn, 1u);
+        umma(tm + kN, A[0], B[2], id, acc0);
+        umma(tm + kN, A[0], B[3], id, 1u);
+        umma(tm + kN, A[1], B[2], id, 1u);
+        umma(tm + kN, A[2], B[0], id, 1u);
+        umma(tm + kN, A[2], B[1], id, 1u);
+        umma(tm + kN, A[3], B[0], id, 1u);
+    }
+}
+
+// Operand sources.  load_a(row, q, k0, v) fills the 8 values K = k0+8q.. of
+// A row `row`; load_b(col, q, k0, v) those of right-hand side `col`.
+struct Phase1 {
+    // stacked rows of R (conj of the stored R^H rows) times x gathered over the source atoms
+    const float2* fac;
+    const long long* rowoff;
+    const int* rowt;
+    const int* S;
+    const float2* x;
+    int64_t ldx;
+    int np, nK, row_begin, rows, c0, ncol;
+    __device__ __forceinline__ void load_a(int row, int q, int k0, float2 (&v)[8]) const {
+        const int j = k0 + 8 * q;
+        if (row >= rows || j >= nK) {
+            zero8(v);
+            return;
+        }
+        const float2* src = fac + rowoff[row_begin + row] + j;
+        if (j + 8 <= nK) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float4 w = __ldcs(reinterpret_cast<const float4*>(src) + e);
+                v[2 * e] = make_float2(w.x, -w.y);
+                v[2 * e + 1] = make_float2(w.z, -w.w);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float2 w = j + e < nK ? __ldcs(src + e) : make_float2(0.f, 0.f);
+                v[e] = make_float2(w.x, -w.y);
+            }
+        }
+    }
+    __device__ __forceinline__ void load_b(int col, int q, int k0, float2 (&v)[8]) const {
+        const int j = k0 + 8 * q;
+        if (col >= ncol || j >= nK) {
+            zero8(v);
+            return;
+        }
+        const float2* xc = x + (int64_t)(c0 + col) * ldx;
+        const int slot = j / np, off = j - slot * np;
+        if (j + 8 <= nK && off + 8 <= np) {
+            const float4* p = reinterpret_cast<const float4*>(xc + (int64_t)S[slot] * np + off);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float4 w = __ldg(p + e);
+                v[2 * e] = make_float2(w.x, w.y);
+                v[2 * e + 1] = make_float2(w.z, w.w);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int jj = j + e;
+                if (jj < nK) {
+                    const int sl = jj / np, of = jj - sl * np;
+                    v[e] = __ldg(xc + (int64_t)S[sl] * np + of);
+                } else {
+                    v[e] = make_float2(0.f, 0.f);
+                }
+            }
+        }
+    }
+};
+
+struct Phase2 {
+    // rows p0.. of one atom in every Q_b touching it, times the matching t_b entries
+    const float2* fac;
+    const long long* qoff;
+    const int* tidx;
+    const float2* t;
+    int64_t ldt;
+    int64_t kbase;
+    int nK, p0, rows, c0, ncol;
+    __device__ __forceinline__ void load_a(int row, int q, int k0, float2 (&v)[8]) const {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int kk = k0 + 8 * q + e;
+            v[e] = (row < rows && kk < nK) ? __ldcs(fac + qoff[kbase + kk] + p0 + row) : make_float2(0.f, 0.f);
+        }
+    }
+    __device__ __forceinline__ void load_b(int col, int q, int k0, float2 (&v)[8]) const {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int kk = k0 + 8 * q + e;
+            v[e] = (col < ncol && kk < nK) ? __ldg(t + tidx[kbase + kk] + (int64_t)(c0 + col) * ldt)
+                                           : make_float2(0.f, 0.f);
+        }
+    }
+};
+
+// A segments: phase 1 keeps the 4 K chunks of a row on neighbouring threads
+// (contiguous R rows), phase 2 keeps rows on neighbouring threads (contiguous
+// Q columns)
+template <bool kRowFast>
+__device__ __forceinline__ void a_seg(int s, int& row, int& q) {
+    if (kRowFast) {
+        row = s & (kM - 1);
+        q = s >> 7;
+    } else {
+        row = s >> 2;
+        q = s & 3;
+    }
+}
+
+struct Ctl {
+    uint64_t mbar[2];
+    uint32_t tmem;
+    int ok;
+};
+
+// One output tile (rows x ncol) over K = nK: stages g0, g0+1, ... of this CTA.
+// Returns false when a wait gave up.  On return every thread may read the
+// accumulators (when nK > 0).
+template <class Src, bool kRowFast>
+__device__ bool run_tile(const Src& src, Stage* stages, Ctl& ctl, uint32_t& g, int nK, int nmma) {
+    const int tid = threadIdx.x;
+    const int nst = (nK + kKS - 1) / kKS;
+    for (int st = 0; st < nst; ++st, ++g) {
+        const int k0 = st * kKS;
+        Stage& S = stages[g & 1];
+        float2 va[4][8], vb[2][8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int row, q;
+            a_seg<kRowFast>(tid + i * kThr, row, q);
+            src.load_a(row, q, k0, va[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int s = tid + i * kThr;
+            src.load_b(s >> 2, s & 3, k0, vb[i]);
+        }
+        // the stage buffer is free once the MMAs issued two stages ago are done
+        if (tid == 0) ctl.ok = (g < 2) ? 1 : (mbar_wait(smem_u32(&ctl.mbar[g & 1]), ((g >> 1) - 1) & 1) ? 1 : 0);
+        __syncthreads();
+        if (!ctl.ok) return false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int row, q;
+            a_seg<kRowFast>(tid + i * kThr, row, q);
+            put8<kChunksA>(S.a, q * kM + row, va[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int s = tid + i * kThr;
+            put8<kChunksB>(S.b, (s & 3) * kN + (s >> 2), vb[i]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            issue_stage(S, ctl.tmem, nmma, st == 0);
+            umma_commit(smem_u32(&ctl.mbar[g & 1]));
+        }
+    }
+    if (nst > 0) {
+        const uint32_t gl = g - 1;
+        if (tid == 0) ctl.ok = mbar_wait(smem_u32(&ctl.mbar[gl & 1]), (gl >> 1) & 1) ? 1 : 0;
+        __syncthreads();
+        if (!ctl.ok) return false;
+        fence_after();
+    }
+    return true;
+}
+
+// out[rowidx(r) + c * ld] = (D_r, D_i)[r, c] for r < rows, c < ncol (zeros when nK == 0)
+template <class RowIdx>
+__device__ void epilogue(const Ctl& ctl, bool have, int rows, int ncol, RowIdx rowidx, float2* out, int64_t ld) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = warp * 32 + lane;
+    const uint32_t base = ctl.tmem + ((uint32_t)(warp * 32) << 16);
+    const bool mine = r < rows;
+    const int64_t ri = mine ? rowidx(r) : 0;
+    for (int cb = 0; cb < ncol; cb += 16) {
+        float vr[16], vi[16];
+        if (have) {
+            tmem_ld16(base + cb, vr);
+            tmem_ld16(base + kN + cb, vi);
+            tmem_wait_ld();
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) vr[i] = vi[i] = 0.f;
+        }
+        if (mine) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (cb + i < ncol) out[ri + (int64_t)(cb + i) * ld] = make_float2(vr[i], vi[i]);
+        }
+    }
+    fence_before();
+    __syncthreads();  // accumulators read before the next tile overwrites them
+}
+
+__device__ void setup(Ctl& ctl) {
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&ctl.mbar[0]));
+        mbar_init(smem_u32(&ctl.mbar[1]));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+}
+
+// leave: if a wait gave up, give the tensor core one more bounded chance to
+// finish what was issued, then free the tensor memory
+__device__ void teardown(Ctl& ctl, bool failed, uint32_t g, int* err) {
+    if (failed) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            if (g > 0) mbar_wait(smem_u32(&ctl.mbar[(g - 1) & 1]), ((g - 1) >> 1) & 1);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(ctl.tmem), "r"(kTmemCols)
+                     : "memory");
+}
+
+__global__ void __launch_bounds__(kThr) u1_kernel(const FarBlockDev* __restrict__ blocks,
+                                                  const int* __restrict__ batoms, const int4* __restrict__ items,
+                                                  const int* __restrict__ cta_ptr,
+                                                  const long long* __restrict__ rowoff, const int* __restrict__ rowt,
+                                                  const float2* __restrict__ fac, const float2* __restrict__ x,
+                                                  int64_t ldx, int np, float2* __restrict__ t, int64_t ldt, int nrhs,
+                                                  int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    Stage* stages = reinterpret_cast<Stage*>(smem);
+    __shared__ Ctl ctl;
+    setup(ctl);
+    uint32_t g = 0;
+    bool failed = false;
+    for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1] && !failed; ++it) {
+        const int4 item = items[it];
+        const FarBlockDev B = blocks[item.x];
+        for (int c0 = 0; c0 < nrhs && !failed; c0 += kN) {
+            Phase1 src{fac, rowoff, rowt, batoms + B.s_off, x, ldx, np, B.n, item.y, item.z, c0, min(kN, nrhs - c0)};
+            const int nmma = max(16, (src.ncol + 15) / 16 * 16);
+            if (!run_tile<Phase1, false>(src, stages, ctl, g, B.n, nmma)) {
+                failed = true;
+                break;
+            }
+            const int* rt = rowt + item.y;
+            epilogue(ctl, B.n > 0, item.z, src.ncol, [rt](int r) { return (int64_t)rt[r]; }, t + (int64_t)c0 * ldt,
+                     ldt);
+        }
+    }
+    teardown(ctl, failed, g, err);
+}
+
+__global__ void __launch_bounds__(kThr) u2_kernel(const int4* __restrict__ items, const int* __restrict__ cta_ptr,
+                                                  const long long* __restrict__ qoff, const int* __restrict__ tidx,
+                                                  const long long* __restrict__ kptr, const float2* __restrict__ fac,
+                                                  const float2* __restrict__ t, int64_t ldt, int np,
+                                                  float2* __restrict__ F, int64_t ldf, int nrhs, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    Stage* stages = reinterpret_cast<Stage*>(smem);
+    __shared__ Ctl ctl;
+    setup(ctl);
+    uint32_t g = 0;
+    bool failed = false;
+    for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1] && !failed; ++it) {
+        const int4 item = items[it];
+        const int a = item.x, p0 = item.y, rows = item.z - item.y;
+        const long long kb = kptr[a];
+        const int nK = (int)(kptr[a + 1] - kb);
+        for (int c0 = 0; c0 < nrhs && !failed; c0 += kN) {
+            Phase2 src{fac, qoff, tidx, t, ldt, kb, nK, p0, rows, c0, min(kN, nrhs - c0)};
+            const int nmma = max(16, (src.ncol + 15) / 16 * 16);
+            if (!run_tile<Phase2, true>(src, stages, ctl, g, nK, nmma)) {
+                failed = true;
+                break;
+            }
+            const int64_t rb = (int64_t)a * np + p0;
+            epilogue(ctl, nK > 0, rows, src.ncol, [rb](int r) { return rb + r; }, F + (int64_t)c0 * ldf, ldf);
+        }
+    }
+    teardown(ctl, failed, g, err);
+}
+
+std::once_flag g_umma_attr_once;
+
+}  // namespace
+
+void umma_prepare(Op& op, cudaStream_t s) {
+    if (op.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "the tcgen05 apply needs VIE_C64 factors");
+    build_umma_lists(op);
+    std::call_once(g_umma_attr_once, [] {
+        cudaFuncSetAttribute(u1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        cudaFuncSetAttribute(u2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    });
+    if (!op.d_err.p) {
+        op.d_err.alloc(sizeof(int));
+        VIE_CUDA(cudaMemsetAsync(op.d_err.p, 0, sizeof(int), s));
+    }
+}
+
+void apply_far_umma(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s) {
+    umma_prepare(op, s);
+    if (((uintptr_t)x & 15) || (ldx & 1)) fail(VIE_ERR_INVALID_ARG, "tensor-core apply: x must be 16-byte aligned");
+    const size_t need = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(float2);
+    if (op.d_t.bytes < need) op.d_t.alloc(need);
+    const float2* fac = op.d_factors.as<float2>();
+    if (op.n_u1_items > 0) {
+        u1_kernel<<<op.n_cta_u, kThr, kSmemBytes, s>>>(
+            op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(), op.d_u1_items.as<int4>(), op.d_u1_cta.as<int>(),
+            op.d_u1_rowoff.as<long long>(), op.d_u1_rowt.as<int>(), fac, x, ldx, op.np, op.d_t.as<float2>(),
+            op.t_total, nrhs, op.d_err.as<int>());
+        VIE_CHECK_LAUNCH();
+    }
+    u2_kernel<<<op.n_cta_u, kThr, kSmemBytes, s>>>(
+        op.d_u2_items.as<int4>(), op.d_u2_cta.as<int>(), op.d_u2_qoff.as<long long>(), op.d_u2_tidx.as<int>(),
+        op.d_u2_kptr.as<long long>(), fac, op.d_t.as<float2>(), op.t_total, op.np, F, ldf, nrhs, op.d_err.as<int>());
+    VIE_CHECK_LAUNCH();
+}
+
+}  // namespace vie

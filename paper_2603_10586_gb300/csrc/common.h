@@ -159,8 +159,16 @@ struct Op {
     DevBuf d_p1_items, d_p1_cta;       // phase 1 items and per-CTA ranges
     DevBuf d_p2_items, d_p2_cta, d_p2_csr, d_p2_ent;
     int n_p1_items = 0, n_p2_items = 0, n_cta = 0;
-    DevBuf d_t1_items, d_t1_cta, d_t2_items, d_t2_cta;  // tensor-core path (64-row items)
+    DevBuf d_t1_items, d_t1_cta, d_t2_items, d_t2_cta;  // warp-MMA tensor path (64-row items)
     int n_t1_items = 0, n_t2_items = 0, n_cta_tc = 0;
+    // tcgen05 tensor path (built on first use): phase 1 stacks the R rows of
+    // all blocks with the same source atoms (one gathered x for up to 128
+    // rows), phase 2 walks one virtual K axis over all blocks of an atom
+    bool umma_ready = false;
+    DevBuf d_u1_rowoff, d_u1_rowt, d_u1_items, d_u1_cta;
+    DevBuf d_u2_qoff, d_u2_tidx, d_u2_kptr, d_u2_items, d_u2_cta;
+    int n_u1_items = 0, n_u2_items = 0, n_cta_u = 0;
+    DevBuf d_err;  // set by a tensor-core kernel whose bounded wait gave up
     // scratch
     DevBuf d_t, d_F;
     DevBuf d_xs;  // float64 vectors split into float32 head + tail (double-float apply)
@@ -232,6 +240,12 @@ template <class TF, class TX>
 void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, cudaStream_t s);
 
 void apply_static(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s);
+// work lists of the tcgen05 multi-RHS apply (host.cpp); idempotent
+void build_umma_lists(Op& op);
+// far part with c64 factors and c64 vectors, split-precision bf16 on tcgen05
+void apply_far_umma(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
+// everything the tcgen05 apply allocates or configures, done ahead of graph capture
+void umma_prepare(Op& op, cudaStream_t s);
 // far part with c64 factors and c128 vectors in double-float arithmetic
 void apply_far_df(Op& op, const double2* x, int64_t ldx, double2* F, int64_t ldf, int nrhs, cudaStream_t s);
 // apply_tc.cu: several right-hand sides on the tensor cores (BF16x3)

@@ -325,6 +325,87 @@ void build_apply_lists(Op& op) {
     upload(op.d_t2_cta, e2);
     upload(op.d_p2_csr, csr);
     upload(op.d_p2_ent, flat.empty() ? std::vector<int2>{make_int2(0, 0)} : flat);
+    op.umma_ready = false;
+}
+
+void build_umma_lists(Op& op) {
+    if (op.umma_ready) return;
+    const int nb = (int)op.blocks.size();
+    constexpr int kRows = 128;
+    op.n_cta_u = op.ctx->n_sm * 2;
+    // phase 1: blocks with the same source atoms share x_J, so their R rows
+    // are stacked into one tall operand and cut into 128-row tiles
+    std::map<std::vector<int>, std::vector<int>> groups;
+    for (int i = 0; i < nb; ++i) {
+        const auto& b = op.blocks[i];
+        if (b.rank == 0) continue;
+        std::vector<int> key(op.block_atoms.begin() + b.s_off, op.block_atoms.begin() + b.s_off + b.ns);
+        groups[key].push_back(i);
+    }
+    std::vector<long long> rowoff;
+    std::vector<int> rowt;
+    std::vector<int4> it1;
+    std::vector<double> w1;
+    for (const auto& kv : groups) {
+        const int rep = kv.second.front();
+        const int64_t start = (int64_t)rowoff.size();
+        for (int i : kv.second) {
+            const auto& b = op.blocks[i];
+            for (int k = 0; k < b.rank; ++k) {
+                rowoff.push_back((long long)(b.rh_off + (int64_t)k * b.n));
+                rowt.push_back((int)(b.t_off_vec + k));
+            }
+        }
+        const int64_t total = (int64_t)rowoff.size() - start;
+        for (int64_t r0 = 0; r0 < total; r0 += kRows) {
+            const int nr = (int)std::min<int64_t>(kRows, total - r0);
+            it1.push_back(make_int4(rep, (int)(start + r0), nr, 0));
+            w1.push_back((double)(nr + 32) * op.blocks[rep].n);
+        }
+    }
+    // phase 2: per atom every (block, rank index) as one virtual K axis
+    std::vector<std::vector<int2>> ent(op.N);
+    for (int i = 0; i < nb; ++i) {
+        const auto& b = op.blocks[i];
+        if (b.rank == 0) continue;
+        for (int s = 0; s < b.nt; ++s) ent[op.block_atoms[b.t_off + s]].push_back(make_int2(i, s));
+    }
+    std::vector<long long> qoff, kptr(op.N + 1, 0);
+    std::vector<int> tidx;
+    std::vector<int4> it2;
+    std::vector<double> w2;
+    for (int a = 0; a < op.N; ++a) {
+        for (auto e : ent[a]) {
+            const auto& b = op.blocks[e.x];
+            for (int k = 0; k < b.rank; ++k) {
+                qoff.push_back((long long)(b.q_off + (int64_t)e.y * op.np + (int64_t)k * b.m));
+                tidx.push_back((int)(b.t_off_vec + k));
+            }
+        }
+        kptr[a + 1] = (long long)qoff.size();
+        const double K = (double)(kptr[a + 1] - kptr[a]);
+        for (int p0 = 0; p0 < op.np; p0 += kRows) {
+            const int p1 = std::min(op.np, p0 + kRows);
+            it2.push_back(make_int4(a, p0, p1, 0));
+            w2.push_back((double)(p1 - p0 + 32) * (K + 1.0));
+        }
+    }
+    std::vector<int4> q1, q2;
+    std::vector<int> e1, e2;
+    pack_lpt(it1, w1, op.n_cta_u, q1, e1);
+    pack_lpt(it2, w2, op.n_cta_u, q2, e2);
+    op.n_u1_items = (int)q1.size();
+    op.n_u2_items = (int)q2.size();
+    upload(op.d_u1_rowoff, rowoff.empty() ? std::vector<long long>{0} : rowoff);
+    upload(op.d_u1_rowt, rowt.empty() ? std::vector<int>{0} : rowt);
+    upload(op.d_u1_items, q1.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : q1);
+    upload(op.d_u1_cta, e1);
+    upload(op.d_u2_qoff, qoff.empty() ? std::vector<long long>{0} : qoff);
+    upload(op.d_u2_tidx, tidx.empty() ? std::vector<int>{0} : tidx);
+    upload(op.d_u2_kptr, kptr);
+    upload(op.d_u2_items, q2.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : q2);
+    upload(op.d_u2_cta, e2);
+    op.umma_ready = true;
 }
 
 }  // namespace vie

@@ -90,6 +90,6 @@ void op_apply_fused64(Op& op, const double2* x, double2* y, int nrhs, cudaStream
 void op_precond64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s);
 // size the operator's apply workspaces for nrhs float64 columns (no allocation
 // may happen while a CUDA graph is being captured)
-void op_reserve(Op& op, int nrhs);
+void op_reserve(Op& op, int nrhs, int precision, cudaStream_t s);
 
 }  // namespace vie

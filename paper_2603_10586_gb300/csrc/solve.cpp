@@ -92,7 +92,7 @@ struct Gmres {
         Rl.alloc(vec);
         Wl.alloc(vec);
         W.alloc(vec);
-        op_reserve(op, nrhs);
+        op_reserve(op, nrhs, o.precision, s);
         VIE_CUDA(cudaMemsetAsync(ctr.p, 0, KR_NCTR * sizeof(int), s));
         VIE_CUDA(cudaMemsetAsync(hist.p, 0, 512 * sizeof(double), s));
         a.n = n;
@@ -232,6 +232,11 @@ struct Gmres {
         VIE_CUDA(cudaMemcpyAsync(h_pinned + KR_NCTR, done.p, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
         VIE_CUDA(cudaStreamSynchronize(s));
         if (h_pinned[KR_NAN]) fail(VIE_ERR_NAN, "non-finite residual in GMRES");
+        if (op.d_err.p) {
+            int e = 0;
+            VIE_CUDA(cudaMemcpy(&e, op.d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+            if (e) fail(VIE_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
+        }
     }
 
     void run(const double2* b, double2* X) {

@@ -313,3 +313,22 @@ def test_solver_history_and_limits(tiny_op, tiny_dense):
     assert status2 == vie.VIE_ERR_NOT_CONVERGED and st2["iterations"] == 3 and st2["residual"] > 1e-12
     with pytest.raises(vie.VieError):
         tiny_op.solve(np.tile(kh, (1025, 1)), np.tile(pol, (1025, 1)))
+
+
+@pytest.mark.parametrize("nrhs", [3, 16, 64])
+def test_bf16x3_apply_4cube_array(ctx, nrhs):
+    # 8x8 array of 4^3-voxel cubes (240 unknowns per atom, three tree levels):
+    # the tensor-core apply against the float32 SIMT apply of the same factors
+    import torch as th
+    g = workloads.square_array(8, 4)
+    op = vie.Operator(ctx, g)
+    op.compress(1e-4, vie.C64)
+    X = th.from_numpy(workloads.random_complex(op.n, 7, cols=nrhs).T.astype(np.complex64).copy()).cuda()
+    Y = th.zeros_like(X)
+    Yr = th.zeros_like(X)
+    for fl in (0, vie.FUSE_PRECOND):
+        op.apply(X.data_ptr(), Y.data_ptr(), nrhs, vie.BF16X3, fl)
+        op.apply(X.data_ptr(), Yr.data_ptr(), nrhs, vie.C64, fl)
+        th.cuda.synchronize()
+        assert rel(Y.cpu().numpy(), Yr.cpu().numpy()) < 5e-5
+    op.close()
