@@ -231,6 +231,21 @@ def run_profile(args):
     from paper_2603_10586_gb300 import vie
     torch.cuda.set_device(0)
     ctx = vie.Context(0)
+    if args.profile_case == "multirhs-small":
+        # 16x16 array of 4^3-voxel cubes, 64 right-hand sides, tensor-core applies
+        g = workloads.square_array(16, 4)
+        op = vie.Operator(ctx, g)
+        info = op.compress(TOL_COMPRESS, vie.C64)
+        x = torch.randn((64, op.n), dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            op.apply(x.data_ptr(), y.data_ptr(), 64, vie.BF16X3, vie.FUSE_PRECOND)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": args.profile_case, "n": op.n, "nrhs": 64,
+                          "factor_entries": info["factor_entries"]}), flush=True)
+        op.close()
+        ctx.close()
+        return 0
     if args.profile_case == "small":
         g, kh, pol = workloads.square_array(8, 6), *workloads.normal_incidence()
     else:
@@ -264,7 +279,7 @@ def main():
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--profile", action="store_true", help="one untimed step for ncu captures")
-    ap.add_argument("--profile-case", default="scale", choices=["scale", "small"])
+    ap.add_argument("--profile-case", default="scale", choices=["scale", "small", "multirhs-small"])
     args = ap.parse_args()
     if args.profile:
         return run_profile(args)

@@ -42,7 +42,7 @@ namespace {
 constexpr int kM = 128;                 // output rows per tile
 constexpr int kN = 64;                  // right-hand sides per pass
 constexpr int kKS = 32;                 // complex K values per stage
-constexpr int kThr = 128;               // four warps
+constexpr int kThr = 256;               // eight warps (two per tensor-memory lane quarter)
 constexpr int kTmemCols = 128;          // D_r: [0, 64), D_i: [64, 128)
 constexpr int kChunksA = kM * kKS / 8;  // 16-byte chunks per A plane (512)
 constexpr int kChunksB = kN * kKS / 8;  // 16-byte chunks per B plane (256)
@@ -58,9 +58,7 @@ struct Stage {
     uint4 b[4][kChunksB];
 };
 constexpr size_t kStageBytes = sizeof(Stage);  // 48 KiB
-// two stages plus a guard band, so that no descriptor reach can leave the
-// allocation whatever the stride interpretation
-constexpr size_t kSmemBytes = 2 * kStageBytes + 12 * 1024;
+constexpr size_t kSmemBytes = 2 * kStageBytes;  // two stages: 96 KiB, two CTAs per SM
 
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
@@ -130,28 +128,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// split 8 complex values into the 16-byte chunk of each plane
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+// split two floats (K positions 2e, 2e+1) into packed bf16 hi and lo words
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // a in the low half
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
 }
-__device__ __forceinline__ void split1(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
-    h = __float2bfloat16_rn(v);
-    l = __float2bfloat16_rn(v - __bfloat162float(h));
-}
+// 8 complex values -> the 16-byte chunk of each plane
 template <int CHUNKS>
 __device__ __forceinline__ void put8(uint4 (*planes)[CHUNKS], int chunk, const float2 (&v)[8]) {
     uint32_t rh[4], rl[4], ih[4], il[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        __nv_bfloat16 h0, l0, h1, l1;
-        split1(v[2 * e].x, h0, l0);
-        split1(v[2 * e + 1].x, h1, l1);
-        rh[e] = pack2(h0, h1);
-        rl[e] = pack2(l0, l1);
-        split1(v[2 * e].y, h0, l0);
-        split1(v[2 * e + 1].y, h1, l1);
-        ih[e] = pack2(h0, h1);
-        il[e] = pack2(l0, l1);
+        split2(v[2 * e].x, v[2 * e + 1].x, rh[e], rl[e]);
+        split2(v[2 * e].y, v[2 * e + 1].y, ih[e], il[e]);
     }
     planes[0][chunk] = make_uint4(rh[0], rh[1], rh[2], rh[3]);
     planes[1][chunk] = make_uint4(rl[0], rl[1], rl[2], rl[3]);
@@ -286,7 +277,7 @@ struct Phase2 {
 // (contiguous R rows), phase 2 keeps rows on neighbouring threads (contiguous
 // Q columns)
 template <bool kRowFast>
-__device__ __forceinline__ void a_seg(int s, int& row, int& q) {
+__device__ __forceinline__ void a_seg(int s, int& row, int& q) {  // s in [0, 512)
     if (kRowFast) {
         row = s & (kM - 1);
         q = s >> 7;
@@ -305,6 +296,7 @@ struct Ctl {
 // One output tile (rows x ncol) over K = nK: stages g0, g0+1, ... of this CTA.
 // Returns false when a wait gave up.  On return every thread may read the
 // accumulators (when nK > 0).
+
 template <class Src, bool kRowFast>
 __device__ bool run_tile(const Src& src, Stage* stages, Ctl& ctl, uint32_t& g, int nK, int nmma) {
     const int tid = threadIdx.x;
@@ -312,33 +304,26 @@ __device__ bool run_tile(const Src& src, Stage* stages, Ctl& ctl, uint32_t& g, i
     for (int st = 0; st < nst; ++st, ++g) {
         const int k0 = st * kKS;
         Stage& S = stages[g & 1];
-        float2 va[4][8], vb[2][8];
+        // A: 512 segments of 8 values, B: 256 (two and one per thread)
+        float2 va[2][8], vb[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 2; ++i) {
             int row, q;
             a_seg<kRowFast>(tid + i * kThr, row, q);
             src.load_a(row, q, k0, va[i]);
         }
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int s = tid + i * kThr;
-            src.load_b(s >> 2, s & 3, k0, vb[i]);
-        }
+        src.load_b(tid >> 2, tid & 3, k0, vb);
         // the stage buffer is free once the MMAs issued two stages ago are done
         if (tid == 0) ctl.ok = (g < 2) ? 1 : (mbar_wait(smem_u32(&ctl.mbar[g & 1]), ((g >> 1) - 1) & 1) ? 1 : 0);
         __syncthreads();
         if (!ctl.ok) return false;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 2; ++i) {
             int row, q;
             a_seg<kRowFast>(tid + i * kThr, row, q);
             put8<kChunksA>(S.a, q * kM + row, va[i]);
         }
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int s = tid + i * kThr;
-            put8<kChunksB>(S.b, (s & 3) * kN + (s >> 2), vb[i]);
-        }
+        put8<kChunksB>(S.b, (tid & 3) * kN + (tid >> 2), vb);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
@@ -357,15 +342,18 @@ __device__ bool run_tile(const Src& src, Stage* stages, Ctl& ctl, uint32_t& g, i
     return true;
 }
 
-// out[rowidx(r) + c * ld] = (D_r, D_i)[r, c] for r < rows, c < ncol (zeros when nK == 0)
+// out[rowidx(r) + c * ld] = (D_r, D_i)[r, c] for r < rows, c < ncol (zeros when nK == 0).
+// A warp reads the tensor-memory lanes of its quarter (warp % 4); warps 0-3
+// take columns 0-31, warps 4-7 columns 32-63.
 template <class RowIdx>
 __device__ void epilogue(const Ctl& ctl, bool have, int rows, int ncol, RowIdx rowidx, float2* out, int64_t ld) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = warp * 32 + lane;
-    const uint32_t base = ctl.tmem + ((uint32_t)(warp * 32) << 16);
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane;
+    const uint32_t base = ctl.tmem + ((uint32_t)(quarter * 32) << 16);
     const bool mine = r < rows;
     const int64_t ri = mine ? rowidx(r) : 0;
-    for (int cb = 0; cb < ncol; cb += 16) {
+    for (int cb = half * 32; cb < min(ncol, half * 32 + 32); cb += 16) {
         float vr[16], vi[16];
         if (have) {
             tmem_ld16(base + cb, vr);
