@@ -69,6 +69,21 @@ enum vie_precision {
                          refinement residual) */
 };
 
+/* Implementations of the far part of a complex float32 apply (the paper's
+ * method fixes what is computed, not how; these are the kernel variants the
+ * autotuner chooses between).  The SIMT variants read every factor element
+ * once per group of 1, 2, 4 or 8 right-hand sides; the tensor-core variants
+ * compute in split bf16 (admissible for VIE_BF16X3 only). */
+enum vie_variant {
+    VIE_VAR_AUTO = 0,
+    VIE_VAR_SIMT_R1 = 1,
+    VIE_VAR_SIMT_R2 = 2,
+    VIE_VAR_SIMT_R4 = 3,
+    VIE_VAR_SIMT_R8 = 4,
+    VIE_VAR_MMA_BF16X3 = 5,     /* warp-level mma.sync, 64-row tiles */
+    VIE_VAR_TCGEN05_BF16X3 = 6  /* tcgen05 MMAs with tensor-memory accumulators, 128-row tiles */
+};
+
 /* vie_apply flags */
 #define VIE_APPLY_FUSE_PRECOND 1 /* y = x + Z_D^-1 (far part of Zs x) = P^-1 Zs x */
 #define VIE_APPLY_DENSE 2        /* y = Zs x with the uncompressed operator: every
@@ -131,7 +146,17 @@ typedef struct vie_solve_opts {
     int launch;                /* 0: each restart cycle is one CUDA graph (Arnoldi steps in a
                                   conditional while-node, no host round trip inside a cycle);
                                   1: the host launches every step and reads the continue flag */
+    int autotune;              /* 1: run vie_tune for the first cycle's right-hand-side count
+                                  (unless already tuned) before the solve */
 } vie_solve_opts;
+
+/* Result of vie_tune. */
+typedef struct vie_tune_result {
+    int variant;               /* the variant now used for (precision, nrhs) */
+    int n_candidates;
+    int candidates[8];         /* vie_variant values that were timed */
+    double ms[8];              /* best of three timed far applies per candidate */
+} vie_tune_result;
 
 typedef struct vie_solve_stats {
     int iterations;            /* Arnoldi steps of the slowest right-hand side */
@@ -227,6 +252,23 @@ int vie_rhs(vie_op* op, const vie_incident* inc, int nrhs, void* b, int64_t ld, 
 int vie_solve(vie_op* op, const vie_incident* inc, int nrhs, const vie_solve_opts* opts,
               void* I_out, vie_solve_stats* stats);
 
+/* vie_solve_batch (no paper counterpart; a batching of vie_solve): solves
+ * `count` problems together, e.g. arrays of different size, wavelength or
+ * permittivity made of meta-atoms with the same voxels per edge, all
+ * compressed with VIE_C64 factors on one context.  The operators are joined
+ * into one block-diagonal operator (no block couples two problems), so each
+ * problem's result is what vie_solve would give it; what changes is that
+ * every phase of the far apply is one persistent launch over all problems'
+ * work and every Arnoldi step serves all of them.
+ * inc[p], nrhs[p]: right-hand sides of problem p (sum at most 1024);
+ * I_out[p]: its c128 n_p x nrhs[p] solution (host or device per
+ * opts->out_on_device); stats[p] (may be NULL): its statistics (applies,
+ * refinements and history are those of the shared lockstep).
+ * opts->precision VIE_C64 or VIE_BF16X3.  The joined operator holds a copy of
+ * the factors for the duration of the call. */
+int vie_solve_batch(vie_op* const* ops, int count, const vie_incident* inc, const int* nrhs,
+                    const vie_solve_opts* opts, void* const* I_out, vie_solve_stats* stats);
+
 /* vie_fields: outputs from a solution I (host c128, n x nrhs, ld = n):
  * mode 0: far-field amplitude F(rhat) = -j k/(4 pi) (I - rhat rhat) int J exp(j k rhat.r) dV
  *         for the unit directions dirs[3 npts]; E_out host c128 [3 npts nrhs].
@@ -306,6 +348,16 @@ int64_t vie_footprint_bytes(int64_t n, int np, int nrhs, int restart, int64_t fa
 /* Number of libvie kernels launched by this process so far (all contexts);
  * cuBLAS kernels are not counted.  Diagnostic, thread-safe. */
 int64_t vie_kernel_launches(void);
+
+/* vie_tune (no paper counterpart; a project-written autotuner): times every
+ * far-apply variant admissible for `precision` (VIE_C64: the SIMT tiles;
+ * VIE_BF16X3: those and the two tensor-core kernels) on nrhs right-hand sides
+ * of this operator, with CUDA events on the context stream, and keeps the
+ * fastest for every later apply and solve whose right-hand-side count has
+ * the same floor(log2).  force_variant > 0 sets that variant without timing
+ * (VIE_ERR_INVALID_ARG if it is not admissible).  Synchronises the context
+ * stream; not callable during stream capture.  result may be NULL. */
+int vie_tune(vie_op* op, int precision, int nrhs, int force_variant, vie_tune_result* result);
 
 #ifdef __cplusplus
 }

@@ -33,7 +33,7 @@ void op_apply_fused32(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t
     const int64_t n = op.n();
     ensure_F(op, (size_t)n * nrhs * sizeof(float2));
     float2* F = op.d_F.as<float2>();
-    apply_far<float2, float2>(op, x, n, F, n, nrhs, s);
+    far32(op, x, n, F, n, nrhs, VIE_C64, s);
     self_gemm<float2, float2>(op, op.d_inv32.as<float2>(), x, n, F, n, y, n, nrhs, 1, s);
 }
 
@@ -42,7 +42,7 @@ void op_apply_fused_bf16x3(Op& op, const float2* x, float2* y, int nrhs, cudaStr
     const int64_t n = op.n();
     ensure_F(op, (size_t)n * nrhs * sizeof(float2));
     float2* F = op.d_F.as<float2>();
-    apply_far_umma(op, x, n, F, n, nrhs, s);
+    far32(op, x, n, F, n, nrhs, VIE_BF16X3, s);
     self_gemm<float2, float2>(op, op.d_inv32.as<float2>(), x, n, F, n, y, n, nrhs, 1, s);
 }
 
@@ -358,7 +358,7 @@ int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int prec
                 if (o.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "VIE_C64 applies need VIE_C64 factors");
                 ensure_F(o, (size_t)o.n() * nrhs * sizeof(float2));
                 float2* F = o.d_F.as<float2>();
-                apply_far<float2, float2>(o, (const float2*)x, o.n(), F, o.n(), nrhs, s);
+                far32(o, (const float2*)x, o.n(), F, o.n(), nrhs, VIE_C64, s);
                 self_gemm<float2, float2>(o, o.d_zself32.as<float2>(), (const float2*)x, o.n(), F, o.n(),
                                           (float2*)y, o.n(), nrhs, 0, s);
             }
@@ -368,7 +368,7 @@ int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int prec
                 if (o.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "VIE_BF16X3 applies need VIE_C64 factors");
                 ensure_F(o, (size_t)o.n() * nrhs * sizeof(float2));
                 float2* F = o.d_F.as<float2>();
-                apply_far_umma(o, (const float2*)x, o.n(), F, o.n(), nrhs, s);
+                far32(o, (const float2*)x, o.n(), F, o.n(), nrhs, VIE_BF16X3, s);
                 self_gemm<float2, float2>(o, o.d_zself32.as<float2>(), (const float2*)x, o.n(), F, o.n(),
                                           (float2*)y, o.n(), nrhs, 0, s);
             }
@@ -437,6 +437,27 @@ int vie_solve(vie_op* op, const vie_incident* inc, int nrhs, const vie_solve_opt
     });
     if (st != VIE_OK) return st;
     if (result != VIE_OK && ctx_of(op)) ctx_of(op)->c.err = "GMRES did not reach the tolerance";
+    return result;
+}
+
+int vie_solve_batch(vie_op* const* ops, int count, const vie_incident* inc, const int* nrhs,
+                    const vie_solve_opts* opts, void* const* I_out, vie_solve_stats* stats) {
+    if (!ops || count < 1 || !inc || !nrhs || !opts || !I_out) return VIE_ERR_INVALID_ARG;
+    for (int p = 0; p < count; ++p)
+        if (!ops[p] || !I_out[p]) return VIE_ERR_INVALID_ARG;
+    int result = VIE_OK;
+    int st = guarded(ctx_of(ops[0]), [&] {
+        set_device(*ops[0]->o.ctx);
+        std::vector<Op*> v(count);
+        std::vector<void*> outs(count);
+        for (int p = 0; p < count; ++p) {
+            v[p] = &ops[p]->o;
+            outs[p] = I_out[p];
+        }
+        result = solve_batch(v, inc, nrhs, opts, outs.data(), stats);
+    });
+    if (st != VIE_OK) return st;
+    if (result != VIE_OK && ctx_of(ops[0])) ctx_of(ops[0])->c.err = "GMRES did not reach the tolerance";
     return result;
 }
 
@@ -618,6 +639,15 @@ int vie_export_far_block(vie_op* op, int64_t i, int* tatoms, int* satoms, void* 
 }
 
 int64_t vie_kernel_launches(void) { return g_kernel_launches.load(); }
+
+int vie_tune(vie_op* op, int precision, int nrhs, int force_variant, vie_tune_result* result) {
+    if (!op) return VIE_ERR_INVALID_ARG;
+    return guarded(ctx_of(op), [&] {
+        Op& o = op->o;
+        set_device(*o.ctx);
+        tune_entry(o, precision, nrhs, force_variant, result, o.ctx->stream);
+    });
+}
 
 int vie_plan_far_blocks(const double* xy, int n_atoms, int* levels, int64_t* n_blocks, int* out, int64_t out_len,
                         int64_t* out_needed) {

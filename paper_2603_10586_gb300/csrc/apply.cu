@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(256, 3) p1_kernel(const FarBlockDev* __restric
                                                  const int* __restrict__ batoms, const int4* __restrict__ items,
                                                  const int* __restrict__ cta_ptr, const TF* __restrict__ factors,
                                                  const TX* __restrict__ x, int64_t ldx, int np,
-                                                 TX* __restrict__ t, int64_t ldt, int nrhs) {
+                                                 TX* __restrict__ t, int64_t ldt, int nrhs,
+                                                 const int2* __restrict__ colr) {
     using TA = typename AccOf<TX>::t;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -149,12 +150,13 @@ __global__ void __launch_bounds__(256, 3) p1_kernel(const FarBlockDev* __restric
         const FarBlockDev B = blocks[item.x];
         const TF* RH = factors + B.rh_off;
         const int* S = batoms + B.s_off;
+        const int2 cr = colr ? colr[item.w] : make_int2(0, nrhs);  // right-hand sides of this problem
         for (int k = item.y + warp * ROWS; k < item.z; k += nwarps * ROWS) {
             const int nrow = min(ROWS, item.z - k);
             const TF* rows[ROWS];
 #pragma unroll
             for (int r = 0; r < ROWS; ++r) rows[r] = RH + (int64_t)(k + min(r, nrow - 1)) * B.n;
-            for (int c0 = 0; c0 < nrhs; ++c0) {
+            for (int c0 = cr.x; c0 < cr.y; ++c0) {
                 TA acc[ROWS];
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) acc[r] = acc_zero<TA>();
@@ -215,7 +217,8 @@ __global__ void __launch_bounds__(256) p2_kernel(const FarBlockDev* __restrict__
                                                  const int4* __restrict__ items, const int* __restrict__ cta_ptr,
                                                  const int* __restrict__ csr, const int2* __restrict__ ent,
                                                  const TF* __restrict__ factors, const TX* __restrict__ t,
-                                                 int64_t ldt, int np, TO* __restrict__ F, int64_t ldf, int nrhs) {
+                                                 int64_t ldt, int np, TO* __restrict__ F, int64_t ldf, int nrhs,
+                                                 const int2* __restrict__ colr) {
     using TA = typename AccOf<TX>::t;
     __shared__ TA red[3][64][2];
     const int rp = threadIdx.x & 63, kg = threadIdx.x >> 6;
@@ -224,7 +227,8 @@ __global__ void __launch_bounds__(256) p2_kernel(const FarBlockDev* __restrict__
         const int a = item.x;
         const int row = item.y + 2 * rp;
         const bool active = row < item.z;
-        for (int c0 = 0; c0 < nrhs; ++c0) {
+        const int2 cr = colr ? colr[item.w] : make_int2(0, nrhs);
+        for (int c0 = cr.x; c0 < cr.y; ++c0) {
             TA acc0 = acc_zero<TA>(), acc1 = acc_zero<TA>();
             if (active) {
                 for (int e = csr[a]; e < csr[a + 1]; ++e) {
@@ -282,7 +286,8 @@ __global__ void __launch_bounds__(256, 2) p1m_kernel(const FarBlockDev* __restri
                                                   const int* __restrict__ batoms, const int4* __restrict__ items,
                                                   const int* __restrict__ cta_ptr, const TF* __restrict__ factors,
                                                   const TX* __restrict__ x, int64_t ldx, int np,
-                                                  TX* __restrict__ t, int64_t ldt, int nrhs) {
+                                                  TX* __restrict__ t, int64_t ldt, int nrhs,
+                                                  const int2* __restrict__ colr) {
     using TA = typename AccOf<TX>::t;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -291,12 +296,13 @@ __global__ void __launch_bounds__(256, 2) p1m_kernel(const FarBlockDev* __restri
         const FarBlockDev B = blocks[item.x];
         const TF* RH = factors + B.rh_off;
         const int* S = batoms + B.s_off;
+        const int2 cr = colr ? colr[item.w] : make_int2(0, nrhs);
         for (int k = item.y + warp * 2; k < item.z; k += nwarps * 2) {
             const bool two = k + 1 < item.z;
             const TF* row0 = RH + (int64_t)k * B.n;
             const TF* row1 = RH + (int64_t)(two ? k + 1 : k) * B.n;
-            for (int c0 = 0; c0 < nrhs; c0 += NR) {
-                const int nr = min(NR, nrhs - c0);
+            for (int c0 = cr.x; c0 < cr.y; c0 += NR) {
+                const int nr = min(NR, cr.y - c0);
                 TA a0[NR], a1[NR];
 #pragma unroll
                 for (int r = 0; r < NR; ++r) a0[r] = a1[r] = acc_zero<TA>();
@@ -341,7 +347,8 @@ __global__ void __launch_bounds__(256, 2) p2m_kernel(const FarBlockDev* __restri
                                                   const int4* __restrict__ items, const int* __restrict__ cta_ptr,
                                                   const int* __restrict__ csr, const int2* __restrict__ ent,
                                                   const TF* __restrict__ factors, const TX* __restrict__ t,
-                                                  int64_t ldt, int np, TO* __restrict__ F, int64_t ldf, int nrhs) {
+                                                  int64_t ldt, int np, TO* __restrict__ F, int64_t ldf, int nrhs,
+                                                  const int2* __restrict__ colr) {
     using TA = typename AccOf<TX>::t;
     __shared__ TA red[3][64][2][NR];
     const int rp = threadIdx.x & 63, kg = threadIdx.x >> 6;
@@ -350,8 +357,9 @@ __global__ void __launch_bounds__(256, 2) p2m_kernel(const FarBlockDev* __restri
         const int a = item.x;
         const int row = item.y + 2 * rp;
         const bool active = row < item.z;
-        for (int c0 = 0; c0 < nrhs; c0 += NR) {
-            const int nr = min(NR, nrhs - c0);
+        const int2 cr = colr ? colr[item.w] : make_int2(0, nrhs);
+        for (int c0 = cr.x; c0 < cr.y; c0 += NR) {
+            const int nr = min(NR, cr.y - c0);
             TA a0[NR], a1[NR];
 #pragma unroll
             for (int r = 0; r < NR; ++r) a0[r] = a1[r] = acc_zero<TA>();
@@ -412,29 +420,74 @@ void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, c
         if (op.n_p1_items > 0) {
             p1m_kernel<TF, TX, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
                                                      op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, x, ldx,
-                                                     op.np, op.d_t.as<TX>(), op.t_total, nrhs);
+                                                     op.np, op.d_t.as<TX>(), op.t_total, nrhs, op.colr);
             VIE_CHECK_LAUNCH();
         }
         p2m_kernel<TF, TX, TX, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
                                                  op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(),
-                                                 fac, op.d_t.as<TX>(), op.t_total, op.np, F, ldf, nrhs);
+                                                 fac, op.d_t.as<TX>(), op.t_total, op.np, F, ldf, nrhs, op.colr);
         VIE_CHECK_LAUNCH();
         return;
     }
     if (op.n_p1_items > 0) {
         p1_kernel<TF, TX, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
                                                 op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, x, ldx,
-                                                op.np, op.d_t.as<TX>(), op.t_total, nrhs);
+                                                op.np, op.d_t.as<TX>(), op.t_total, nrhs, op.colr);
         VIE_CHECK_LAUNCH();
     }
     p2_kernel<TF, TX, TX><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
                                          op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(),
-                                         fac, op.d_t.as<TX>(), op.t_total, op.np, F, ldf, nrhs);
+                                         fac, op.d_t.as<TX>(), op.t_total, op.np, F, ldf, nrhs, op.colr);
     VIE_CHECK_LAUNCH();
 }
 
 template void apply_far<float2, float2>(Op&, const float2*, int64_t, float2*, int64_t, int, cudaStream_t);
 template void apply_far<double2, double2>(Op&, const double2*, int64_t, double2*, int64_t, int, cudaStream_t);
+
+// complex float32 far apply with nr right-hand sides per factor read (1, 2, 4, 8):
+// the tile shapes the autotuner chooses between
+void apply_far_simt32(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, int nr,
+                      cudaStream_t s) {
+    const size_t need = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(float2);
+    if (op.d_t.bytes < need) op.d_t.alloc(need);
+    const float2* fac = op.d_factors.as<float2>();
+    float2* t = op.d_t.as<float2>();
+    const int nc = op.n_cta;
+    const FarBlockDev* bl = op.d_blocks.as<FarBlockDev>();
+#define VIE_P1M(NR)                                                                                              \
+    p1m_kernel<float2, float2, NR><<<nc, 256, 0, s>>>(bl, op.d_block_atoms.as<int>(), op.d_p1_items.as<int4>(), \
+                                                      op.d_p1_cta.as<int>(), fac, x, ldx, op.np, t, op.t_total, nrhs, \
+                                                      op.colr)
+#define VIE_P2M(NR)                                                                                               \
+    p2m_kernel<float2, float2, float2, NR><<<nc, 256, 0, s>>>(bl, op.d_p2_items.as<int4>(), op.d_p2_cta.as<int>(), \
+                                                              op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(), fac, t,  \
+                                                              op.t_total, op.np, F, ldf, nrhs, op.colr)
+    if (op.n_p1_items > 0) {
+        switch (nr) {
+            case 1: p1_kernel<float2, float2, 4><<<nc, 256, 0, s>>>(bl, op.d_block_atoms.as<int>(),
+                                                                    op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(),
+                                                                    fac, x, ldx, op.np, t, op.t_total, nrhs, op.colr); break;
+            case 2: VIE_P1M(2); break;
+            case 4: VIE_P1M(4); break;
+            case 8: VIE_P1M(8); break;
+            default: fail(VIE_ERR_INVALID_ARG, "unknown SIMT tile");
+        }
+        VIE_CHECK_LAUNCH();
+    }
+    switch (nr) {
+        case 1: p2_kernel<float2, float2, float2><<<nc, 256, 0, s>>>(bl, op.d_p2_items.as<int4>(),
+                                                                     op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(),
+                                                                     op.d_p2_ent.as<int2>(), fac, t, op.t_total,
+                                                                     op.np, F, ldf, nrhs, op.colr); break;
+        case 2: VIE_P2M(2); break;
+        case 4: VIE_P2M(4); break;
+        case 8: VIE_P2M(8); break;
+        default: fail(VIE_ERR_INVALID_ARG, "unknown SIMT tile");
+    }
+    VIE_CHECK_LAUNCH();
+#undef VIE_P1M
+#undef VIE_P2M
+}
 
 namespace {
 // x (complex float64, n x nrhs, leading dimension ldx) -> float32 head + tail
@@ -468,25 +521,25 @@ void apply_far_df(Op& op, const double2* x, int64_t ldx, double2* F, int64_t ldf
         if (op.n_p1_items > 0) {
             p1m_kernel<float2, float4, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
                                                              op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, xs,
-                                                             n, op.np, t, op.t_total, nrhs);
+                                                             n, op.np, t, op.t_total, nrhs, op.colr);
             VIE_CHECK_LAUNCH();
         }
         p2m_kernel<float2, float4, double2, 4><<<nc, 256, 0, s>>>(
             op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(), op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(),
-            op.d_p2_ent.as<int2>(), fac, t, op.t_total, op.np, F, ldf, nrhs);
+            op.d_p2_ent.as<int2>(), fac, t, op.t_total, op.np, F, ldf, nrhs, op.colr);
         VIE_CHECK_LAUNCH();
         return;
     }
     if (op.n_p1_items > 0) {
         p1_kernel<float2, float4, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
                                                         op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, xs, n,
-                                                        op.np, t, op.t_total, nrhs);
+                                                        op.np, t, op.t_total, nrhs, op.colr);
         VIE_CHECK_LAUNCH();
     }
     p2_kernel<float2, float4, double2><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
                                                           op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(),
                                                           op.d_p2_ent.as<int2>(), fac, t, op.t_total, op.np, F, ldf,
-                                                          nrhs);
+                                                          nrhs, op.colr);
     VIE_CHECK_LAUNCH();
 }
 
@@ -536,12 +589,12 @@ void apply_static(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s) 
     if (op.n_p1_items > 0) {
         p1_kernel<float2, float2, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
                                                         op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, x, n,
-                                                        op.np, t, op.t_total, nrhs);
+                                                        op.np, t, op.t_total, nrhs, nullptr);
         VIE_CHECK_LAUNCH();
     }
     p2_kernel<float2, float2, float2><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
                                                  op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(),
-                                                 fac, t, op.t_total, op.np, y, n, nrhs);
+                                                 fac, t, op.t_total, op.np, y, n, nrhs, nullptr);
     VIE_CHECK_LAUNCH();
     // y = Z_ii x + y, each element read and written by the same thread
     self_gemm<float2, float2>(op, op.d_zself32.as<float2>(), x, n, y, n, y, n, nrhs, 0, s);

@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kThr) u1_kernel(const FarBlockDev* __restrict_
                                                   const long long* __restrict__ rowoff, const int* __restrict__ rowt,
                                                   const float2* __restrict__ fac, const float2* __restrict__ x,
                                                   int64_t ldx, int np, float2* __restrict__ t, int64_t ldt, int nrhs,
-                                                  int* err) {
+                                                  const int2* __restrict__ colr, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     Stage* stages = reinterpret_cast<Stage*>(smem);
     __shared__ Ctl ctl;
@@ -423,8 +423,9 @@ __global__ void __launch_bounds__(kThr) u1_kernel(const FarBlockDev* __restrict_
     for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1] && !failed; ++it) {
         const int4 item = items[it];
         const FarBlockDev B = blocks[item.x];
-        for (int c0 = 0; c0 < nrhs && !failed; c0 += kN) {
-            Phase1 src{fac, rowoff, rowt, batoms + B.s_off, x, ldx, np, B.n, item.y, item.z, c0, min(kN, nrhs - c0)};
+        const int2 cr = colr ? colr[item.w] : make_int2(0, nrhs);  // right-hand sides of this problem
+        for (int c0 = cr.x; c0 < cr.y && !failed; c0 += kN) {
+            Phase1 src{fac, rowoff, rowt, batoms + B.s_off, x, ldx, np, B.n, item.y, item.z, c0, min(kN, cr.y - c0)};
             const int nmma = max(16, (src.ncol + 15) / 16 * 16);
             if (!run_tile<Phase1, false>(src, stages, ctl, g, B.n, nmma)) {
                 failed = true;
@@ -442,7 +443,8 @@ __global__ void __launch_bounds__(kThr) u2_kernel(const int4* __restrict__ items
                                                   const long long* __restrict__ qoff, const int* __restrict__ tidx,
                                                   const long long* __restrict__ kptr, const float2* __restrict__ fac,
                                                   const float2* __restrict__ t, int64_t ldt, int np,
-                                                  float2* __restrict__ F, int64_t ldf, int nrhs, int* err) {
+                                                  float2* __restrict__ F, int64_t ldf, int nrhs,
+                                                  const int2* __restrict__ colr, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     Stage* stages = reinterpret_cast<Stage*>(smem);
     __shared__ Ctl ctl;
@@ -454,8 +456,9 @@ __global__ void __launch_bounds__(kThr) u2_kernel(const int4* __restrict__ items
         const int a = item.x, p0 = item.y, rows = item.z - item.y;
         const long long kb = kptr[a];
         const int nK = (int)(kptr[a + 1] - kb);
-        for (int c0 = 0; c0 < nrhs && !failed; c0 += kN) {
-            Phase2 src{fac, qoff, tidx, t, ldt, kb, nK, p0, rows, c0, min(kN, nrhs - c0)};
+        const int2 cr = colr ? colr[item.w] : make_int2(0, nrhs);
+        for (int c0 = cr.x; c0 < cr.y && !failed; c0 += kN) {
+            Phase2 src{fac, qoff, tidx, t, ldt, kb, nK, p0, rows, c0, min(kN, cr.y - c0)};
             const int nmma = max(16, (src.ncol + 15) / 16 * 16);
             if (!run_tile<Phase2, true>(src, stages, ctl, g, nK, nmma)) {
                 failed = true;
@@ -495,12 +498,13 @@ void apply_far_umma(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf
         u1_kernel<<<op.n_cta_u, kThr, kSmemBytes, s>>>(
             op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(), op.d_u1_items.as<int4>(), op.d_u1_cta.as<int>(),
             op.d_u1_rowoff.as<long long>(), op.d_u1_rowt.as<int>(), fac, x, ldx, op.np, op.d_t.as<float2>(),
-            op.t_total, nrhs, op.d_err.as<int>());
+            op.t_total, nrhs, op.colr, op.d_err.as<int>());
         VIE_CHECK_LAUNCH();
     }
     u2_kernel<<<op.n_cta_u, kThr, kSmemBytes, s>>>(
         op.d_u2_items.as<int4>(), op.d_u2_cta.as<int>(), op.d_u2_qoff.as<long long>(), op.d_u2_tidx.as<int>(),
-        op.d_u2_kptr.as<long long>(), fac, op.d_t.as<float2>(), op.t_total, op.np, F, ldf, nrhs, op.d_err.as<int>());
+        op.d_u2_kptr.as<long long>(), fac, op.d_t.as<float2>(), op.t_total, op.np, F, ldf, nrhs, op.colr,
+        op.d_err.as<int>());
     VIE_CHECK_LAUNCH();
 }
 

@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <complex>
+#include <map>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -169,6 +170,15 @@ struct Op {
     DevBuf d_u2_qoff, d_u2_tidx, d_u2_kptr, d_u2_items, d_u2_cta;
     int n_u1_items = 0, n_u2_items = 0, n_cta_u = 0;
     DevBuf d_err;  // set by a tensor-core kernel whose bounded wait gave up
+    // batched operators (several problems as one block-diagonal operator,
+    // batch.cpp): problem of every block, atom and type, and during a solve
+    // the device table of each problem's right-hand-side columns [x, y)
+    int nprob = 1;
+    std::vector<int> block_prob, atom_prob, type_prob;
+    const int2* colr = nullptr;
+    // far-apply variant per (precision, log2 of the right-hand-side count),
+    // chosen by the autotuner or set by the caller
+    std::map<std::pair<int, int>, int> variant;
     // scratch
     DevBuf d_t, d_F;
     DevBuf d_xs;  // float64 vectors split into float32 head + tail (double-float apply)
@@ -190,7 +200,7 @@ struct Ctx {
 
 // device-side block description used by the apply kernels
 struct FarBlockDev {
-    int m, n, rank, nt, ns, t_off, s_off, pad;
+    int m, n, rank, nt, ns, t_off, s_off, prob;  // prob: problem of a batched (union) operator
     long long q_off, rh_off, tvec_off;
 };
 
@@ -240,6 +250,16 @@ template <class TF, class TX>
 void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, cudaStream_t s);
 
 void apply_static(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s);
+// complex float32 SIMT far apply with nr (1, 2, 4, 8) right-hand sides per factor read
+void apply_far_simt32(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, int nr,
+                      cudaStream_t s);
+// far apply of float32 vectors by the variant chosen for (precision, nrhs)
+void far32(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, int precision, cudaStream_t s);
+int far_variant(const Op& op, int precision, int nrhs);
+// time the admissible variants for (precision, nrhs), keep the fastest
+int tune_far(Op& op, int precision, int nrhs, cudaStream_t s, std::vector<int>& cand, std::vector<double>& ms);
+int tune_entry(Op& op, int precision, int nrhs, int force, vie_tune_result* res, cudaStream_t s);
+bool tuned(const Op& op, int precision, int nrhs);
 // work lists of the tcgen05 multi-RHS apply (host.cpp); idempotent
 void build_umma_lists(Op& op);
 // far part with c64 factors and c64 vectors, split-precision bf16 on tcgen05
@@ -255,6 +275,8 @@ void apply_far_bf16x3(Op& op, const float2* x, int64_t ldx, float2* F, int64_t l
 void compress_operator(Op& op, double tol, int prec);
 
 // solve.cpp
+int solve_batch(const std::vector<Op*>& ops, const vie_incident* incs, const int* nrhs, const vie_solve_opts* o,
+                void** I_out, vie_solve_stats* st);
 int solve(Op& op, const vie_incident* inc, int nrhs, const vie_solve_opts* o, void* I_out,
           vie_solve_stats* st);
 

@@ -234,7 +234,8 @@ void build_apply_lists(Op& op) {
         auto& b = op.blocks[i];
         b.t_off_vec = toff;
         toff += b.rank;
-        hb[i] = FarBlockDev{b.m, b.n, b.rank, b.nt, b.ns, b.t_off, b.s_off, 0, (long long)b.q_off,
+        const int prob = op.block_prob.empty() ? 0 : op.block_prob[i];
+        hb[i] = FarBlockDev{b.m, b.n, b.rank, b.nt, b.ns, b.t_off, b.s_off, prob, (long long)b.q_off,
                             (long long)b.rh_off, (long long)b.t_off_vec};
     }
     op.t_total = toff;
@@ -253,7 +254,7 @@ void build_apply_lists(Op& op) {
         int rc = 32;
         for (int k0 = 0; k0 < b.rank; k0 += rc) {
             int k1 = std::min(b.rank, k0 + rc);
-            it1.push_back(make_int4(i, k0, k1, 0));
+            it1.push_back(make_int4(i, k0, k1, op.block_prob.empty() ? 0 : op.block_prob[i]));
             w1.push_back((double)(k1 - k0) * b.n);
         }
     }
@@ -287,7 +288,7 @@ void build_apply_lists(Op& op) {
     for (int a = 0; a < op.N; ++a)
         for (int p0 = 0; p0 < op.np; p0 += rows_per_item) {
             int p1e = std::min(op.np, p0 + rows_per_item);
-            it2.push_back(make_int4(a, p0, p1e, 0));
+            it2.push_back(make_int4(a, p0, p1e, op.atom_prob.empty() ? 0 : op.atom_prob[a]));
             w2.push_back((double)(p1e - p0) * (rsum[a] + 1.0));
         }
     std::vector<int4> p2;
@@ -359,7 +360,7 @@ void build_umma_lists(Op& op) {
         const int64_t total = (int64_t)rowoff.size() - start;
         for (int64_t r0 = 0; r0 < total; r0 += kRows) {
             const int nr = (int)std::min<int64_t>(kRows, total - r0);
-            it1.push_back(make_int4(rep, (int)(start + r0), nr, 0));
+            it1.push_back(make_int4(rep, (int)(start + r0), nr, op.block_prob.empty() ? 0 : op.block_prob[rep]));
             w1.push_back((double)(nr + 32) * op.blocks[rep].n);
         }
     }
@@ -386,7 +387,7 @@ void build_umma_lists(Op& op) {
         const double K = (double)(kptr[a + 1] - kptr[a]);
         for (int p0 = 0; p0 < op.np; p0 += kRows) {
             const int p1 = std::min(op.np, p0 + kRows);
-            it2.push_back(make_int4(a, p0, p1, 0));
+            it2.push_back(make_int4(a, p0, p1, op.atom_prob.empty() ? 0 : op.atom_prob[a]));
             w2.push_back((double)(p1 - p0 + 32) * (K + 1.0));
         }
     }

@@ -38,8 +38,13 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return s;
 }
 
-__device__ __forceinline__ double2* basis(const KrylovArgs& a, int slot, int col) {
-    return a.V + ((int64_t)slot * (a.m + 1) + col) * a.n;
+// rows of a right-hand-side column and its basis
+struct Rows {
+    int64_t lo, len;
+    double2* V;  // basis vector l at V + l * len
+};
+__device__ __forceinline__ Rows rows_of(const KrylovArgs& a, int c) {
+    return {a.col_lo[c], a.col_len[c], a.V + a.col_voff[c]};
 }
 
 __global__ void k_cycle_start(KrylovArgs a, int k) {
@@ -58,15 +63,17 @@ __global__ void k_cycle_start(KrylovArgs a, int k) {
 template <class TX>
 __global__ void __launch_bounds__(kT) k_gather(KrylovArgs a, const double2* __restrict__ W, TX* __restrict__ Xg) {
     const int i = blockIdx.y;
-    const int64_t n = a.n, stride = (int64_t)gridDim.x * kT;
-    TX* x = Xg + (int64_t)i * n;
+    const int c = a.cols[i];
+    const Rows R = rows_of(a, c);
+    const int64_t n = R.len, stride = (int64_t)gridDim.x * kT;
+    TX* x = Xg + (int64_t)i * a.n + R.lo;
     if (!a.cycling[i]) {
         for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += stride) st(x, r, make_double2(0.0, 0.0));
         return;
     }
     const int j = a.ctr[KR_J];
-    double2* v = basis(a, i, j);
-    const double2* src = j == 0 ? W + (int64_t)a.cols[i] * n : v;
+    double2* v = R.V + (int64_t)j * n;
+    const double2* src = j == 0 ? W + (int64_t)c * a.n + R.lo : v;
     const double sc = a.inv[i];
     for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += stride) {
         const double2 e = sc * src[r];
@@ -78,16 +85,18 @@ __global__ void __launch_bounds__(kT) k_gather(KrylovArgs a, const double2* __re
 // partial h[col] = sum_r conj(V[r, col]) w[r] over one row chunk, 8 columns per CTA.
 // Pass 1 takes w from the operator output and stores it as basis column j+1.
 template <class TW, bool kFirst>
-__global__ void __launch_bounds__(kT) k_mdot(KrylovArgs a, const TW* __restrict__ Y, int64_t rows_per) {
+__global__ void __launch_bounds__(kT) k_mdot(KrylovArgs a, const TW* __restrict__ Y) {
     const int i = blockIdx.z, cg = blockIdx.y;
     if (!a.cycling[i]) return;
     const int j = a.ctr[KR_J];
     const int ncols = j + 1;
     if (cg * kCG >= ncols) return;
-    const int64_t n = a.n;
-    const double2* V = basis(a, i, 0);
-    double2* w = basis(a, i, j + 1);
-    const TW* y = Y + (int64_t)i * n;
+    const Rows R = rows_of(a, a.cols[i]);
+    const int64_t n = R.len;
+    const double2* V = R.V;
+    double2* w = R.V + (int64_t)(j + 1) * n;
+    const TW* y = kFirst ? Y + (int64_t)i * a.n + R.lo : nullptr;
+    const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
     double2 acc[kCG];
 #pragma unroll
@@ -192,9 +201,10 @@ __global__ void __launch_bounds__(kT) k_maxpy(KrylovArgs a) {
     __shared__ double sh[kT / 32];
     if ((int)threadIdx.x <= j) hs[threadIdx.x] = a.h[i * 64 + threadIdx.x];
     __syncthreads();
-    const int64_t n = a.n;
-    const double2* V = basis(a, i, 0);
-    double2* w = basis(a, i, j + 1);
+    const Rows R = rows_of(a, a.cols[i]);
+    const int64_t n = R.len;
+    const double2* V = R.V;
+    double2* w = R.V + (int64_t)(j + 1) * n;
     double nacc = 0.0;
     for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) {
         double2 acc = w[r];
@@ -299,9 +309,10 @@ __global__ void __launch_bounds__(kT) k_xupdate(KrylovArgs a, double2* __restric
     __shared__ double2 ys[64];
     if ((int)threadIdx.x < jd) ys[threadIdx.x] = a.y[(int64_t)i * 64 + threadIdx.x];
     __syncthreads();
-    const int64_t n = a.n;
-    const double2* V = basis(a, i, 0);
-    double2* x = X + (int64_t)a.cols[i] * n;
+    const Rows R = rows_of(a, a.cols[i]);
+    const int64_t n = R.len;
+    const double2* V = R.V;
+    double2* x = X + (int64_t)a.cols[i] * a.n + R.lo;
     for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) {
         double2 acc = x[r];
         for (int l = 0; l < jd; ++l) cfma(acc, V[(int64_t)l * n + r], ys[l]);
@@ -309,28 +320,33 @@ __global__ void __launch_bounds__(kT) k_xupdate(KrylovArgs a, double2* __restric
     }
 }
 
-__global__ void __launch_bounds__(kT) k_gather_cols(const double2* __restrict__ src, const int* __restrict__ cols,
-                                                   double2* __restrict__ dst, int64_t n) {
+__global__ void __launch_bounds__(kT) k_gather_cols(KrylovArgs a, const double2* __restrict__ src,
+                                                   double2* __restrict__ dst) {
     const int i = blockIdx.y;
-    const double2* s = src + (int64_t)cols[i] * n;
-    double2* d = dst + (int64_t)i * n;
+    const Rows R = rows_of(a, a.cols[i]);
+    const int64_t n = R.len;
+    const double2* s = src + (int64_t)a.cols[i] * a.n + R.lo;
+    double2* d = dst + (int64_t)i * a.n + R.lo;
     for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) d[r] = s[r];
 }
 
-__global__ void __launch_bounds__(kT) k_sub_cols(const double2* __restrict__ b, const int* __restrict__ cols,
-                                                const double2* __restrict__ T, double2* __restrict__ R, int64_t n) {
+__global__ void __launch_bounds__(kT) k_sub_cols(KrylovArgs a, const double2* __restrict__ b,
+                                                const double2* __restrict__ T, double2* __restrict__ R) {
     const int i = blockIdx.y;
-    const double2* bc = b + (int64_t)cols[i] * n;
-    const double2* t = T + (int64_t)i * n;
-    double2* rr = R + (int64_t)i * n;
+    const Rows rw = rows_of(a, a.cols[i]);
+    const int64_t n = rw.len;
+    const double2* bc = b + (int64_t)a.cols[i] * a.n + rw.lo;
+    const double2* t = T + (int64_t)i * a.n + rw.lo;
+    double2* rr = R + (int64_t)i * a.n + rw.lo;
     for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) rr[r] = bc[r] - t[r];
 }
 
 __global__ void __launch_bounds__(kT) k_scatter_norm(KrylovArgs a, const double2* Wl, double2* W) {
     const int i = blockIdx.y;
-    const int64_t n = a.n;
-    const double2* src = Wl + (int64_t)i * n;
-    double2* dst = W + (int64_t)a.cols[i] * n;
+    const Rows R = rows_of(a, a.cols[i]);
+    const int64_t n = R.len;
+    const double2* src = Wl + (int64_t)i * a.n + R.lo;
+    double2* dst = W + (int64_t)a.cols[i] * a.n + R.lo;
     __shared__ double sh[kT / 32];
     double acc = 0.0;
     for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) {
@@ -362,9 +378,12 @@ __global__ void k_cycle_end(KrylovArgs a, int k, int nblk, int init) {
     }
 }
 
-__global__ void __launch_bounds__(kT) k_colnorm_partial(const double2* __restrict__ A, int64_t n, double* part) {
+__global__ void __launch_bounds__(kT) k_colnorm_partial(KrylovArgs a, const double2* __restrict__ A,
+                                                       const int* __restrict__ cols, double* part) {
     const int i = blockIdx.y;
-    const double2* x = A + (int64_t)i * n;
+    const Rows R = rows_of(a, cols ? cols[i] : i);
+    const int64_t n = R.len;
+    const double2* x = A + (int64_t)i * a.n + R.lo;
     __shared__ double sh[kT / 32];
     double acc = 0.0;
     for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) {
@@ -414,18 +433,17 @@ void kr_gather(const KrylovArgs& a, const double2* W, void* Xg, bool c64, int k,
 
 void kr_project(const KrylovArgs& a, const void* Y, bool c64, int pass, int k, int nchunk, int nblk, cudaStream_t s) {
     const int ncg = (a.m + kCG - 1) / kCG;
-    const int64_t rows_per = (a.n + nchunk - 1) / nchunk;
     dim3 gd(nchunk, ncg, k);
     if (pass == 1) {
-        if (c64) k_mdot<float2, true><<<gd, kT, 0, s>>>(a, static_cast<const float2*>(Y), rows_per);
-        else k_mdot<double2, true><<<gd, kT, 0, s>>>(a, static_cast<const double2*>(Y), rows_per);
+        if (c64) k_mdot<float2, true><<<gd, kT, 0, s>>>(a, static_cast<const float2*>(Y));
+        else k_mdot<double2, true><<<gd, kT, 0, s>>>(a, static_cast<const double2*>(Y));
         VIE_CHECK_LAUNCH();
         k_reduce<true><<<k, kT, 0, s>>>(a, nchunk);
         VIE_CHECK_LAUNCH();
         k_maxpy<false><<<dim3(nblk, k), kT, 0, s>>>(a);
         VIE_CHECK_LAUNCH();
     } else {
-        k_mdot<double2, false><<<gd, kT, 0, s>>>(a, nullptr, rows_per);
+        k_mdot<double2, false><<<gd, kT, 0, s>>>(a, nullptr);
         VIE_CHECK_LAUNCH();
         k_reduce<false><<<k, kT, 0, s>>>(a, nchunk);
         VIE_CHECK_LAUNCH();
@@ -449,14 +467,14 @@ void kr_update(const KrylovArgs& a, double2* X, int k, int nblk, cudaStream_t s)
     VIE_CHECK_LAUNCH();
 }
 
-void kr_gather_cols(const double2* src, const int* cols, double2* dst, int64_t n, int k, int nblk, cudaStream_t s) {
-    k_gather_cols<<<dim3(nblk, k), kT, 0, s>>>(src, cols, dst, n);
+void kr_gather_cols(const KrylovArgs& a, const double2* src, double2* dst, int k, int nblk, cudaStream_t s) {
+    k_gather_cols<<<dim3(nblk, k), kT, 0, s>>>(a, src, dst);
     VIE_CHECK_LAUNCH();
 }
 
-void kr_sub_cols(const double2* b, const int* cols, const double2* T, double2* R, int64_t n, int k, int nblk,
+void kr_sub_cols(const KrylovArgs& a, const double2* b, const double2* T, double2* R, int k, int nblk,
                  cudaStream_t s) {
-    k_sub_cols<<<dim3(nblk, k), kT, 0, s>>>(b, cols, T, R, n);
+    k_sub_cols<<<dim3(nblk, k), kT, 0, s>>>(a, b, T, R);
     VIE_CHECK_LAUNCH();
 }
 
@@ -473,9 +491,9 @@ void kr_cycle_end(const KrylovArgs& a, int k, int nblk, int init, cudaStream_t s
     VIE_CHECK_LAUNCH();
 }
 
-void kr_colnorms(const double2* A, int64_t n, int k, int nblk, const int* cols, double* d_part, double* d_out,
-                 cudaStream_t s) {
-    k_colnorm_partial<<<dim3(nblk, k), kT, 0, s>>>(A, n, d_part);
+void kr_colnorms(const KrylovArgs& a, const double2* A, int k, int nblk, const int* cols, double* d_part,
+                 double* d_out, cudaStream_t s) {
+    k_colnorm_partial<<<dim3(nblk, k), kT, 0, s>>>(a, A, cols, d_part);
     VIE_CHECK_LAUNCH();
     k_colnorm_final<<<(k + 255) / 256, 256, 0, s>>>(d_part, nblk, k, cols, d_out);
     VIE_CHECK_LAUNCH();

@@ -18,14 +18,20 @@ enum : int {
 
 // Pointers into the solver's device state, passed by value to every kernel.
 // Slot i (< k) of a restart cycle works on column cols[i] of the n x nrhs
-// right-hand side, solution and residual arrays.
+// right-hand side, solution and residual arrays.  Column c only uses rows
+// [col_lo[c], col_lo[c] + col_len[c]) of them (all n rows for one operator;
+// its own problem's rows for a batched block-diagonal operator), and its
+// Krylov basis is col_len[c] x (m+1) at V + col_voff[c].
 struct KrylovArgs {
     int64_t n;
+    const long long* col_lo;
+    const long long* col_len;
+    const long long* col_voff;
     int m;            // restart length (<= 63)
     int nblk_max;     // row blocks the norm partials are laid out for
     double tol;
     int maxit;
-    double2* V;       // [slot][m+1][n] float64 basis
+    double2* V;       // per column: col_len x (m+1) float64 basis
     double2* H;       // [slot][m][m+1] Hessenberg columns (rotated in place)
     double2* g;       // [slot][m+1] rotated right-hand side of the least-squares problem
     double2* cs;      // [slot][m] Givens cosines
@@ -64,18 +70,47 @@ void kr_project(const KrylovArgs& a, const void* Y, bool c64, int pass, int k, i
 void kr_givens(const KrylovArgs& a, int k, int nblk, cudaGraphConditionalHandle hnd, int use_handle, cudaStream_t s);
 // X[:, cols[i]] += V_i y_i with y_i = H_i^-1 g_i
 void kr_update(const KrylovArgs& a, double2* X, int k, int nblk, cudaStream_t s);
-// dst[:, i] = src[:, cols[i]]
-void kr_gather_cols(const double2* src, const int* cols, double2* dst, int64_t n, int k, int nblk, cudaStream_t s);
+// dst[:, i] = src[:, cols[i]] (the rows of that column)
+void kr_gather_cols(const KrylovArgs& a, const double2* src, double2* dst, int k, int nblk, cudaStream_t s);
 // R[:, i] = b[:, cols[i]] - T[:, i]
-void kr_sub_cols(const double2* b, const int* cols, const double2* T, double2* R, int64_t n, int k, int nblk,
-                 cudaStream_t s);
+void kr_sub_cols(const KrylovArgs& a, const double2* b, const double2* T, double2* R, int k, int nblk, cudaStream_t s);
 // W[:, cols[i]] = Wl[:, i] (W may equal Wl with cols the identity) and its squared-norm partials
 void kr_scatter_norm(const KrylovArgs& a, const double2* Wl, double2* W, int k, int nblk, cudaStream_t s);
 // beta, res and done of the slots' columns from the norm partials; init also sets beta0
 void kr_cycle_end(const KrylovArgs& a, int k, int nblk, int init, cudaStream_t s);
-// norms of the k columns of A (n x k) into d_out[cols ? cols[i] : i]; d_part holds k * nblk doubles
-void kr_colnorms(const double2* A, int64_t n, int k, int nblk, const int* cols, double* d_part, double* d_out,
-                 cudaStream_t s);
+// norms of the k columns of A (n x k, column i holding the rows of column
+// cols ? cols[i] : i) into d_out[cols ? cols[i] : i]; d_part holds k * nblk doubles
+void kr_colnorms(const KrylovArgs& a, const double2* A, int k, int nblk, const int* cols, double* d_part,
+                 double* d_out, cudaStream_t s);
+
+// Rows of every right-hand-side column: all n rows for one operator, the
+// column's own problem for a batched (block-diagonal) operator, whose
+// columns are grouped by problem.
+struct ColumnLayout {
+    std::vector<long long> lo, len;
+    std::vector<int> prob;  // problem of each column
+    int nprob = 1;
+    static ColumnLayout single(int64_t n, int nrhs) {
+        ColumnLayout L;
+        L.lo.assign(nrhs, 0);
+        L.len.assign(nrhs, n);
+        L.prob.assign(nrhs, 0);
+        return L;
+    }
+};
+
+// outcome of one lockstep solve, per right-hand-side column
+struct GmresOutcome {
+    std::vector<double> res, rnorm, bnorm, hist;
+    std::vector<int> iters;
+    int applies = 0, refinements = 0;
+};
+void check_solve_opts(const Op& op, const vie_solve_opts* o, int nrhs);
+// restarted GMRES of every column of b (device, n x nrhs) into X
+GmresOutcome run_gmres(Op& op, const ColumnLayout& lay, const double2* b, double2* X, const vie_solve_opts& o,
+                       int nrhs);
+// stats of columns [c0, c1); returns VIE_OK or VIE_ERR_NOT_CONVERGED
+int fill_stats(const GmresOutcome& r, int c0, int c1, double tol, double t0, vie_solve_stats* st);
 
 // operator applications used by the solver (solve.cpp / api.cpp)
 // y = P^-1 Zs x in complex float32 (fused preconditioner), x, y: n x nrhs, ld = n

@@ -107,14 +107,17 @@ template <class TM, class TX>
 __global__ void __launch_bounds__(256) type_gemm(const TM* __restrict__ M, int np, const int* __restrict__ atoms,
                                                  int n_atoms, int nrhs, const TX* __restrict__ B, int64_t ldb,
                                                  const TX* __restrict__ ADD, int64_t ldadd, TX* __restrict__ Y,
-                                                 int64_t ldy) {
+                                                 int64_t ldy, const int2* __restrict__ colr, int prob) {
     using R = decltype(TM().x);
     using TA = typename C2<R>::t;
     constexpr int BM = 32, BN = 32, BK = 32;
     __shared__ TA sM[BK][BM + 1];
     __shared__ TA sB[BK][BN + 1];
-    const int ncols = n_atoms * nrhs;
+    // right-hand sides of this type's problem (all of them for a single operator)
+    const int2 cr = colr ? colr[prob] : make_int2(0, nrhs);
+    const int ncols = n_atoms * (cr.y - cr.x);
     const int row0 = blockIdx.x * BM, col0 = blockIdx.y * BN;
+    if (col0 >= ncols) return;
     const int tr = threadIdx.x % 16, tc = threadIdx.x / 16;  // 16 x 16 threads, 2 x 2 each
     TA acc[2][2];
     for (int a = 0; a < 2; ++a)
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(256) type_gemm(const TM* __restrict__ M, int n
             int gc = col0 + c, gk = k0 + kk;
             TA v = mk(R(0), R(0));
             if (gc < ncols && gk < np) {
-                int a = atoms[gc % n_atoms], rhs = gc / n_atoms;
+                int a = atoms[gc % n_atoms], rhs = cr.x + gc / n_atoms;
                 v = cvt<TA>(B[(int64_t)a * np + gk + (int64_t)rhs * ldb]);
             }
             sB[kk][c] = v;
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(256) type_gemm(const TM* __restrict__ M, int n
     for (int b = 0; b < 2; ++b) {
         int gc = col0 + tc + 16 * b;
         if (gc >= ncols) continue;
-        int a_ = atoms[gc % n_atoms], rhs = gc / n_atoms;
+        int a_ = atoms[gc % n_atoms], rhs = cr.x + gc / n_atoms;
         for (int a = 0; a < 2; ++a) {
             int gr = row0 + tr + 16 * a;
             if (gr >= np) continue;
@@ -218,7 +221,8 @@ void self_gemm(Op& op, const TM* M, const TX* X, int64_t ldx, const TX* C, int64
         int64_t ldb = mode == 1 ? ldc : ldx;
         const TX* ADD = mode == 0 ? C : (mode == 1 ? X : nullptr);
         int64_t ldadd = mode == 0 ? ldc : ldx;
-        type_gemm<TM, TX><<<grid, 256, 0, s>>>(Mt, np, atoms, na, nrhs, Bop, ldb, ADD, ldadd, Y, ldy);
+        const int prob = op.type_prob.empty() ? 0 : op.type_prob[t];
+        type_gemm<TM, TX><<<grid, 256, 0, s>>>(Mt, np, atoms, na, nrhs, Bop, ldb, ADD, ldadd, Y, ldy, op.colr, prob);
         VIE_CHECK_LAUNCH();
     }
 }

@@ -42,25 +42,41 @@ struct CycleGraph {
 struct Gmres {
     Op& op;
     const vie_solve_opts& o;
+    const ColumnLayout& lay;
     cudaStream_t s, s_body = nullptr;
     int64_t n;
     int m, nrhs, n_sm;
     bool c64;  // inner applies on float32 vectors
     DevBuf V, H, g, cs, sn, h, y, part, npart, nsq, rpart, inv, cycling, jdone, cols, iters, done, beta0, beta, res, rnorm,
-        bnorm, hist, ctr;
+        bnorm, hist, ctr, col_lo, col_len, col_voff, colr;
+    std::vector<int2> h_colr;
     DevBuf Xg, Yg, Xl, T, Rl, Wl, W;
     KrylovArgs a{};
     std::map<int, CycleGraph> graphs;
     int* h_pinned = nullptr;  // [KR_NCTR + nrhs] host-visible copy of counters and done flags
 
-    Gmres(Op& op_, const vie_solve_opts& o_, int nrhs_)
-        : op(op_), o(o_), s(op_.ctx->stream), n(op_.n()), nrhs(nrhs_), n_sm(op_.ctx->n_sm) {
+    Gmres(Op& op_, const vie_solve_opts& o_, int nrhs_, const ColumnLayout& lay_)
+        : op(op_), o(o_), lay(lay_), s(op_.ctx->stream), n(op_.n()), nrhs(nrhs_), n_sm(op_.ctx->n_sm) {
         m = std::max(1, std::min(o.restart > 0 ? o.restart : 60, 63));
         c64 = !(o.precision == VIE_C128 || !o.precond);
         const int S = nrhs;
         const int nblk_max = kr_nblk(n, 1, n_sm);
         const int nchunk_max = kr_nchunk(n, 1, m, n_sm);
-        V.alloc((size_t)S * (m + 1) * n * sizeof(double2));
+        // the basis of column c: col_len[c] x (m+1) at col_voff[c]
+        std::vector<long long> voff(nrhs);
+        long long vtot = 0;
+        for (int c = 0; c < nrhs; ++c) {
+            voff[c] = vtot;
+            vtot += (long long)(m + 1) * lay.len[c];
+        }
+        V.alloc((size_t)vtot * sizeof(double2));
+        upload(col_lo, lay.lo);
+        upload(col_len, lay.len);
+        upload(col_voff, voff);
+        if (lay.nprob > 1) {
+            colr.alloc(lay.nprob * sizeof(int2));
+            h_colr.assign(lay.nprob, make_int2(0, 0));
+        }
         H.alloc((size_t)S * m * (m + 1) * sizeof(double2));
         g.alloc((size_t)S * (m + 1) * sizeof(double2));
         cs.alloc((size_t)S * m * sizeof(double2));
@@ -96,6 +112,9 @@ struct Gmres {
         VIE_CUDA(cudaMemsetAsync(ctr.p, 0, KR_NCTR * sizeof(int), s));
         VIE_CUDA(cudaMemsetAsync(hist.p, 0, 512 * sizeof(double), s));
         a.n = n;
+        a.col_lo = col_lo.as<long long>();
+        a.col_len = col_len.as<long long>();
+        a.col_voff = col_voff.as<long long>();
         a.m = m;
         a.nblk_max = nblk_max;
         a.tol = o.tol > 0 ? o.tol : 1e-6;
@@ -159,10 +178,10 @@ struct Gmres {
     void launch_post(int k, const double2* b, double2* X, cudaStream_t st) {
         const int nblk = kr_nblk(n, k, n_sm);
         kr_update(a, X, k, nblk, st);
-        kr_gather_cols(X, a.cols, Xl.as<double2>(), n, k, nblk, st);
+        kr_gather_cols(a, X, Xl.as<double2>(), k, nblk, st);
         op_apply64(op, Xl.as<double2>(), T.as<double2>(), k, st);
-        kr_sub_cols(b, a.cols, T.as<double2>(), Rl.as<double2>(), n, k, nblk, st);
-        kr_colnorms(Rl.as<double2>(), n, k, nblk, a.cols, rpart.as<double>(), a.rnorm, st);
+        kr_sub_cols(a, b, T.as<double2>(), Rl.as<double2>(), k, nblk, st);
+        kr_colnorms(a, Rl.as<double2>(), k, nblk, a.cols, rpart.as<double>(), a.rnorm, st);
         if (o.precond) op_precond64(op, Rl.as<double2>(), Wl.as<double2>(), k, st);
         else VIE_CUDA(cudaMemcpyAsync(Wl.p, Rl.p, (size_t)n * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
         kr_scatter_norm(a, Wl.as<double2>(), W.as<double2>(), k, nblk, st);
@@ -239,17 +258,37 @@ struct Gmres {
         }
     }
 
+    // a batched operator's kernels take each problem's right-hand sides from
+    // the column-range table: slots (or columns) [x, y) belong to problem p
+    void set_colr(const std::vector<int>& slot_cols) {
+        if (lay.nprob <= 1) return;
+        std::fill(h_colr.begin(), h_colr.end(), make_int2(0, 0));
+        for (int i = 0; i < (int)slot_cols.size(); ++i) {
+            int2& r = h_colr[lay.prob[slot_cols[i]]];
+            if (r.y == 0) r.x = i;
+            r.y = i + 1;
+        }
+        VIE_CUDA(cudaMemcpyAsync(colr.p, h_colr.data(), lay.nprob * sizeof(int2), cudaMemcpyHostToDevice, s));
+        VIE_CUDA(cudaStreamSynchronize(s));  // h_colr is reused for the next cycle
+        op.colr = colr.as<int2>();
+    }
+
     void run(const double2* b, double2* X) {
+        struct ResetColr {
+            Op& o;
+            ~ResetColr() { o.colr = nullptr; }
+        } reset{op};
         VIE_CUDA(cudaMemsetAsync(X, 0, (size_t)n * nrhs * sizeof(double2), s));
         // W = M^-1 b, beta0 = ||W|| per column
-        if (o.precond) op_precond64(op, b, W.as<double2>(), nrhs, s);
-        else VIE_CUDA(cudaMemcpyAsync(W.p, b, (size_t)n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, s));
         std::vector<int> ident(nrhs);
         for (int c = 0; c < nrhs; ++c) ident[c] = c;
+        set_colr(ident);
+        if (o.precond) op_precond64(op, b, W.as<double2>(), nrhs, s);
+        else VIE_CUDA(cudaMemcpyAsync(W.p, b, (size_t)n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, s));
         VIE_CUDA(cudaMemcpyAsync(cols.p, ident.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
         const int nb1 = kr_nblk(n, nrhs, n_sm);
         // x = 0: the unpreconditioned residual is b
-        kr_colnorms(b, n, nrhs, nb1, nullptr, rpart.as<double>(), bnorm.as<double>(), s);
+        kr_colnorms(a, b, nrhs, nb1, nullptr, rpart.as<double>(), bnorm.as<double>(), s);
         VIE_CUDA(cudaMemcpyAsync(rnorm.p, bnorm.p, nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
         kr_scatter_norm(a, W.as<double2>(), W.as<double2>(), nrhs, nb1, s);
         kr_cycle_end(a, nrhs, nb1, 1, s);
@@ -261,7 +300,13 @@ struct Gmres {
                 if (!h_pinned[KR_NCTR + c]) live.push_back(c);
             if (live.empty()) break;
             const int k = (int)live.size();
+            if (o.autotune && c64 && !tuned(op, o.precision == VIE_BF16X3 ? VIE_BF16X3 : VIE_C64, k)) {
+                std::vector<int> cand;
+                std::vector<double> ms;
+                tune_far(op, o.precision == VIE_BF16X3 ? VIE_BF16X3 : VIE_C64, k, s, cand, ms);
+            }
             VIE_CUDA(cudaMemcpyAsync(cols.p, live.data(), k * sizeof(int), cudaMemcpyHostToDevice, s));
+            set_colr(live);
             const int it0 = h_pinned[KR_IT];
             if (o.launch == 1) {
                 launch_pre(k, s);
@@ -284,14 +329,65 @@ struct Gmres {
 
 }  // namespace
 
-int solve(Op& op, const vie_incident* inc, int nrhs, const vie_solve_opts* o, void* I_out, vie_solve_stats* st) {
+void check_solve_opts(const Op& op, const vie_solve_opts* o, int nrhs) {
     if (op.fprec == 0) fail(VIE_ERR_STATE, "operator is not compressed");
     if (o->precision == VIE_C128 && op.fprec != VIE_C128)
         fail(VIE_ERR_INVALID_ARG, "an all-float64 solve needs VIE_C128 factors");
     if (o->precision != VIE_C128 && o->precision != VIE_C64 && o->precision != VIE_BF16X3 && o->precision != 0)
         fail(VIE_ERR_INVALID_ARG, "solve precision must be VIE_C64, VIE_BF16X3 or VIE_C128");
     if (o->launch != 0 && o->launch != 1) fail(VIE_ERR_INVALID_ARG, "solve launch must be 0 (graph) or 1 (host loop)");
-    if (nrhs < 1 || nrhs > 1024) fail(VIE_ERR_INVALID_ARG, "vie_solve takes 1 to 1024 right-hand sides");
+    if (nrhs < 1 || nrhs > 1024) fail(VIE_ERR_INVALID_ARG, "a solve takes 1 to 1024 right-hand sides");
+}
+
+GmresOutcome run_gmres(Op& op, const ColumnLayout& lay, const double2* b, double2* X, const vie_solve_opts& o,
+                       int nrhs) {
+    cudaStream_t s = op.ctx->stream;
+    Gmres G(op, o, nrhs, lay);
+    G.run(b, X);
+    GmresOutcome r;
+    r.rnorm.resize(nrhs);
+    r.bnorm.resize(nrhs);
+    r.res.resize(nrhs);
+    r.iters.resize(nrhs);
+    std::vector<double> hh(512);
+    std::vector<int> hc(KR_NCTR);
+    VIE_CUDA(cudaMemcpyAsync(r.rnorm.data(), G.rnorm.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaMemcpyAsync(r.bnorm.data(), G.bnorm.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaMemcpyAsync(r.res.data(), G.res.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaMemcpyAsync(r.iters.data(), G.iters.p, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaMemcpyAsync(hh.data(), G.hist.p, 512 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaMemcpyAsync(hc.data(), G.ctr.p, KR_NCTR * sizeof(int), cudaMemcpyDeviceToHost, s));
+    VIE_CUDA(cudaStreamSynchronize(s));
+    r.applies = hc[KR_APPLIES];
+    r.refinements = hc[KR_REFIN];
+    r.hist.assign(hh.begin(), hh.begin() + std::min(512, hc[KR_IT]));
+    return r;
+}
+
+int fill_stats(const GmresOutcome& r, int c0, int c1, double tol, double t0, vie_solve_stats* st) {
+    double worst = 0.0, worst_true = 0.0;
+    int iters = 0, status = VIE_OK;
+    for (int c = c0; c < c1; ++c) {
+        worst_true = std::max(worst_true, r.bnorm[c] > 0 ? r.rnorm[c] / r.bnorm[c] : 0.0);
+        worst = std::max(worst, r.res[c]);
+        iters = std::max(iters, r.iters[c]);
+        if (r.res[c] > tol) status = VIE_ERR_NOT_CONVERGED;
+    }
+    if (st) {
+        st->iterations = iters;
+        st->applies = r.applies;
+        st->refinements = r.refinements;
+        st->residual = worst;
+        st->true_residual = worst_true;
+        st->t_solve_s = now_s() - t0;
+        st->n_history = (int)r.hist.size();
+        for (int i = 0; i < st->n_history; ++i) st->history[i] = r.hist[i];
+    }
+    return status;
+}
+
+int solve(Op& op, const vie_incident* inc, int nrhs, const vie_solve_opts* o, void* I_out, vie_solve_stats* st) {
+    check_solve_opts(op, o, nrhs);
     cudaStream_t s = op.ctx->stream;
     const int64_t n = op.n();
     double t0 = now_s();
@@ -307,41 +403,13 @@ int solve(Op& op, const vie_incident* inc, int nrhs, const vie_solve_opts* o, vo
         xdev.alloc((size_t)n * nrhs * sizeof(double2));
         X = xdev.as<double2>();
     }
-    Gmres G(op, *o, nrhs);
-    G.run(b.as<double2>(), X);
-    // unpreconditioned relative residual ||b - Zs x|| / ||b|| with the compressed
-    // operator, from each column's last refinement (x has not changed since)
-    std::vector<double> hn(2 * nrhs), hres(nrhs), hh(512);
-    std::vector<int> hit(nrhs), hc(KR_NCTR);
-    VIE_CUDA(cudaMemcpyAsync(hn.data(), G.rnorm.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-    VIE_CUDA(cudaMemcpyAsync(hn.data() + nrhs, G.bnorm.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-    VIE_CUDA(cudaMemcpyAsync(hres.data(), G.res.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-    VIE_CUDA(cudaMemcpyAsync(hit.data(), G.iters.p, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
-    VIE_CUDA(cudaMemcpyAsync(hh.data(), G.hist.p, 512 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    VIE_CUDA(cudaMemcpyAsync(hc.data(), G.ctr.p, KR_NCTR * sizeof(int), cudaMemcpyDeviceToHost, s));
-    if (!o->out_on_device)
+    const ColumnLayout lay = ColumnLayout::single(n, nrhs);
+    const GmresOutcome r = run_gmres(op, lay, b.as<double2>(), X, *o, nrhs);
+    if (!o->out_on_device) {
         VIE_CUDA(cudaMemcpyAsync(I_out, X, (size_t)n * nrhs * sizeof(double2), cudaMemcpyDeviceToHost, s));
-    VIE_CUDA(cudaStreamSynchronize(s));
-    const double tol = o->tol > 0 ? o->tol : 1e-6;
-    double worst = 0.0, worst_true = 0.0;
-    int iters = 0, status = VIE_OK;
-    for (int c = 0; c < nrhs; ++c) {
-        worst_true = std::max(worst_true, hn[nrhs + c] > 0 ? hn[c] / hn[nrhs + c] : 0.0);
-        worst = std::max(worst, hres[c]);
-        iters = std::max(iters, hit[c]);
-        if (hres[c] > tol) status = VIE_ERR_NOT_CONVERGED;
+        VIE_CUDA(cudaStreamSynchronize(s));
     }
-    if (st) {
-        st->iterations = iters;
-        st->applies = hc[KR_APPLIES];
-        st->refinements = hc[KR_REFIN];
-        st->residual = worst;
-        st->true_residual = worst_true;
-        st->t_solve_s = now_s() - t0;
-        st->n_history = std::min(512, hc[KR_IT]);
-        for (int i = 0; i < st->n_history; ++i) st->history[i] = hh[i];
-    }
-    return status;
+    return fill_stats(r, 0, nrhs, o->tol > 0 ? o->tol : 1e-6, t0, st);
 }
 
 }  // namespace vie

@@ -14,12 +14,19 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libvie.so")
 
 VIE_OK = 0
+VIE_ERR_INVALID_ARG = -1
+VIE_ERR_OOM = -2
+VIE_ERR_CUDA = -3
 VIE_ERR_NOT_CONVERGED = -4
+VIE_ERR_BREAKDOWN = -5
+VIE_ERR_NAN = -6
 VIE_ERR_TIMEOUT = -7
 VIE_ERR_ADMISSION = -8
+VIE_ERR_STATE = -9
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED", -5: "BREAKDOWN",
           -6: "NAN", -7: "TIMEOUT", -8: "ADMISSION", -9: "STATE"}
 C64, C128, BF16X3, C64_ACC64 = 1, 2, 3, 4
+VAR_SIMT_R1, VAR_SIMT_R2, VAR_SIMT_R4, VAR_SIMT_R8, VAR_MMA_BF16X3, VAR_TCGEN05_BF16X3 = 1, 2, 3, 4, 5, 6
 NOALLOC_SCRATCH_ELEMS = 1 << 22   # VIE_NOALLOC_SCRATCH_ELEMS
 FUSE_PRECOND = 1
 DENSE = 2
@@ -59,7 +66,12 @@ class IncidentC(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_iters", C.c_int), ("precision", C.c_int),
-                ("out_on_device", C.c_int), ("precond", C.c_int), ("launch", C.c_int)]
+                ("out_on_device", C.c_int), ("precond", C.c_int), ("launch", C.c_int), ("autotune", C.c_int)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("variant", C.c_int), ("n_candidates", C.c_int), ("candidates", C.c_int * 8),
+                ("ms", C.c_double * 8)]
 
 
 class SolveStats(C.Structure):
@@ -92,7 +104,7 @@ EXPORTS = ["vie_create", "vie_destroy", "vie_last_error", "vie_assemble", "vie_c
            "vie_op_get_info", "vie_apply", "vie_precond", "vie_rhs", "vie_solve", "vie_fields",
            "vie_export_block", "vie_far_block_info", "vie_export_far_block", "vie_serve", "vie_submit",
            "vie_poll", "vie_result_free", "vie_server_stop", "vie_footprint_bytes", "vie_kernel_launches",
-           "vie_apply_noalloc", "vie_plan_far_blocks", "vie_lpt_assign"]
+           "vie_apply_noalloc", "vie_plan_far_blocks", "vie_lpt_assign", "vie_tune", "vie_solve_batch"]
 
 _lib = None
 
@@ -133,6 +145,9 @@ def load():
         "vie_server_stop": (C.c_int, [vp]),
         "vie_footprint_bytes": (i64, [i64, C.c_int, C.c_int, C.c_int, i64]),
         "vie_kernel_launches": (i64, []),
+        "vie_tune": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.POINTER(TuneResult)]),
+        "vie_solve_batch": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(IncidentC), C.POINTER(C.c_int),
+                                      C.POINTER(SolveOpts), C.POINTER(vp), C.POINTER(SolveStats)]),
         "vie_apply_noalloc": (C.c_int, [vp, vp, vp, C.c_int, i64, vp]),
         "vie_plan_far_blocks": (C.c_int, [C.POINTER(dbl), C.c_int, C.POINTER(C.c_int), C.POINTER(i64),
                                           C.POINTER(C.c_int), i64, C.POINTER(i64)]),
@@ -246,6 +261,13 @@ class Operator:
         self.ctx.check(self.L.vie_apply(self.h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(nrhs), self.n,
                                         int(precision), int(flags), _stream(stream)))
 
+    def tune(self, precision=C64, nrhs=1, force=0):
+        """vie_tune: time the far-apply variants (or set `force`); returns the choice and timings."""
+        r = TuneResult()
+        self.ctx.check(self.L.vie_tune(self.h, int(precision), int(nrhs), int(force), C.byref(r)))
+        return {"variant": r.variant,
+                "ms": {int(r.candidates[i]): float(r.ms[i]) for i in range(r.n_candidates)}}
+
     def apply_noalloc(self, x_ptr, y_ptr, nrhs=1, stream=None):
         """vie_apply_noalloc: y = Zs x (c64) with the library's static scratch."""
         self.ctx.check(self.L.vie_apply_noalloc(self.h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(nrhs), self.n,
@@ -261,10 +283,10 @@ class Operator:
                                       _stream(stream)))
 
     def solve(self, khat, pol, tol=1e-6, restart=60, max_iters=2000, precision=C64, precond=1, out_ptr=None,
-              launch=0):
+              launch=0, autotune=0):
         """Returns (I (numpy complex128 n x nrhs, or None with out_ptr), stats dict, status)."""
         inc, keep, nrhs = _incident_struct(khat, pol)
-        o = SolveOpts(tol, restart, max_iters, precision, 1 if out_ptr else 0, precond, launch)
+        o = SolveOpts(tol, restart, max_iters, precision, 1 if out_ptr else 0, precond, launch, autotune)
         st = SolveStats()
         out = None
         if out_ptr is None:
@@ -332,6 +354,29 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+def solve_batch(ops, incidents, tol=1e-6, restart=60, max_iters=2000, precision=C64, launch=0):
+    """vie_solve_batch: solve several problems (operators on one context) in one
+    lockstep over their block-diagonal union.  incidents[p] = (khat, pol).
+    Returns ([I_p numpy complex128 n_p x nrhs_p], [stats dict], status)."""
+    B = len(ops)
+    ctx = ops[0].ctx
+    incs = (IncidentC * B)()
+    keep, nr, outs = [], (C.c_int * B)(), []
+    for p, (kh, pol) in enumerate(incidents):
+        inc, k, n_r = _incident_struct(kh, pol)
+        incs[p] = inc
+        keep.append(k)
+        nr[p] = n_r
+        outs.append(np.zeros((n_r, ops[p].n), np.complex128))
+    handles = (C.c_void_p * B)(*[op.h.value for op in ops])
+    optrs = (C.c_void_p * B)(*[o.ctypes.data for o in outs])
+    so = SolveOpts(tol, restart, max_iters, precision, 0, 1, launch, 0)
+    stats = (SolveStats * B)()
+    status = ctx.check(ctx.L.vie_solve_batch(handles, B, incs, nr, C.byref(so), optrs, stats),
+                       ok=(VIE_OK, VIE_ERR_NOT_CONVERGED))
+    return [o.T for o in outs], [stats[p].as_dict() for p in range(B)], status
 
 
 def plan_far_blocks(centres):

@@ -332,3 +332,46 @@ def test_bf16x3_apply_4cube_array(ctx, nrhs):
         th.cuda.synchronize()
         assert rel(Y.cpu().numpy(), Yr.cpu().numpy()) < 5e-5
     op.close()
+
+
+# ------------------------------------------------------------------- autotuner
+def test_autotune_variants_agree(ctx, tiny_dense):
+    import torch as th
+    P, Z, _, _, _ = tiny_dense
+    g, _, _ = workloads.config("tiny")
+    op = vie.Operator(ctx, g)
+    op.compress(1e-4, vie.C64)
+    nrhs = 5
+    X = th.from_numpy(workloads.random_complex(P.n, 3, cols=nrhs).T.astype(np.complex64).copy()).cuda()
+    res = op.tune(vie.C64, nrhs)
+    assert res["variant"] in (vie.VAR_SIMT_R1, vie.VAR_SIMT_R2, vie.VAR_SIMT_R4, vie.VAR_SIMT_R8)
+    assert set(res["ms"]) == {vie.VAR_SIMT_R1, vie.VAR_SIMT_R2, vie.VAR_SIMT_R4, vie.VAR_SIMT_R8}
+    assert all(t > 0 for t in res["ms"].values())
+    out = {}
+    for v in (vie.VAR_SIMT_R1, vie.VAR_SIMT_R2, vie.VAR_SIMT_R4, vie.VAR_SIMT_R8):
+        op.tune(vie.C64, nrhs, force=v)
+        Y = th.zeros_like(X)
+        op.apply(X.data_ptr(), Y.data_ptr(), nrhs, vie.C64, vie.FUSE_PRECOND)
+        th.cuda.synchronize()
+        out[v] = Y.cpu().numpy()
+    # the register tiles keep every column's summation order: bit-identical
+    assert np.array_equal(out[vie.VAR_SIMT_R2], out[vie.VAR_SIMT_R4])
+    assert np.array_equal(out[vie.VAR_SIMT_R4], out[vie.VAR_SIMT_R8])
+    assert rel(out[vie.VAR_SIMT_R1], out[vie.VAR_SIMT_R4]) < 1e-6
+    # split-precision variants are admissible for VIE_BF16X3 only
+    with pytest.raises(vie.VieError):
+        op.tune(vie.C64, nrhs, force=vie.VAR_TCGEN05_BF16X3)
+    for v in (vie.VAR_MMA_BF16X3, vie.VAR_TCGEN05_BF16X3):
+        op.tune(vie.BF16X3, nrhs, force=v)
+        Y = th.zeros_like(X)
+        op.apply(X.data_ptr(), Y.data_ptr(), nrhs, vie.BF16X3, vie.FUSE_PRECOND)
+        th.cuda.synchronize()
+        assert rel(Y.cpu().numpy(), out[vie.VAR_SIMT_R4]) < 5e-5
+    res = op.tune(vie.BF16X3, 64)
+    assert res["variant"] in range(1, 7) and len(res["ms"]) == 6
+    kh, pol = workloads.angle_sweep(2, 30.0)
+    I, st, status = op.solve(kh, pol, tol=1e-6, precision=vie.BF16X3, autotune=1)
+    assert status == vie.VIE_OK
+    for c in range(len(kh)):
+        assert rel(I[:, c], np.linalg.solve(Z, A.rhs(P, kh[c], pol[c]))) <= 5e-4
+    op.close()
