@@ -222,6 +222,127 @@ def run_serving(args):
     return 0
 
 
+def run_multirhs(args):
+    """--multirhs: the 64-right-hand-side workload (32x32 array of 4^3-voxel cubes,
+    245,760 unknowns; 32 polar angles x 2 polarisations).  Times
+      - the mixed-precision batched solve: c64 factors, all 64 right-hand sides in
+        one lockstep GMRES, far apply on the tensor cores (BF16x3, tcgen05), float64
+        refinement;
+      - the same lockstep with float32 SIMT applies;
+      - the plain all-float64 single-RHS solve (c128 factors, one right-hand side at a
+        time) on --fp64-sample right-hand sides, scaled to 64;
+    and the largest relative difference between the batched and float64 currents
+    on the sampled right-hand sides (the equal-accuracy check, bound 5e-4)."""
+    import torch
+    from paper_2603_10586_gb300 import vie
+    torch.cuda.set_device(0)
+    ctx = vie.Context(0)
+    g, kh, pol = workloads.config("multirhs")
+    s = len(kh)
+    sample = list(range(0, s, max(1, s // args.fp64_sample)))[: args.fp64_sample]
+    out = {"metric": "multi-RHS solves/s", "unit": "solves/s", "workload": "32x32 array of 4^3-voxel cubes, 64 RHS",
+           "nrhs": s}
+    op = vie.Operator(ctx, g)
+    t0 = time.perf_counter()
+    op.compress(TOL_COMPRESS, vie.C128)
+    out["compress_c128_s"] = time.perf_counter() - t0
+    ref = {}
+    t_fp64 = 0.0
+    for c in sample:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        I, st, status = op.solve(kh[c:c + 1], pol[c:c + 1], tol=TOL_SOLVE, precision=vie.C128)
+        torch.cuda.synchronize()
+        t_fp64 += time.perf_counter() - t0
+        ref[c] = I[:, 0]
+        assert status == vie.VIE_OK
+    op.close()
+    per_rhs = t_fp64 / len(sample)
+    out["fp64_single"] = {"sample": sample, "s_per_rhs": per_rhs, "solves_per_s": 1.0 / per_rhs,
+                          "scaled_64_s": per_rhs * s}
+    op = vie.Operator(ctx, g)
+    t0 = time.perf_counter()
+    info = op.compress(TOL_COMPRESS, vie.C64)
+    out["compress_c64_s"] = time.perf_counter() - t0
+    out["factor_entries"] = info["factor_entries"]
+    for prec, name in ((vie.BF16X3, "bf16x3_lockstep"), (vie.C64, "c64_lockstep")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        I, st, status = op.solve(kh, pol, tol=TOL_SOLVE, precision=prec)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        assert status == vie.VIE_OK
+        diff = max(float(np.linalg.norm(I[:, c] - ref[c]) / np.linalg.norm(ref[c])) for c in sample)
+        out[name] = {"s": t, "solves_per_s": s / t, "iterations": st["iterations"],
+                     "residual": st["residual"], "true_residual": st["true_residual"],
+                     "max_rel_diff_vs_fp64": diff, "speedup_vs_fp64_single": per_rhs * s / t}
+    x = torch.randn((s, op.n), dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    for prec, name in ((vie.BF16X3, "bf16x3"), (vie.C64, "c64")):
+        for _ in range(3):
+            op.apply(x.data_ptr(), y.data_ptr(), s, prec, vie.FUSE_PRECOND)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(10):
+            op.apply(x.data_ptr(), y.data_ptr(), s, prec, vie.FUSE_PRECOND)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        fbytes = 8.0 * info["factor_entries"]
+        out["apply_" + name] = {"ms": ms, "factor_GBs": fbytes / ms / 1e6,
+                                "hbm_frac": fbytes / ms / 1e6 / peaks()[0],
+                                "complex_TFLOPs": 8.0 * s * info["factor_entries"] / ms / 1e9}
+    print(json.dumps(out), flush=True)
+    op.close()
+    ctx.close()
+    return 0
+
+
+def run_batch(args):
+    """--batch: the serving mix (arrays of 8x8..48x48 cubes of 3^3 voxels, lambda ~
+    U[0.9, 1.1], eps ~ U[8, 14], 1-8 RHS; --requests problems, seed 7) solved one
+    vie_solve after another and as one vie_solve_batch (block-diagonal union, one
+    persistent apply launch per phase over all problems), operators built
+    beforehand.  Reports right-hand sides per second both ways, each the median of
+    three runs, and the largest difference between the two solutions."""
+    import torch
+    from paper_2603_10586_gb300 import vie
+    torch.cuda.set_device(0)
+    ctx = vie.Context(0)
+    reqs = workloads.serving_stream(args.requests, seed=7, ns_range=(8, 48))
+    ops = []
+    for r in reqs:
+        op = vie.Operator(ctx, r.geometry)
+        op.compress(TOL_COMPRESS, vie.C64)
+        ops.append(op)
+    nrhs = sum(len(r.khat) for r in reqs)
+    out = {"metric": "batched solves/s", "unit": "solves/s", "problems": len(reqs), "nrhs": nrhs,
+           "sizes": [r.ns for r in reqs], "n": [op.n for op in ops], "precision": {}}
+    for prec, name in ((vie.C64, "c64"), (vie.BF16X3, "bf16x3")):
+        seq_t, bat_t = [], []
+        for rep in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            seq = [op.solve(r.khat, r.pol, tol=TOL_SOLVE, precision=prec)[0] for op, r in zip(ops, reqs)]
+            torch.cuda.synchronize()
+            seq_t.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            bat, st, status = vie.solve_batch(ops, [(r.khat, r.pol) for r in reqs], tol=TOL_SOLVE, precision=prec)
+            torch.cuda.synchronize()
+            bat_t.append(time.perf_counter() - t0)
+            assert status == vie.VIE_OK
+        diff = max(float(np.linalg.norm(a - b) / np.linalg.norm(a)) for a, b in zip(seq, bat))
+        ts, tb = float(np.median(seq_t)), float(np.median(bat_t))
+        out["precision"][name] = {"sequential_s": ts, "batched_s": tb, "sequential": nrhs / ts,
+                                  "batched": nrhs / tb, "speedup": ts / tb, "max_rel_diff": diff}
+    print(json.dumps(out), flush=True)
+    for op in ops:
+        op.close()
+    ctx.close()
+    return 0
+
+
 def run_profile(args):
     """--profile: one untimed solve from geometry followed by 20 fused applies, for
     ncu captures (no warm-up, no timing, no baseline).  --profile-case small uses
@@ -278,6 +399,9 @@ def main():
     ap.add_argument("--serving", action="store_true", help="the request-stream workload instead")
     ap.add_argument("--requests", type=int, default=32)
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--batch", action="store_true", help="sequential against batched solves of the serving mix")
+    ap.add_argument("--multirhs", action="store_true", help="the 64-RHS workload against float64 single-RHS solves")
+    ap.add_argument("--fp64-sample", type=int, default=2)
     ap.add_argument("--profile", action="store_true", help="one untimed step for ncu captures")
     ap.add_argument("--profile-case", default="scale", choices=["scale", "small", "multirhs-small"])
     args = ap.parse_args()
@@ -287,6 +411,10 @@ def main():
         return run_reference(args)
     if args.serving:
         return run_serving(args)
+    if args.batch:
+        return run_batch(args)
+    if args.multirhs:
+        return run_multirhs(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

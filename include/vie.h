@@ -81,7 +81,10 @@ enum vie_variant {
     VIE_VAR_SIMT_R4 = 3,
     VIE_VAR_SIMT_R8 = 4,
     VIE_VAR_MMA_BF16X3 = 5,     /* warp-level mma.sync, 64-row tiles */
-    VIE_VAR_TCGEN05_BF16X3 = 6  /* tcgen05 MMAs with tensor-memory accumulators, 128-row tiles */
+    VIE_VAR_TCGEN05_BF16X3 = 6, /* tcgen05 MMAs with tensor-memory accumulators, 128-row tiles */
+    VIE_VAR_TCGEN05_PACKED_BF16X3 = 7 /* as 6, with the factors split once into bf16 planes in the
+                                         shared-memory stage layout and moved by bulk TMA copies (needs
+                                         ~1.1x the factor memory; runs as 6 when that is not free) */
 };
 
 /* vie_apply flags */
@@ -264,8 +267,9 @@ int vie_solve(vie_op* op, const vie_incident* inc, int nrhs, const vie_solve_opt
  * I_out[p]: its c128 n_p x nrhs[p] solution (host or device per
  * opts->out_on_device); stats[p] (may be NULL): its statistics (applies,
  * refinements and history are those of the shared lockstep).
- * opts->precision VIE_C64 or VIE_BF16X3.  The joined operator holds a copy of
- * the factors for the duration of the call. */
+ * opts->precision VIE_C64 or VIE_BF16X3.  The joined operator reads every
+ * problem's factors in place (no copy); it holds the self blocks and the work
+ * lists for the duration of the call. */
 int vie_solve_batch(vie_op* const* ops, int count, const vie_incident* inc, const int* nrhs,
                     const vie_solve_opts* opts, void* const* I_out, vie_solve_stats* stats);
 

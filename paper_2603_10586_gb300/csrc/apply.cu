@@ -414,7 +414,7 @@ template <class TF, class TX>
 void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, cudaStream_t s) {
     size_t need = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(TX);
     if (op.d_t.bytes < need) op.d_t.alloc(need);
-    const TF* fac = op.d_factors.as<TF>();
+    const TF* fac = op.fac<TF>();
     const int nc = op.n_cta;
     if (nrhs > 1) {
         if (op.n_p1_items > 0) {
@@ -450,7 +450,7 @@ void apply_far_simt32(Op& op, const float2* x, int64_t ldx, float2* F, int64_t l
                       cudaStream_t s) {
     const size_t need = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(float2);
     if (op.d_t.bytes < need) op.d_t.alloc(need);
-    const float2* fac = op.d_factors.as<float2>();
+    const float2* fac = op.fac<float2>();
     float2* t = op.d_t.as<float2>();
     const int nc = op.n_cta;
     const FarBlockDev* bl = op.d_blocks.as<FarBlockDev>();
@@ -513,7 +513,7 @@ void apply_far_df(Op& op, const double2* x, int64_t ldx, double2* F, int64_t ldf
     if (op.d_xs.bytes < need_x) op.d_xs.alloc(need_x);
     float4* xs = op.d_xs.as<float4>();
     float4* t = op.d_t.as<float4>();
-    const float2* fac = op.d_factors.as<float2>();
+    const float2* fac = op.fac<float2>();
     const int nc = op.n_cta;
     k_split_hl<<<op.ctx->n_sm * 8, 256, 0, s>>>(x, ldx, n, nrhs, xs);
     VIE_CHECK_LAUNCH();
@@ -581,7 +581,7 @@ void apply_static(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s) 
                                       " complex scratch elements needed (sum of ranks x nrhs), the static array holds " +
                                       std::to_string(kStaticScratchElems));
     float2* t = static_scratch_address(op.ctx->device);
-    const float2* fac = op.d_factors.as<float2>();
+    const float2* fac = op.fac<float2>();
     const int nc = op.n_cta;
     const int64_t n = op.n();
     // every element of t[0, t_total * nrhs) is written by phase 1 before phase 2

@@ -257,7 +257,7 @@ void apply_far_bf16x3(Op& op, const float2* x, int64_t ldx, float2* F, int64_t l
     size_t need = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(float2);
     if (op.d_t.bytes < need) op.d_t.alloc(need);
     const size_t sm = 2 * sizeof(Planes);  // 40 KiB
-    const float2* fac = op.d_factors.as<float2>();
+    const float2* fac = op.fac<float2>();
     if (op.n_t1_items > 0) {
         p1_tc_kernel<<<op.n_cta_tc, kThreads, sm, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
                                                        op.d_t1_items.as<int4>(), op.d_t1_cta.as<int>(), fac, x, ldx,

@@ -288,10 +288,24 @@ __device__ __forceinline__ void a_seg(int s, int& row, int& q) {  // s in [0, 51
 }
 
 struct Ctl {
-    uint64_t mbar[2];
+    uint64_t mbar[2];  // MMAs of the stage in buffer b done
+    uint64_t tma[2];   // packed variant: A of the stage in buffer b landed
     uint32_t tmem;
     int ok;
 };
+
+constexpr int kStageChunksA = 4 * kChunksA;      // 16-byte chunks of one packed A stage (2048)
+constexpr uint32_t kStageBytesA = kStageChunksA * 16;  // 32 KiB
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+// bulk copy global -> shared memory, completion counted on the mbarrier
+__device__ __forceinline__ void tma_bulk(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
 
 // One output tile (rows x ncol) over K = nK: stages g0, g0+1, ... of this CTA.
 // Returns false when a wait gave up.  On return every thread may read the
@@ -342,6 +356,65 @@ __device__ bool run_tile(const Src& src, Stage* stages, Ctl& ctl, uint32_t& g, i
     return true;
 }
 
+// The packed variant: the A operand of every stage is already split into bf16
+// planes in the stage layout (packA, 32 KiB per stage), so one thread moves
+// it with a bulk copy, one stage ahead, while the warps split only B.
+// `alive` (thread 0's) turns false when a wait gave up.
+__device__ __forceinline__ void issue_a(Ctl& ctl, Stage* stages, uint32_t g, const uint4* src) {
+    const uint32_t mb = smem_u32(&ctl.tma[g & 1]);
+    mbar_expect_tx(mb, kStageBytesA);
+    tma_bulk(smem_u32(&stages[g & 1].a[0][0]), src, kStageBytesA, mb);
+}
+
+template <class Src>
+__device__ bool run_tile_tma(const Src& src, const uint4* packA, Stage* stages, Ctl& ctl, uint32_t& g, int nK,
+                             int nmma, bool& alive) {
+    const int tid = threadIdx.x;
+    const int nst = (nK + kKS - 1) / kKS;
+    for (int st = 0; st < nst; ++st, ++g) {
+        Stage& S = stages[g & 1];
+        float2 vb[8];
+        src.load_b(tid >> 2, tid & 3, st * kKS, vb);
+        if (tid == 0) {
+            // a buffer is free once the MMAs issued two stages before it are done
+            if (st == 0 && alive) {
+                if (g >= 2) alive = mbar_wait(smem_u32(&ctl.mbar[g & 1]), ((g >> 1) - 1) & 1);
+                if (alive) issue_a(ctl, stages, g, packA);
+            }
+            if (st + 1 < nst && alive) {
+                const uint32_t g1 = g + 1;
+                if (g1 >= 2) alive = mbar_wait(smem_u32(&ctl.mbar[g1 & 1]), ((g1 >> 1) - 1) & 1);
+                if (alive) issue_a(ctl, stages, g1, packA + (int64_t)(st + 1) * kStageChunksA);
+            }
+            ctl.ok = alive ? 1 : 0;
+        }
+        __syncthreads();
+        if (!ctl.ok) return false;
+        put8<kChunksB>(S.b, (tid & 3) * kN + (tid >> 2), vb);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && alive) {
+            alive = mbar_wait(smem_u32(&ctl.tma[g & 1]), (g >> 1) & 1);
+            if (alive) {
+                fence_after();
+                issue_stage(S, ctl.tmem, nmma, st == 0);
+                umma_commit(smem_u32(&ctl.mbar[g & 1]));
+            }
+        }
+    }
+    if (nst > 0) {
+        const uint32_t gl = g - 1;
+        if (tid == 0) {
+            if (alive) alive = mbar_wait(smem_u32(&ctl.mbar[gl & 1]), (gl >> 1) & 1);
+            ctl.ok = alive ? 1 : 0;
+        }
+        __syncthreads();
+        if (!ctl.ok) return false;
+        fence_after();
+    }
+    return true;
+}
+
 // out[rowidx(r) + c * ld] = (D_r, D_i)[r, c] for r < rows, c < ncol (zeros when nK == 0).
 // A warp reads the tensor-memory lanes of its quarter (warp % 4); warps 0-3
 // take columns 0-31, warps 4-7 columns 32-63.
@@ -377,6 +450,8 @@ __device__ void setup(Ctl& ctl) {
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(&ctl.mbar[0]));
         mbar_init(smem_u32(&ctl.mbar[1]));
+        mbar_init(smem_u32(&ctl.tma[0]));
+        mbar_init(smem_u32(&ctl.tma[1]));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if ((threadIdx.x >> 5) == 0) {
@@ -471,6 +546,120 @@ __global__ void __launch_bounds__(kThr) u2_kernel(const int4* __restrict__ items
     teardown(ctl, failed, g, err);
 }
 
+// ---- packed variant ---------------------------------------------------------
+// pack: one CTA per work item writes the item's A operand, stage after stage,
+// in the shared-memory stage layout (zero padding past the last row / K value)
+__global__ void __launch_bounds__(kThr) pack1_kernel(const FarBlockDev* __restrict__ blocks,
+                                                     const int4* __restrict__ items, const long long* __restrict__ pk,
+                                                     const long long* __restrict__ rowoff,
+                                                     const float2* __restrict__ fac, int np, uint4* __restrict__ out) {
+    const int4 item = items[blockIdx.x];
+    const FarBlockDev B = blocks[item.x];
+    const Phase1 src{fac, rowoff, nullptr, nullptr, nullptr, 0, np, B.n, item.y, item.z, 0, 0};
+    const int nst = (B.n + kKS - 1) / kKS;
+    uint4* base = out + pk[blockIdx.x] * kStageChunksA;
+    for (int st = 0; st < nst; ++st) {
+        uint4(*planes)[kChunksA] = reinterpret_cast<uint4(*)[kChunksA]>(base + (int64_t)st * kStageChunksA);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            int row, q;
+            a_seg<false>(threadIdx.x + i * kThr, row, q);
+            float2 v[8];
+            src.load_a(row, q, st * kKS, v);
+            put8<kChunksA>(planes, q * kM + row, v);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThr) pack2_kernel(const int4* __restrict__ items, const long long* __restrict__ pk,
+                                                     const long long* __restrict__ qoff,
+                                                     const long long* __restrict__ kptr,
+                                                     const float2* __restrict__ fac, uint4* __restrict__ out) {
+    const int4 item = items[blockIdx.x];
+    const int a = item.x;
+    const long long kb = kptr[a];
+    const int nK = (int)(kptr[a + 1] - kb);
+    const Phase2 src{fac, qoff, nullptr, nullptr, 0, kb, nK, item.y, item.z - item.y, 0, 0};
+    const int nst = (nK + kKS - 1) / kKS;
+    uint4* base = out + pk[blockIdx.x] * kStageChunksA;
+    for (int st = 0; st < nst; ++st) {
+        uint4(*planes)[kChunksA] = reinterpret_cast<uint4(*)[kChunksA]>(base + (int64_t)st * kStageChunksA);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            int row, q;
+            a_seg<true>(threadIdx.x + i * kThr, row, q);
+            float2 v[8];
+            src.load_a(row, q, st * kKS, v);
+            put8<kChunksA>(planes, q * kM + row, v);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThr) u1p_kernel(const FarBlockDev* __restrict__ blocks,
+                                                   const int* __restrict__ batoms, const int4* __restrict__ items,
+                                                   const int* __restrict__ cta_ptr, const long long* __restrict__ pk,
+                                                   const uint4* __restrict__ pack, const int* __restrict__ rowt,
+                                                   const float2* __restrict__ x, int64_t ldx, int np,
+                                                   float2* __restrict__ t, int64_t ldt, int nrhs,
+                                                   const int2* __restrict__ colr, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    Stage* stages = reinterpret_cast<Stage*>(smem);
+    __shared__ Ctl ctl;
+    setup(ctl);
+    uint32_t g = 0;
+    bool failed = false, alive = true;
+    for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1] && !failed; ++it) {
+        const int4 item = items[it];
+        const FarBlockDev B = blocks[item.x];
+        const int2 cr = colr ? colr[item.w] : make_int2(0, nrhs);
+        for (int c0 = cr.x; c0 < cr.y && !failed; c0 += kN) {
+            Phase1 src{nullptr, nullptr, rowt, batoms + B.s_off, x, ldx, np, B.n, item.y, item.z, c0,
+                       min(kN, cr.y - c0)};
+            const int nmma = max(16, (src.ncol + 15) / 16 * 16);
+            if (!run_tile_tma(src, pack + pk[it] * kStageChunksA, stages, ctl, g, B.n, nmma, alive)) {
+                failed = true;
+                break;
+            }
+            const int* rt = rowt + item.y;
+            epilogue(ctl, B.n > 0, item.z, src.ncol, [rt](int r) { return (int64_t)rt[r]; }, t + (int64_t)c0 * ldt,
+                     ldt);
+        }
+    }
+    teardown(ctl, failed, g, err);
+}
+
+__global__ void __launch_bounds__(kThr) u2p_kernel(const int4* __restrict__ items, const int* __restrict__ cta_ptr,
+                                                   const long long* __restrict__ pk, const uint4* __restrict__ pack,
+                                                   const int* __restrict__ tidx, const long long* __restrict__ kptr,
+                                                   const float2* __restrict__ t, int64_t ldt, int np,
+                                                   float2* __restrict__ F, int64_t ldf, int nrhs,
+                                                   const int2* __restrict__ colr, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    Stage* stages = reinterpret_cast<Stage*>(smem);
+    __shared__ Ctl ctl;
+    setup(ctl);
+    uint32_t g = 0;
+    bool failed = false, alive = true;
+    for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1] && !failed; ++it) {
+        const int4 item = items[it];
+        const int a = item.x, p0 = item.y, rows = item.z - item.y;
+        const long long kb = kptr[a];
+        const int nK = (int)(kptr[a + 1] - kb);
+        const int2 cr = colr ? colr[item.w] : make_int2(0, nrhs);
+        for (int c0 = cr.x; c0 < cr.y && !failed; c0 += kN) {
+            Phase2 src{nullptr, nullptr, tidx, t, ldt, kb, nK, p0, rows, c0, min(kN, cr.y - c0)};
+            const int nmma = max(16, (src.ncol + 15) / 16 * 16);
+            if (!run_tile_tma(src, pack + pk[it] * kStageChunksA, stages, ctl, g, nK, nmma, alive)) {
+                failed = true;
+                break;
+            }
+            const int64_t rb = (int64_t)a * np + p0;
+            epilogue(ctl, nK > 0, rows, src.ncol, [rb](int r) { return rb + r; }, F + (int64_t)c0 * ldf, ldf);
+        }
+    }
+    teardown(ctl, failed, g, err);
+}
+
 std::once_flag g_umma_attr_once;
 
 }  // namespace
@@ -481,6 +670,8 @@ void umma_prepare(Op& op, cudaStream_t s) {
     std::call_once(g_umma_attr_once, [] {
         cudaFuncSetAttribute(u1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         cudaFuncSetAttribute(u2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        cudaFuncSetAttribute(u1p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        cudaFuncSetAttribute(u2p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     });
     if (!op.d_err.p) {
         op.d_err.alloc(sizeof(int));
@@ -493,7 +684,7 @@ void apply_far_umma(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf
     if (((uintptr_t)x & 15) || (ldx & 1)) fail(VIE_ERR_INVALID_ARG, "tensor-core apply: x must be 16-byte aligned");
     const size_t need = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(float2);
     if (op.d_t.bytes < need) op.d_t.alloc(need);
-    const float2* fac = op.d_factors.as<float2>();
+    const float2* fac = op.fac<float2>();
     if (op.n_u1_items > 0) {
         u1_kernel<<<op.n_cta_u, kThr, kSmemBytes, s>>>(
             op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(), op.d_u1_items.as<int4>(), op.d_u1_cta.as<int>(),
@@ -505,6 +696,59 @@ void apply_far_umma(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf
         op.d_u2_items.as<int4>(), op.d_u2_cta.as<int>(), op.d_u2_qoff.as<long long>(), op.d_u2_tidx.as<int>(),
         op.d_u2_kptr.as<long long>(), fac, op.d_t.as<float2>(), op.t_total, op.np, F, ldf, nrhs, op.colr,
         op.d_err.as<int>());
+    VIE_CHECK_LAUNCH();
+}
+
+size_t umma_pack_bytes(const Op& op) { return (size_t)(op.u1_stages + op.u2_stages) * kStageBytesA; }
+
+bool umma_pack(Op& op, cudaStream_t s) {
+    umma_prepare(op, s);
+    if (op.umma_packed) return true;
+    if (op.umma_pack_failed) return false;
+    const size_t b1 = (size_t)op.u1_stages * kStageBytesA, b2 = (size_t)op.u2_stages * kStageBytesA;
+    size_t free_b = 0, total_b = 0;
+    VIE_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    if (b1 + b2 + ((size_t)1 << 30) > free_b) {  // keep 1 GiB for the solver
+        op.umma_pack_failed = true;
+        return false;
+    }
+    op.d_u1_pack.alloc(std::max<size_t>(b1, 16));
+    op.d_u2_pack.alloc(std::max<size_t>(b2, 16));
+    if (op.n_u1_items > 0) {
+        pack1_kernel<<<op.n_u1_items, kThr, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_u1_items.as<int4>(),
+                                                    op.d_u1_pk.as<long long>(), op.d_u1_rowoff.as<long long>(),
+                                                    op.fac<float2>(), op.np, op.d_u1_pack.as<uint4>());
+        VIE_CHECK_LAUNCH();
+    }
+    if (op.n_u2_items > 0) {
+        pack2_kernel<<<op.n_u2_items, kThr, 0, s>>>(op.d_u2_items.as<int4>(), op.d_u2_pk.as<long long>(),
+                                                    op.d_u2_qoff.as<long long>(), op.d_u2_kptr.as<long long>(),
+                                                    op.fac<float2>(), op.d_u2_pack.as<uint4>());
+        VIE_CHECK_LAUNCH();
+    }
+    op.umma_packed = true;
+    return true;
+}
+
+void apply_far_umma_packed(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s) {
+    if (!umma_pack(op, s)) {  // not enough memory for the packed planes: the kernel that splits A itself
+        apply_far_umma(op, x, ldx, F, ldf, nrhs, s);
+        return;
+    }
+    if (((uintptr_t)x & 15) || (ldx & 1)) fail(VIE_ERR_INVALID_ARG, "tensor-core apply: x must be 16-byte aligned");
+    const size_t need = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(float2);
+    if (op.d_t.bytes < need) op.d_t.alloc(need);
+    if (op.n_u1_items > 0) {
+        u1p_kernel<<<op.n_cta_u, kThr, kSmemBytes, s>>>(
+            op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(), op.d_u1_items.as<int4>(), op.d_u1_cta.as<int>(),
+            op.d_u1_pk.as<long long>(), op.d_u1_pack.as<uint4>(), op.d_u1_rowt.as<int>(), x, ldx, op.np,
+            op.d_t.as<float2>(), op.t_total, nrhs, op.colr, op.d_err.as<int>());
+        VIE_CHECK_LAUNCH();
+    }
+    u2p_kernel<<<op.n_cta_u, kThr, kSmemBytes, s>>>(
+        op.d_u2_items.as<int4>(), op.d_u2_cta.as<int>(), op.d_u2_pk.as<long long>(), op.d_u2_pack.as<uint4>(),
+        op.d_u2_tidx.as<int>(), op.d_u2_kptr.as<long long>(), op.d_t.as<float2>(), op.t_total, op.np, F, ldf, nrhs,
+        op.colr, op.d_err.as<int>());
     VIE_CHECK_LAUNCH();
 }
 

@@ -10,6 +10,8 @@
 // kernel over the work items of all problems, balanced across the CTAs by
 // the greedy least-loaded rule of App. C, and each Arnoldi step of the
 // lockstep solve (one CUDA graph per restart cycle) serves every problem.
+// The joined operator reads each problem's factors in place (no copy); only
+// the small self blocks are concatenated.
 // Each item and each self-block product only touches the right-hand sides
 // of its own problem (a per-problem column range), and each Krylov vector
 // only the rows of its problem.
@@ -53,12 +55,18 @@ std::unique_ptr<Op> make_union(const std::vector<Op*>& ops) {
     U->fprec = VIE_C64;
     U->nprob = (int)ops.size();
     const int np = o0.np;
-    std::vector<const DevBuf*> fac, z64, i64, z32, i32;
-    std::vector<size_t> fb, b64, b32;
-    int64_t fac_off = 0;  // complex float32 elements
+    std::vector<const DevBuf*> z64, i64, z32, i32;
+    std::vector<size_t> b64, b32;
+    // the factors stay where they are: offsets from the lowest buffer address
+    // (cudaMalloc returns 256-byte aligned addresses, so the distances are
+    // whole complex float32 elements)
+    const char* base = static_cast<const char*>(o0.d_factors.p);
+    for (Op* p : ops) base = std::min(base, static_cast<const char*>(p->d_factors.p));
+    U->factors_view = base;
     int atom_off = 0, type_off = 0, batom_off = 0, block_off = 0;
     for (int p = 0; p < (int)ops.size(); ++p) {
         const Op& P = *ops[p];
+        const int64_t fac_off = (int64_t)((static_cast<const char*>(P.d_factors.p) - base) / sizeof(float2));
         U->L = std::max(U->L, P.L);
         U->tol = std::max(U->tol, P.tol);
         for (int a = 0; a < P.N; ++a) {
@@ -78,9 +86,6 @@ std::unique_ptr<Op> make_union(const std::vector<Op*>& ops) {
             U->block_prob.push_back(p);
         }
         U->factor_entries += P.factor_entries;
-        fac.push_back(&P.d_factors);
-        fb.push_back(P.d_factors.bytes);
-        fac_off += (int64_t)(P.d_factors.bytes / sizeof(float2));
         const size_t e = (size_t)P.T * np * np;
         z64.push_back(&P.d_zself64);
         i64.push_back(&P.d_inv64);
@@ -95,7 +100,6 @@ std::unique_ptr<Op> make_union(const std::vector<Op*>& ops) {
     }
     U->N = atom_off;
     U->T = type_off;
-    copy_concat(U->d_factors, fac, fb, s);
     copy_concat(U->d_zself64, z64, b64, s);
     copy_concat(U->d_inv64, i64, b64, s);
     copy_concat(U->d_zself32, z32, b32, s);

@@ -152,6 +152,12 @@ struct Op {
     int fprec = 0;
     double tol = 0;
     DevBuf d_factors;
+    // a batched operator does not copy its problems' factors: its block offsets
+    // are relative to this base address (the lowest of their buffers)
+    const void* factors_view = nullptr;
+    template <class T> const T* fac() const {
+        return static_cast<const T*>(factors_view ? factors_view : d_factors.p);
+    }
     int64_t factor_entries = 0;
     int64_t t_total = 0;               // sum of ranks
     // apply work lists (device)
@@ -168,6 +174,11 @@ struct Op {
     bool umma_ready = false;
     DevBuf d_u1_rowoff, d_u1_rowt, d_u1_items, d_u1_cta;
     DevBuf d_u2_qoff, d_u2_tidx, d_u2_kptr, d_u2_items, d_u2_cta;
+    // packed variant: each item's A operand pre-split into bf16 planes in the
+    // shared-memory stage layout (32 KiB per 32-wide K stage), copied by bulk TMA
+    DevBuf d_u1_pk, d_u2_pk, d_u1_pack, d_u2_pack;  // stage offsets per item, planes
+    long long u1_stages = 0, u2_stages = 0;
+    bool umma_packed = false, umma_pack_failed = false;
     int n_u1_items = 0, n_u2_items = 0, n_cta_u = 0;
     DevBuf d_err;  // set by a tensor-core kernel whose bounded wait gave up
     // batched operators (several problems as one block-diagonal operator,
@@ -266,6 +277,12 @@ void build_umma_lists(Op& op);
 void apply_far_umma(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
 // everything the tcgen05 apply allocates or configures, done ahead of graph capture
 void umma_prepare(Op& op, cudaStream_t s);
+// packed tcgen05 variant: split the factors once into bf16 planes in the stage
+// layout (false when the free memory cannot hold them); the apply runs the
+// unpacked kernel when packing is not possible
+bool umma_pack(Op& op, cudaStream_t s);
+size_t umma_pack_bytes(const Op& op);
+void apply_far_umma_packed(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
 // far part with c64 factors and c128 vectors in double-float arithmetic
 void apply_far_df(Op& op, const double2* x, int64_t ldx, double2* F, int64_t ldf, int nrhs, cudaStream_t s);
 // apply_tc.cu: several right-hand sides on the tensor cores (BF16x3)

@@ -406,6 +406,23 @@ void build_umma_lists(Op& op) {
     upload(op.d_u2_kptr, kptr);
     upload(op.d_u2_items, q2.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : q2);
     upload(op.d_u2_cta, e2);
+    // packed variant: every item's A operand as whole 32-wide K stages, item
+    // after item in work-list order; offsets in stages
+    auto stage_offsets = [](const std::vector<int4>& items, auto nk_of, std::vector<long long>& off) {
+        off.assign(items.size() + 1, 0);
+        for (size_t i = 0; i < items.size(); ++i) off[i + 1] = off[i] + (nk_of(items[i]) + 31) / 32;
+    };
+    std::vector<long long> pk1, pk2;
+    stage_offsets(q1, [&](const int4& it) { return (long long)op.blocks[it.x].n; }, pk1);
+    stage_offsets(q2, [&](const int4& it) { return kptr[it.x + 1] - kptr[it.x]; }, pk2);
+    op.u1_stages = pk1.back();
+    op.u2_stages = pk2.back();
+    upload(op.d_u1_pk, pk1);
+    upload(op.d_u2_pk, pk2);
+    op.umma_packed = false;
+    op.umma_pack_failed = false;
+    op.d_u1_pack.release();
+    op.d_u2_pack.release();
     op.umma_ready = true;
 }
 

@@ -271,6 +271,16 @@ __global__ void k_givens(KrylovArgs a, int k, int nblk, cudaGraphConditionalHand
     __shared__ double se[1024];
     se[i] = est;
     const int any = __syncthreads_or(cyc ? 1 : 0);
+    if (a.colr && i < k) {
+        // the first slot of each problem retires the problem once none of its slots iterates
+        const int p = a.col_prob[a.cols[i]];
+        const int2 r = a.colr_cycle[p];
+        if (i == r.x) {
+            int live = 0;
+            for (int t = r.x; t < r.y; ++t) live |= a.cycling[t];
+            if (!live) a.colr[p] = make_int2(0, 0);
+        }
+    }
     if (i == 0) {
         double mx = 0.0;
         for (int t = 0; t < (int)blockDim.x; ++t) mx = fmax(mx, se[t]);

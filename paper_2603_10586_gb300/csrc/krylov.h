@@ -53,6 +53,13 @@ struct KrylovArgs {
     double* rnorm;    // [nrhs] ||b - Zs x|| at the latest refinement
     double* hist;     // [512] largest estimated residual per lockstep iteration
     int* ctr;         // [KR_NCTR]
+    // batched operators only (null otherwise): problem of every column, the
+    // cycle's slot range of every problem, and the table the apply kernels read,
+    // in which a problem whose right-hand sides have all stopped iterating in
+    // this cycle gets an empty range (its work items are skipped)
+    const int* col_prob;
+    const int2* colr_cycle;
+    int2* colr;
 };
 
 // launch shapes: row blocks of the (rows, slot) kernels and row chunks of the

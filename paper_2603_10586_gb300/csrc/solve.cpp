@@ -48,7 +48,7 @@ struct Gmres {
     int m, nrhs, n_sm;
     bool c64;  // inner applies on float32 vectors
     DevBuf V, H, g, cs, sn, h, y, part, npart, nsq, rpart, inv, cycling, jdone, cols, iters, done, beta0, beta, res, rnorm,
-        bnorm, hist, ctr, col_lo, col_len, col_voff, colr;
+        bnorm, hist, ctr, col_lo, col_len, col_voff, colr, colr_cycle, col_prob;
     std::vector<int2> h_colr;
     DevBuf Xg, Yg, Xl, T, Rl, Wl, W;
     KrylovArgs a{};
@@ -75,6 +75,8 @@ struct Gmres {
         upload(col_voff, voff);
         if (lay.nprob > 1) {
             colr.alloc(lay.nprob * sizeof(int2));
+            colr_cycle.alloc(lay.nprob * sizeof(int2));
+            upload(col_prob, lay.prob);
             h_colr.assign(lay.nprob, make_int2(0, 0));
         }
         H.alloc((size_t)S * m * (m + 1) * sizeof(double2));
@@ -115,6 +117,9 @@ struct Gmres {
         a.col_lo = col_lo.as<long long>();
         a.col_len = col_len.as<long long>();
         a.col_voff = col_voff.as<long long>();
+        a.col_prob = lay.nprob > 1 ? col_prob.as<int>() : nullptr;
+        a.colr_cycle = lay.nprob > 1 ? colr_cycle.as<int2>() : nullptr;
+        a.colr = lay.nprob > 1 ? colr.as<int2>() : nullptr;
         a.m = m;
         a.nblk_max = nblk_max;
         a.tol = o.tol > 0 ? o.tol : 1e-6;
@@ -163,7 +168,16 @@ struct Gmres {
         }
     }
 
-    void launch_pre(int k, cudaStream_t st) { kr_cycle_start(a, k, st); }
+    // the apply kernels' column table starts every cycle, and its refinement, complete
+    void restore_colr(cudaStream_t st) {
+        if (lay.nprob > 1)
+            VIE_CUDA(cudaMemcpyAsync(colr.p, colr_cycle.p, lay.nprob * sizeof(int2), cudaMemcpyDeviceToDevice, st));
+    }
+
+    void launch_pre(int k, cudaStream_t st) {
+        restore_colr(st);
+        kr_cycle_start(a, k, st);
+    }
 
     void launch_body(int k, cudaStream_t st, cudaGraphConditionalHandle hnd, int use_handle) {
         const int nblk = kr_nblk(n, k, n_sm), nchunk = kr_nchunk(n, k, m, n_sm);
@@ -177,6 +191,7 @@ struct Gmres {
     // x += V y, then the float64 refinement residual W = M^-1 (b - Zs x) of the slots' columns
     void launch_post(int k, const double2* b, double2* X, cudaStream_t st) {
         const int nblk = kr_nblk(n, k, n_sm);
+        restore_colr(st);
         kr_update(a, X, k, nblk, st);
         kr_gather_cols(a, X, Xl.as<double2>(), k, nblk, st);
         op_apply64(op, Xl.as<double2>(), T.as<double2>(), k, st);
@@ -268,6 +283,7 @@ struct Gmres {
             if (r.y == 0) r.x = i;
             r.y = i + 1;
         }
+        VIE_CUDA(cudaMemcpyAsync(colr_cycle.p, h_colr.data(), lay.nprob * sizeof(int2), cudaMemcpyHostToDevice, s));
         VIE_CUDA(cudaMemcpyAsync(colr.p, h_colr.data(), lay.nprob * sizeof(int2), cudaMemcpyHostToDevice, s));
         VIE_CUDA(cudaStreamSynchronize(s));  // h_colr is reused for the next cycle
         op.colr = colr.as<int2>();

@@ -24,7 +24,8 @@ int bucket(int nrhs) {
 
 bool admissible(int precision, int v) {
     if (v >= VIE_VAR_SIMT_R1 && v <= VIE_VAR_SIMT_R8) return true;
-    return precision == VIE_BF16X3 && (v == VIE_VAR_MMA_BF16X3 || v == VIE_VAR_TCGEN05_BF16X3);
+    return precision == VIE_BF16X3 &&
+           (v == VIE_VAR_MMA_BF16X3 || v == VIE_VAR_TCGEN05_BF16X3 || v == VIE_VAR_TCGEN05_PACKED_BF16X3);
 }
 
 int default_variant(int precision, int nrhs) {
@@ -48,6 +49,7 @@ void far32(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrh
         case VIE_VAR_SIMT_R8: apply_far_simt32(op, x, ldx, F, ldf, nrhs, 8, s); break;
         case VIE_VAR_MMA_BF16X3: apply_far_bf16x3(op, x, ldx, F, ldf, nrhs, s); break;
         case VIE_VAR_TCGEN05_BF16X3: apply_far_umma(op, x, ldx, F, ldf, nrhs, s); break;
+        case VIE_VAR_TCGEN05_PACKED_BF16X3: apply_far_umma_packed(op, x, ldx, F, ldf, nrhs, s); break;
         default: fail(VIE_ERR_STATE, "unknown far-apply variant");
     }
 }
@@ -58,7 +60,7 @@ int tune_far(Op& op, int precision, int nrhs, cudaStream_t s, std::vector<int>& 
     if (nrhs < 1 || nrhs > 1024) fail(VIE_ERR_INVALID_ARG, "vie_tune: 1 to 1024 right-hand sides");
     cand.clear();
     ms.clear();
-    for (int v = VIE_VAR_SIMT_R1; v <= VIE_VAR_TCGEN05_BF16X3; ++v) {
+    for (int v = VIE_VAR_SIMT_R1; v <= VIE_VAR_TCGEN05_PACKED_BF16X3; ++v) {
         if (!admissible(precision, v)) continue;
         if (v >= VIE_VAR_SIMT_R2 && v <= VIE_VAR_SIMT_R8 && nrhs == 1) continue;  // same as R1
         cand.push_back(v);
@@ -66,7 +68,10 @@ int tune_far(Op& op, int precision, int nrhs, cudaStream_t s, std::vector<int>& 
     const int64_t n = op.n();
     DevBuf x((size_t)n * nrhs * sizeof(float2)), F((size_t)n * nrhs * sizeof(float2));
     VIE_CUDA(cudaMemsetAsync(x.p, 0, (size_t)n * nrhs * sizeof(float2), s));
-    if (precision == VIE_BF16X3) umma_prepare(op, s);
+    if (precision == VIE_BF16X3) {
+        umma_prepare(op, s);
+        umma_pack(op, s);
+    }
     cudaEvent_t e0, e1;
     VIE_CUDA(cudaEventCreate(&e0));
     VIE_CUDA(cudaEventCreate(&e1));
