@@ -300,8 +300,9 @@ def run_multirhs(args):
 
 
 def run_batch(args):
-    """--batch: the serving mix (arrays of 8x8..48x48 cubes of 3^3 voxels, lambda ~
-    U[0.9, 1.1], eps ~ U[8, 14], 1-8 RHS; --requests problems, seed 7) solved one
+    """--batch: the serving mix (arrays of 8x8..SxS cubes of 3^3 voxels, S =
+    --batch-max-side (48), lambda ~ U[0.9, 1.1], eps ~ U[8, 14], 1-8 RHS;
+    --requests problems, seed 7) solved one
     vie_solve after another and as one vie_solve_batch (block-diagonal union, one
     persistent apply launch per phase over all problems), operators built
     beforehand.  Reports right-hand sides per second both ways, each the median of
@@ -310,7 +311,7 @@ def run_batch(args):
     from paper_2603_10586_gb300 import vie
     torch.cuda.set_device(0)
     ctx = vie.Context(0)
-    reqs = workloads.serving_stream(args.requests, seed=7, ns_range=(8, 48))
+    reqs = workloads.serving_stream(args.requests, seed=7, ns_range=(8, args.batch_max_side))
     ops = []
     for r in reqs:
         op = vie.Operator(ctx, r.geometry)
@@ -318,6 +319,7 @@ def run_batch(args):
         ops.append(op)
     nrhs = sum(len(r.khat) for r in reqs)
     out = {"metric": "batched solves/s", "unit": "solves/s", "problems": len(reqs), "nrhs": nrhs,
+           "sides": [8, args.batch_max_side],
            "sizes": [r.ns for r in reqs], "n": [op.n for op in ops], "precision": {}}
     for prec, name in ((vie.C64, "c64"), (vie.BF16X3, "bf16x3")):
         seq_t, bat_t = [], []
@@ -401,6 +403,7 @@ def main():
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--batch", action="store_true", help="sequential against batched solves of the serving mix")
     ap.add_argument("--multirhs", action="store_true", help="the 64-RHS workload against float64 single-RHS solves")
+    ap.add_argument("--batch-max-side", type=int, default=48, help="largest array side of the --batch mix")
     ap.add_argument("--fp64-sample", type=int, default=2)
     ap.add_argument("--profile", action="store_true", help="one untimed step for ncu captures")
     ap.add_argument("--profile-case", default="scale", choices=["scale", "small", "multirhs-small"])
