@@ -67,7 +67,7 @@ void op_apply_fused64(Op& op, const double2* x, double2* y, int nrhs, cudaStream
 void op_reserve(Op& op, int nrhs, int precision, cudaStream_t s) {
     if (precision == VIE_BF16X3) {
         umma_prepare(op, s);
-        if (far_variant(op, VIE_BF16X3, nrhs) == VIE_VAR_TCGEN05_PACKED_BF16X3) umma_pack(op, s);
+        umma_pack(op, s);  // any cycle's right-hand-side count may choose the packed variant
     }
     ensure_F(op, (size_t)op.n() * nrhs * sizeof(double2));
     const size_t need = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(double2);

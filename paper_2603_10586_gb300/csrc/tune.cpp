@@ -30,7 +30,7 @@ bool admissible(int precision, int v) {
 
 int default_variant(int precision, int nrhs) {
     if (nrhs == 1) return VIE_VAR_SIMT_R1;
-    if (precision == VIE_BF16X3 && nrhs >= 8) return VIE_VAR_TCGEN05_BF16X3;
+    if (precision == VIE_BF16X3 && nrhs >= 8) return VIE_VAR_TCGEN05_PACKED_BF16X3;
     return VIE_VAR_SIMT_R4;
 }
 
