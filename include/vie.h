@@ -97,6 +97,10 @@ typedef struct vie_ctx_opts {
     int device;            /* CUDA device ordinal */
     size_t hbm_budget;     /* bytes the context may allocate (0 = free memory - 4 GiB) */
     int verbose;           /* 0 quiet, 1 stage timings on stderr */
+    int no_sharing;        /* 0 (default): far blocks that are translated copies of one another
+                              (same level, same atom types, same relative atom positions, as in a
+                              periodic array of identical meta-atoms) are formed and compressed once
+                              and share their factors; 1: every far block is compressed */
 } vie_ctx_opts;
 
 /* Metasurface geometry (host memory, copied by vie_assemble).
@@ -128,6 +132,8 @@ typedef struct vie_op_info {
     double tol;                /* compression tolerance */
     int64_t apply_bytes;       /* algorithmic bytes of one single-RHS c64 apply */
     double t_assemble_s, t_compress_s;
+    int64_t stored_entries;    /* factor entries held in memory: translated copies of a far block
+                                  share one set of factors (see vie_ctx_opts.no_sharing) */
 } vie_op_info;
 
 /* Plane-wave incident fields E0 = p exp(-j k khat . r), one per right-hand side. */

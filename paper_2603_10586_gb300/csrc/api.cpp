@@ -122,6 +122,7 @@ int vie_create(vie_ctx** out, const vie_ctx_opts* opts) {
         c.owner = ctx.get();
         c.device = opts ? opts->device : 0;
         c.verbose = opts ? opts->verbose : 0;
+        c.no_sharing = opts ? opts->no_sharing : 0;
         int ndev = 0;
         VIE_CUDA(cudaGetDeviceCount(&ndev));
         if (c.device < 0 || c.device >= ndev) fail(VIE_ERR_INVALID_ARG, "no such CUDA device");
@@ -335,6 +336,7 @@ int vie_op_get_info(const vie_op* op, vie_op_info* info) {
     info->apply_bytes = 8 * (o.factor_entries + (int64_t)o.T * o.np * o.np + 2 * o.n());
     info->t_assemble_s = o.t_assemble;
     info->t_compress_s = o.t_compress;
+    info->stored_entries = o.stored_entries;
     return VIE_OK;
 }
 

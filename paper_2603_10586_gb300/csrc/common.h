@@ -158,7 +158,8 @@ struct Op {
     template <class T> const T* fac() const {
         return static_cast<const T*>(factors_view ? factors_view : d_factors.p);
     }
-    int64_t factor_entries = 0;
+    int64_t factor_entries = 0;         // sum over far blocks of (m + n) r (what an apply multiplies)
+    int64_t stored_entries = 0;         // of those, held in memory (translated copies share storage)
     int64_t t_total = 0;               // sum of ranks
     // apply work lists (device)
     DevBuf d_blocks;                   // FarBlockDev[nb]
@@ -206,6 +207,7 @@ struct Ctx {
     std::string err;
     size_t budget = 0;
     int verbose = 0;
+    int no_sharing = 0;
     void* owner = nullptr;  // the C-ABI handle holding this context
 };
 

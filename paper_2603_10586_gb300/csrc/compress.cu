@@ -583,15 +583,59 @@ struct Compressor {
         }
     }
 
+    // Translated copies: two far blocks with the same level, the same atom
+    // types and the same atom positions relative to their first target atom
+    // are the same matrix (the entries depend on the atoms' types and relative
+    // positions only; the copies differ by the rounding of the centres).  The
+    // first block of each such class is its representative; the others share
+    // its factors.  Classes are keyed on the displacements quantised far below
+    // any geometric scale, so only exact translates are joined.
+    std::vector<int> canon;
+    void find_classes() {
+        const size_t nb = op.blocks.size();
+        canon.resize(nb);
+        for (size_t i = 0; i < nb; ++i) canon[i] = (int)i;
+        if (op.ctx->no_sharing) return;
+        double span = 0.0;
+        for (double c : op.centres) span = std::max(span, std::abs(c));
+        const double q = 1e-9 * std::max(span, 1e-30);
+        std::map<std::vector<long long>, int> first;
+        std::vector<long long> key;
+        for (size_t i = 0; i < nb; ++i) {
+            const FarBlock& b = op.blocks[i];
+            key.clear();
+            key.push_back(b.level);
+            key.push_back(b.nt);
+            key.push_back(b.ns);
+            const int a0 = op.block_atoms[b.t_off];
+            auto add = [&](int a) {
+                key.push_back(op.types[a]);
+                for (int d = 0; d < 3; ++d)
+                    key.push_back(std::llround((op.centres[3 * a + d] - op.centres[3 * a0 + d]) / q));
+            };
+            for (int x = 0; x < b.nt; ++x) add(op.block_atoms[b.t_off + x]);
+            for (int x = 0; x < b.ns; ++x) add(op.block_atoms[b.s_off + x]);
+            auto it = first.find(key);
+            if (it == first.end()) first.emplace(key, (int)i);
+            else canon[i] = it->second;
+        }
+    }
+
     void run() {
         where.assign(op.blocks.size(), {-1, 0});
-        // group blocks by (level, m, n, box distance), coarse levels first; blocks
-        // of one class have similar ranks: one pilot block learns the rank, the
-        // rest start from a sketch of that size plus a margin
+        find_classes();
+        // Of each pair of mirror classes the one whose representative comes first
+        // is compressed; the other representative takes the transposed factors
+        // (reciprocity, below).  Representatives are grouped by (level, m, n, box
+        // distance), coarse levels first; blocks of one group have similar
+        // ranks: one pilot block learns the rank, the rest start from a sketch
+        // of that size plus a margin.
         std::map<std::tuple<int, int, int, int, int>, std::vector<int>> groups;
         for (size_t i = 0; i < op.blocks.size(); ++i) {
             auto& b = op.blocks[i];
-            b.derived = b.mirror >= 0 && b.mirror < (int)i;
+            b.derived = false;
+            if (canon[i] != (int)i) continue;  // shares its representative's factors
+            b.derived = b.mirror >= 0 && canon[b.mirror] < (int)i;
             if (b.derived) continue;
             groups[{b.level, b.m, b.n, b.dist, b.dmin}].push_back((int)i);
         }
@@ -616,16 +660,19 @@ struct Compressor {
                 batch(sub, hint);
             }
         }
-        // consolidate into one factor store (mirrors take their partner's rank)
+        // consolidate into one factor store: derived representatives take their
+        // mirror class's rank, shared blocks their representative's rank and storage
         op.factor_entries = 0;
+        op.stored_entries = 0;
         for (size_t i = 0; i < op.blocks.size(); ++i) {
             auto& b = op.blocks[i];
-            if (b.derived) b.rank = op.blocks[b.mirror].rank;
+            if (b.derived) b.rank = op.blocks[canon[b.mirror]].rank;
         }
         int64_t total = 0;
         std::vector<int64_t> qoff(op.blocks.size());
         for (size_t i = 0; i < op.blocks.size(); ++i) {
             auto& b = op.blocks[i];
+            if (canon[i] != (int)i) continue;
             qoff[i] = total;
             total += (int64_t)b.rank * (b.m + b.n);
             total = (total + 31) / 32 * 32;
@@ -633,9 +680,18 @@ struct Compressor {
         op.d_factors.alloc((size_t)std::max<int64_t>(total, 32) * sizeof(T2));
         for (size_t i = 0; i < op.blocks.size(); ++i) {
             auto& b = op.blocks[i];
+            if (canon[i] != (int)i) {
+                const FarBlock& c = op.blocks[canon[i]];
+                b.rank = c.rank;
+                b.q_off = c.q_off;
+                b.rh_off = c.rh_off;
+                op.factor_entries += (int64_t)b.rank * (b.m + b.n);
+                continue;
+            }
             b.q_off = qoff[i];
             b.rh_off = qoff[i] + (int64_t)b.rank * b.m;
             op.factor_entries += (int64_t)b.rank * (b.m + b.n);
+            op.stored_entries += (int64_t)b.rank * (b.m + b.n);
             if (b.rank == 0) continue;
             if (!b.derived) {
                 const T2* src = stores[where[i].first].template as<T2>() + where[i].second;
@@ -643,8 +699,9 @@ struct Compressor {
                                          (size_t)b.rank * (b.m + b.n) * sizeof(T2), cudaMemcpyDeviceToDevice, s));
             } else {
                 // mirror of block p (A' = A_p^T): Q' = conj(R_p^H), R'^H = conj(Q_p)
-                const FarBlock& p = op.blocks[b.mirror];
-                const T2* src = stores[where[b.mirror].first].template as<T2>() + where[b.mirror].second;
+                const int pi = canon[b.mirror];
+                const FarBlock& p = op.blocks[pi];
+                const T2* src = stores[where[pi].first].template as<T2>() + where[pi].second;
                 const int64_t nq = (int64_t)p.rank * p.m, nr = (int64_t)p.rank * p.n;
                 k_conj_copy<T2><<<(unsigned)std::min<int64_t>(4096, (nr + 255) / 256), 256, 0, s>>>(
                     src + nq, op.d_factors.as<T2>() + b.q_off, nr);

@@ -40,7 +40,7 @@ class VieError(RuntimeError):
 
 
 class CtxOpts(C.Structure):
-    _fields_ = [("device", C.c_int), ("hbm_budget", C.c_size_t), ("verbose", C.c_int)]
+    _fields_ = [("device", C.c_int), ("hbm_budget", C.c_size_t), ("verbose", C.c_int), ("no_sharing", C.c_int)]
 
 
 class GeometryC(C.Structure):
@@ -55,7 +55,7 @@ class OpInfo(C.Structure):
                 ("factor_entries", C.c_int64), ("self_entries", C.c_int64), ("gain", C.c_double),
                 ("rank_min", C.c_int), ("rank_max", C.c_int), ("rank_mean", C.c_double),
                 ("factor_precision", C.c_int), ("tol", C.c_double), ("apply_bytes", C.c_int64),
-                ("t_assemble_s", C.c_double), ("t_compress_s", C.c_double)]
+                ("t_assemble_s", C.c_double), ("t_compress_s", C.c_double), ("stored_entries", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -189,10 +189,10 @@ def _ip(a):
 
 
 class Context:
-    def __init__(self, device=0, hbm_budget=0, verbose=0):
+    def __init__(self, device=0, hbm_budget=0, verbose=0, no_sharing=0):
         self.L = load()
         self.h = C.c_void_p()
-        opts = CtxOpts(device, hbm_budget, verbose)
+        opts = CtxOpts(device, hbm_budget, verbose, no_sharing)
         st = self.L.vie_create(C.byref(self.h), C.byref(opts))
         if st != VIE_OK:
             raise VieError(st, "vie_create failed")

@@ -395,3 +395,43 @@ def test_tcgen05_packed_equals_unpacked(ctx):
             out[v] = Y.cpu().numpy()
         assert np.array_equal(out[vie.VAR_TCGEN05_BF16X3], out[vie.VAR_TCGEN05_PACKED_BF16X3])
     op.close()
+
+
+# ------------------------------------------------------- translated copies share
+def test_translated_blocks_share_factors(ctx, tiny_op, tiny_dense):
+    P, Z, b, kh, pol = tiny_dense
+    info = tiny_op.info()
+    # 4 x 4 array of identical cubes: 240 far blocks, 48 distinct box offsets
+    assert info["stored_entries"] * 4 < info["factor_entries"]
+    blocks = tiny_op.far_blocks()
+    for blk in blocks:  # every block, shared or not, meets its own bound
+        rows = C.atom_rows(P, blk["tatoms"])
+        cols = C.atom_rows(P, blk["satoms"])
+        Ab = Z[np.ix_(rows, cols)]
+        assert np.linalg.norm(Ab - blk["Q"] @ blk["R"]) <= 1e-4 * np.linalg.norm(Ab)
+    ctx2 = vie.Context(0, no_sharing=1)
+    g, _, _ = workloads.config("tiny")
+    op2 = vie.Operator(ctx2, g)
+    info2 = op2.compress(1e-4, vie.C64)
+    assert info2["stored_entries"] == info2["factor_entries"]
+    I2, _, s2 = op2.solve(kh[None], pol[None], tol=1e-6)
+    I1, _, s1 = tiny_op.solve(kh[None], pol[None], tol=1e-6)
+    ref = np.linalg.solve(Z, b)
+    assert s1 == s2 == vie.VIE_OK and rel(I1[:, 0], ref) <= 5e-4 and rel(I2[:, 0], ref) <= 5e-4
+    op2.close()
+    ctx2.close()
+
+
+def test_graded_array_solve(ctx):
+    # three meta-atom types: only blocks with the same types and relative
+    # positions share factors
+    g = workloads.graded_array(4, 3, seed=0)
+    P = problem_from_geometry(g)
+    Z = A.dense_matrix(P)
+    op = vie.Operator(ctx, g)
+    op.compress(1e-4, vie.C64)
+    kh, pol = workloads.normal_incidence()
+    I, st, status = op.solve(kh, pol, tol=1e-6)
+    assert status == vie.VIE_OK
+    assert rel(I[:, 0], np.linalg.solve(Z, A.rhs(P, kh[0], pol[0]))) <= 5e-4
+    op.close()
