@@ -637,7 +637,12 @@ struct Compressor {
             if (canon[i] != (int)i) continue;  // shares its representative's factors
             b.derived = b.mirror >= 0 && canon[b.mirror] < (int)i;
             if (b.derived) continue;
-            groups[{b.level, b.m, b.n, b.dist, b.dmin}].push_back((int)i);
+            // with shared copies a distance group holds one to three
+            // representatives: compress all representatives of a level and
+            // shape in one batch (their bases grow together) instead of one
+            // pilot after another
+            if (op.ctx->no_sharing) groups[{b.level, b.m, b.n, b.dist, b.dmin}].push_back((int)i);
+            else groups[{b.level, b.m, b.n, 0, 0}].push_back((int)i);
         }
         const size_t budget = std::max<size_t>((size_t)2 << 30, std::min<size_t>(op.ctx->budget / 3, (size_t)48 << 30));
         for (auto& g : groups) {
@@ -649,7 +654,7 @@ struct Compressor {
             int bs = (int)std::max<size_t>(1, std::min<size_t>(4096, budget / per));  // blocks run along grid y
             if (const char* e = std::getenv("VIE_COMPRESS_MAX_BATCH")) bs = std::max(1, std::min(bs, std::atoi(e)));
             size_t i0 = 0;
-            if (!class_rank.count(cls) && ids.size() > 1 && (size_t)m * n >= ((size_t)1 << 20)) {
+            if (op.ctx->no_sharing && !class_rank.count(cls) && ids.size() > 1 && (size_t)m * n >= ((size_t)1 << 20)) {
                 batch({ids[0]}, kChunk);  // pilot
                 i0 = 1;
             }
