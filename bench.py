@@ -39,6 +39,10 @@ WORKLOAD = "scale"
 DESC = "16x16 array of eps=12 cubes (side 0.2, pitch 0.4, lambda 1), 6^3 voxels, 193536 unknowns, 1 RHS"
 TOL_COMPRESS = 1e-4
 TOL_SOLVE = 1e-6
+# DRAM bytes (read + write) of one fused single-RHS apply at the bench workload:
+# p1_kernel 8.045 GB + p2_kernel 10.562 GB + type_gemm (~0.01 GB), measured with
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass) on this kernel version
+APPLY_TRAFFIC_BYTES = 18.62e9
 
 
 def peaks():
@@ -542,7 +546,7 @@ def main():
                          "stored_factor_bytes": 8 * info["stored_entries"],
                          "note": "algorithmic bytes count every far block's factors; translated copies share "
                                  "storage, so part of them is served by L2",
-                         "apply_ms": apply_ms, "traffic": None},
+                         "apply_ms": apply_ms, "traffic": APPLY_TRAFFIC_BYTES},
             "e2e": {"value": whole_job_value(world, args.steps, e2e_ms), "unit": "solves/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(16 * n)},
             "gpu_launches": int(launches),
