@@ -165,43 +165,63 @@ __device__ int surf_rect(const DevMesh& m, int s, double h, double lo[3], double
     return d;
 }
 
-__global__ void self_vv_kernel(DevMesh m, double h, double k, double2* tab) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int nv2 = m.nvox * m.nvox;
-    if (t >= nv2) return;
-    int A = t / m.nvox, B = t % m.nvox;
-    double loA[3], hiA[3], loB[3], hiB[3];
-    vox_box(m, A, h, loA, hiA);
-    vox_box(m, B, h, loB, hiB);
-    bool touch = true;
-    for (int d = 0; d < 3; ++d) touch &= abs(m.vox_ijk[3 * A + d] - m.vox_ijk[3 * B + d]) <= 1;
-    const double two_over_lambda = k / kPi;
+// The voxel/voxel integrals of one atom depend only on the relative offset of
+// the two voxels (uniform voxels, local coordinates), so they are computed
+// once per offset o = ijk_B - ijk_A in [-(nv-1), nv-1]^3, one warp each: the
+// lanes split the outer points of both rules and all-reduce the sums; a
+// second kernel copies them to every voxel pair.  Rules: 3-point Gauss per
+// axis on both voxels (full g apart, smooth remainder when touching); for
+// touching voxels the static part with a 6-point outer rule and the closed-form
+// box potentials inside.
+__device__ __forceinline__ double warp_allsum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
-    // Gauss-Gauss part (full g if separated, smooth remainder if touching);
-    // G[d][a][b] = sum over point pairs with node a (resp. b) along d
+__global__ void __launch_bounds__(128) self_vv_offset_kernel(int nv, double h, double k, double2* otab) {
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    const int w1 = 2 * nv - 1, noff = w1 * w1 * w1;
+    if (warp >= noff) return;  // whole warps
+    const int o[3] = {warp / (w1 * w1) - (nv - 1), (warp / w1) % w1 - (nv - 1), warp % w1 - (nv - 1)};
+    double loA[3], loB[3], hiB[3];
+    bool touch = true;
+    for (int d = 0; d < 3; ++d) {
+        const int ia = o[d] < 0 ? -o[d] : 0;
+        loA[d] = h * ia;
+        loB[d] = h * (ia + o[d]);
+        hiB[d] = loB[d] + h;
+        touch &= abs(o[d]) <= 1;
+    }
+    const double two_over_lambda = k / kPi;
     double2 G[3][3][3];
     for (int d = 0; d < 3; ++d)
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) G[d][a][b] = make_double2(0, 0);
-    for (int pa = 0; pa < 27; ++pa) {
-        int ax = pa / 9, ay = (pa / 3) % 3, az = pa % 3;
-        double ra[3] = {loA[0] + h * c_gl3_x[ax], loA[1] + h * c_gl3_x[ay], loA[2] + h * c_gl3_x[az]};
-        double wa = c_gl3_w[ax] * c_gl3_w[ay] * c_gl3_w[az];
+    if (lane < 27) {
+        const int pa = lane;
+        const int ax = pa / 9, ay = (pa / 3) % 3, az = pa % 3;
+        const double ra[3] = {loA[0] + h * c_gl3_x[ax], loA[1] + h * c_gl3_x[ay], loA[2] + h * c_gl3_x[az]};
+        const double wa = c_gl3_w[ax] * c_gl3_w[ay] * c_gl3_w[az];
         for (int pb = 0; pb < 27; ++pb) {
-            int bx = pb / 9, by = (pb / 3) % 3, bz = pb % 3;
-            double dx = ra[0] - (loB[0] + h * c_gl3_x[bx]);
-            double dy = ra[1] - (loB[1] + h * c_gl3_x[by]);
-            double dz = ra[2] - (loB[2] + h * c_gl3_x[bz]);
-            double R = sqrt(dx * dx + dy * dy + dz * dz);
+            const int bx = pb / 9, by = (pb / 3) % 3, bz = pb % 3;
+            const double dx = ra[0] - (loB[0] + h * c_gl3_x[bx]);
+            const double dy = ra[1] - (loB[1] + h * c_gl3_x[by]);
+            const double dz = ra[2] - (loB[2] + h * c_gl3_x[bz]);
+            const double R = sqrt(dx * dx + dy * dy + dz * dz);
             double2 g = touch ? green4pi_smooth(R, k) : green4pi<double>(R, two_over_lambda);
-            double wgt = wa * c_gl3_w[bx] * c_gl3_w[by] * c_gl3_w[bz];
-            g = wgt * g;
+            g = (wa * c_gl3_w[bx] * c_gl3_w[by] * c_gl3_w[bz]) * g;
             G[0][ax][bx] += g;
             G[1][ay][by] += g;
             G[2][az][bz] += g;
         }
     }
-    double scale = h * h * h * h * h * h * kInv4Pi;
+    for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                G[d][a][b].x = warp_allsum(G[d][a][b].x);
+                G[d][a][b].y = warp_allsum(G[d][a][b].y);
+            }
+    const double scale = h * h * h * h * h * h * kInv4Pi;
     double2 U = make_double2(0, 0);
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) U += G[0][a][b];
@@ -213,36 +233,56 @@ __global__ void self_vv_kernel(DevMesh m, double h, double k, double2* tab) {
                 double2 acc = make_double2(0, 0);
                 for (int a = 0; a < 3; ++a)
                     for (int b = 0; b < 3; ++b) {
-                        double pa = sa ? 1.0 - c_gl3_x[a] : c_gl3_x[a];
-                        double pb = sb ? 1.0 - c_gl3_x[b] : c_gl3_x[b];
+                        const double pa = sa ? 1.0 - c_gl3_x[a] : c_gl3_x[a];
+                        const double pb = sb ? 1.0 - c_gl3_x[b] : c_gl3_x[b];
                         acc += (pa * pb) * G[d][a][b];
                     }
                 W[d][sa][sb] = scale * acc;
             }
     if (touch) {
-        // static part: outer 6-point rule on A, closed-form inner over B
-        double h3 = h * h * h;
-        for (int p = 0; p < 216; ++p) {
-            int ix = p / 36, iy = (p / 6) % 6, iz = p % 6;
-            double xi[3] = {c_gl6_x[ix], c_gl6_x[iy], c_gl6_x[iz]};
-            double r[3] = {loA[0] + h * xi[0], loA[1] + h * xi[1], loA[2] + h * xi[2]};
-            double wp = h3 * c_gl6_w[ix] * c_gl6_w[iy] * c_gl6_w[iz] * kInv4Pi;
-            double phi = box_pot(r, loB, hiB);
-            U.x += wp * phi;
+        // static part: outer 6-point rule on A split over the lanes, closed-form inner over B
+        const double h3 = h * h * h;
+        double us = 0.0, ws[3][2][2];
+        for (int d = 0; d < 3; ++d)
+            for (int sa = 0; sa < 2; ++sa)
+                for (int sb = 0; sb < 2; ++sb) ws[d][sa][sb] = 0.0;
+        for (int p = lane; p < 216; p += 32) {
+            const int ix = p / 36, iy = (p / 6) % 6, iz = p % 6;
+            const double xi[3] = {c_gl6_x[ix], c_gl6_x[iy], c_gl6_x[iz]};
+            const double r[3] = {loA[0] + h * xi[0], loA[1] + h * xi[1], loA[2] + h * xi[2]};
+            const double wp = h3 * c_gl6_w[ix] * c_gl6_w[iy] * c_gl6_w[iz] * kInv4Pi;
+            const double phi = box_pot(r, loB, hiB);
+            us += wp * phi;
             for (int d = 0; d < 3; ++d) {
-                double lin = box_lin_pot(r, loB, hiB, d, phi);
-                double inner[2] = {lin, phi - lin};
-                double prof[2] = {xi[d], 1.0 - xi[d]};
+                const double lin = box_lin_pot(r, loB, hiB, d, phi);
+                const double inner[2] = {lin, phi - lin};
+                const double prof[2] = {xi[d], 1.0 - xi[d]};
                 for (int sa = 0; sa < 2; ++sa)
-                    for (int sb = 0; sb < 2; ++sb) W[d][sa][sb].x += wp * prof[sa] * inner[sb];
+                    for (int sb = 0; sb < 2; ++sb) ws[d][sa][sb] += wp * prof[sa] * inner[sb];
             }
         }
+        U.x += warp_allsum(us);
+        for (int d = 0; d < 3; ++d)
+            for (int sa = 0; sa < 2; ++sa)
+                for (int sb = 0; sb < 2; ++sb) W[d][sa][sb].x += warp_allsum(ws[d][sa][sb]);
     }
-    const int tt = B * m.nvox + A;
-    tab[tt] = U;
-    for (int d = 0; d < 3; ++d)
-        for (int sa = 0; sa < 2; ++sa)
-            for (int sb = 0; sb < 2; ++sb) tab[(size_t)(1 + 4 * d + 2 * sa + sb) * nv2 + tt] = W[d][sa][sb];
+    if (lane == 0) {
+        otab[warp] = U;
+        for (int d = 0; d < 3; ++d)
+            for (int sa = 0; sa < 2; ++sa)
+                for (int sb = 0; sb < 2; ++sb) otab[(size_t)(1 + 4 * d + 2 * sa + sb) * noff + warp] = W[d][sa][sb];
+    }
+}
+
+__global__ void self_vv_expand_kernel(DevMesh m, const double2* __restrict__ otab, double2* __restrict__ tab) {
+    const int nv2 = m.nvox * m.nvox;
+    const int tt = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tt >= nv2) return;
+    const int B = tt / m.nvox, A = tt % m.nvox;
+    const int w1 = 2 * m.nv - 1, noff = w1 * w1 * w1;
+    int idx = 0;
+    for (int d = 0; d < 3; ++d) idx = idx * w1 + (m.vox_ijk[3 * B + d] - m.vox_ijk[3 * A + d] + m.nv - 1);
+    for (int q = 0; q < 13; ++q) tab[(size_t)q * nv2 + tt] = otab[(size_t)q * noff + idx];
 }
 
 // uniform voxel/sheet combinations of one atom with itself
@@ -747,13 +787,18 @@ void assemble_self_blocks(Op& op) {
     const int np = m.np;
     size_t stride = table_stride(m);
     DevBuf tab(stride * sizeof(double2));
+    const int w1o = 2 * m.nv - 1;
+    DevBuf otab((size_t)13 * w1o * w1o * w1o * sizeof(double2));  // voxel/voxel integrals per offset
     op.d_zself64.alloc((size_t)op.T * np * np * sizeof(double2));
     DevBuf jobs(sizeof(PairJob)), dst(sizeof(void*)), ldb(sizeof(int64_t));
     cudaStream_t s = op.ctx->stream;
     for (int t = 0; t < op.T; ++t) {
         double h = op.h[t];
         int nv2 = m.nvox * m.nvox;
-        self_vv_kernel<<<(nv2 + 63) / 64, 64, 0, s>>>(m, h, op.k, tab.as<double2>());
+        const int w1 = 2 * m.nv - 1, noff = w1 * w1 * w1;
+        self_vv_offset_kernel<<<(noff * 32 + 127) / 128, 128, 0, s>>>(m.nv, h, op.k, otab.as<double2>());
+        VIE_CHECK_LAUNCH();
+        self_vv_expand_kernel<<<(nv2 + 255) / 256, 256, 0, s>>>(m, otab.as<double2>(), tab.as<double2>());
         VIE_CHECK_LAUNCH();
         int ns = std::max(m.nvox, m.nsurf) * m.nsurf;
         self_surf_kernel<<<dim3((ns + 63) / 64, 3), 64, 0, s>>>(m, h, op.k, tab.as<double2>());
