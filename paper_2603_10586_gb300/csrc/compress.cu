@@ -388,7 +388,13 @@ struct Compressor {
             int rmax = *std::max_element(r.begin(), r.end());
             bool all = std::all_of(conv.begin(), conv.end(), [](int c) { return c; });
             if (all) break;
-            int scols = step == 0 ? s0 : kChunk;
+            // later sketches grow with the rank still being found (half of it, 32 to
+            // 256 columns): fewer passes over the formed blocks; columns are still
+            // orthogonalised and tested 32 at a time, so the ranks do not change
+            int rlive = 0;
+            for (int q = 0; q < nb; ++q)
+                if (!conv[q]) rlive = std::max(rlive, r[q]);
+            int scols = step == 0 ? s0 : std::min(256, std::max(kChunk, ((rlive / 2 + kChunk - 1) / kChunk) * kChunk));
             scols = std::min(scols, rcap_pad - rmax);
             if (scols <= 0) {
                 // every unconverged block has a full basis: exact
