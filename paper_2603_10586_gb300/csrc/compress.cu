@@ -116,6 +116,51 @@ __global__ void k_gram_partial(const T2* Y, int m, int64_t stride, int nchunk, d
     }
     part[((size_t)b * nchunk + c) * kChunk * kChunk + i + j * kChunk] = cvt<double2>(acc);
 }
+// The first Gram of the float32 compressor in double-float arithmetic on the
+// float32 pipes (this GPU's float64 rate is a small fraction of its float32
+// rate): the float32 inputs are exact, each product is formed exactly with an
+// FMA (two-product) and each addition keeps its error (two-sum), ~48 bits as
+// the float64 version above gives to within its own rounding.
+__device__ __forceinline__ void df_prod_add(float& h, float& l, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);
+    const float sum = __fadd_rn(h, p);
+    const float bv = __fsub_rn(sum, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(sum, bv)), __fsub_rn(p, bv));
+    h = sum;
+    l = __fadd_rn(l, __fadd_rn(err, e));
+}
+__global__ void k_gram_partial_df(const float2* Y, int m, int64_t stride, int nchunk, double2* part) {
+    const int b = blockIdx.y, c = blockIdx.x;
+    const int per = (m + nchunk - 1) / nchunk;
+    const int lo = c * per, hi = min(m, lo + per);
+    const float2* y = Y + b * stride;
+    __shared__ float2 rows[64][kChunk + 1];
+    const int i = threadIdx.x % kChunk, j = threadIdx.x / kChunk;  // 1024 threads
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    const bool upper = i <= j;  // Hermitian: the reduce mirrors the lower triangle
+    for (int r0 = lo; r0 < hi; r0 += 64) {
+        for (int e = threadIdx.x; e < 64 * kChunk; e += blockDim.x) {
+            int rr = e % 64, cc = e / 64;
+            int r = r0 + rr;
+            rows[rr][cc] = r < hi ? y[r + (int64_t)cc * m] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        int nr = min(64, hi - r0);
+        if (upper)
+            for (int rr = 0; rr < nr; ++rr) {
+                const float2 a = rows[rr][i], v = rows[rr][j];  // conj(a) v
+                df_prod_add(rh, rl, a.x, v.x);
+                df_prod_add(rh, rl, a.y, v.y);
+                df_prod_add(ih, il, a.x, v.y);
+                df_prod_add(ih, il, -a.y, v.x);
+            }
+        __syncthreads();
+    }
+    part[((size_t)b * nchunk + c) * kChunk * kChunk + i + j * kChunk] =
+        make_double2((double)rh + (double)rl, (double)ih + (double)il);
+}
+
 __global__ void k_gram_reduce(const double2* part, int nchunk, double2* G) {
     const int b = blockIdx.x;
     const int e = threadIdx.x;  // kChunk^2 threads
@@ -475,9 +520,14 @@ struct Compressor {
                                       (long long)m * rcap_pad, Cb.as<T2>(), rcap_pad, (long long)rcap_pad * kChunk,
                                       one, Yc, m, ys, nb);
                     }
-                    if (pass == 0)
-                        k_gram_partial<T2, double2><<<dim3(nchunk, nb), 1024, 0, s>>>(Yc, m, ys, nchunk,
-                                                                                    gpart.as<double2>());
+                    if (pass == 0) {
+                        if constexpr (std::is_same<T2, float2>::value)
+                            k_gram_partial_df<<<dim3(nchunk, nb), 1024, 0, s>>>(Yc, m, ys, nchunk,
+                                                                                gpart.as<double2>());
+                        else
+                            k_gram_partial<T2, double2><<<dim3(nchunk, nb), 1024, 0, s>>>(Yc, m, ys, nchunk,
+                                                                                        gpart.as<double2>());
+                    }
                     else
                         k_gram_partial<T2, T2><<<dim3(nchunk, nb), 1024, 0, s>>>(Yc, m, ys, nchunk,
                                                                                gpart.as<double2>());
