@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <array>
 #include <map>
 
 #include "common.h"
@@ -116,6 +117,30 @@ __global__ void k_gram_partial(const T2* Y, int m, int64_t stride, int nchunk, d
     }
     part[((size_t)b * nchunk + c) * kChunk * kChunk + i + j * kChunk] = cvt<double2>(acc);
 }
+// Atom-pair blocks are formed once per distinct (types, displacement) and
+// placed into every far block that holds that pair: job j copies the np x np
+// block `src[j]` (ld np) to rows row_off, columns col_off of its block.
+struct PlaceJob {
+    int dst, row_off, col_off, src;
+};
+template <class T2>
+__global__ void k_place_pairs(const PlaceJob* __restrict__ jobs, const T2* __restrict__ ublk, int np,
+                              T2* const* __restrict__ dst, int64_t ld) {
+    const PlaceJob jb = jobs[blockIdx.y];
+    const T2* src = ublk + (int64_t)jb.src * np * np;
+    T2* out = dst[jb.dst] + jb.row_off + (int64_t)jb.col_off * ld;
+    const int64_t total = (int64_t)np * np;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / np), r = (int)(e - (int64_t)c * np);
+        out[r + (int64_t)c * ld] = src[e];
+    }
+}
+__global__ void k_gather_norms(const PlaceJob* __restrict__ jobs, int n, const double* __restrict__ unorm,
+                               double* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = unorm[jobs[j].src];
+}
+
 // The first Gram of the float32 compressor in double-float arithmetic on the
 // float32 pipes (this GPU's float64 rate is a small fraction of its float32
 // rate): the float32 inputs are exact, each product is formed exactly with an
@@ -370,6 +395,74 @@ struct Compressor {
         return now_s();
     }
 
+    // The Galerkin block of two distinct atoms depends only on their types and
+    // displacement.  Unless sharing is off, each distinct (types, displacement)
+    // among the jobs is formed once into a scratch block and copied to every
+    // position that holds it; otherwise every job is formed in place.
+    // norm (device, per job): squared Frobenius norm of the job's block.
+    void form_pairs(const std::vector<PairJob>& jobs, const std::vector<void*>& dst, const std::vector<int64_t>& ld,
+                    double* norm) {
+        const int np = op.np;
+        if (!op.ctx->no_sharing) {
+            double span = 0.0;
+            for (double c : op.centres) span = std::max(span, std::abs(c));
+            const double qu = 1e-9 * std::max(span, 1e-30);
+            std::map<std::array<long long, 5>, int> uid;
+            std::vector<PairJob> ujobs;
+            std::vector<PlaceJob> place(jobs.size());
+            for (size_t j = 0; j < jobs.size(); ++j) {
+                const int a = jobs[j].a, b = jobs[j].b;
+                std::array<long long, 5> key{op.types[a], op.types[b],
+                                             std::llround((op.centres[3 * b] - op.centres[3 * a]) / qu),
+                                             std::llround((op.centres[3 * b + 1] - op.centres[3 * a + 1]) / qu),
+                                             std::llround((op.centres[3 * b + 2] - op.centres[3 * a + 2]) / qu)};
+                auto it = uid.find(key);
+                int u;
+                if (it == uid.end()) {
+                    u = (int)ujobs.size();
+                    uid.emplace(key, u);
+                    ujobs.push_back(PairJob{a, b, u, 0, 0});
+                } else {
+                    u = it->second;
+                }
+                place[j] = PlaceJob{jobs[j].dst, jobs[j].row_off, jobs[j].col_off, u};
+            }
+            const size_t ubytes = ujobs.size() * (size_t)np * np * sizeof(T2);
+            // worth it when pairs repeat, and when the distinct blocks fit a modest scratch
+            if (ujobs.size() * 2 <= jobs.size() && ubytes <= ((size_t)16 << 30)) {
+                DevBuf ublk(ubytes), unorm(ujobs.size() * sizeof(double));
+                std::vector<void*> udst(ujobs.size());
+                std::vector<int64_t> uld(ujobs.size(), np);
+                for (size_t u = 0; u < ujobs.size(); ++u) udst[u] = ublk.as<T2>() + u * (size_t)np * np;
+                DevBuf dj, dd, dl, dp, dq;
+                upload(dj, ujobs);
+                upload(dd, udst);
+                upload(dl, uld);
+                assemble_pairs<T>(op, dj.as<PairJob>(), (int)ujobs.size(), dd.as<void* const>(), dl.as<int64_t>(), s,
+                                  unorm.as<double>());
+                upload(dp, place);
+                upload(dq, dst);
+                // every destination block of one batch has the same leading dimension
+                for (size_t j0 = 0; j0 < place.size(); j0 += 65535) {
+                    const int cnt = (int)std::min<size_t>(65535, place.size() - j0);
+                    k_place_pairs<T2><<<dim3(std::min(64, (np * np + 255) / 256), cnt), 256, 0, s>>>(
+                        dp.as<PlaceJob>() + j0, ublk.as<T2>(), np, dq.as<T2* const>(), ld[0]);
+                    VIE_CHECK_LAUNCH();
+                }
+                k_gather_norms<<<((int)place.size() + 255) / 256, 256, 0, s>>>(dp.as<PlaceJob>(), (int)place.size(),
+                                                                           unorm.as<double>(), norm);
+                VIE_CHECK_LAUNCH();
+                VIE_CUDA(cudaStreamSynchronize(s));  // scratch goes out of scope
+                return;
+            }
+        }
+        DevBuf dj, dd, dl;
+        upload(dj, jobs);
+        upload(dd, dst);
+        upload(dl, ld);
+        assemble_pairs<T>(op, dj.as<PairJob>(), (int)jobs.size(), dd.as<void* const>(), dl.as<int64_t>(), s, norm);
+    }
+
     // compress one batch of equally sized blocks
     void batch(const std::vector<int>& ids, int s0_hint) {
         double t0 = mark();
@@ -395,13 +488,8 @@ struct Compressor {
                         jobs.push_back(PairJob{op.block_atoms[b.t_off + i], op.block_atoms[b.s_off + j], q, i * np,
                                                j * np});
             }
-            DevBuf dj, dd, dl;
-            upload(dj, jobs);
-            upload(dd, dst);
-            upload(dl, ld);
             jobnorm.alloc(jobs.size() * sizeof(double));
-            assemble_pairs<T>(op, dj.as<PairJob>(), (int)jobs.size(), dd.as<void* const>(), dl.as<int64_t>(), s,
-                              jobnorm.as<double>());
+            form_pairs(jobs, dst, ld, jobnorm.as<double>());
         }
         double t1 = mark();
         tim[0] += t1 - t0;
