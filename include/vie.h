@@ -211,7 +211,9 @@ int vie_op_get_info(const vie_op* op, vie_op_info* info);
  * the far part on the tensor cores, relative error ~1e-5).
  * flags: VIE_APPLY_FUSE_PRECOND returns P^-1 Zs x instead of Zs x;
  * VIE_APPLY_DENSE applies the uncompressed matrix (works before vie_compress).
- * x and y must not overlap.  Asynchronous on `stream`. */
+ * x and y must be 16-byte aligned (cudaMalloc'd buffers are) and must not
+ * overlap; either violation fails with VIE_ERR_INVALID_ARG before anything is
+ * launched.  Asynchronous on `stream`. */
 int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int precision,
               int flags, vie_stream stream);
 
@@ -235,7 +237,8 @@ int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int prec
  *    in it has to start at zero.  Calls that overlap on the GPU (different
  *    streams, or different operators on one device) race on the array: order
  *    them on one stream or synchronise between them.
- *  - x, y: device pointers, c64, n x nrhs, ld = n, not overlapping; the
+ *  - x, y: device pointers, c64, n x nrhs, ld = n, 16-byte aligned and not
+ *    overlapping (VIE_ERR_INVALID_ARG otherwise); the
  *    operator must hold VIE_C64 factors.  Asynchronous on `stream` (NULL =
  *    the context's stream). */
 #define VIE_NOALLOC_SCRATCH_ELEMS (1LL << 22)
@@ -248,12 +251,14 @@ int vie_precond(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int pr
                 vie_stream stream);
 
 /* vie_rhs: b = j k v0, v0_i = int w_i . E0 (eq. matrixeq), Gauss-Legendre 3 points
- * per voxel axis; b is a device pointer, c128, n x nrhs, leading dimension ld. */
+ * per voxel axis; b is a device pointer (16-byte aligned), c128, n x nrhs,
+ * leading dimension ld. */
 int vie_rhs(vie_op* op, const vie_incident* inc, int nrhs, void* b, int64_t ld, vie_stream stream);
 
 /* vie_solve (Sec. 6: left-preconditioned GMRES, Sec. 4 preconditioner):
  * solves Zs I = b for the plane waves in `inc`; writes I (c128, n x nrhs,
- * column-major, ld = n) to I_out (host or device per opts->out_on_device).
+ * column-major, ld = n) to I_out (host or device per opts->out_on_device; a
+ * device I_out must be 16-byte aligned).
  * The right-hand sides iterate in lockstep: every Arnoldi step applies the
  * operator once to all of them still iterating (each keeps its own Krylov
  * space); the solve returns when all have converged or max_iters is hit.

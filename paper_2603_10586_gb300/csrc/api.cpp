@@ -109,6 +109,19 @@ vie_ctx* ctx_of(vie_op* op) { return op ? static_cast<vie_ctx*>(op->o.ctx->owner
 
 void set_device(Ctx& c) { VIE_CUDA(cudaSetDevice(c.device)); }
 
+// Caller vectors: 16-byte aligned (the apply kernels read two complex float32
+// entries as one 16-byte load) and, for an input / output pair of `bytes`
+// bytes each, disjoint.  Checked before anything is launched.
+void check_vectors(const char* who, const void* x, const void* y, size_t bytes) {
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
+        fail(VIE_ERR_INVALID_ARG, std::string(who) + ": vectors must be 16-byte aligned");
+    const char* a = static_cast<const char*>(x);
+    const char* b = static_cast<const char*>(y);
+    if (y && a < b + bytes && b < a + bytes) fail(VIE_ERR_INVALID_ARG, std::string(who) + ": x and y overlap");
+}
+
+size_t elem_bytes(int precision) { return (precision == VIE_C128 || precision == VIE_C64_ACC64) ? 16 : 8; }
+
 }  // namespace
 
 extern "C" {
@@ -346,15 +359,16 @@ int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int prec
         Op& o = op->o;
         set_device(*o.ctx);
         if (!x || !y || nrhs < 1 || ld != o.n()) fail(VIE_ERR_INVALID_ARG, "vie_apply: bad vectors (ld must be n)");
+        check_vectors("vie_apply", x, y, (size_t)o.n() * nrhs * elem_bytes(precision));
         if (o.fprec == 0 && !(flags & VIE_APPLY_DENSE)) fail(VIE_ERR_STATE, "operator is not compressed");
         cudaStream_t s = stream ? (cudaStream_t)stream : o.ctx->stream;
         const bool fuse = flags & VIE_APPLY_FUSE_PRECOND;
         if (flags & VIE_APPLY_DENSE) {
             if (fuse) fail(VIE_ERR_INVALID_ARG, "VIE_APPLY_DENSE cannot be combined with the preconditioner");
+            if (nrhs != 1) fail(VIE_ERR_INVALID_ARG, "VIE_APPLY_DENSE takes one right-hand side");
             if (precision == VIE_C64) dense_apply_c64(o, (const float2*)x, (float2*)y, s);
             else if (precision == VIE_C128) dense_apply_c128(o, (const double2*)x, (double2*)y, s);
             else fail(VIE_ERR_INVALID_ARG, "VIE_APPLY_DENSE needs VIE_C64 or VIE_C128");
-            if (nrhs != 1) fail(VIE_ERR_INVALID_ARG, "VIE_APPLY_DENSE takes one right-hand side");
             return;
         }
         if (precision == VIE_C64) {
@@ -394,7 +408,7 @@ int vie_apply_noalloc(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, 
         Op& o = op->o;
         set_device(*o.ctx);
         if (!x || !y || nrhs < 1 || ld != o.n()) fail(VIE_ERR_INVALID_ARG, "vie_apply_noalloc: bad vectors (ld must be n)");
-        if (x == y) fail(VIE_ERR_INVALID_ARG, "vie_apply_noalloc: x and y must not overlap");
+        check_vectors("vie_apply_noalloc", x, y, (size_t)o.n() * nrhs * sizeof(float2));
         if (o.fprec == 0) fail(VIE_ERR_STATE, "operator is not compressed");
         apply_static(o, (const float2*)x, (float2*)y, nrhs, stream ? (cudaStream_t)stream : o.ctx->stream);
     });
@@ -406,6 +420,7 @@ int vie_precond(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int pr
         Op& o = op->o;
         set_device(*o.ctx);
         if (!x || !y || nrhs < 1 || ld != o.n()) fail(VIE_ERR_INVALID_ARG, "vie_precond: bad vectors (ld must be n)");
+        check_vectors("vie_precond", x, y, (size_t)o.n() * nrhs * elem_bytes(precision));
         cudaStream_t s = stream ? (cudaStream_t)stream : o.ctx->stream;
         if (precision == VIE_C64)
             self_gemm<float2, float2>(o, o.d_inv32.as<float2>(), (const float2*)x, o.n(), nullptr, 0, (float2*)y,
@@ -423,6 +438,7 @@ int vie_rhs(vie_op* op, const vie_incident* inc, int nrhs, void* b, int64_t ld, 
         Op& o = op->o;
         set_device(*o.ctx);
         if (ld < o.n()) fail(VIE_ERR_INVALID_ARG, "ld < n");
+        check_vectors("vie_rhs", b, nullptr, 0);
         cudaStream_t s = stream ? (cudaStream_t)stream : o.ctx->stream;
         DevBuf kh(3 * nrhs * sizeof(double)), pl(6 * nrhs * sizeof(double));
         VIE_CUDA(cudaMemcpyAsync(kh.p, inc->khat, 3 * nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -438,6 +454,7 @@ int vie_solve(vie_op* op, const vie_incident* inc, int nrhs, const vie_solve_opt
     int result = VIE_OK;
     int st = guarded(ctx_of(op), [&] {
         set_device(*op->o.ctx);
+        if (opts->out_on_device) check_vectors("vie_solve", I_out, nullptr, 0);
         result = solve(op->o, inc, nrhs, opts, I_out, stats);
     });
     if (st != VIE_OK) return st;
@@ -458,6 +475,7 @@ int vie_solve_batch(vie_op* const* ops, int count, const vie_incident* inc, cons
         for (int p = 0; p < count; ++p) {
             v[p] = &ops[p]->o;
             outs[p] = I_out[p];
+            if (opts->out_on_device) check_vectors("vie_solve_batch", I_out[p], nullptr, 0);
         }
         result = solve_batch(v, inc, nrhs, opts, outs.data(), stats);
     });

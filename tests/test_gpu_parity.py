@@ -435,3 +435,68 @@ def test_graded_array_solve(ctx):
     assert status == vie.VIE_OK
     assert rel(I[:, 0], np.linalg.solve(Z, A.rhs(P, kh[0], pol[0]))) <= 5e-4
     op.close()
+
+
+# ------------------------------------- other materials, grids and array shapes
+@pytest.mark.parametrize("ns,nv,eps", [(4, 3, complex(12.0, -3.0)), (4, 2, 12.0), (3, 4, complex(6.0, -0.5))])
+def test_array_solve_against_dense(ctx, ns, nv, eps):
+    # a lossy permittivity (Im eps < 0 under exp(j w t), Sec. 2), coarser (36 unknowns per
+    # atom) and finer (240) voxel grids, and a 3 x 3 array whose quadtree
+    # leaves part of its boxes empty: the GPU solve against a direct solve of
+    # the oracle's dense matrix
+    g = workloads.square_array(ns, nv, eps=eps)
+    P = problem_from_geometry(g)
+    Z = A.dense_matrix(P)
+    op = vie.Operator(ctx, g)
+    op.compress(1e-4, vie.C64)
+    kh, pol = workloads.normal_incidence()
+    I, st, status = op.solve(kh, pol, tol=1e-6)
+    assert status == vie.VIE_OK and st["residual"] <= 1e-6
+    assert rel(I[:, 0], np.linalg.solve(Z, A.rhs(P, kh[0], pol[0]))) <= 5e-4
+    ext, sca = op.sigma(I, kh, pol)[0]
+    v0 = A.rhs_v0(P, kh[0], pol[0])
+    assert abs(ext - OF.sigma_ext(I[:, 0], v0)) < 1e-10 * abs(ext)
+    assert abs(sca - OF.sigma_sca(P, I[:, 0])) < 1e-10 * abs(sca)
+    if np.imag(eps) != 0:
+        assert ext > sca * (1 + 1e-2)             # absorption: extinction exceeds scattering
+    else:
+        assert abs(ext - sca) < 1e-3 * ext        # optical theorem (lossless)
+    op.close()
+
+
+# ------------------------------------------------------------ C-ABI error paths
+def test_apply_rejects_bad_arguments(tiny_op):
+    # every case is refused before anything is launched; all pointers stay in bounds
+    import torch as th
+    n = tiny_op.n
+    buf = th.zeros(2 * n + 4, dtype=th.complex64, device="cuda")
+    y = th.zeros(2 * n, dtype=th.complex64, device="cuda")
+    x128 = th.zeros(n, dtype=th.complex128, device="cuda")
+    y128 = th.zeros(n, dtype=th.complex128, device="cuda")
+
+    def status(fn):
+        with pytest.raises(vie.VieError) as e:
+            fn()
+        return e.value.status
+
+    bad = vie.VIE_ERR_INVALID_ARG
+    x0 = buf.data_ptr()
+    # off the 16-byte grid (the c64 kernels read complex pairs as one 16-byte load)
+    assert status(lambda: tiny_op.apply(x0 + 8, y.data_ptr(), 1, vie.C64, 0)) == bad
+    assert status(lambda: tiny_op.apply(x0, y.data_ptr() + 8, 1, vie.BF16X3, vie.FUSE_PRECOND)) == bad
+    assert status(lambda: tiny_op.precond(x0 + 8, y.data_ptr(), 1, vie.C64)) == bad
+    # overlapping input and output
+    assert status(lambda: tiny_op.apply(x0, x0 + 16, 1, vie.C64, 0)) == bad
+    assert status(lambda: tiny_op.apply(x0, x0, 1, vie.C64, vie.FUSE_PRECOND)) == bad
+    # float64 factors wanted, an unknown precision, a dense apply of two columns
+    assert status(lambda: tiny_op.apply(x128.data_ptr(), y128.data_ptr(), 1, vie.C128, 0)) == bad
+    assert status(lambda: tiny_op.apply(x0, y.data_ptr(), 1, 99, 0)) == bad
+    assert status(lambda: tiny_op.apply(x0, y.data_ptr(), 2, vie.C64, vie.DENSE)) == bad
+    assert status(lambda: tiny_op.apply(x0, y.data_ptr(), 0, vie.C64, 0)) == bad
+    # the context is still usable and the rejected calls wrote nothing
+    th.cuda.synchronize()
+    assert th.count_nonzero(y).item() == 0
+    buf[:n] = 1 + 1j
+    tiny_op.apply(x0, y.data_ptr(), 1, vie.C64, 0)
+    th.cuda.synchronize()
+    assert th.isfinite(th.view_as_real(y[:n])).all().item() and th.count_nonzero(y[:n]).item() == n

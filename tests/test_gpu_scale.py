@@ -118,6 +118,37 @@ def test_scale_apply_parity_sampled_atoms(scale_op):
         assert rel(y[atom * npp:(atom + 1) * npp], ref) < 1e-5
 
 
+def test_scale_bf16x3_multi_rhs_apply(scale_op):
+    # 64 right-hand sides through the tensor-core (BF16x3) apply at full size:
+    # rows of two atoms for three columns against the oracle on the exported
+    # factors (float64), every entry against the float32 SIMT apply
+    op, g, _, _ = scale_op
+    P = problem_from_geometry(g)
+    npp, n, k = op.np, op.n, 64
+    xs = workloads.random_complex(n, 4321, cols=k)                 # n x k
+    X = torch.from_numpy(np.ascontiguousarray(xs.T).astype(np.complex64)).cuda()
+    Y, Yr = torch.empty_like(X), torch.empty_like(X)
+    for fl in (vie.FUSE_PRECOND, 0):
+        op.apply(X.data_ptr(), Y.data_ptr(), k, vie.BF16X3, fl)
+        op.apply(X.data_ptr(), Yr.data_ptr(), k, vie.C64, fl)
+        torch.cuda.synchronize()
+        assert rel(Y.cpu().numpy(), Yr.cpu().numpy()) < 5e-5, fl
+    y = Y.cpu().numpy()                                            # k x n, Zs x
+    x = xs.astype(np.complex64).astype(np.complex128)
+    meta = op.far_blocks(with_factors=False)
+    Zs = A.self_block(P, 0)
+    cols = [0, 37, 63]
+    for atom in (5, 200):
+        rows = slice(atom * npp, (atom + 1) * npp)
+        idx = [i for i, b in enumerate(meta) if atom in set(b["tatoms"].tolist())]
+        ref = Zs @ x[rows][:, cols]
+        for b in op.far_blocks(indices=idx):
+            slot = list(b["tatoms"]).index(atom)
+            src = OC.atom_rows(P, b["satoms"])
+            ref = ref + b["Q"][slot * npp:(slot + 1) * npp] @ (b["R"] @ x[src][:, cols])
+        assert rel(y[cols][:, rows].T, ref) < 5e-5, atom
+
+
 def test_scale_solve(scale_op):
     op, g, kh, pol = scale_op
     n = op.n

@@ -53,5 +53,10 @@ def test_noalloc_apply_matches_regular_apply():
     yb = torch.zeros_like(xb)
     with pytest.raises(vie.VieError):
         op.apply_noalloc(xb.data_ptr(), yb.data_ptr(), big)
+    # so are vectors off the 16-byte grid and overlapping vectors (both in bounds)
+    for xp, yp in ((xs[0].data_ptr() + 8, y_na[0].data_ptr()), (xs[0].data_ptr(), xs[0].data_ptr() + 16)):
+        with pytest.raises(vie.VieError) as e:
+            op.apply_noalloc(xp, yp, 1)
+        assert e.value.status == vie.VIE_ERR_INVALID_ARG
     op.close()
     ctx.close()
