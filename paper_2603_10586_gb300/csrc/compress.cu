@@ -27,6 +27,8 @@
 #include <array>
 #include <map>
 
+#include <cuda_bf16.h>
+
 #include "common.h"
 #include "cplx.cuh"
 
@@ -35,7 +37,7 @@ namespace vie {
 namespace {
 
 constexpr int kChunk = 32;    // columns orthonormalised at a time
-constexpr int kRankCap = 1536; // largest rank a block may take (larger: error)
+constexpr int kRankCap = 2048; // largest rank a block may take (larger: error)
 
 // ------------------------------------------------------------------ kernels
 __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
@@ -93,8 +95,9 @@ __global__ void k_reduce_rows(const double* part, int nchunk, int nb, double* ou
 // accumulated in ACC (double2 for a general block; float2 is enough once the
 // block is close to orthonormal), stored as double2
 template <class T2, class ACC>
-__global__ void k_gram_partial(const T2* Y, int m, int64_t stride, int nchunk, double2* part) {
+__global__ void k_gram_partial(const T2* Y, int m, int64_t stride, int nchunk, double2* part, const int* active) {
     const int b = blockIdx.y, c = blockIdx.x;
+    if (!active[b]) return;
     const int per = (m + nchunk - 1) / nchunk;
     const int lo = c * per, hi = min(m, lo + per);
     const T2* y = Y + b * stride;
@@ -155,8 +158,10 @@ __device__ __forceinline__ void df_prod_add(float& h, float& l, float a, float b
     h = sum;
     l = __fadd_rn(l, __fadd_rn(err, e));
 }
-__global__ void k_gram_partial_df(const float2* Y, int m, int64_t stride, int nchunk, double2* part) {
+__global__ void k_gram_partial_df(const float2* Y, int m, int64_t stride, int nchunk, double2* part,
+                                  const int* active) {
     const int b = blockIdx.y, c = blockIdx.x;
+    if (!active[b]) return;
     const int per = (m + nchunk - 1) / nchunk;
     const int lo = c * per, hi = min(m, lo + per);
     const float2* y = Y + b * stride;
@@ -186,8 +191,9 @@ __global__ void k_gram_partial_df(const float2* Y, int m, int64_t stride, int nc
         make_double2((double)rh + (double)rl, (double)ih + (double)il);
 }
 
-__global__ void k_gram_reduce(const double2* part, int nchunk, double2* G) {
+__global__ void k_gram_reduce(const double2* part, int nchunk, double2* G, const int* active) {
     const int b = blockIdx.x;
+    if (!active[b]) return;
     const int e = threadIdx.x;  // kChunk^2 threads
     const int i = e % kChunk, j = e / kChunk;
     if (i > j) return;
@@ -311,6 +317,130 @@ __global__ void k_gather_cols(const T2* src, int64_t rows, const long long* src_
         d[i] = s[i];
 }
 
+// ------------------------------------------- split bf16 operands (float32 path)
+// The sketch Y = A Omega and the projection R^H = A^H Q run as real bf16
+// GEMMs with float32 accumulation on split operands: every float32 value x is
+// carried as hi = bf16(x) and lo = bf16(x - hi) (16 significant bits, relative
+// error <= 2^-17).  Omega is drawn in bf16 (a Gaussian rounded to bf16 is as
+// good a test matrix), so the sketch needs hi and lo of A only (two products);
+// R^H takes hi.hi + hi.lo + lo.hi.  Both errors are ~1e-5 relative, well
+// inside the tol / 3 margin of the range finder at the float32 tolerances
+// (1e-4 .. 1e-3); the Gram-Schmidt projections keep float32 accuracy.
+//
+// Layout of a formed block after the split: column j of A (8 m bytes as
+// complex float32) holds, in the same bytes, [Re hi | Im hi | Re lo | Im lo],
+// m bf16 each.  Read with ld = m it is an m x 4n matrix (plane p of column j
+// is column 4 j + p); read with ld = 4 m it is a 4 m x n matrix.
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ void split_bf16(float x, bf16& hi, bf16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// column per CTA: the whole column is read into shared memory before its
+// bytes are rewritten as the four planes
+__global__ void k_split_cols(float2* A, int m) {
+    extern __shared__ float2 col[];
+    float2* c = A + (int64_t)blockIdx.x * m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] = c[i];
+    __syncthreads();
+    bf16* p = reinterpret_cast<bf16*>(c);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        bf16 rh, rl, ih, il;
+        split_bf16(col[i].x, rh, rl);
+        split_bf16(col[i].y, ih, il);
+        p[i] = rh;
+        p[m + i] = ih;
+        p[2 * m + i] = rl;
+        p[3 * m + i] = il;
+    }
+}
+
+// The real 4n x 2s right-hand side B of the sketch (ld 4n) from a complex
+// Gaussian W (n x s) rounded to bf16: rows 4j and 4j+2 hold [Re W_j, Im W_j],
+// rows 4j+1 and 4j+3 hold [-Im W_j, Re W_j], so that with A read as m x 4n
+// the product is [Re(A W) | Im(A W)] (m x 2s).
+__global__ void k_gauss_bf16(bf16* B, int n, int s, uint64_t seed) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * s) return;
+    const int j = (int)(t % n), c = (int)(t / n);
+    uint64_t a = splitmix64(seed ^ (uint64_t)(2 * t));
+    uint64_t b = splitmix64(seed ^ (uint64_t)(2 * t + 1));
+    double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+    double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+    double r = sqrt(-log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    const bf16 wr = __float2bfloat16_rn((float)(r * cs)), wi = __float2bfloat16_rn((float)(r * sn));
+    const bf16 nwi = __hneg(wi);
+    const int64_t ld = 4 * (int64_t)n, c0 = (int64_t)c * ld, c1 = (int64_t)(s + c) * ld;
+    for (int h = 0; h < 2; ++h) {
+        const int64_t row = 4 * (int64_t)j + 2 * h;
+        B[row + c0] = wr;
+        B[row + c1] = wi;
+        B[row + 1 + c0] = nwi;
+        B[row + 1 + c1] = wr;
+    }
+}
+
+// Right-hand sides of R^H = A^H Q from Q (m x r complex, ld m):
+// Bh (4m x 2r, ld 4m): column c = [Re Q; Im Q; Re Q; Im Q]_c (hi parts),
+// column r + c = [Im Q; -Re Q; Im Q; -Re Q]_c; Bl (2m x 2r, ld 2m): the lo
+// parts of the first halves.  With A read as 4m x n, A^T Bh + A_hi^T Bl =
+// [Re R^H | Im R^H] (n x 2r).
+__global__ void k_split_q(const float2* Q, int m, int r, int64_t qstride, bf16* Bh, int64_t hstride, bf16* Bl,
+                          int64_t lstride) {
+    const int b = blockIdx.y;
+    const float2* q = Q + b * qstride;
+    bf16* bh = Bh + b * hstride;
+    bf16* bl = Bl + b * lstride;
+    const int64_t total = (int64_t)m * r;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / m), i = (int)(e - (int64_t)c * m);
+        const float2 v = q[i + (int64_t)c * m];
+        bf16 rh, rl, ih, il;
+        split_bf16(v.x, rh, rl);
+        split_bf16(v.y, ih, il);
+        const bf16 nrh = __hneg(rh), nrl = __hneg(rl);
+        bf16* h0 = bh + (int64_t)c * 4 * m;
+        bf16* h1 = bh + (int64_t)(r + c) * 4 * m;
+        h0[i] = rh; h0[m + i] = ih; h0[2 * m + i] = rh; h0[3 * m + i] = ih;
+        h1[i] = ih; h1[m + i] = nrh; h1[2 * m + i] = ih; h1[3 * m + i] = nrh;
+        bf16* l0 = bl + (int64_t)c * 2 * m;
+        bf16* l1 = bl + (int64_t)(r + c) * 2 * m;
+        l0[i] = rl; l0[m + i] = il;
+        l1[i] = il; l1[m + i] = nrl;
+    }
+}
+
+// out[list[y]] (rows x cols complex, ld rows) from F[list[y]] (rows x 2 cols
+// real, ld rows: real parts then imaginary parts)
+__global__ void k_join_planes(const float* F, int rows, int cols, int64_t fstride, float2* out, int64_t ostride,
+                              const int* list) {
+    const int b = list ? list[blockIdx.y] : (int)blockIdx.y;
+    const float* f = F + b * fstride;
+    float2* o = out + b * ostride;
+    const int64_t total = (int64_t)rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        o[e] = make_float2(f[e], f[e + total]);
+}
+
+void gemm_bf16(cublasHandle_t h, cublasOperation_t ta, int m, int n, int k, const bf16* A, int lda, long long sa,
+               const bf16* B, int ldb, long long sb, float beta, float* C, int ldc, long long sc, int batch) {
+    const float one = 1.f;
+    if (batch == 1)
+        VIE_BLAS(cublasGemmEx(h, ta, CUBLAS_OP_N, m, n, k, &one, A, CUDA_R_16BF, lda, B, CUDA_R_16BF, ldb, &beta, C,
+                              CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT));
+    else
+        VIE_BLAS(cublasGemmStridedBatchedEx(h, ta, CUBLAS_OP_N, m, n, k, &one, A, CUDA_R_16BF, lda, sa, B, CUDA_R_16BF,
+                                            ldb, sb, &beta, C, CUDA_R_32F, ldc, sc, batch, CUBLAS_COMPUTE_32F,
+                                            CUBLAS_GEMM_DEFAULT));
+}
+
+// largest block height whose column fits the split kernel's shared memory
+constexpr int kSplitMaxRows = 200 * 1024 / 8;
+
 // ------------------------------------------------------------------ cuBLAS
 template <class T> struct Blas;
 template <> struct Blas<float> {
@@ -386,6 +516,32 @@ struct Compressor {
         VIE_CHECK_LAUNCH();
         k_reduce_rows<<<(nb + 127) / 128, 128, 0, s>>>(part.as<double>(), nchunk, nb, out);
         VIE_CHECK_LAUNCH();
+    }
+
+    // Per-block pointers of one chunk's projections, for the listed blocks:
+    // [Q_q ...][Y_q ...][C_q ...] (the table is read by the GEMMs in stream order)
+    void proj_ptrs(DevBuf& buf, const std::vector<int>& list, T2* Qb, int64_t qs, T2* Yb, int64_t ys, T2* Cbb,
+                   int64_t cs) {
+        const size_t L = list.size();
+        if (L == 0) return;
+        std::vector<T2*> hp(3 * L);
+        for (size_t i = 0; i < L; ++i) {
+            hp[i] = Qb + list[i] * qs;
+            hp[L + i] = Yb + list[i] * ys;
+            hp[2 * L + i] = Cbb + list[i] * cs;
+        }
+        VIE_CUDA(cudaMemcpyAsync(buf.p, hp.data(), hp.size() * sizeof(T2*), cudaMemcpyHostToDevice, s));
+    }
+    // one classical Gram-Schmidt pass of the chunks against their blocks' first K
+    // basis columns: C = Q^H Y, Y -= Q C
+    void project(const DevBuf& buf, int L, int K, int m, int ldc) {
+        if (L == 0 || K == 0) return;
+        T2* const* p = buf.as<T2* const>();
+        const T2 one = mk(T(1), T(0)), zero = mk(T(0), T(0)), mone = mk(T(-1), T(0));
+        Blas<T>::gemm_ptr(h, CUBLAS_OP_C, CUBLAS_OP_N, K, kChunk, m, one, (const T2* const*)p, m,
+                          (const T2* const*)(p + L), m, zero, p + 2 * L, ldc, L);
+        Blas<T>::gemm_ptr(h, CUBLAS_OP_N, CUBLAS_OP_N, m, kChunk, K, mone, (const T2* const*)p, m,
+                          (const T2* const*)(p + 2 * L), ldc, one, p + L, m, L);
     }
 
     double tim[5] = {0, 0, 0, 0, 0};  // form, sketch loop, R, compaction, total
@@ -499,6 +655,16 @@ struct Compressor {
         VIE_CHECK_LAUNCH();
         std::vector<double> hnorm(nb);
         VIE_CUDA(cudaMemcpyAsync(hnorm.data(), normA.p, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+        // float32 path: the formed blocks become split bf16 planes, in place
+        const char* sp = std::getenv("VIE_COMPRESS_SPLIT");
+        const bool split = std::is_same<T, float>::value && m <= kSplitMaxRows && !(sp && sp[0] == '0');
+        const bf16* Ap = reinterpret_cast<const bf16*>(A.p);
+        if (split) {
+            const size_t smem = (size_t)m * sizeof(float2);
+            VIE_CUDA(cudaFuncSetAttribute(k_split_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_split_cols<<<(unsigned)((int64_t)nb * n), 256, smem, s>>>(reinterpret_cast<float2*>(A.p), m);
+            VIE_CHECK_LAUNCH();
+        }
 
         // 2. adaptive range finder
         DevBuf Q((size_t)nb * m * rcap_pad * sizeof(T2));
@@ -508,6 +674,7 @@ struct Compressor {
         DevBuf Cb((size_t)nb * rcap_pad * kChunk * sizeof(T2));
         DevBuf gpart, G((size_t)nb * kChunk * kChunk * sizeof(double2)), Minv((size_t)nb * kChunk * kChunk * sizeof(T2));
         DevBuf d_active(nb * sizeof(int)), d_rbase(nb * sizeof(int));
+        DevBuf pbuf1((size_t)3 * nb * sizeof(void*)), pbuf2((size_t)3 * nb * sizeof(void*));
         std::vector<int> r(nb, 0), conv(nb, 0);
         // first sketch: the rank prior of this block class (one pass over A), then
         // 32-column passes for the blocks that still need more
@@ -534,16 +701,59 @@ struct Compressor {
                 for (int q = 0; q < nb; ++q) conv[q] = 1;
                 break;
             }
-            DevBuf W((size_t)n * scols * sizeof(T2)), Y((size_t)nb * m * scols * sizeof(T2));
-            k_gauss<T2><<<(unsigned)(((int64_t)n * scols + 255) / 256), 256, 0, s>>>(W.as<T2>(), (int64_t)n * scols,
-                                                                                     seed + 7919ull * step);
-            VIE_CHECK_LAUNCH();
+            DevBuf Y((size_t)nb * m * scols * sizeof(T2));
+            const uint64_t sseed = seed + 7919ull * step;
             ++step;
             const T2 one = mk(T(1), T(0)), zero = mk(T(0), T(0)), mone = mk(T(-1), T(0));
-            if (step == 1) {
+            if (split) {
+                // [Re Y | Im Y] = A (m x 4n planes) B (4n x 2 scols), then joined
+                DevBuf Wb((size_t)8 * n * scols * sizeof(bf16)), Yf((size_t)nb * m * 2 * scols * sizeof(float));
+                k_gauss_bf16<<<(unsigned)(((int64_t)n * scols + 255) / 256), 256, 0, s>>>(Wb.as<bf16>(), n, scols,
+                                                                                          sseed);
+                VIE_CHECK_LAUNCH();
+                std::vector<int> list;
+                for (int q = 0; q < nb; ++q)
+                    if (!conv[q]) list.push_back(q);
+                const long long fs = 2LL * m * scols;
+                if ((int)list.size() == nb) {
+                    gemm_bf16(h, CUBLAS_OP_N, m, 2 * scols, 4 * n, Ap, m, 4 * mn, Wb.as<bf16>(), 4 * n, 0, 0.f,
+                              Yf.as<float>(), m, fs, nb);
+                } else {
+                    std::vector<const void*> pa, pb;
+                    std::vector<void*> pc;
+                    for (int q : list) {
+                        pa.push_back(Ap + (size_t)q * 4 * mn);
+                        pb.push_back(Wb.p);
+                        pc.push_back(Yf.as<float>() + (size_t)q * fs);
+                    }
+                    DevBuf da, db, dc;
+                    upload(da, pa);
+                    upload(db, pb);
+                    upload(dc, pc);
+                    const float f1 = 1.f, f0 = 0.f;
+                    VIE_BLAS(cublasGemmBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_N, m, 2 * scols, 4 * n, &f1,
+                                                 da.as<const void* const>(), CUDA_R_16BF, m, db.as<const void* const>(),
+                                                 CUDA_R_16BF, 4 * n, &f0, dc.as<void* const>(), CUDA_R_32F, m,
+                                                 (int)list.size(), CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT));
+                    VIE_CUDA(cudaStreamSynchronize(s));
+                }
+                DevBuf dl;
+                upload(dl, list);
+                k_join_planes<<<dim3((unsigned)std::min<int64_t>(1024, ((int64_t)m * scols + 255) / 256),
+                                     (unsigned)list.size()),
+                                256, 0, s>>>(Yf.as<float>(), m, scols, fs, reinterpret_cast<float2*>(Y.p),
+                                             (int64_t)m * scols, dl.as<int>());
+                VIE_CHECK_LAUNCH();
+                VIE_CUDA(cudaStreamSynchronize(s));  // Wb, Yf go out of scope
+            } else {
+              DevBuf W((size_t)n * scols * sizeof(T2));
+              k_gauss<T2><<<(unsigned)(((int64_t)n * scols + 255) / 256), 256, 0, s>>>(W.as<T2>(),
+                                                                                       (int64_t)n * scols, sseed);
+              VIE_CHECK_LAUNCH();
+              if (step == 1) {
                 Blas<T>::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, scols, n, one, A.as<T2>(), m, mn, W.as<T2>(), n, 0, zero,
                               Y.as<T2>(), m, (long long)m * scols, nb);
-            } else {
+              } else {
                 std::vector<const T2*> pa, pb;
                 std::vector<T2*> pc;
                 for (int q = 0; q < nb; ++q)
@@ -558,19 +768,21 @@ struct Compressor {
                 upload(dc, pc);
                 Blas<T>::gemm_ptr(h, CUBLAS_OP_N, CUBLAS_OP_N, m, scols, n, one, da.as<const T2* const>(), m,
                                   db.as<const T2* const>(), n, zero, dc.as<T2* const>(), m, (int)pa.size());
-                VIE_CUDA(cudaStreamSynchronize(s));
+              }
+              VIE_CUDA(cudaStreamSynchronize(s));  // W goes out of scope
             }
             for (int c0 = 0; c0 < scols; c0 += kChunk) {
                 T2* Yc = Y.as<T2>() + (int64_t)c0 * m;
                 const long long ys = (long long)m * scols;
                 rmax = *std::max_element(r.begin(), r.end());
-                for (int pass = 0; pass < 2 && rmax > 0; ++pass) {
-                    Blas<T>::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, rmax, kChunk, m, one, Q.as<T2>(), m,
-                                  (long long)m * rcap_pad, Yc, m, ys, zero, Cb.as<T2>(), rcap_pad,
-                                  (long long)rcap_pad * kChunk, nb);
-                    Blas<T>::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, kChunk, rmax, mone, Q.as<T2>(), m,
-                                  (long long)m * rcap_pad, Cb.as<T2>(), rcap_pad, (long long)rcap_pad * kChunk, one,
-                                  Yc, m, ys, nb);
+                // the blocks still growing all hold rmax columns; converged ones are left out
+                std::vector<int> live;
+                for (int q = 0; q < nb; ++q)
+                    if (!conv[q]) live.push_back(q);
+                if (rmax > 0) {
+                    proj_ptrs(pbuf1, live, Q.as<T2>(), (int64_t)m * rcap_pad, Yc, ys, Cb.as<T2>(),
+                              (int64_t)rcap_pad * kChunk);
+                    for (int pass = 0; pass < 2; ++pass) project(pbuf1, (int)live.size(), rmax, m, rcap_pad);
                 }
                 sumsq(Yc, (int64_t)m * kChunk, ys, nb, est.as<double>(), part);
                 std::vector<double> he(nb);
@@ -597,30 +809,34 @@ struct Compressor {
                 int nchunk = std::max(1, std::min(64, m / 256));
                 size_t gneed = (size_t)nb * nchunk * kChunk * kChunk * sizeof(double2);
                 if (gpart.bytes < gneed) gpart.alloc(gneed);
+                std::vector<int> act;
+                for (int q = 0; q < nb; ++q)
+                    if (active[q]) act.push_back(q);
+                if (rmax > 0)
+                    proj_ptrs(pbuf2, act, Q.as<T2>(), (int64_t)m * rcap_pad, Yc, ys, Cb.as<T2>(),
+                              (int64_t)rcap_pad * kChunk);
                 for (int pass = 0; pass < 2; ++pass) {
                     if (pass == 1 && rmax > 0) {
                         // the normalisation above scales up whatever overlap with the
                         // basis the float32 projection left behind: project once more
-                        Blas<T>::gemm(h, CUBLAS_OP_C, CUBLAS_OP_N, rmax, kChunk, m, one, Q.as<T2>(), m,
-                                      (long long)m * rcap_pad, Yc, m, ys, zero, Cb.as<T2>(), rcap_pad,
-                                      (long long)rcap_pad * kChunk, nb);
-                        Blas<T>::gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, kChunk, rmax, mone, Q.as<T2>(), m,
-                                      (long long)m * rcap_pad, Cb.as<T2>(), rcap_pad, (long long)rcap_pad * kChunk,
-                                      one, Yc, m, ys, nb);
+                        project(pbuf2, (int)act.size(), rmax, m, rcap_pad);
                     }
                     if (pass == 0) {
                         if constexpr (std::is_same<T2, float2>::value)
                             k_gram_partial_df<<<dim3(nchunk, nb), 1024, 0, s>>>(Yc, m, ys, nchunk,
-                                                                                gpart.as<double2>());
+                                                                                gpart.as<double2>(),
+                                                                                d_active.as<int>());
                         else
-                            k_gram_partial<T2, double2><<<dim3(nchunk, nb), 1024, 0, s>>>(Yc, m, ys, nchunk,
-                                                                                        gpart.as<double2>());
+                            k_gram_partial<T2, double2><<<dim3(nchunk, nb), 1024, 0, s>>>(
+                                Yc, m, ys, nchunk, gpart.as<double2>(), d_active.as<int>());
                     }
                     else
                         k_gram_partial<T2, T2><<<dim3(nchunk, nb), 1024, 0, s>>>(Yc, m, ys, nchunk,
-                                                                               gpart.as<double2>());
+                                                                               gpart.as<double2>(),
+                                                                               d_active.as<int>());
                     VIE_CHECK_LAUNCH();
-                    k_gram_reduce<<<nb, kChunk * kChunk, 0, s>>>(gpart.as<double2>(), nchunk, G.as<double2>());
+                    k_gram_reduce<<<nb, kChunk * kChunk, 0, s>>>(gpart.as<double2>(), nchunk, G.as<double2>(),
+                                                                 d_active.as<int>());
                     VIE_CHECK_LAUNCH();
                     k_chol<T2><<<nb, dim3(kChunk, kChunk), 0, s>>>(G.as<double2>(), Minv.as<T2>(),
                                                                     d_active.as<int>(), alive.as<unsigned char>(),
@@ -649,7 +865,45 @@ struct Compressor {
         std::vector<unsigned char> halive((size_t)nb * rcap_pad);
         VIE_CUDA(cudaMemcpyAsync(halive.data(), alive.p, halive.size(), cudaMemcpyDeviceToHost, s));
         DevBuf RH((size_t)nb * n * std::max(rmax, 1) * sizeof(T2));
-        if (rmax > 0) {
+        if (rmax > 0 && split) {
+            // [Re R^H | Im R^H] = A^T Bh + A_hi^T Bl (A read as 4m x n), joined per block
+            const float2* Qf = reinterpret_cast<const float2*>(Q.p);
+            float2* RHf = reinterpret_cast<float2*>(RH.p);
+            if (mn >= ((int64_t)1 << 22)) {
+                DevBuf Bh((size_t)8 * m * rmax * sizeof(bf16)), Bl((size_t)4 * m * rmax * sizeof(bf16)),
+                    F((size_t)2 * n * rmax * sizeof(float));
+                for (int q = 0; q < nb; ++q) {
+                    if (r[q] <= 0) continue;
+                    const int rq = r[q];
+                    k_split_q<<<dim3((unsigned)std::min<int64_t>(4096, ((int64_t)m * rq + 255) / 256), 1), 256, 0,
+                                s>>>(Qf + (size_t)q * m * rcap_pad, m, rq, 0, Bh.as<bf16>(), 0, Bl.as<bf16>(), 0);
+                    VIE_CHECK_LAUNCH();
+                    gemm_bf16(h, CUBLAS_OP_T, n, 2 * rq, 4 * m, Ap + (size_t)q * 4 * mn, 4 * m, 0, Bh.as<bf16>(),
+                              4 * m, 0, 0.f, F.as<float>(), n, 0, 1);
+                    gemm_bf16(h, CUBLAS_OP_T, n, 2 * rq, 2 * m, Ap + (size_t)q * 4 * mn, 4 * m, 0, Bl.as<bf16>(),
+                              2 * m, 0, 1.f, F.as<float>(), n, 0, 1);
+                    k_join_planes<<<dim3((unsigned)std::min<int64_t>(4096, ((int64_t)n * rq + 255) / 256), 1), 256,
+                                    0, s>>>(F.as<float>(), n, rq, 0, RHf + (size_t)q * n * rmax, 0, nullptr);
+                    VIE_CHECK_LAUNCH();
+                }
+                VIE_CUDA(cudaStreamSynchronize(s));
+            } else {
+                const long long hs = 8LL * m * rmax, ls = 4LL * m * rmax, fs = 2LL * n * rmax;
+                DevBuf Bh((size_t)nb * hs * sizeof(bf16)), Bl((size_t)nb * ls * sizeof(bf16)),
+                    F((size_t)nb * fs * sizeof(float));
+                k_split_q<<<dim3((unsigned)std::min<int64_t>(1024, ((int64_t)m * rmax + 255) / 256), nb), 256, 0,
+                            s>>>(Qf, m, rmax, (int64_t)m * rcap_pad, Bh.as<bf16>(), hs, Bl.as<bf16>(), ls);
+                VIE_CHECK_LAUNCH();
+                gemm_bf16(h, CUBLAS_OP_T, n, 2 * rmax, 4 * m, Ap, 4 * m, 4 * mn, Bh.as<bf16>(), 4 * m, hs, 0.f,
+                          F.as<float>(), n, fs, nb);
+                gemm_bf16(h, CUBLAS_OP_T, n, 2 * rmax, 2 * m, Ap, 4 * m, 4 * mn, Bl.as<bf16>(), 2 * m, ls, 1.f,
+                          F.as<float>(), n, fs, nb);
+                k_join_planes<<<dim3((unsigned)std::min<int64_t>(1024, ((int64_t)n * rmax + 255) / 256), nb), 256, 0,
+                                s>>>(F.as<float>(), n, rmax, fs, RHf, (int64_t)n * rmax, nullptr);
+                VIE_CHECK_LAUNCH();
+                VIE_CUDA(cudaStreamSynchronize(s));
+            }
+        } else if (rmax > 0) {
             const T2 one = mk(T(1), T(0)), zero = mk(T(0), T(0));
             if (mn >= ((int64_t)1 << 22)) {
                 // large blocks: one GEMM per block with its own rank
