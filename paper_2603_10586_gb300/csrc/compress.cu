@@ -7,10 +7,11 @@
 // equally sized blocks is formed on the device and compressed together with
 // a blocked adaptive randomised range finder:
 //   Y = A Omega (Gaussian test matrix), project Y against the current basis
-//   twice (classical Gram-Schmidt, two passes), estimate the residual energy
+//   (classical Gram-Schmidt), estimate the residual energy
 //   ||(I - Q Q^H) A||_F^2 ~ ||Y||_F^2 / s from the projected block, stop when
 //   the estimate is below (tol / 3)^2 ||A||_F^2, else orthonormalise the block
-//   (Cholesky QR twice, Gram matrix accumulated in float64) and append it.
+//   (Cholesky QR twice, the first Gram matrix accumulated to ~48 bits, a
+//   second Gram-Schmidt pass between the two) and append it.
 // The factor-of-3 margin makes a violation of the bound improbable for the
 // 32-column estimator used here (a chi-square tail below 1/9 of its mean).
 // Plain GEMMs go to cuBLAS; the Gram, Cholesky, triangular product, norms,
@@ -126,13 +127,31 @@ __global__ void k_gram_partial(const T2* Y, int m, int64_t stride, int nchunk, d
 struct PlaceJob {
     int dst, row_off, col_off, src;
 };
+// With `planes` (float32 blocks only) the destination is written directly in
+// the split bf16 layout described below (ld = block height).
 template <class T2>
 __global__ void k_place_pairs(const PlaceJob* __restrict__ jobs, const T2* __restrict__ ublk, int np,
-                              T2* const* __restrict__ dst, int64_t ld) {
+                              T2* const* __restrict__ dst, int64_t ld, int planes) {
     const PlaceJob jb = jobs[blockIdx.y];
     const T2* src = ublk + (int64_t)jb.src * np * np;
-    T2* out = dst[jb.dst] + jb.row_off + (int64_t)jb.col_off * ld;
     const int64_t total = (int64_t)np * np;
+    if (planes) {
+        __nv_bfloat16* base = reinterpret_cast<__nv_bfloat16*>(dst[jb.dst]);
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const int c = (int)(e / np), r = (int)(e - (int64_t)c * np);
+            const T2 v = src[e];
+            __nv_bfloat16* col = base + (int64_t)(jb.col_off + c) * 4 * ld + jb.row_off + r;
+            const float x = (float)v.x, y = (float)v.y;
+            const __nv_bfloat16 xh = __float2bfloat16_rn(x), yh = __float2bfloat16_rn(y);
+            col[0] = xh;
+            col[ld] = yh;
+            col[2 * ld] = __float2bfloat16_rn(x - __bfloat162float(xh));
+            col[3 * ld] = __float2bfloat16_rn(y - __bfloat162float(yh));
+        }
+        return;
+    }
+    T2* out = dst[jb.dst] + jb.row_off + (int64_t)jb.col_off * ld;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(e / np), r = (int)(e - (int64_t)c * np);
         out[r + (int64_t)c * ld] = src[e];
@@ -228,20 +247,24 @@ __global__ void __launch_bounds__(kChunk * kChunk) k_chol(const double2* G, T2* 
         if (tx == 0) gmax = v;
     }
     __syncthreads();
-    // right-looking Cholesky: one column per step, the trailing update in parallel
+    // right-looking Cholesky: one column per step, the trailing update in
+    // parallel.  One thread takes the pivot's square root and reciprocal (this
+    // GPU's float64 divide and square root are slow); the column is scaled by
+    // the reciprocal.
+    __shared__ double pinv[kChunk];
     for (int k = 0; k < kChunk; ++k) {
-        const double d = L[k][k].x;
-        const bool dk = !(d > 1e-8 * gmax) || gmax <= 0.0;
+        if (tx == k && ty == k) {
+            const double d = L[k][k].x;
+            const bool dk = !(d > 1e-8 * gmax) || gmax <= 0.0;
+            const double sq = dk ? 1.0 : sqrt(d);
+            pinv[k] = dk ? 0.0 : 1.0 / sq;
+            L[k][k] = make_double2(sq, 0.0);
+            dead[k] = dk;
+        }
         __syncthreads();
-        if (tx == k) {
-            if (ty > k) {
-                double2 v = L[ty][k];
-                double sq = dk ? 0.0 : sqrt(d);
-                L[ty][k] = dk ? make_double2(0, 0) : make_double2(v.x / sq, v.y / sq);
-            } else if (ty == k) {
-                L[k][k] = make_double2(dk ? 1.0 : sqrt(d), 0.0);
-                dead[k] = dk;
-            }
+        if (tx == k && ty > k) {
+            const double2 v = L[ty][k];
+            L[ty][k] = dead[k] ? make_double2(0, 0) : make_double2(v.x * pinv[k], v.y * pinv[k]);
         }
         __syncthreads();
         if (ty > k && tx > k && tx <= ty) {
@@ -252,14 +275,16 @@ __global__ void __launch_bounds__(kChunk * kChunk) k_chol(const double2* G, T2* 
         }
         __syncthreads();
     }
-    // X = L^-1 by forward substitution, all columns at once
+    // X = L^-1 by forward substitution, all columns at once; X is lower
+    // triangular, so column tx only changes from step tx on.  A dead pivot has
+    // L[j][j] = 1 and a zero column below it.
     for (int j = 0; j < kChunk; ++j) {
-        if (ty == j) {
-            const double dj = L[j][j].x;
-            X[j][tx] = make_double2(X[j][tx].x / dj, X[j][tx].y / dj);
+        if (ty == j && tx <= j && !dead[j]) {
+            const double r = pinv[j];
+            X[j][tx] = make_double2(X[j][tx].x * r, X[j][tx].y * r);
         }
         __syncthreads();
-        if (ty > j) {
+        if (ty > j && tx <= j) {
             double2 a = L[ty][j], x = X[j][tx];
             X[ty][tx].x -= a.x * x.x - a.y * x.y;
             X[ty][tx].y -= a.x * x.y + a.y * x.x;
@@ -338,22 +363,28 @@ __device__ __forceinline__ void split_bf16(float x, bf16& hi, bf16& lo) {
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// column per CTA: the whole column is read into shared memory before its
-// bytes are rewritten as the four planes
+// column per CTA (m even): the whole column is read into shared memory
+// before its bytes are rewritten as the four planes, two rows at a time
 __global__ void k_split_cols(float2* A, int m) {
-    extern __shared__ float2 col[];
+    extern __shared__ float4 col4[];
     float2* c = A + (int64_t)blockIdx.x * m;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] = c[i];
+    const int h = m / 2;
+    const float4* c4 = reinterpret_cast<const float4*>(c);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < h; i += blockDim.x) col4[i] = c4[i];
     __syncthreads();
-    bf16* p = reinterpret_cast<bf16*>(c);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        bf16 rh, rl, ih, il;
-        split_bf16(col[i].x, rh, rl);
-        split_bf16(col[i].y, ih, il);
-        p[i] = rh;
-        p[m + i] = ih;
-        p[2 * m + i] = rl;
-        p[3 * m + i] = il;
+    __nv_bfloat162* p = reinterpret_cast<__nv_bfloat162*>(c);
+    for (int i = threadIdx.x; i < h; i += blockDim.x) {
+        const float4 v = col4[i];  // rows 2i (x, y) and 2i + 1 (z, w)
+        bf16 rh0, rl0, ih0, il0, rh1, rl1, ih1, il1;
+        split_bf16(v.x, rh0, rl0);
+        split_bf16(v.y, ih0, il0);
+        split_bf16(v.z, rh1, rl1);
+        split_bf16(v.w, ih1, il1);
+        p[i] = __halves2bfloat162(rh0, rh1);
+        p[h + i] = __halves2bfloat162(ih0, ih1);
+        p[2 * h + i] = __halves2bfloat162(rl0, rl1);
+        p[3 * h + i] = __halves2bfloat162(il0, il1);
     }
 }
 
@@ -534,13 +565,13 @@ struct Compressor {
     }
     // one classical Gram-Schmidt pass of the chunks against their blocks' first K
     // basis columns: C = Q^H Y, Y -= Q C
-    void project(const DevBuf& buf, int L, int K, int m, int ldc) {
+    void project(const DevBuf& buf, int L, int K, int m, int ldc, int ncol) {
         if (L == 0 || K == 0) return;
         T2* const* p = buf.as<T2* const>();
         const T2 one = mk(T(1), T(0)), zero = mk(T(0), T(0)), mone = mk(T(-1), T(0));
-        Blas<T>::gemm_ptr(h, CUBLAS_OP_C, CUBLAS_OP_N, K, kChunk, m, one, (const T2* const*)p, m,
+        Blas<T>::gemm_ptr(h, CUBLAS_OP_C, CUBLAS_OP_N, K, ncol, m, one, (const T2* const*)p, m,
                           (const T2* const*)(p + L), m, zero, p + 2 * L, ldc, L);
-        Blas<T>::gemm_ptr(h, CUBLAS_OP_N, CUBLAS_OP_N, m, kChunk, K, mone, (const T2* const*)p, m,
+        Blas<T>::gemm_ptr(h, CUBLAS_OP_N, CUBLAS_OP_N, m, ncol, K, mone, (const T2* const*)p, m,
                           (const T2* const*)(p + 2 * L), ldc, one, p + L, m, L);
     }
 
@@ -556,8 +587,10 @@ struct Compressor {
     // among the jobs is formed once into a scratch block and copied to every
     // position that holds it; otherwise every job is formed in place.
     // norm (device, per job): squared Frobenius norm of the job's block.
-    void form_pairs(const std::vector<PairJob>& jobs, const std::vector<void*>& dst, const std::vector<int64_t>& ld,
-                    double* norm) {
+    // With `planes` the copies are written in the split bf16 layout; returns
+    // whether they were (the blocks formed in place are complex float32).
+    bool form_pairs(const std::vector<PairJob>& jobs, const std::vector<void*>& dst, const std::vector<int64_t>& ld,
+                    double* norm, bool planes) {
         const int np = op.np;
         if (!op.ctx->no_sharing) {
             double span = 0.0;
@@ -602,14 +635,14 @@ struct Compressor {
                 for (size_t j0 = 0; j0 < place.size(); j0 += 65535) {
                     const int cnt = (int)std::min<size_t>(65535, place.size() - j0);
                     k_place_pairs<T2><<<dim3(std::min(64, (np * np + 255) / 256), cnt), 256, 0, s>>>(
-                        dp.as<PlaceJob>() + j0, ublk.as<T2>(), np, dq.as<T2* const>(), ld[0]);
+                        dp.as<PlaceJob>() + j0, ublk.as<T2>(), np, dq.as<T2* const>(), ld[0], planes ? 1 : 0);
                     VIE_CHECK_LAUNCH();
                 }
                 k_gather_norms<<<((int)place.size() + 255) / 256, 256, 0, s>>>(dp.as<PlaceJob>(), (int)place.size(),
                                                                            unorm.as<double>(), norm);
                 VIE_CHECK_LAUNCH();
                 VIE_CUDA(cudaStreamSynchronize(s));  // scratch goes out of scope
-                return;
+                return planes;
             }
         }
         DevBuf dj, dd, dl;
@@ -617,6 +650,7 @@ struct Compressor {
         upload(dd, dst);
         upload(dl, ld);
         assemble_pairs<T>(op, dj.as<PairJob>(), (int)jobs.size(), dd.as<void* const>(), dl.as<int64_t>(), s, norm);
+        return false;
     }
 
     // compress one batch of equally sized blocks
@@ -630,6 +664,11 @@ struct Compressor {
         const int rcap_pad = ((rcap + kChunk - 1) / kChunk) * kChunk;
         const int64_t mn = (int64_t)m * n;
 
+        // float32 path: the formed blocks become split bf16 planes
+        const char* sp = std::getenv("VIE_COMPRESS_SPLIT");
+        const bool split = std::is_same<T, float>::value && m <= kSplitMaxRows && m % 2 == 0 &&
+                           !(sp && sp[0] == '0');
+        bool in_planes = false;
         // 1. form the blocks (col-major m x n, ld = m) and their squared norms
         DevBuf A((size_t)nb * mn * sizeof(T2)), jobnorm;
         {
@@ -645,7 +684,7 @@ struct Compressor {
                                                j * np});
             }
             jobnorm.alloc(jobs.size() * sizeof(double));
-            form_pairs(jobs, dst, ld, jobnorm.as<double>());
+            in_planes = form_pairs(jobs, dst, ld, jobnorm.as<double>(), split);
         }
         double t1 = mark();
         tim[0] += t1 - t0;
@@ -655,14 +694,11 @@ struct Compressor {
         VIE_CHECK_LAUNCH();
         std::vector<double> hnorm(nb);
         VIE_CUDA(cudaMemcpyAsync(hnorm.data(), normA.p, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
-        // float32 path: the formed blocks become split bf16 planes, in place
-        const char* sp = std::getenv("VIE_COMPRESS_SPLIT");
-        const bool split = std::is_same<T, float>::value && m <= kSplitMaxRows && !(sp && sp[0] == '0');
         const bf16* Ap = reinterpret_cast<const bf16*>(A.p);
-        if (split) {
+        if (split && !in_planes) {  // formed in place as complex float32: split now
             const size_t smem = (size_t)m * sizeof(float2);
             VIE_CUDA(cudaFuncSetAttribute(k_split_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_split_cols<<<(unsigned)((int64_t)nb * n), 256, smem, s>>>(reinterpret_cast<float2*>(A.p), m);
+            k_split_cols<<<(unsigned)((int64_t)nb * n), 512, smem, s>>>(reinterpret_cast<float2*>(A.p), m);
             VIE_CHECK_LAUNCH();
         }
 
@@ -674,7 +710,7 @@ struct Compressor {
         DevBuf Cb((size_t)nb * rcap_pad * kChunk * sizeof(T2));
         DevBuf gpart, G((size_t)nb * kChunk * kChunk * sizeof(double2)), Minv((size_t)nb * kChunk * kChunk * sizeof(T2));
         DevBuf d_active(nb * sizeof(int)), d_rbase(nb * sizeof(int));
-        DevBuf pbuf1((size_t)3 * nb * sizeof(void*)), pbuf2((size_t)3 * nb * sizeof(void*));
+        DevBuf pbuf1((size_t)3 * nb * sizeof(void*)), pbuf2((size_t)3 * nb * sizeof(void*)), Cpan;
         std::vector<int> r(nb, 0), conv(nb, 0);
         // first sketch: the rank prior of this block class (one pass over A), then
         // 32-column passes for the blocks that still need more
@@ -771,18 +807,34 @@ struct Compressor {
               }
               VIE_CUDA(cudaStreamSynchronize(s));  // W goes out of scope
             }
+            // Classical Gram-Schmidt of the new columns: the panel once against the
+            // basis it starts from (one GEMM pair for all of its columns), each
+            // 32-column chunk once against the columns this panel has added, and
+            // after its normalisation once more against the whole basis (Cholesky
+            // QR, pass 2 below).  The blocks still growing all hold rmax
+            // columns; converged ones are left out.
+            const int rp = rmax;
+            if (rp > 0) {
+                std::vector<int> live;
+                for (int q = 0; q < nb; ++q)
+                    if (!conv[q]) live.push_back(q);
+                const size_t need = (size_t)nb * rp * scols * sizeof(T2);
+                if (Cpan.bytes < need) Cpan.alloc(need);
+                proj_ptrs(pbuf1, live, Q.as<T2>(), (int64_t)m * rcap_pad, Y.as<T2>(), (int64_t)m * scols,
+                          Cpan.as<T2>(), (int64_t)rp * scols);
+                project(pbuf1, (int)live.size(), rp, m, rp, scols);
+            }
             for (int c0 = 0; c0 < scols; c0 += kChunk) {
                 T2* Yc = Y.as<T2>() + (int64_t)c0 * m;
                 const long long ys = (long long)m * scols;
                 rmax = *std::max_element(r.begin(), r.end());
-                // the blocks still growing all hold rmax columns; converged ones are left out
                 std::vector<int> live;
                 for (int q = 0; q < nb; ++q)
                     if (!conv[q]) live.push_back(q);
-                if (rmax > 0) {
-                    proj_ptrs(pbuf1, live, Q.as<T2>(), (int64_t)m * rcap_pad, Yc, ys, Cb.as<T2>(),
+                if (rmax > rp) {
+                    proj_ptrs(pbuf1, live, Q.as<T2>() + (int64_t)rp * m, (int64_t)m * rcap_pad, Yc, ys, Cb.as<T2>(),
                               (int64_t)rcap_pad * kChunk);
-                    for (int pass = 0; pass < 2; ++pass) project(pbuf1, (int)live.size(), rmax, m, rcap_pad);
+                    project(pbuf1, (int)live.size(), rmax - rp, m, rcap_pad, kChunk);
                 }
                 sumsq(Yc, (int64_t)m * kChunk, ys, nb, est.as<double>(), part);
                 std::vector<double> he(nb);
@@ -819,7 +871,7 @@ struct Compressor {
                     if (pass == 1 && rmax > 0) {
                         // the normalisation above scales up whatever overlap with the
                         // basis the float32 projection left behind: project once more
-                        project(pbuf2, (int)act.size(), rmax, m, rcap_pad);
+                        project(pbuf2, (int)act.size(), rmax, m, rcap_pad, kChunk);
                     }
                     if (pass == 0) {
                         if constexpr (std::is_same<T2, float2>::value)
