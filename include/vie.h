@@ -82,9 +82,14 @@ enum vie_variant {
     VIE_VAR_SIMT_R8 = 4,
     VIE_VAR_MMA_BF16X3 = 5,     /* warp-level mma.sync, 64-row tiles */
     VIE_VAR_TCGEN05_BF16X3 = 6, /* tcgen05 MMAs with tensor-memory accumulators, 128-row tiles */
-    VIE_VAR_TCGEN05_PACKED_BF16X3 = 7 /* as 6, with the factors split once into bf16 planes in the
-                                         shared-memory stage layout and moved by bulk TMA copies (needs
-                                         ~1.1x the factor memory; runs as 6 when that is not free) */
+    VIE_VAR_TCGEN05_PACKED_BF16X3 = 7, /* as 6, with the factors split once into bf16 planes in the
+                                          shared-memory stage layout and moved by bulk TMA copies (needs
+                                          ~1.1x the factor memory; runs as 6 when that is not free) */
+    VIE_VAR_SIMT_SHARED = 8 /* complex float32, one right-hand side at a time: far blocks that share
+                               their factors (translated copies) are applied together, each factor
+                               element read once per group of up to 8 copies; partial products are
+                               summed per target atom in a fixed order (default for one right-hand
+                               side when the operator has translated copies) */
 };
 
 /* vie_apply flags */

@@ -74,6 +74,7 @@ void op_reserve(Op& op, int nrhs, int precision, cudaStream_t s) {
     if (op.d_t.bytes < need) op.d_t.alloc(need);
     const size_t need_x = (size_t)op.n() * nrhs * sizeof(float4);
     if (op.fprec == VIE_C64 && op.d_xs.bytes < need_x) op.d_xs.alloc(need_x);
+    if (op.fprec == VIE_C64) shared_reserve(op);
 }
 
 void op_precond64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s) {

@@ -408,7 +408,221 @@ __global__ void __launch_bounds__(256, 2) p2m_kernel(const FarBlockDev* __restri
     }
 }
 
+// ---------------------------------------------------------------------------
+// Shared factors, one right-hand side (column `col` of x; t and P hold that
+// column only).  An item covers up to NR blocks of one class (the same R and
+// Q): cmem[item.x .. item.x + item.w) lists them.
+// Phase 1: t_j = R x[S_j] for each member j, every R element read once per
+// item; the row layout and summation order follow p1m_kernel.
+// ---------------------------------------------------------------------------
+template <int NR>
+__global__ void __launch_bounds__(256, 2) p1c_kernel(const FarBlockDev* __restrict__ blocks,
+                                                  const int* __restrict__ batoms, const int4* __restrict__ items,
+                                                  const int* __restrict__ cta_ptr, const int* __restrict__ cmem,
+                                                  const float2* __restrict__ factors, const float2* __restrict__ x,
+                                                  int np, float2* __restrict__ t, const int2* __restrict__ colr,
+                                                  int col) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1]; ++it) {
+        const int4 item = items[it];
+        const int* mem = cmem + item.x;
+        const int nm = item.w;
+        const FarBlockDev B = blocks[mem[0]];
+        if (colr) {
+            const int2 cr = colr[B.prob];
+            if (col < cr.x || col >= cr.y) continue;
+        }
+        const float2* RH = factors + B.rh_off;
+        const int* S[NR];
+        long long to[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const FarBlockDev Bj = blocks[mem[min(r, nm - 1)]];
+            S[r] = batoms + Bj.s_off;
+            to[r] = Bj.tvec_off;
+        }
+        for (int k = item.y + warp * 2; k < item.z; k += nwarps * 2) {
+            const bool two = k + 1 < item.z;
+            const float2* row0 = RH + (int64_t)k * B.n;
+            const float2* row1 = RH + (int64_t)(two ? k + 1 : k) * B.n;
+            float2 a0[NR], a1[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) a0[r] = a1[r] = make_float2(0.f, 0.f);
+            int c = 2 * lane;
+            int slot = c / np, off = c - slot * np;
+            for (; c < B.n; c += 64) {
+                const Pair<float2> ra = ldpair_stream(row0 + c);
+                const Pair<float2> rb = ldpair_stream(row1 + c);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    if (r < nm) {
+                        const Pair<float2> xv = ldpair(x + (int64_t)S[r][slot] * np + off);
+                        mac_conj(a0[r], ra.a, xv.a);
+                        mac_conj(a0[r], ra.b, xv.b);
+                        mac_conj(a1[r], rb.a, xv.a);
+                        mac_conj(a1[r], rb.b, xv.b);
+                    }
+                }
+                off += 64;
+                while (off >= np) { off -= np; ++slot; }
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                float2 v0 = a0[r], v1 = a1[r];
+                for (int o = 16; o > 0; o >>= 1) {
+                    v0 += shfl_down2(v0, o);
+                    v1 += shfl_down2(v1, o);
+                }
+                if (lane == 0 && r < nm) {
+                    t[to[r] + k] = v0;
+                    if (two) t[to[r] + k + 1] = v1;
+                }
+            }
+        }
+    }
+}
+
+// Phase 2 partials: item = (members, target slot sl, rows p0..p1 of the slot
+// packed as p0 | p1 << 16).  P[poff_j + sl np + row] = Q[sl rows] t_j, every
+// Q element read once per item; 64 row pairs x 4 rank groups as in p2m_kernel.
+template <int NR>
+__global__ void __launch_bounds__(256, 2) p2c_kernel(const FarBlockDev* __restrict__ blocks,
+                                                  const int4* __restrict__ items, const int* __restrict__ cta_ptr,
+                                                  const int* __restrict__ cmem, const long long* __restrict__ poff,
+                                                  const float2* __restrict__ factors, const float2* __restrict__ t,
+                                                  int np, float2* __restrict__ P, const int2* __restrict__ colr,
+                                                  int col) {
+    __shared__ float2 red[3][64][2][NR];
+    const int rp = threadIdx.x & 63, kg = threadIdx.x >> 6;
+    for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1]; ++it) {
+        const int4 item = items[it];
+        const int* mem = cmem + item.x;
+        const int nm = item.w, sl = item.y, p0 = item.z & 0xffff, p1 = item.z >> 16;
+        const FarBlockDev B = blocks[mem[0]];
+        if (colr) {
+            const int2 cr = colr[B.prob];
+            if (col < cr.x || col >= cr.y) continue;  // uniform over the CTA
+        }
+        const int row = p0 + 2 * rp;
+        const bool active = row < p1;
+        long long to[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) to[r] = blocks[mem[min(r, nm - 1)]].tvec_off;
+        float2 a0[NR], a1[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) a0[r] = a1[r] = make_float2(0.f, 0.f);
+        if (active) {
+            const float2* Q = factors + B.q_off + (int64_t)sl * np + row;
+            int k = kg;
+            for (; k + 12 < B.rank; k += 16) {
+                Pair<float2> q[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) q[u] = ldpair_stream(Q + (int64_t)(k + 4 * u) * B.m);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int r = 0; r < NR; ++r)
+                        if (r < nm) {
+                            const float2 tv = t[to[r] + k + 4 * u];
+                            mac(a0[r], q[u].a, tv);
+                            mac(a1[r], q[u].b, tv);
+                        }
+            }
+            for (; k < B.rank; k += 4) {
+                const Pair<float2> q = ldpair_stream(Q + (int64_t)k * B.m);
+#pragma unroll
+                for (int r = 0; r < NR; ++r)
+                    if (r < nm) {
+                        const float2 tv = t[to[r] + k];
+                        mac(a0[r], q.a, tv);
+                        mac(a1[r], q.b, tv);
+                    }
+            }
+        }
+        if (kg > 0)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                red[kg - 1][rp][0][r] = a0[r];
+                red[kg - 1][rp][1][r] = a1[r];
+            }
+        __syncthreads();
+        if (kg == 0 && active) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (r >= nm) continue;
+                float2 v0 = a0[r], v1 = a1[r];
+                for (int g = 0; g < 3; ++g) {
+                    v0 += red[g][rp][0][r];
+                    v1 += red[g][rp][1][r];
+                }
+                float2* out = P + poff[mem[r]] + (int64_t)sl * np + row;
+                out[0] = v0;
+                out[1] = v1;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// F[a rows] = sum of the partial products of the (block, slot) entries of atom
+// a, in the order of its entry list (deterministic); one row per thread
+__global__ void __launch_bounds__(128) p2r_kernel(const int4* __restrict__ items, const int* __restrict__ cta_ptr,
+                                                 const int* __restrict__ csr, const int2* __restrict__ ent,
+                                                 const long long* __restrict__ poff, const float2* __restrict__ P,
+                                                 int np, float2* __restrict__ F, const int2* __restrict__ colr,
+                                                 int col) {
+    for (int it = cta_ptr[blockIdx.x]; it < cta_ptr[blockIdx.x + 1]; ++it) {
+        const int4 item = items[it];
+        const int a = item.x, row = item.y + (int)threadIdx.x;
+        if (row >= item.z) continue;
+        if (colr) {
+            const int2 cr = colr[item.w];
+            if (col < cr.x || col >= cr.y) continue;
+        }
+        float2 acc = make_float2(0.f, 0.f);
+        for (int e = csr[a]; e < csr[a + 1]; ++e) {
+            const int2 en = ent[e];
+            acc += P[poff[en.x] + (int64_t)en.y * np + row];
+        }
+        F[(int64_t)a * np + row] = acc;
+    }
+}
+
 }  // namespace
+
+void shared_reserve(Op& op) {
+    const size_t need = (size_t)std::max<int64_t>(op.part_total, 1) * sizeof(float2);
+    if (op.d_part.bytes < need) op.d_part.alloc(need);
+    const size_t nt = (size_t)std::max<int64_t>(op.t_total, 1) * sizeof(float2);
+    if (op.d_t.bytes < nt) op.d_t.alloc(nt);
+}
+
+void apply_far_shared(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s) {
+    shared_reserve(op);
+    const float2* fac = op.fac<float2>();
+    float2* t = op.d_t.as<float2>();
+    float2* P = op.d_part.as<float2>();
+    const FarBlockDev* bl = op.d_blocks.as<FarBlockDev>();
+    for (int c = 0; c < nrhs; ++c) {
+        if (op.n_c1_items > 0) {
+            p1c_kernel<8><<<op.n_cta_c, 256, 0, s>>>(bl, op.d_block_atoms.as<int>(), op.d_c1_items.as<int4>(),
+                                                     op.d_c1_cta.as<int>(), op.d_cmem.as<int>(), fac, x + c * ldx,
+                                                     op.np, t, op.colr, c);
+            VIE_CHECK_LAUNCH();
+        }
+        if (op.n_c2_items > 0) {
+            p2c_kernel<8><<<op.n_cta_c, 256, 0, s>>>(bl, op.d_c2_items.as<int4>(), op.d_c2_cta.as<int>(),
+                                                     op.d_cmem.as<int>(), op.d_poff.as<long long>(), fac, t, op.np,
+                                                     P, op.colr, c);
+            VIE_CHECK_LAUNCH();
+        }
+        p2r_kernel<<<op.n_cta, 128, 0, s>>>(op.d_p2_items.as<int4>(), op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(),
+                                            op.d_p2_ent.as<int2>(), op.d_poff.as<long long>(), P, op.np,
+                                            F + c * ldf, op.colr, c);
+        VIE_CHECK_LAUNCH();
+    }
+}
 
 template <class TF, class TX>
 void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, cudaStream_t s) {

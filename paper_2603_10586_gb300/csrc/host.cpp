@@ -327,6 +327,63 @@ void build_apply_lists(Op& op) {
     upload(op.d_p2_csr, csr);
     upload(op.d_p2_ent, flat.empty() ? std::vector<int2>{make_int2(0, 0)} : flat);
     op.umma_ready = false;
+
+    // shared-factor path: classes of blocks with the same factor storage, in
+    // groups of up to 8 members; phase 1 items of 32 rows of R, phase 2 items
+    // of one target slot and 128 rows of it
+    {
+        std::map<std::pair<long long, int>, std::vector<int>> cls;
+        std::vector<long long> poff(std::max(nb, 1), 0);
+        int64_t ptot = 0;
+        for (int i = 0; i < nb; ++i) {
+            const auto& b = op.blocks[i];
+            poff[i] = ptot;
+            if (b.rank == 0) continue;
+            ptot += (int64_t)b.nt * op.np;
+            cls[{(long long)b.rh_off, op.block_prob.empty() ? 0 : op.block_prob[i]}].push_back(i);
+        }
+        std::vector<int> cmem;
+        std::vector<int4> c1, c2;
+        std::vector<double> v1, v2;
+        int64_t nmem = 0;
+        for (const auto& kv : cls) {
+            const auto& mem = kv.second;
+            nmem += (int64_t)mem.size();
+            const auto& b = op.blocks[mem[0]];
+            for (size_t g = 0; g < mem.size(); g += 8) {
+                const int first = (int)cmem.size();
+                const int cnt = (int)std::min<size_t>(8, mem.size() - g);
+                for (int j = 0; j < cnt; ++j) cmem.push_back(mem[g + j]);
+                for (int k0 = 0; k0 < b.rank; k0 += 32) {
+                    const int k1 = std::min(b.rank, k0 + 32);
+                    c1.push_back(make_int4(first, k0, k1, cnt));
+                    v1.push_back((double)(k1 - k0) * b.n * (1.0 + 0.25 * cnt));
+                }
+                for (int sl = 0; sl < b.nt; ++sl)
+                    for (int p0 = 0; p0 < op.np; p0 += 128) {
+                        const int p1e = std::min(op.np, p0 + 128);
+                        c2.push_back(make_int4(first, sl, p0 | (p1e << 16), cnt));
+                        v2.push_back((double)(p1e - p0) * b.rank * (1.0 + 0.25 * cnt));
+                    }
+            }
+        }
+        op.share_mean = cls.empty() ? 1.0 : (double)nmem / (double)cls.size();
+        op.part_total = ptot;
+        op.n_cta_c = op.ctx->n_sm * 2;
+        std::vector<int4> q1, q2;
+        std::vector<int> e1, e2;
+        pack_lpt(c1, v1, op.n_cta_c, q1, e1);
+        pack_lpt(c2, v2, op.n_cta_c, q2, e2);
+        op.n_c1_items = (int)q1.size();
+        op.n_c2_items = (int)q2.size();
+        upload(op.d_c1_items, q1.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : q1);
+        upload(op.d_c1_cta, e1);
+        upload(op.d_c2_items, q2.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : q2);
+        upload(op.d_c2_cta, e2);
+        upload(op.d_cmem, cmem.empty() ? std::vector<int>{0} : cmem);
+        upload(op.d_poff, poff);
+        op.d_part.release();  // sized on first use (shared_reserve)
+    }
 }
 
 void build_umma_lists(Op& op) {

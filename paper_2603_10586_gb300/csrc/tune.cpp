@@ -2,8 +2,9 @@
 //
 // The far part of a complex float32 apply has several implementations: the
 // SIMT kernels with 1, 2, 4 or 8 right-hand sides per factor read (register
-// tiles), and for split-precision requests the warp-MMA and the tcgen05
-// tensor-core kernels.  Which is fastest depends on the right-hand-side count
+// tiles), the SIMT kernels that apply translated copies of a block together
+// (one factor read per group of copies), and for split-precision requests the
+// warp-MMA and the tcgen05 tensor-core kernels.  Which is fastest depends on the right-hand-side count
 // and on the operator (rank distribution, atom size), so the choice is made by
 // timing on the operator itself and is remembered per power-of-two bucket of
 // the right-hand-side count.
@@ -23,13 +24,15 @@ int bucket(int nrhs) {
 }
 
 bool admissible(int precision, int v) {
-    if (v >= VIE_VAR_SIMT_R1 && v <= VIE_VAR_SIMT_R8) return true;
+    if ((v >= VIE_VAR_SIMT_R1 && v <= VIE_VAR_SIMT_R8) || v == VIE_VAR_SIMT_SHARED) return true;
     return precision == VIE_BF16X3 &&
            (v == VIE_VAR_MMA_BF16X3 || v == VIE_VAR_TCGEN05_BF16X3 || v == VIE_VAR_TCGEN05_PACKED_BF16X3);
 }
 
-int default_variant(int precision, int nrhs) {
-    if (nrhs == 1) return VIE_VAR_SIMT_R1;
+int default_variant(const Op& op, int precision, int nrhs) {
+    // one right-hand side: read shared factors once per group of copies when
+    // the operator has translated copies
+    if (nrhs == 1) return op.share_mean > 1.5 ? VIE_VAR_SIMT_SHARED : VIE_VAR_SIMT_R1;
     if (precision == VIE_BF16X3 && nrhs >= 8) return VIE_VAR_TCGEN05_PACKED_BF16X3;
     return VIE_VAR_SIMT_R4;
 }
@@ -38,7 +41,7 @@ int default_variant(int precision, int nrhs) {
 
 int far_variant(const Op& op, int precision, int nrhs) {
     auto it = op.variant.find({precision, bucket(nrhs)});
-    return it != op.variant.end() ? it->second : default_variant(precision, nrhs);
+    return it != op.variant.end() ? it->second : default_variant(op, precision, nrhs);
 }
 
 void far32(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, int precision, cudaStream_t s) {
@@ -50,6 +53,7 @@ void far32(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrh
         case VIE_VAR_MMA_BF16X3: apply_far_bf16x3(op, x, ldx, F, ldf, nrhs, s); break;
         case VIE_VAR_TCGEN05_BF16X3: apply_far_umma(op, x, ldx, F, ldf, nrhs, s); break;
         case VIE_VAR_TCGEN05_PACKED_BF16X3: apply_far_umma_packed(op, x, ldx, F, ldf, nrhs, s); break;
+        case VIE_VAR_SIMT_SHARED: apply_far_shared(op, x, ldx, F, ldf, nrhs, s); break;
         default: fail(VIE_ERR_STATE, "unknown far-apply variant");
     }
 }
@@ -60,9 +64,10 @@ int tune_far(Op& op, int precision, int nrhs, cudaStream_t s, std::vector<int>& 
     if (nrhs < 1 || nrhs > 1024) fail(VIE_ERR_INVALID_ARG, "vie_tune: 1 to 1024 right-hand sides");
     cand.clear();
     ms.clear();
-    for (int v = VIE_VAR_SIMT_R1; v <= VIE_VAR_TCGEN05_PACKED_BF16X3; ++v) {
+    for (int v = VIE_VAR_SIMT_R1; v <= VIE_VAR_SIMT_SHARED; ++v) {
         if (!admissible(precision, v)) continue;
         if (v >= VIE_VAR_SIMT_R2 && v <= VIE_VAR_SIMT_R8 && nrhs == 1) continue;  // same as R1
+        if (v == VIE_VAR_SIMT_SHARED && nrhs > 1) continue;  // one column at a time
         cand.push_back(v);
     }
     const int64_t n = op.n();

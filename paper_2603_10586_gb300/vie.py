@@ -28,6 +28,7 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED"
 C64, C128, BF16X3, C64_ACC64 = 1, 2, 3, 4
 VAR_SIMT_R1, VAR_SIMT_R2, VAR_SIMT_R4, VAR_SIMT_R8, VAR_MMA_BF16X3, VAR_TCGEN05_BF16X3 = 1, 2, 3, 4, 5, 6
 VAR_TCGEN05_PACKED_BF16X3 = 7
+VAR_SIMT_SHARED = 8
 NOALLOC_SCRATCH_ELEMS = 1 << 22   # VIE_NOALLOC_SCRATCH_ELEMS
 FUSE_PRECOND = 1
 DENSE = 2

@@ -46,8 +46,11 @@ def test_batch_equals_separate_solves(precision):
         I1, st1, s1 = op.solve(kh, pol, tol=1e-6, precision=precision)
         assert s1 == vie.VIE_OK
         assert stats[p]["residual"] <= 1e-6
-        # the same method on the same operator: agreement far below the tolerance
-        assert rel(Is[p], I1) <= 1e-7
+        # the same method on the same operator; the far sums may run in another
+        # order (a single right-hand side takes the shared-factor kernel, the
+        # batch the multi-column one), so the two converged solutions agree to
+        # the solve tolerance rather than to float32 rounding
+        assert rel(Is[p], I1) <= 1e-6
         assert abs(stats[p]["iterations"] - st1["iterations"]) <= 2
     # accuracy against the oracle's dense solve for the two smaller problems
     for p in (0, 2):

@@ -377,6 +377,46 @@ def test_autotune_variants_agree(ctx, tiny_dense):
     op.close()
 
 
+def test_shared_factor_apply(ctx, tiny_dense):
+    # one right-hand side: the translated copies of a block applied together
+    # (each shared factor read once per group of copies, the default when the
+    # operator has copies) against the per-block kernel and the oracle
+    import torch as th
+    P, Z, _, _, _ = tiny_dense
+    g, kh, pol = workloads.config("tiny")
+    op = vie.Operator(ctx, g)
+    op.compress(1e-4, vie.C64)
+    orc, _ = _oracle_op_from_gpu(op, P, Z)
+    xs = workloads.random_complex(P.n, 91, cols=3).T.copy()
+    X = th.from_numpy(xs.astype(np.complex64)).cuda()
+    res = op.tune(vie.C64, 1)
+    assert set(res["ms"]) == {vie.VAR_SIMT_R1, vie.VAR_SIMT_SHARED}
+    out = {}
+    for v in (vie.VAR_SIMT_R1, vie.VAR_SIMT_SHARED):
+        op.tune(vie.C64, 1, force=v)
+        op.tune(vie.C64, 3, force=v)
+        for fl in (0, vie.FUSE_PRECOND):
+            Y = th.zeros_like(X)
+            op.apply(X.data_ptr(), Y.data_ptr(), 1, vie.C64, fl)
+            Y3 = th.zeros_like(X)
+            op.apply(X.data_ptr(), Y3.data_ptr(), 3, vie.C64, fl)   # one column at a time
+            th.cuda.synchronize()
+            out[v, fl] = Y.cpu().numpy()[0]
+            out[v, fl, 3] = Y3.cpu().numpy()
+    for fl in (0, vie.FUSE_PRECOND):
+        assert rel(out[vie.VAR_SIMT_SHARED, fl], out[vie.VAR_SIMT_R1, fl]) < 1e-6
+        assert np.array_equal(out[vie.VAR_SIMT_SHARED, fl, 3][0], out[vie.VAR_SIMT_SHARED, fl])
+    ref = np.stack([orc.apply(x) for x in xs])
+    assert rel(out[vie.VAR_SIMT_SHARED, 0, 3], ref) < 1e-5
+    # deterministic summation order: graph-captured and host-launched solves agree bit for bit
+    op.tune(vie.C64, 1, force=vie.VAR_SIMT_SHARED)
+    Ig, stg, sg = op.solve(kh, pol, tol=1e-6, restart=8, launch=0)
+    Ih, sth, sh = op.solve(kh, pol, tol=1e-6, restart=8, launch=1)
+    assert sg == sh == vie.VIE_OK and np.array_equal(Ig, Ih)
+    assert rel(Ig[:, 0], np.linalg.solve(Z, A.rhs(P, kh[0], pol[0]))) <= 5e-4
+    op.close()
+
+
 def test_tcgen05_packed_equals_unpacked(ctx):
     # the packed variant feeds the tensor core the same bf16 planes in the same
     # MMA order (moved by bulk copies instead of split by the warps): bit-identical
