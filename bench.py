@@ -39,10 +39,10 @@ WORKLOAD = "scale"
 DESC = "16x16 array of eps=12 cubes (side 0.2, pitch 0.4, lambda 1), 6^3 voxels, 193536 unknowns, 1 RHS"
 TOL_COMPRESS = 1e-4
 TOL_SOLVE = 1e-6
-# DRAM bytes (read + write) of one fused single-RHS apply at the bench workload:
-# p1_kernel 8.045 GB + p2_kernel 10.562 GB + type_gemm (~0.01 GB), measured with
-# ncu (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass) on this kernel version
-APPLY_TRAFFIC_BYTES = 18.62e9
+# DRAM bytes (read + write) of one fused single-RHS apply at the bench workload,
+# measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass) on
+# the kernels the apply runs; None until measured for the current kernels
+APPLY_TRAFFIC_BYTES = None
 
 
 def peaks():
@@ -544,8 +544,11 @@ def main():
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "algorithmic_bytes": info["apply_bytes"],
                          "stored_factor_bytes": 8 * info["stored_entries"],
-                         "note": "algorithmic bytes count every far block's factors; translated copies share "
-                                 "storage, so part of them is served by L2",
+                         "stored_frac": 8 * info["stored_entries"] / (apply_ms * 1e-3) / 1e9 / peak,
+                         "note": "algorithmic bytes count every far block's factors (one read per block); "
+                                 "translated copies share storage and the single-RHS kernel reads a shared "
+                                 "factor once per group of up to 8 copies, so it moves fewer bytes: "
+                                 "stored_frac is the stored factor bytes over the same time",
                          "apply_ms": apply_ms, "traffic": APPLY_TRAFFIC_BYTES},
             "e2e": {"value": whole_job_value(world, args.steps, e2e_ms), "unit": "solves/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(16 * n)},
