@@ -41,9 +41,8 @@ TOL_COMPRESS = 1e-4
 TOL_SOLVE = 1e-6
 # DRAM bytes (read + write) of one fused single-RHS apply at the bench workload,
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass) on
-# the shared-factor kernels the apply runs: p1c_kernel 3.551 GB + p2c_kernel
-# 3.759 GB + p2r_kernel 0.088 GB (+ type_gemm, ~0.01 GB)
-APPLY_TRAFFIC_BYTES = 7.41e9
+# the kernels the apply runs; None until measured for the current kernels
+APPLY_TRAFFIC_BYTES = None
 
 
 def peaks():
@@ -548,7 +547,7 @@ def main():
                          "stored_frac": 8 * info["stored_entries"] / (apply_ms * 1e-3) / 1e9 / peak,
                          "note": "algorithmic bytes count every far block's factors (one read per block); "
                                  "translated copies share storage and the single-RHS kernel reads a shared "
-                                 "factor once per group of up to 8 copies, so it moves fewer bytes: "
+                                 "factor once per group of up to 4 copies, so it moves fewer bytes: "
                                  "stored_frac is the stored factor bytes over the same time",
                          "apply_ms": apply_ms, "traffic": APPLY_TRAFFIC_BYTES},
             "e2e": {"value": whole_job_value(world, args.steps, e2e_ms), "unit": "solves/s",

@@ -87,7 +87,7 @@ enum vie_variant {
                                           ~1.1x the factor memory; runs as 6 when that is not free) */
     VIE_VAR_SIMT_SHARED = 8 /* complex float32, one right-hand side at a time: far blocks that share
                                their factors (translated copies) are applied together, each factor
-                               element read once per group of up to 8 copies; partial products are
+                               element read once per group of up to 4 copies; partial products are
                                summed per target atom in a fixed order (default for one right-hand
                                side when the operator has translated copies) */
 };

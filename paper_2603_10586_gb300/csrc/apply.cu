@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(256, 2) p2m_kernel(const FarBlockDev* __restri
 // item; the row layout and summation order follow p1m_kernel.
 // ---------------------------------------------------------------------------
 template <int NR>
-__global__ void __launch_bounds__(256, 2) p1c_kernel(const FarBlockDev* __restrict__ blocks,
+__global__ void __launch_bounds__(256, 3) p1c_kernel(const FarBlockDev* __restrict__ blocks,
                                                   const int* __restrict__ batoms, const int4* __restrict__ items,
                                                   const int* __restrict__ cta_ptr, const int* __restrict__ cmem,
                                                   const float2* __restrict__ factors, const float2* __restrict__ x,
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(256, 2) p1c_kernel(const FarBlockDev* __restri
 // packed as p0 | p1 << 16).  P[poff_j + sl np + row] = Q[sl rows] t_j, every
 // Q element read once per item; 64 row pairs x 4 rank groups as in p2m_kernel.
 template <int NR>
-__global__ void __launch_bounds__(256, 2) p2c_kernel(const FarBlockDev* __restrict__ blocks,
+__global__ void __launch_bounds__(256, 3) p2c_kernel(const FarBlockDev* __restrict__ blocks,
                                                   const int4* __restrict__ items, const int* __restrict__ cta_ptr,
                                                   const int* __restrict__ cmem, const long long* __restrict__ poff,
                                                   const float2* __restrict__ factors, const float2* __restrict__ t,
@@ -606,13 +606,13 @@ void apply_far_shared(Op& op, const float2* x, int64_t ldx, float2* F, int64_t l
     const FarBlockDev* bl = op.d_blocks.as<FarBlockDev>();
     for (int c = 0; c < nrhs; ++c) {
         if (op.n_c1_items > 0) {
-            p1c_kernel<8><<<op.n_cta_c, 256, 0, s>>>(bl, op.d_block_atoms.as<int>(), op.d_c1_items.as<int4>(),
+            p1c_kernel<Op::kShareGroup><<<op.n_cta_c, 256, 0, s>>>(bl, op.d_block_atoms.as<int>(), op.d_c1_items.as<int4>(),
                                                      op.d_c1_cta.as<int>(), op.d_cmem.as<int>(), fac, x + c * ldx,
                                                      op.np, t, op.colr, c);
             VIE_CHECK_LAUNCH();
         }
         if (op.n_c2_items > 0) {
-            p2c_kernel<8><<<op.n_cta_c, 256, 0, s>>>(bl, op.d_c2_items.as<int4>(), op.d_c2_cta.as<int>(),
+            p2c_kernel<Op::kShareGroup><<<op.n_cta_c, 256, 0, s>>>(bl, op.d_c2_items.as<int4>(), op.d_c2_cta.as<int>(),
                                                      op.d_cmem.as<int>(), op.d_poff.as<long long>(), fac, t, op.np,
                                                      P, op.colr, c);
             VIE_CHECK_LAUNCH();

@@ -171,9 +171,10 @@ struct Op {
     int n_t1_items = 0, n_t2_items = 0, n_cta_tc = 0;
     // shared-factor path: blocks with the same factor storage (translated
     // copies) form a class; members of a class are listed together in
-    // d_cmem and each item covers up to 8 of them.  Phase 2 writes one
+    // d_cmem and each item covers up to kShareGroup of them.  Phase 2 writes one
     // partial product per (block, target slot) at d_poff[block] + slot np.
     DevBuf d_cmem, d_c1_items, d_c1_cta, d_c2_items, d_c2_cta, d_poff, d_part;
+    static constexpr int kShareGroup = 4;  // members per item (register tile of the kernels)
     int n_c1_items = 0, n_c2_items = 0, n_cta_c = 0;
     int64_t part_total = 0;             // complex entries of the partial products
     double share_mean = 1.0;            // far blocks per factor class (rank > 0)
@@ -294,7 +295,7 @@ bool umma_pack(Op& op, cudaStream_t s);
 size_t umma_pack_bytes(const Op& op);
 void apply_far_umma_packed(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
 // complex float32 far apply reading each shared factor once per group of up to
-// 8 translated copies (one right-hand side at a time)
+// Op::kShareGroup translated copies (one right-hand side at a time)
 void apply_far_shared(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
 void shared_reserve(Op& op);
 // far part with c64 factors and c128 vectors in double-float arithmetic

@@ -329,8 +329,8 @@ void build_apply_lists(Op& op) {
     op.umma_ready = false;
 
     // shared-factor path: classes of blocks with the same factor storage, in
-    // groups of up to 8 members; phase 1 items of 32 rows of R, phase 2 items
-    // of one target slot and 128 rows of it
+    // groups of up to Op::kShareGroup members; phase 1 items of 32 rows of R,
+    // phase 2 items of one target slot and 128 rows of it
     {
         std::map<std::pair<long long, int>, std::vector<int>> cls;
         std::vector<long long> poff(std::max(nb, 1), 0);
@@ -350,9 +350,10 @@ void build_apply_lists(Op& op) {
             const auto& mem = kv.second;
             nmem += (int64_t)mem.size();
             const auto& b = op.blocks[mem[0]];
-            for (size_t g = 0; g < mem.size(); g += 8) {
+            const size_t G = Op::kShareGroup;
+            for (size_t g = 0; g < mem.size(); g += G) {
                 const int first = (int)cmem.size();
-                const int cnt = (int)std::min<size_t>(8, mem.size() - g);
+                const int cnt = (int)std::min<size_t>(G, mem.size() - g);
                 for (int j = 0; j < cnt; ++j) cmem.push_back(mem[g + j]);
                 for (int k0 = 0; k0 < b.rank; k0 += 32) {
                     const int k1 = std::min(b.rank, k0 + 32);
@@ -369,7 +370,7 @@ void build_apply_lists(Op& op) {
         }
         op.share_mean = cls.empty() ? 1.0 : (double)nmem / (double)cls.size();
         op.part_total = ptot;
-        op.n_cta_c = op.ctx->n_sm * 2;
+        op.n_cta_c = op.ctx->n_sm * 3;
         std::vector<int4> q1, q2;
         std::vector<int> e1, e2;
         pack_lpt(c1, v1, op.n_cta_c, q1, e1);
