@@ -41,8 +41,9 @@ TOL_COMPRESS = 1e-4
 TOL_SOLVE = 1e-6
 # DRAM bytes (read + write) of one fused single-RHS apply at the bench workload,
 # measured with ncu (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass) on
-# the kernels the apply runs; None until measured for the current kernels
-APPLY_TRAFFIC_BYTES = None
+# the shared-factor kernels the apply runs (groups of 4 copies): p1c_kernel
+# 3.797 GB + p2c_kernel 4.020 GB + p2r_kernel 0.088 GB (+ type_gemm, ~0.01 GB)
+APPLY_TRAFFIC_BYTES = 7.92e9
 
 
 def peaks():
