@@ -345,12 +345,13 @@ __global__ void k_gather_cols(const T2* src, int64_t rows, const long long* src_
 // ------------------------------------------- split bf16 operands (float32 path)
 // The sketch Y = A Omega and the projection R^H = A^H Q run as real bf16
 // GEMMs with float32 accumulation on split operands: every float32 value x is
-// carried as hi = bf16(x) and lo = bf16(x - hi) (16 significant bits, relative
-// error <= 2^-17).  Omega is drawn in bf16 (a Gaussian rounded to bf16 is as
-// good a test matrix), so the sketch needs hi and lo of A only (two products);
-// R^H takes hi.hi + hi.lo + lo.hi.  Both errors are ~1e-5 relative, well
-// inside the tol / 3 margin of the range finder at the float32 tolerances
-// (1e-4 .. 1e-3); the Gram-Schmidt projections keep float32 accuracy.
+// carried as hi = bf16(x) and lo = bf16(x - hi) (16 significant bits: each
+// rounding to bf16 is within 2^-8 relative, so |x - hi - lo| <= 2^-16 |x|).
+// Omega is drawn in bf16 (a Gaussian rounded to bf16 is as good a test
+// matrix), so the sketch needs hi and lo of A only (two products); R^H takes
+// hi.hi + hi.lo + lo.hi.  Both errors stay below ~1e-5 relative, inside the
+// tol / 3 margin of the range finder at the float32 tolerances (1e-4 ..
+// 1e-3); the Gram-Schmidt projections keep float32 accuracy.
 //
 // Layout of a formed block after the split: column j of A (8 m bytes as
 // complex float32) holds, in the same bytes, [Re hi | Im hi | Re lo | Im lo],
