@@ -81,3 +81,70 @@ def test_footprint_model_is_monotone(lib):
     assert vie.footprint_bytes(20000, 108, 1, 60, 10 ** 7) > a
     assert vie.footprint_bytes(10000, 108, 4, 60, 10 ** 7) > a
     assert vie.footprint_bytes(10000, 108, 1, 60, 10 ** 8) > a
+
+
+STRUCTS = {  # C struct of include/vie.h -> ctypes class of the binding
+    "vie_ctx_opts": "CtxOpts", "vie_geometry": "GeometryC", "vie_op_info": "OpInfo",
+    "vie_incident": "IncidentC", "vie_solve_opts": "SolveOpts", "vie_tune_result": "TuneResult",
+    "vie_solve_stats": "SolveStats", "vie_serve_opts": "ServeOpts", "vie_request": "RequestC",
+    "vie_result": "ResultC",
+}
+
+
+def test_struct_layouts_match_binding(tmp_path):
+    # a layout drift between the header and the ctypes binding would pass wrong
+    # arguments silently: compile the header with the host compiler and compare
+    # every struct's size and every field's offset
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2603_10586_gb300 import vie
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vie.h"', "int main(void) {"]
+    expect = []
+    for cname, pyname in STRUCTS.items():
+        cls = getattr(vie, pyname)
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        expect.append(ctypes.sizeof(cls))
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {fname}));')
+            expect.append(getattr(cls, fname).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
+
+
+def test_header_constants_match_binding():
+    from paper_2603_10586_gb300 import vie
+    src = open(os.path.join(ROOT, "include", "vie.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"\b(VIE_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    consts.update({k: int(v) for k, v in re.findall(r"#define\s+(VIE_[A-Z0-9_]+)\s+(-?\d+)\b", src)})
+    consts["VIE_NOALLOC_SCRATCH_ELEMS"] = 1 << 22
+    assert re.search(r"#define\s+VIE_NOALLOC_SCRATCH_ELEMS\s+\(1LL << 22\)", src)
+    rename = {"VIE_APPLY_FUSE_PRECOND": "FUSE_PRECOND", "VIE_APPLY_DENSE": "DENSE",
+              "VIE_NOALLOC_SCRATCH_ELEMS": "NOALLOC_SCRATCH_ELEMS"}
+    checked = 0
+    for name, value in consts.items():
+        if name in rename:
+            py = rename[name]
+        elif name.startswith("VIE_VAR_"):
+            py = name[4:]
+        elif name.startswith("VIE_ERR_") or name == "VIE_OK":
+            py = name
+        else:
+            py = name[4:]
+        if not hasattr(vie, py):
+            continue
+        assert getattr(vie, py) == value, (name, py)
+        checked += 1
+    for name in ("VIE_OK", "VIE_ERR_INVALID_ARG", "VIE_C64", "VIE_BF16X3", "VIE_VAR_SIMT_SHARED",
+                 "VIE_APPLY_FUSE_PRECOND"):
+        assert name in consts
+    assert checked >= 20
