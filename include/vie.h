@@ -222,8 +222,12 @@ int vie_op_get_info(const vie_op* op, vie_op_info* info);
 int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int precision,
               int flags, vie_stream stream);
 
-/* vie_apply_noalloc: y = Zs x exactly as vie_apply(op, x, y, nrhs, ld, VIE_C64, 0,
- * stream) computes it, but without allocating any device memory.  The paper
+/* vie_apply_noalloc: y = Zs x, the same product as vie_apply(op, x, y, nrhs, ld,
+ * VIE_C64, 0, stream) to float32 rounding (the summation order differs), but
+ * without allocating any device memory.  It always runs the per-column SIMT
+ * kernels, so for nrhs > 1 every factor is read once per column (up to nrhs
+ * times the traffic of vie_apply, which reads a factor once for all columns).
+ * The paper
  * has no counterpart: it is an interface for callers that cannot call
  * cudaMalloc between set-up and use, for instance code whose device memory is
  * all handed to its own pool allocator (a new cudaMalloc could fail or
@@ -237,7 +241,9 @@ int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int prec
  *    before anything is launched.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the life of the
+ *    process: do not call this entry point again after cudaDeviceReset on
+ *    that device (the reset destroys the context the address belongs to).
  *  - Every call on a device shares the one array and overwrites it; nothing
  *    in it has to start at zero.  Calls that overlap on the GPU (different
  *    streams, or different operators on one device) race on the array: order

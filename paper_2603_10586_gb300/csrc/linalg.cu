@@ -102,12 +102,16 @@ __global__ void c64_to_c128(const float2* s, double2* d, int64_t n) {
 // lives at a * np + r + c * ld.  32 x 32 output tile per CTA (enough CTAs for a
 // few hundred atoms), 256 threads, each a 2 x 2 sub-tile; K staged through
 // shared memory 32 at a time.
+// ADD may be Y itself (y = Z_ii x + y in place): every output element is read
+// from ADD and then written to Y by the one thread that owns it, so ADD and Y
+// carry no __restrict__ and ADD is read through the ordinary (coherent) path.
+// B must not overlap Y.
 // ---------------------------------------------------------------------------
 template <class TM, class TX>
 __global__ void __launch_bounds__(256) type_gemm(const TM* __restrict__ M, int np, const int* __restrict__ atoms,
                                                  int n_atoms, int nrhs, const TX* __restrict__ B, int64_t ldb,
-                                                 const TX* __restrict__ ADD, int64_t ldadd, TX* __restrict__ Y,
-                                                 int64_t ldy, const int2* __restrict__ colr, int prob) {
+                                                 const TX* ADD, int64_t ldadd, TX* Y, int64_t ldy,
+                                                 const int2* __restrict__ colr, int prob) {
     using R = decltype(TM().x);
     using TA = typename C2<R>::t;
     constexpr int BM = 32, BN = 32, BK = 32;
