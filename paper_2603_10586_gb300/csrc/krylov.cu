@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kT) k_mdot(KrylovArgs a, const TW* __restrict_
         if (col < ncols) {
             double2 s = make_double2(0.0, 0.0);
             for (int w2 = 0; w2 < kT / 32; ++w2) s += sh[w2][threadIdx.x];
-            a.part[((int64_t)i * 64 + col) * gridDim.x + blockIdx.x] = s;
+            a.part[((int64_t)i * a.hs + col) * gridDim.x + blockIdx.x] = s;
         }
     }
 }
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kT) k_reduce(KrylovArgs a, int nchunk) {
     const int j = a.ctr[KR_J];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int col = wid; col <= j; col += kT / 32) {
-        const double2* p = a.part + ((int64_t)i * 64 + col) * nchunk;
+        const double2* p = a.part + ((int64_t)i * a.hs + col) * nchunk;
         double re = 0.0, im = 0.0;
         for (int x = lane; x < nchunk; x += 32) {
             re += p[x].x;
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kT) k_reduce(KrylovArgs a, int nchunk) {
         }
         if (lane == 0) {
             const double2 s = make_double2(re, im);
-            a.h[i * 64 + col] = s;
+            a.h[(int64_t)i * a.hs + col] = s;
             double2* Hc = a.H + ((int64_t)i * a.m + j) * (a.m + 1);
             if (kFirst) Hc[col] = s;
             else Hc[col] += s;
@@ -197,9 +197,9 @@ __global__ void __launch_bounds__(kT) k_maxpy(KrylovArgs a) {
     const int i = blockIdx.y;
     if (!a.cycling[i]) return;
     const int j = a.ctr[KR_J];
-    __shared__ double2 hs[64];
+    __shared__ double2 hs[kMaxRestart + 1];
     __shared__ double sh[kT / 32];
-    if ((int)threadIdx.x <= j) hs[threadIdx.x] = a.h[i * 64 + threadIdx.x];
+    for (int c = threadIdx.x; c <= j; c += kT) hs[c] = a.h[(int64_t)i * a.hs + c];
     __syncthreads();
     const Rows R = rows_of(a, a.cols[i]);
     const int64_t n = R.len;
@@ -302,7 +302,7 @@ __global__ void k_backsub(KrylovArgs a, int k) {
     const int jd = a.jdone[i], m = a.m;
     const double2* H = a.H + (int64_t)i * m * (m + 1);
     const double2* g = a.g + (int64_t)i * (m + 1);
-    double2* y = a.y + (int64_t)i * 64;
+    double2* y = a.y + (int64_t)i * a.hs;
     for (int r = jd - 1; r >= 0; --r) {
         double2 acc = g[r];
         for (int l = r + 1; l < jd; ++l) acc -= cmul(H[r + (int64_t)l * (m + 1)], y[l]);
@@ -316,8 +316,8 @@ __global__ void __launch_bounds__(kT) k_xupdate(KrylovArgs a, double2* __restric
     const int i = blockIdx.y;
     const int jd = a.jdone[i];
     if (jd == 0) return;
-    __shared__ double2 ys[64];
-    if ((int)threadIdx.x < jd) ys[threadIdx.x] = a.y[(int64_t)i * 64 + threadIdx.x];
+    __shared__ double2 ys[kMaxRestart];
+    for (int l = threadIdx.x; l < jd; l += kT) ys[l] = a.y[(int64_t)i * a.hs + l];
     __syncthreads();
     const Rows R = rows_of(a, a.cols[i]);
     const int64_t n = R.len;

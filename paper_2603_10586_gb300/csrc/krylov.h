@@ -5,6 +5,9 @@
 
 namespace vie {
 
+// Longest restart cycle (basis vectors per right-hand side, minus one).
+constexpr int kMaxRestart = 512;
+
 // Counters kept on the device.
 enum : int {
     KR_J = 0,        // Arnoldi step within the current restart cycle
@@ -27,7 +30,8 @@ struct KrylovArgs {
     const long long* col_lo;
     const long long* col_len;
     const long long* col_voff;
-    int m;            // restart length (<= 63)
+    int m;            // restart length (<= kMaxRestart)
+    int hs;           // per-slot stride of h, y and the projection partials (>= m + 1)
     int nblk_max;     // row blocks the norm partials are laid out for
     double tol;
     int maxit;
@@ -36,9 +40,9 @@ struct KrylovArgs {
     double2* g;       // [slot][m+1] rotated right-hand side of the least-squares problem
     double2* cs;      // [slot][m] Givens cosines
     double2* sn;      // [slot][m] Givens sines
-    double2* h;       // [slot][64] coefficients of the current Gram-Schmidt pass
-    double2* y;       // [slot][64] least-squares solution of the cycle
-    double2* part;    // [slot][64][nchunk] projection partial sums
+    double2* h;       // [slot][hs] coefficients of the current Gram-Schmidt pass
+    double2* y;       // [slot][hs] least-squares solution of the cycle
+    double2* part;    // [slot][hs][nchunk] projection partial sums
     double* npart;    // [slot][nblk_max] squared-norm partial sums
     double* nsq;      // [slot] their total
     double* inv;      // [slot] scale the next gather applies to its basis column

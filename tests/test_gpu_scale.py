@@ -68,30 +68,52 @@ def test_scale_product_error_against_uncompressed(scale_op):
     assert eps_prod < 1e-4
 
 
-def test_scale_sampled_blocks_error_bound(scale_op):
+def _mate(blocks, lev, b):
+    return [j for j, c in enumerate(blocks) if c["level"] == lev and
+            list(c["tatoms"]) == list(b["satoms"]) and list(c["satoms"]) == list(b["tatoms"])][0]
+
+
+def test_scale_sampled_blocks_error_bound_against_oracle(scale_op):
+    # levels 3 and 4 (3,024^2 and 756^2 blocks): ||A - Q R||_F <= 1e-4 ||A||_F with
+    # A assembled by the oracle in float64, on the first, middle and last block
+    op, g, _, _ = scale_op
+    P = problem_from_geometry(g)
+    blocks = op.far_blocks(with_factors=False)
+    ids = {}
+    for i, b in enumerate(blocks):
+        ids.setdefault(b["level"], []).append(i)
+    assert sorted(ids) == [2, 3, 4]
+    for lev, sample in ((3, (ids[3][0], ids[3][-1])), (4, (ids[4][0], ids[4][len(ids[4]) // 2], ids[4][-1]))):
+        for i in sample:
+            b = op.far_blocks(indices=[i])[0]
+            Ab = np.block([[A.cross_block(P, int(a), int(c)) for c in b["satoms"]] for a in b["tatoms"]])
+            err = np.linalg.norm(Ab - b["Q"] @ b["R"]) / np.linalg.norm(Ab)
+            assert err <= 1e-4, (lev, i, err)
+            if i < _mate(blocks, lev, b):   # compressed block of its mirror pair: orthonormal Q
+                assert np.linalg.norm(b["Q"].conj().T @ b["Q"] - np.eye(b["rank"])) < 1e-4
+
+
+def test_scale_level2_blocks_error_bound(scale_op):
+    # level 2 (12,096^2, 256 atom pairs each): A from the device's float64
+    # assembly, which equals the oracle's entries to 1e-12 (test_cross_block)
     op, g, _, _ = scale_op
     npp = op.np
     blocks = op.far_blocks(with_factors=False)
-    first = {}
-    for i, b in enumerate(blocks):
-        first.setdefault(b["level"], []).append(i)
-    for lev, ids in first.items():
-        for i in (ids[0], ids[len(ids) // 2], ids[-1]):
-            b = op.far_blocks(indices=[i])[0]
-            Ab = torch.zeros((len(b["tatoms"]) * npp, len(b["satoms"]) * npp), dtype=torch.complex128, device="cuda")
-            for p, a in enumerate(b["tatoms"]):
-                for q, c in enumerate(b["satoms"]):
-                    blk = op.export_block(1, int(a), int(c), vie.C64)
-                    Ab[p * npp:(p + 1) * npp, q * npp:(q + 1) * npp] = torch.from_numpy(np.ascontiguousarray(blk)).cuda()
-            Q = torch.from_numpy(b["Q"]).cuda()
-            R = torch.from_numpy(b["R"]).cuda()
-            err = (torch.linalg.norm(Ab - Q @ R) / torch.linalg.norm(Ab)).item()
-            assert err <= 1.05e-4, (lev, i, err)   # entries in float32 (relative 1e-6)
-            mate = [j for j, c in enumerate(blocks) if c["level"] == lev and
-                    list(c["tatoms"]) == list(b["satoms"]) and list(c["satoms"]) == list(b["tatoms"])][0]
-            if i < mate:   # compressed block of its mirror pair: orthonormal Q
-                eye = torch.eye(b["rank"], dtype=Q.dtype, device="cuda")
-                assert torch.linalg.norm(Q.conj().T @ Q - eye).item() < 1e-4
+    ids = [i for i, b in enumerate(blocks) if b["level"] == 2]
+    for i in (ids[0], ids[len(ids) // 2], ids[-1]):
+        b = op.far_blocks(indices=[i])[0]
+        Ab = torch.zeros((len(b["tatoms"]) * npp, len(b["satoms"]) * npp), dtype=torch.complex128, device="cuda")
+        for p, a in enumerate(b["tatoms"]):
+            for q, c in enumerate(b["satoms"]):
+                blk = op.export_block(1, int(a), int(c), vie.C128)
+                Ab[p * npp:(p + 1) * npp, q * npp:(q + 1) * npp] = torch.from_numpy(np.ascontiguousarray(blk)).cuda()
+        Q = torch.from_numpy(b["Q"]).cuda()
+        R = torch.from_numpy(b["R"]).cuda()
+        err = (torch.linalg.norm(Ab - Q @ R) / torch.linalg.norm(Ab)).item()
+        assert err <= 1e-4, (i, err)
+        if i < _mate(blocks, 2, b):
+            eye = torch.eye(b["rank"], dtype=Q.dtype, device="cuda")
+            assert torch.linalg.norm(Q.conj().T @ Q - eye).item() < 1e-4
 
 
 def test_scale_apply_parity_sampled_atoms(scale_op):
