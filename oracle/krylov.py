@@ -91,3 +91,45 @@ def gmres(apply_A, b, precond=None, tol=1e-6, restart=None, maxiter=5000):
         r = M(b - apply_A(x))
         if np.linalg.norm(r) / beta0 <= tol:
             return x, dict(iterations=it, history=hist, converged=True)
+
+
+def bicgstab(apply_A, b, precond=None, tol=1e-6, maxiter=5000):
+    """Left-preconditioned BiCGStab (van der Vorst, 1992), the Krylov method the
+    paper weighs against GMRES in Sec. 6, on M^-1 A x = M^-1 b with x0 = 0.
+    Complex inner products <u, v> = sum conj(u) v; the shadow residual is the
+    initial residual.  Stops when the (recursively updated) preconditioned
+    residual satisfies ||r|| / ||M^-1 b|| <= tol.  Returns (x, info) with info =
+    dict(iterations, history, converged)."""
+    M = precond if precond is not None else (lambda v: v)
+    op = lambda v: M(apply_A(v))  # noqa: E731
+    b = np.asarray(b, complex)
+    x = np.zeros_like(b)
+    r = M(b)
+    beta0 = np.linalg.norm(r)
+    hist = []
+    if beta0 == 0:
+        return x, dict(iterations=0, history=hist, converged=True)
+    rhat = r.copy()
+    rho = alpha = omega = 1.0 + 0.0j
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    for it in range(1, maxiter + 1):
+        rho_new = np.vdot(rhat, r)
+        beta = (rho_new / rho) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = op(p)
+        alpha = rho_new / np.vdot(rhat, v)
+        s = r - alpha * v
+        t = op(s)
+        tt = np.vdot(t, t)
+        omega = np.vdot(t, s) / tt if tt != 0 else 0.0
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        rho = rho_new
+        res = np.linalg.norm(r) / beta0
+        hist.append(res)
+        if res <= tol:
+            return x, dict(iterations=it, history=hist, converged=True)
+        if omega == 0:
+            break
+    return x, dict(iterations=len(hist), history=hist, converged=False)

@@ -193,3 +193,49 @@ def test_compressed_solve_matches_dense_direct(tiny):
     assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 5e-4
     _, info0 = K.gmres(lambda v: Z @ v, b, None, tol=1e-6)
     assert info0["iterations"] > info["iterations"]          # the preconditioner helps
+
+
+# ------------------------------------------------------------------- BiCGStab
+def test_bicgstab_matches_library_solve():
+    # a well-conditioned complex system: the BiCGStab iterate converges to the
+    # LAPACK solution
+    rng = np.random.default_rng(21)
+    n = 60
+    Amat = np.eye(n) + 0.3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, info = K.bicgstab(lambda v: Amat @ v, b, tol=1e-12)
+    assert info["converged"]
+    ref = np.linalg.solve(Amat, b)
+    assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
+    # the recursively updated residual is the true one (up to rounding)
+    assert np.linalg.norm(b - Amat @ x) <= 1e-11 * np.linalg.norm(b)
+
+
+def test_bicgstab_two_eigenvalues_terminates_in_two_steps():
+    # r_k = Q_k(A) P_k(A) r_0 with P_k the BiCG polynomial: for a matrix with two
+    # distinct eigenvalues P_2(A) r_0 = 0, so the second iterate is exact
+    rng = np.random.default_rng(4)
+    d = np.where(np.arange(40) % 2 == 0, 1.0, 3.0 - 0.5j)
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 40)) + 1j * rng.standard_normal((40, 40)))
+    Amat = Q @ np.diag(d) @ Q.conj().T
+    b = rng.standard_normal(40) + 1j * rng.standard_normal(40)
+    x, info = K.bicgstab(lambda v: Amat @ v, b, tol=1e-12)
+    assert info["iterations"] <= 2
+    assert np.linalg.norm(Amat @ x - b) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_bicgstab_identity_one_step():
+    b = np.arange(1, 9) * (1 - 0.5j)
+    x, info = K.bicgstab(lambda v: v, b, tol=1e-14)
+    assert info["iterations"] == 1 and np.allclose(x, b, rtol=0, atol=1e-14)
+
+
+def test_bicgstab_preconditioned_vie_solve(tiny):
+    # the 4x4 array with the block-Jacobi preconditioner: the same solution as
+    # the dense direct solve, to the solve tolerance times the conditioning
+    P, Z, b = tiny
+    sb = {0: Z[:P.offsets[1], :P.offsets[1]]}
+    x, info = K.bicgstab(lambda v: Z @ v, b, K.BlockJacobi(P, sb).apply, tol=1e-8)
+    assert info["converged"]
+    ref = np.linalg.solve(Z, b)
+    assert np.linalg.norm(x - ref) <= 1e-6 * np.linalg.norm(ref)
