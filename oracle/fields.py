@@ -8,11 +8,14 @@ Units eps0 = mu0 = c = 1 (so omega = k and the wave impedance is 1), e^{j w t}.
   sigma_sca = closed-surface integral of |F|^2 over the unit sphere
   sigma_ext = Re(I^H v0) / |E0|^2     (power taken from the incident wave)
   p         = int J dV / (j w)                                  (dipole moment)
-The far field uses Gauss-Legendre with Q_SELF points per voxel axis.
+  E_sca(r)  = -j k int J g dV' + (1 / (j k)) grad int q g dV'    (scattered near field,
+              r outside the atoms; q = div J with the boundary sheets: Sec. 2, eq. IntEq)
+The far and near fields use Gauss-Legendre with Q_SELF points per voxel axis
+(per face axis for the charge sheets).
 """
 import numpy as np
 
-from .assembly import voxel_points, _profiles, Q_SELF
+from .assembly import voxel_points, surface_points, _profiles, Q_SELF, FOUR_PI
 
 
 def _voxel_moments(prob, I, rhat, q=Q_SELF):
@@ -94,3 +97,53 @@ def current_at_voxel_centres(prob, I_sol):
                 J[v, mesh.face_dir[f]] += Ia[f] * 0.5 / mesh.h ** 2
         out.append(J)
     return np.concatenate(out)
+
+
+def near_field(prob, I_sol, points, q=Q_SELF):
+    """Scattered field E_sca at points outside the atoms (npts, 3) -> (npts, 3).
+
+    From the potentials of the current and its charge (units eps0 = mu0 = 1,
+    w = k): E = -j k A + (1 / (j k)) grad Phi, A = int J g, Phi = int q g, with
+    q the distributional divergence of J (volume density per voxel plus the
+    boundary sheets), so that -E_sca tested with w_i gives the (j k L + D /
+    (j k)) rows of the Galerkin system (Sec. 3).  grad_r g(r - r') =
+    -(1 + j k R) exp(-j k R) / (4 pi R^2) Rhat."""
+    pts = np.atleast_2d(np.asarray(points, float))
+    k = prob.k
+    E = np.zeros((len(pts), 3), complex)
+    for a in range(prob.n_atoms):
+        mesh = prob.mesh(a)
+        org = prob.origin(a)
+        Ia = I_sol[prob.offsets[a]:prob.offsets[a + 1]]
+        P, w, xi = voxel_points(mesh, org, q)                      # (nvox, q^3, 3)
+        ps = _profiles(xi)                                         # (3, 2, q^3)
+        J = np.zeros((mesh.n_vox, len(w), 3), complex)
+        qv = np.zeros(mesh.n_vox, complex)
+        qs = np.zeros(len(mesh.surf_face), complex)
+        for f in range(mesh.n_faces):
+            d = mesh.face_dir[f]
+            for v, prof in mesh.face_voxels(f):
+                J[v, :, d] += Ia[f] * ps[d, 0 if prof > 0 else 1] / mesh.h ** 2
+            vol, sur = mesh.face_charges(f)
+            for v, c in vol:
+                qv[v] += Ia[f] * c
+            for s_, c in sur:
+                qs[s_] += Ia[f] * c
+        S, sw = surface_points(mesh, org, q)                       # (nsurf, q^2, 3)
+        src_v = P.reshape(-1, 3)
+        for i, r in enumerate(pts):
+            D = r[None, :] - src_v
+            R = np.sqrt((D * D).sum(1))
+            g = np.exp(-1j * k * R) / (FOUR_PI * R)
+            dg = (-(1 + 1j * k * R) * g / R ** 2)[:, None] * D     # grad_r g
+            wv = np.tile(w, mesh.n_vox)
+            E[i] += -1j * k * (wv[:, None] * g[:, None] * J.reshape(-1, 3)).sum(0)
+            E[i] += (1.0 / (1j * k)) * ((wv * np.repeat(qv, len(w)))[:, None] * dg).sum(0)
+            if len(qs):
+                Ds = r[None, :] - S.reshape(-1, 3)
+                Rs = np.sqrt((Ds * Ds).sum(1))
+                gs = np.exp(-1j * k * Rs) / (FOUR_PI * Rs)
+                dgs = (-(1 + 1j * k * Rs) * gs / Rs ** 2)[:, None] * Ds
+                ws = np.tile(sw, len(qs)) * np.repeat(qs, len(sw))
+                E[i] += (1.0 / (1j * k)) * (ws[:, None] * dgs).sum(0)
+    return E

@@ -207,3 +207,31 @@ def test_current_at_voxel_centres_integrates_to_dipole_moment():
     total = (J * vol[:, None]).sum(0)
     p = F.dipole_moment(P, I)
     assert np.allclose(total, 1j * P.k * p, rtol=1e-12, atol=0)
+
+
+def test_near_field_tends_to_far_field(tiny):
+    # far from the array the near field is F(rhat) exp(-j k r) / r up to terms
+    # of relative order 1/(k r) and k D^2 / r
+    P, Z, kh, pol = tiny
+    I = np.linalg.solve(Z, A.rhs(P, kh, pol))
+    dirs = np.array([[0.0, 0.0, 1.0], [0.6, 0.0, 0.8], [0.0, -0.6, -0.8], [1.0, 0.0, 0.0]])
+    r = 2.0e4
+    E = F.near_field(P, I, r * dirs)
+    ref = F.far_field(P, I, dirs) * np.exp(-1j * P.k * r) / r
+    assert np.linalg.norm(E - ref) <= 1e-3 * np.linalg.norm(ref)
+
+
+def test_near_field_of_small_cube_is_the_dipole_field():
+    # a cube of side 0.01 lambda seen from 0.3 lambda: the field of its dipole
+    # moment p, k^2 (n x p) x n / r + (3 n (n.p) - p) (1/r^3 + j k/r^2), times
+    # exp(-j k r) / (4 pi), to the cube's octupole order (a/r)^2
+    P, I, v0, p = _single_cube_alpha(0.01, 2)
+    k = P.k
+    pts = np.array([[0.3, 0.0, 0.0], [0.0, 0.3, 0.0], [0.0, 0.0, -0.3], [0.2, 0.1, 0.15]])
+    E = F.near_field(P, I, pts)
+    for i, x in enumerate(pts):
+        rr = np.linalg.norm(x)
+        n = x / rr
+        Ed = (k * k * np.cross(np.cross(n, p), n) / rr + (3 * n * np.dot(n, p) - p) * (1 / rr ** 3 + 1j * k / rr ** 2))
+        Ed = Ed * np.exp(-1j * k * rr) / (4 * np.pi)
+        assert np.linalg.norm(E[i] - Ed) <= 5e-3 * np.linalg.norm(Ed), i
