@@ -89,7 +89,13 @@ enum vie_variant {
                                their factors (translated copies) are applied together, each factor
                                element read once per group of up to 4 copies; partial products are
                                summed per target atom in a fixed order (default for one right-hand
-                               side when the operator has translated copies) */
+                               side when the operator has translated copies) */,
+    VIE_VAR_TCGEN05_WS_BF16X3 = 9 /* the MMAs and planes of 7 in a warp-specialised persistent kernel
+                                     (one CTA per SM): a producer warp group fills a four-stage
+                                     shared-memory ring (bulk TMA copies of the A planes, split B),
+                                     one thread issues the MMAs, four warps drain two tensor-memory
+                                     accumulator buffers; bit-identical to 7 (default for 8+
+                                     right-hand sides; runs as 6 when the planes do not fit) */
 };
 
 /* vie_apply flags */
@@ -97,6 +103,8 @@ enum vie_variant {
 #define VIE_APPLY_DENSE 2        /* y = Zs x with the uncompressed operator: every
                                     block regenerated on the device and never stored
                                     (accuracy reference; 1 RHS; C64 or C128) */
+#define VIE_APPLY_ADJOINT 4      /* y = Zs^H x with the compressed operator (the Z^H I
+                                    products of Sec. 4); alone, not with the other flags */
 
 typedef struct vie_ctx_opts {
     int device;            /* CUDA device ordinal */
@@ -139,6 +147,9 @@ typedef struct vie_op_info {
     double t_assemble_s, t_compress_s;
     int64_t stored_entries;    /* factor entries held in memory: translated copies of a far block
                                   share one set of factors (see vie_ctx_opts.no_sharing) */
+    int64_t packed_bytes;      /* bytes of the bf16 planes the packed tensor-core apply streams per
+                                  application (every far block's own planes, tiles padded to 128 rows
+                                  and K to 32); 0 until a VIE_BF16X3 apply has built them */
 } vie_op_info;
 
 /* Plane-wave incident fields E0 = p exp(-j k khat . r), one per right-hand side. */
@@ -149,7 +160,7 @@ typedef struct vie_incident {
 
 typedef struct vie_solve_opts {
     double tol;                /* relative residual ||P^-1 (b - Zs I)|| / ||P^-1 b|| (1e-6) */
-    int restart;               /* GMRES restart length m (e.g. 60) */
+    int restart;               /* GMRES restart length m (e.g. 60); larger than 512 is taken as 512 */
     int max_iters;             /* iteration cap (e.g. 2000) */
     int precision;             /* VIE_C64: FP32 inner applies with FP64 Krylov and FP64
                                   residual refinement; VIE_BF16X3: as VIE_C64 but the far part of
@@ -162,6 +173,10 @@ typedef struct vie_solve_opts {
                                   1: the host launches every step and reads the continue flag */
     int autotune;              /* 1: run vie_tune for the first cycle's right-hand-side count
                                   (unless already tuned) before the solve */
+    int method;                /* 0: restarted GMRES (Sec. 6, the paper's choice); 1: BiCGStab, the
+                                  method Sec. 6 compares it with (same preconditioner, precisions and
+                                  stopping test; two applies per iteration; restart and launch are
+                                  not used; vie_solve only) */
 } vie_solve_opts;
 
 /* Result of vie_tune. */
@@ -298,6 +313,12 @@ int vie_solve_batch(vie_op* const* ops, int count, const vie_incident* inc, cons
 /* vie_fields: outputs from a solution I (host c128, n x nrhs, ld = n):
  * mode 0: far-field amplitude F(rhat) = -j k/(4 pi) (I - rhat rhat) int J exp(j k rhat.r) dV
  *         for the unit directions dirs[3 npts]; E_out host c128 [3 npts nrhs].
+ * mode 1: scattered near field E_sca(r) = -j k int J g dV' + (1/(j k)) grad int q g dV' (Sec. 2,
+ *         eq. IntEq: the field of the polarisation current J and its charge q = div J, boundary
+ *         sheets included) at the points dirs[3 npts] (same units as the geometry), which must lie
+ *         outside the atoms (the 3-point Gauss rule per voxel axis is accurate from about a voxel
+ *         away); E_out host c128 [3 npts nrhs] in units of the incident amplitude.  sigma_out
+ *         must be NULL in this mode.
  * sigma_out (host, may be NULL) [2 nrhs]: extinction Re(I^H v0) and scattering
  * cross section (closed surface integral of |F|^2, 24 x 48 rule) for |E0| = 1. */
 int vie_fields(vie_op* op, const vie_incident* inc, const void* I, int nrhs, const double* dirs,

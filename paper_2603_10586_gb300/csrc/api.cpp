@@ -351,7 +351,41 @@ int vie_op_get_info(const vie_op* op, vie_op_info* info) {
     info->t_assemble_s = o.t_assemble;
     info->t_compress_s = o.t_compress;
     info->stored_entries = o.stored_entries;
+    info->packed_bytes = o.umma_packed ? (int64_t)umma_pack_bytes(o) : 0;
     return VIE_OK;
+}
+
+// y = Zs^H x.  Between atoms the rule is symmetric and each mirror block
+// stores the transposed factors of its partner, so the compressed far part F
+// is a symmetric matrix (F^T = F) and F^H x = conj(F conj(x)); the self part
+// uses the conjugate-transposed self blocks (the touching-pair rule is not
+// exactly symmetric).
+static void apply_adjoint(Op& o, const void* x, void* y, int nrhs, int precision, cudaStream_t s) {
+    const int64_t n = o.n(), len = n * nrhs;
+    const bool wide = precision == VIE_C128 || precision == VIE_C64_ACC64;
+    const size_t eb = wide ? sizeof(double2) : sizeof(float2);
+    if (precision == VIE_C128 && o.fprec != VIE_C128) fail(VIE_ERR_INVALID_ARG, "VIE_C128 applies need VIE_C128 factors");
+    if (precision != VIE_C128 && o.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "this precision needs VIE_C64 factors");
+    DevBuf& H = wide ? o.d_zselfH64 : o.d_zselfH32;
+    if (!H.p) {
+        H.alloc((size_t)o.T * o.np * o.np * eb);
+        conj_transpose_blocks(wide ? o.d_zself64.p : o.d_zself32.p, H.p, o.T, o.np, wide, s);
+    }
+    if (o.d_adj.bytes < (size_t)len * eb) o.d_adj.alloc((size_t)len * eb);
+    ensure_F(o, (size_t)len * eb);
+    conj_copy(x, o.d_adj.p, len, wide, s);
+    if (wide) {
+        double2* F = o.d_F.as<double2>();
+        if (o.fprec == VIE_C128) apply_far<double2, double2>(o, o.d_adj.as<double2>(), n, F, n, nrhs, s);
+        else apply_far_df(o, o.d_adj.as<double2>(), n, F, n, nrhs, s);
+        conj_copy(F, F, len, true, s);
+        self_gemm<double2, double2>(o, H.as<double2>(), (const double2*)x, n, F, n, (double2*)y, n, nrhs, 0, s);
+    } else {
+        float2* F = o.d_F.as<float2>();
+        far32(o, o.d_adj.as<float2>(), n, F, n, nrhs, precision, s);
+        conj_copy(F, F, len, false, s);
+        self_gemm<float2, float2>(o, H.as<float2>(), (const float2*)x, n, F, n, (float2*)y, n, nrhs, 0, s);
+    }
 }
 
 int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int precision, int flags, vie_stream stream) {
@@ -364,6 +398,16 @@ int vie_apply(vie_op* op, const void* x, void* y, int nrhs, int64_t ld, int prec
         if (o.fprec == 0 && !(flags & VIE_APPLY_DENSE)) fail(VIE_ERR_STATE, "operator is not compressed");
         cudaStream_t s = stream ? (cudaStream_t)stream : o.ctx->stream;
         const bool fuse = flags & VIE_APPLY_FUSE_PRECOND;
+        if (flags & ~(VIE_APPLY_FUSE_PRECOND | VIE_APPLY_DENSE | VIE_APPLY_ADJOINT))
+            fail(VIE_ERR_INVALID_ARG, "vie_apply: unknown flags");
+        if (flags & VIE_APPLY_ADJOINT) {
+            if (flags != VIE_APPLY_ADJOINT)
+                fail(VIE_ERR_INVALID_ARG, "VIE_APPLY_ADJOINT cannot be combined with other flags");
+            if (precision != VIE_C64 && precision != VIE_BF16X3 && precision != VIE_C128 && precision != VIE_C64_ACC64)
+                fail(VIE_ERR_INVALID_ARG, "unsupported apply precision");
+            apply_adjoint(o, x, y, nrhs, precision, s);
+            return;
+        }
         if (flags & VIE_APPLY_DENSE) {
             if (fuse) fail(VIE_ERR_INVALID_ARG, "VIE_APPLY_DENSE cannot be combined with the preconditioner");
             if (nrhs != 1) fail(VIE_ERR_INVALID_ARG, "VIE_APPLY_DENSE takes one right-hand side");
@@ -491,11 +535,23 @@ int vie_fields(vie_op* op, const vie_incident* inc, const void* I, int nrhs, con
     return guarded(ctx_of(op), [&] {
         Op& o = op->o;
         set_device(*o.ctx);
-        if (mode != 0) fail(VIE_ERR_INVALID_ARG, "only far-field mode 0 is implemented");
+        if (mode != 0 && mode != 1) fail(VIE_ERR_INVALID_ARG, "vie_fields: mode 0 (far field) or 1 (near field)");
         cudaStream_t s = o.ctx->stream;
         const int64_t n = o.n();
         DevBuf dI((size_t)n * nrhs * sizeof(double2));
         VIE_CUDA(cudaMemcpyAsync(dI.p, I, dI.bytes, cudaMemcpyHostToDevice, s));
+        if (mode == 1) {
+            if (!E_out || !dirs || npts < 1) fail(VIE_ERR_INVALID_ARG, "vie_fields: the near field needs points and E_out");
+            for (int64_t i = 0; i < 3 * (int64_t)npts; ++i)
+                if (!std::isfinite(dirs[i])) fail(VIE_ERR_INVALID_ARG, "vie_fields: non-finite point");
+            DevBuf dp((size_t)3 * npts * sizeof(double)), out((size_t)npts * nrhs * 3 * sizeof(double2));
+            VIE_CUDA(cudaMemcpyAsync(dp.p, dirs, dp.bytes, cudaMemcpyHostToDevice, s));
+            near_field_launch(o, dI.p, nrhs, dp.as<double>(), npts, out.p, s);
+            VIE_CUDA(cudaMemcpyAsync(E_out, out.p, out.bytes, cudaMemcpyDeviceToHost, s));
+            VIE_CUDA(cudaStreamSynchronize(s));
+            if (sigma_out) fail(VIE_ERR_INVALID_ARG, "vie_fields: cross sections come with mode 0");
+            return;
+        }
         auto far = [&](const std::vector<double>& d, std::vector<cd>& F) {
             int np_ = (int)(d.size() / 3);
             DevBuf dd(d.size() * sizeof(double)), out((size_t)np_ * nrhs * 3 * sizeof(double2));

@@ -30,6 +30,7 @@
 // its tensor memory.
 #include <cuda_bf16.h>
 
+#include <cstdlib>
 #include <mutex>
 
 #include "common.h"
@@ -660,6 +661,343 @@ __global__ void __launch_bounds__(kThr) u2p_kernel(const int4* __restrict__ item
     teardown(ctl, failed, g, err);
 }
 
+// ---- warp-specialised variant ---------------------------------------------
+// One persistent CTA per SM; the roles run concurrently and meet on mbarriers
+// instead of CTA-wide barriers:
+//   warp 4     one thread starts the bulk copy of the pre-split A planes of
+//              every K stage (32 KiB) into the next free slot of a four-stage
+//              ring, running ahead of everything else;
+//   warps 5-12 four groups of two warps load, split and store the B operand
+//              (x gathered over the source atoms, or t) of a stage; group q
+//              serves ring slot q, so the loads of four stages are in flight
+//              at once;
+//   warp 13    one thread issues the 24 MMAs of a stage once its A copy has
+//              landed and its B planes are stored, and commits them to the
+//              slot's "empty" barrier (the producers refill it) and, at the end
+//              of a tile, to the tile's accumulator barrier;
+//   warps 0-3  epilogue: read the finished tile from tensor memory (warp w
+//              owns lanes 32w..32w+31) and store it.  Tensor memory holds two
+//              accumulator buffers, so the MMAs of the next tile run while the
+//              previous one drains.
+// The MMAs, their order and the planes are those of u1p/u2p, so the results
+// are bit-identical to them.
+// Every wait gives up after `lim` clock cycles: the waiting role raises the
+// CTA's abort flag, every role leaves its loop at its next check, and before
+// the tensor memory is freed and the CTA exits, the bulk copies that were
+// started and the MMAs that were issued are waited for (with the normal ~1 s
+// limit).  The error word then tells the host.
+constexpr int kWsStages = 4;
+constexpr int kWsThr = 448;  // 14 warps
+constexpr int kWsWarpTma = 4, kWsWarpB0 = 5, kWsWarpMma = 13;
+constexpr int kWsTmemCols = 256;
+constexpr size_t kWsSmemBytes = kWsStages * kStageBytes;  // 192 KiB
+
+struct WsCtl {
+    uint64_t full_a[kWsStages];  // A copy of the slot landed (1 arrival + bytes)
+    uint64_t full_b[kWsStages];  // B planes of the slot stored (the slot's 2 producer warps)
+    uint64_t empty[kWsStages];   // MMAs that read the slot are done (1 commit)
+    uint64_t acc_full[2];        // accumulator buffer holds a finished tile (1 commit)
+    uint64_t acc_empty[2];       // epilogue has read the buffer (4 epilogue warps)
+    uint32_t tmem;
+    volatile int abort;
+    uint32_t g_tma, g_mma;       // stages whose A copy was started / whose MMAs were issued
+};
+
+__device__ __forceinline__ void mbar_init_n(uint32_t mbar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+// bounded wait with a caller-given limit
+__device__ __forceinline__ bool mbar_wait_lim(uint32_t mbar, uint32_t parity, long long lim) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > lim) return false;
+    }
+}
+
+// The tiles of this CTA, in the same order for every role: (item, 64-column
+// pass).  Tile::nst = K stages (0: nothing to multiply, the output is zero).
+struct WsTile1 {
+    Phase1 src;
+    int nst, nmma, rows;
+    const int* rt;
+};
+
+template <class Role>
+__device__ void ws_tiles1(const FarBlockDev* blocks, const int* batoms, const int4* items, int it0, int it1,
+                          const int* rowt, const float2* x, int64_t ldx, int np, int nrhs, const int2* colr,
+                          volatile int* abort, Role&& role) {
+    for (int it = it0; it < it1 && !*abort; ++it) {
+        const int4 item = items[it];
+        const FarBlockDev B = blocks[item.x];
+        const int2 cr = colr ? colr[item.w] : make_int2(0, nrhs);
+        for (int c0 = cr.x; c0 < cr.y && !*abort; c0 += kN) {
+            WsTile1 T{Phase1{nullptr, nullptr, rowt, batoms + B.s_off, x, ldx, np, B.n, item.y, item.z, c0,
+                             min(kN, cr.y - c0)},
+                      (B.n + kKS - 1) / kKS, 0, item.z, rowt + item.y};
+            T.nmma = max(16, (T.src.ncol + 15) / 16 * 16);
+            if (!role(T, it, c0)) return;
+        }
+    }
+}
+
+struct WsTile2 {
+    Phase2 src;
+    int nst, nmma, rows;
+    int64_t rb;
+};
+
+template <class Role>
+__device__ void ws_tiles2(const int4* items, int it0, int it1, const int* tidx, const long long* kptr,
+                          const float2* t, int64_t ldt, int np, int nrhs, const int2* colr, volatile int* abort,
+                          Role&& role) {
+    for (int it = it0; it < it1 && !*abort; ++it) {
+        const int4 item = items[it];
+        const int a = item.x, p0 = item.y, rows = item.z - item.y;
+        const long long kb = kptr[a];
+        const int nK = (int)(kptr[a + 1] - kb);
+        const int2 cr = colr ? colr[item.w] : make_int2(0, nrhs);
+        for (int c0 = cr.x; c0 < cr.y && !*abort; c0 += kN) {
+            WsTile2 T{Phase2{nullptr, nullptr, tidx, t, ldt, kb, nK, p0, rows, c0, min(kN, cr.y - c0)},
+                      (nK + kKS - 1) / kKS, 0, rows, (int64_t)a * np + p0};
+            T.nmma = max(16, (T.src.ncol + 15) / 16 * 16);
+            if (!role(T, it, c0)) return;
+        }
+    }
+}
+
+__device__ void ws_setup(WsCtl& ctl) {
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kWsStages; ++i) {
+            mbar_init_n(smem_u32(&ctl.full_a[i]), 1);
+            mbar_init_n(smem_u32(&ctl.full_b[i]), 2);
+            mbar_init_n(smem_u32(&ctl.empty[i]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init_n(smem_u32(&ctl.acc_full[i]), 1);
+            mbar_init_n(smem_u32(&ctl.acc_empty[i]), 4);
+        }
+        ctl.abort = 0;
+        ctl.g_tma = 0;
+        ctl.g_mma = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((threadIdx.x >> 5) == kWsWarpMma) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl.tmem)),
+                     "r"(kWsTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+}
+
+// wait for what is still in flight (started copies, issued MMAs), free the
+// tensor memory, report an abort
+__device__ void ws_teardown(WsCtl& ctl, int* err) {
+    __syncthreads();
+    if (threadIdx.x == kWsWarpTma * 32) {  // the thread that started the copies
+        for (uint32_t g = ctl.g_mma; g < ctl.g_tma; ++g)
+            mbar_wait_lim(smem_u32(&ctl.full_a[g % kWsStages]), (g / kWsStages) & 1, kWaitCycles);
+    }
+    if (threadIdx.x == kWsWarpMma * 32 && ctl.g_mma > 0) {  // the thread that issued the MMAs
+        const uint32_t g = ctl.g_mma - 1;
+        mbar_wait_lim(smem_u32(&ctl.empty[g % kWsStages]), (g / kWsStages) & 1, kWaitCycles);
+    }
+    if (threadIdx.x == 0 && ctl.abort) atomicExch(err, 1);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if ((threadIdx.x >> 5) == kWsWarpMma)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(ctl.tmem), "r"(kWsTmemCols)
+                     : "memory");
+}
+
+// The three roles over one phase's tiles.  Tiles: a callable enumerating the
+// CTA's tiles (ws_tiles1 / ws_tiles2 bound to their arguments); Out: stores row
+// r, column c of the tile (value) to its destination.
+template <class TileT, class Enum, class Out>
+__device__ void ws_run(WsCtl& ctl, Stage* stages, const uint4* pack, const long long* pk, long long lim,
+                       Enum&& enumerate, Out&& out) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int* abort = &ctl.abort;
+    if (warp == kWsWarpTma) {
+        // ---- A copies, one thread
+        if (lane == 0) {
+            uint32_t g = 0;
+            enumerate([&](const TileT& T, int it, int) -> bool {
+                const uint4* packA = pack + pk[it] * kStageChunksA;
+                for (int st = 0; st < T.nst; ++st, ++g) {
+                    const uint32_t slot = g % kWsStages;
+                    if (g >= kWsStages && !mbar_wait_lim(smem_u32(&ctl.empty[slot]), ((g / kWsStages) - 1) & 1, lim))
+                        *abort = 1;
+                    if (*abort) return false;
+                    const uint32_t mb = smem_u32(&ctl.full_a[slot]);
+                    mbar_expect_tx(mb, kStageBytesA);
+                    tma_bulk(smem_u32(&stages[slot].a[0][0]), packA + (int64_t)st * kStageChunksA, kStageBytesA, mb);
+                    ctl.g_tma = g + 1;
+                }
+                return true;
+            });
+        }
+        __syncwarp();
+    } else if (warp >= kWsWarpB0 && warp < kWsWarpMma) {
+        // ---- B operands: group q (two warps, 64 threads) fills ring slot q
+        const int q = (warp - kWsWarpB0) >> 1;
+        const int gtid = tid - (kWsWarpB0 + 2 * q) * 32;
+        uint32_t g = 0;
+        enumerate([&](const TileT& T, int, int) -> bool {
+            for (int st = 0; st < T.nst; ++st, ++g) {
+                if ((int)(g % kWsStages) != q) continue;
+                if (g >= kWsStages) {
+                    bool ok = true;
+                    if (lane == 0) ok = mbar_wait_lim(smem_u32(&ctl.empty[q]), ((g / kWsStages) - 1) & 1, lim);
+                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                    if (!ok) *abort = 1;
+                }
+                if (*abort) return false;
+                Stage& S = stages[q];
+                // all loads of the stage first (up to four segments of 8 values
+                // per thread), then the split and the stores
+                const int nseg = T.nmma * 4;
+                float2 vb[4][8];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int seg = gtid + 64 * u;
+                    if (seg < nseg) T.src.load_b(seg >> 2, seg & 3, st * kKS, vb[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int seg = gtid + 64 * u;
+                    if (seg < nseg) put8<kChunksB>(S.b, (seg & 3) * kN + (seg >> 2), vb[u]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&ctl.full_b[q]));
+            }
+            return true;
+        });
+    } else if (warp == kWsWarpMma) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            uint32_t g = 0, t = 0;
+            enumerate([&](const TileT& T, int, int) -> bool {
+                if (T.nst == 0) return true;
+                const uint32_t ab = t & 1;
+                if (t >= 2 && !mbar_wait_lim(smem_u32(&ctl.acc_empty[ab]), ((t >> 1) - 1) & 1, lim)) {
+                    *abort = 1;
+                    return false;
+                }
+                const uint32_t tm = ctl.tmem + ab * (uint32_t)kTmemCols;
+                for (int st = 0; st < T.nst; ++st, ++g) {
+                    const uint32_t slot = g % kWsStages, par = (g / kWsStages) & 1;
+                    if (*abort || !mbar_wait_lim(smem_u32(&ctl.full_a[slot]), par, lim) ||
+                        !mbar_wait_lim(smem_u32(&ctl.full_b[slot]), par, lim)) {
+                        *abort = 1;
+                        return false;
+                    }
+                    fence_after();
+                    issue_stage(stages[slot], tm, T.nmma, st == 0);
+                    umma_commit(smem_u32(&ctl.empty[slot]));
+                    ctl.g_mma = g + 1;
+                }
+                umma_commit(smem_u32(&ctl.acc_full[ab]));
+                ++t;
+                return true;
+            });
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue (warps 0-3, tensor-memory lane quarter = warp)
+        uint32_t t = 0;
+        const int r = warp * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        enumerate([&](const TileT& T, int, int) -> bool {
+            const int ncol = T.src.ncol;
+            if (T.nst == 0) {
+                if (r < T.rows)
+                    for (int c = 0; c < ncol; ++c) out(T, r, c, make_float2(0.f, 0.f));
+                return true;
+            }
+            const uint32_t ab = t & 1;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait_lim(smem_u32(&ctl.acc_full[ab]), (t >> 1) & 1, lim);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                *abort = 1;
+                return false;
+            }
+            fence_after();
+            const uint32_t base = ctl.tmem + ab * (uint32_t)kTmemCols + lane_base;
+            for (int cb = 0; cb < ncol; cb += 16) {
+                float vr[16], vi[16];
+                tmem_ld16(base + cb, vr);
+                tmem_ld16(base + kN + cb, vi);
+                tmem_wait_ld();
+                if (r < T.rows) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (cb + i < ncol) out(T, r, cb + i, make_float2(vr[i], vi[i]));
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&ctl.acc_empty[ab]));
+            ++t;
+            return true;
+        });
+    }
+}
+
+__global__ void __launch_bounds__(kWsThr, 1) u1w_kernel(const FarBlockDev* __restrict__ blocks,
+                                                        const int* __restrict__ batoms, const int4* __restrict__ items,
+                                                        const int* __restrict__ cta_ptr,
+                                                        const long long* __restrict__ pk,
+                                                        const uint4* __restrict__ pack, const int* __restrict__ rowt,
+                                                        const float2* __restrict__ x, int64_t ldx, int np,
+                                                        float2* __restrict__ t, int64_t ldt, int nrhs,
+                                                        const int2* __restrict__ colr, int* err, long long lim) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    Stage* stages = reinterpret_cast<Stage*>(smem);
+    __shared__ WsCtl ctl;
+    ws_setup(ctl);
+    const int it0 = cta_ptr[blockIdx.x], it1 = cta_ptr[blockIdx.x + 1];
+    ws_run<WsTile1>(
+        ctl, stages, pack, pk, lim,
+        [&](auto&& role) { ws_tiles1(blocks, batoms, items, it0, it1, rowt, x, ldx, np, nrhs, colr, &ctl.abort, role); },
+        [&](const WsTile1& T, int r, int c, float2 v) { t[(int64_t)T.rt[r] + (int64_t)(T.src.c0 + c) * ldt] = v; });
+    ws_teardown(ctl, err);
+}
+
+__global__ void __launch_bounds__(kWsThr, 1) u2w_kernel(const int4* __restrict__ items, const int* __restrict__ cta_ptr,
+                                                        const long long* __restrict__ pk,
+                                                        const uint4* __restrict__ pack, const int* __restrict__ tidx,
+                                                        const long long* __restrict__ kptr,
+                                                        const float2* __restrict__ t, int64_t ldt, int np,
+                                                        float2* __restrict__ F, int64_t ldf, int nrhs,
+                                                        const int2* __restrict__ colr, int* err, long long lim) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    Stage* stages = reinterpret_cast<Stage*>(smem);
+    __shared__ WsCtl ctl;
+    ws_setup(ctl);
+    const int it0 = cta_ptr[blockIdx.x], it1 = cta_ptr[blockIdx.x + 1];
+    ws_run<WsTile2>(
+        ctl, stages, pack, pk, lim,
+        [&](auto&& role) { ws_tiles2(items, it0, it1, tidx, kptr, t, ldt, np, nrhs, colr, &ctl.abort, role); },
+        [&](const WsTile2& T, int r, int c, float2 v) { F[T.rb + r + (int64_t)(T.src.c0 + c) * ldf] = v; });
+    ws_teardown(ctl, err);
+}
+
 std::once_flag g_umma_attr_once;
 
 }  // namespace
@@ -672,6 +1010,8 @@ void umma_prepare(Op& op, cudaStream_t s) {
         cudaFuncSetAttribute(u2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         cudaFuncSetAttribute(u1p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         cudaFuncSetAttribute(u2p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        cudaFuncSetAttribute(u1w_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemBytes);
+        cudaFuncSetAttribute(u2w_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemBytes);
     });
     if (!op.d_err.p) {
         op.d_err.alloc(sizeof(int));
@@ -749,6 +1089,42 @@ void apply_far_umma_packed(Op& op, const float2* x, int64_t ldx, float2* F, int6
         op.d_u2_items.as<int4>(), op.d_u2_cta.as<int>(), op.d_u2_pk.as<long long>(), op.d_u2_pack.as<uint4>(),
         op.d_u2_tidx.as<int>(), op.d_u2_kptr.as<long long>(), op.d_t.as<float2>(), op.t_total, op.np, F, ldf, nrhs,
         op.colr, op.d_err.as<int>());
+    VIE_CHECK_LAUNCH();
+}
+
+// Wait limit of the warp-specialised kernels in clock cycles: ~1 s, or the
+// value of VIE_TEST_WAIT_CYCLES (a test of the timeout path sets it to 0 so
+// that the first wait gives up; the kernels then drain and report).
+static long long ws_wait_limit() {
+    const char* e = std::getenv("VIE_TEST_WAIT_CYCLES");
+    if (e && *e) {
+        const long long v = std::atoll(e);
+        return v < 0 ? 0 : v;
+    }
+    return kWaitCycles;
+}
+
+void apply_far_umma_ws(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s) {
+    if (!umma_pack(op, s)) {  // not enough memory for the packed planes: the kernel that splits A itself
+        apply_far_umma(op, x, ldx, F, ldf, nrhs, s);
+        return;
+    }
+    if (((uintptr_t)x & 15) || (ldx & 1)) fail(VIE_ERR_INVALID_ARG, "tensor-core apply: x must be 16-byte aligned");
+    const size_t need = (size_t)std::max<int64_t>(op.t_total, 1) * nrhs * sizeof(float2);
+    if (op.d_t.bytes < need) op.d_t.alloc(need);
+    const long long lim = ws_wait_limit();
+    const int nc = op.ctx->n_sm;
+    if (op.n_u1_items > 0) {
+        u1w_kernel<<<nc, kWsThr, kWsSmemBytes, s>>>(
+            op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(), op.d_w1_items.as<int4>(), op.d_w1_cta.as<int>(),
+            op.d_w1_pk.as<long long>(), op.d_u1_pack.as<uint4>(), op.d_u1_rowt.as<int>(), x, ldx, op.np,
+            op.d_t.as<float2>(), op.t_total, nrhs, op.colr, op.d_err.as<int>(), lim);
+        VIE_CHECK_LAUNCH();
+    }
+    u2w_kernel<<<nc, kWsThr, kWsSmemBytes, s>>>(
+        op.d_w2_items.as<int4>(), op.d_w2_cta.as<int>(), op.d_w2_pk.as<long long>(), op.d_u2_pack.as<uint4>(),
+        op.d_u2_tidx.as<int>(), op.d_u2_kptr.as<long long>(), op.d_t.as<float2>(), op.t_total, op.np, F, ldf, nrhs,
+        op.colr, op.d_err.as<int>(), lim);
     VIE_CHECK_LAUNCH();
 }
 

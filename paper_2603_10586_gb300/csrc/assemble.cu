@@ -768,6 +768,107 @@ __global__ void radiation_kernel(DevMesh m, GeoPtrs geo, int N, double k, const 
         for (int d = 0; d < 3; ++d) out[((size_t)c * npts + dir) * 3 + d] = red[d][0];
 }
 
+// rooftop face numbering of an atom (x-faces, then y, then z; each direction
+// lexicographic in (i, j, k) with the normal index 0..nv)
+__device__ __forceinline__ int face_index(int nv, int d, int i, int j, int k) {
+    const int base = d * nv * nv * (nv + 1);
+    if (d == 0) return base + (i * nv + j) * nv + k;
+    if (d == 1) return base + (i * (nv + 1) + j) * nv + k;
+    return base + (i * nv + j) * (nv + 1) + k;
+}
+
+// scattered near field E = -j k A + (1 / (j k)) grad Phi at points outside the
+// atoms, A = int J g, Phi = int q g (q = div J with the boundary sheets), one
+// block per (point, rhs): threads take (atom, voxel) pairs, form J at the
+// voxel's 27 Gauss points and its volume charge from the six faces, then the
+// boundary sheets (9 points each); grad_r g = -(1 + j k R) g / R^2 (r - r')
+__global__ void near_field_kernel(DevMesh m, GeoPtrs geo, int N, double k, const double2* I, int nrhs,
+                                  const double* pts, int npts, double2* out) {
+    const int ip = blockIdx.x, c = blockIdx.y;
+    const double px = pts[3 * ip], py = pts[3 * ip + 1], pz = pts[3 * ip + 2];
+    const int64_t n = (int64_t)N * m.np;
+    const double2* Ic = I + (int64_t)c * n;
+    double2 A[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    double2 G[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    const int nv = m.nv;
+    // one Gauss point: w (J (3 components) g, q grad g) added to A and G
+    auto add = [&](double rx, double ry, double rz, double w, const double2* Jp, double2 q) {
+        const double dx = px - rx, dy = py - ry, dz = pz - rz;
+        const double R = sqrt(dx * dx + dy * dy + dz * dz);
+        double sn, cs;
+        sincos(k * R, &sn, &cs);
+        const double2 g = (1.0 / (4.0 * M_PI * R)) * make_double2(cs, -sn);     // exp(-j k R) / (4 pi R)
+        const double2 f = (-1.0 / (R * R)) * cmul(make_double2(1.0, k * R), g);  // grad g = f (r - r')
+        if (Jp)
+            for (int d = 0; d < 3; ++d) A[d] += w * cmul(Jp[d], g);
+        const double2 qf = w * cmul(q, f);
+        G[0] += dx * qf;
+        G[1] += dy * qf;
+        G[2] += dz * qf;
+    };
+    for (int64_t e = threadIdx.x; e < (int64_t)N * m.nvox; e += blockDim.x) {
+        const int atom = (int)(e / m.nvox), v = (int)(e % m.nvox);
+        const double side = geo.sides[geo.types[atom]], h = side / nv;
+        const int vi = m.vox_ijk[3 * v], vj = m.vox_ijk[3 * v + 1], vk = m.vox_ijk[3 * v + 2];
+        const double2* Ia = Ic + (int64_t)atom * m.np;
+        double2 lo_f[3], up_f[3];
+        for (int d = 0; d < 3; ++d) {
+            int a0[3] = {vi, vj, vk};
+            lo_f[d] = Ia[face_index(nv, d, a0[0], a0[1], a0[2])];
+            a0[d] += 1;
+            up_f[d] = Ia[face_index(nv, d, a0[0], a0[1], a0[2])];
+        }
+        const double2 q = (1.0 / (h * h * h)) * ((up_f[0] - lo_f[0]) + (up_f[1] - lo_f[1]) + (up_f[2] - lo_f[2]));
+        const double ox = geo.centres[3 * atom] - 0.5 * side + h * vi;
+        const double oy = geo.centres[3 * atom + 1] - 0.5 * side + h * vj;
+        const double oz = geo.centres[3 * atom + 2] - 0.5 * side + h * vk;
+        for (int p = 0; p < 27; ++p) {
+            const int ix = p / 9, iy = (p / 3) % 3, iz = p % 3;
+            const double xi[3] = {c_gl3_x[ix], c_gl3_x[iy], c_gl3_x[iz]};
+            const double w = h * h * h * c_gl3_w[ix] * c_gl3_w[iy] * c_gl3_w[iz];
+            double2 Jp[3];
+            for (int d = 0; d < 3; ++d) Jp[d] = (1.0 / (h * h)) * ((1.0 - xi[d]) * lo_f[d] + xi[d] * up_f[d]);
+            add(ox + h * xi[0], oy + h * xi[1], oz + h * xi[2], w, Jp, q);
+        }
+    }
+    for (int64_t e = threadIdx.x; e < (int64_t)N * m.nsurf; e += blockDim.x) {
+        const int atom = (int)(e / m.nsurf), sf = (int)(e % m.nsurf);
+        const double side = geo.sides[geo.types[atom]], h = side / nv;
+        const int f = m.surf_face[sf];
+        const int4 fi = m.face[f];
+        const int d = fi.x, v = fi.y >= 0 ? fi.y : fi.z;
+        const double2 sig = (m.sheet_sign[f] / (h * h)) * Ic[(int64_t)atom * m.np + f];
+        double o[3];
+        for (int a = 0; a < 3; ++a) o[a] = geo.centres[3 * atom + a] - 0.5 * side + h * m.vox_ijk[3 * v + a];
+        if (fi.y >= 0) o[d] += h;  // the face is the top of its lower voxel
+        const int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
+        for (int p = 0; p < 9; ++p) {
+            const int i1 = p / 3, i2 = p % 3;
+            double r[3] = {o[0], o[1], o[2]};
+            r[a1] += h * c_gl3_x[i1];
+            r[a2] += h * c_gl3_x[i2];
+            add(r[0], r[1], r[2], h * h * c_gl3_w[i1] * c_gl3_w[i2], nullptr, sig);
+        }
+    }
+    __shared__ double2 red[6][256];
+    for (int d = 0; d < 3; ++d) {
+        red[d][threadIdx.x] = A[d];
+        red[3 + d][threadIdx.x] = G[d];
+    }
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+            for (int d = 0; d < 6; ++d) red[d][threadIdx.x] += red[d][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int d = 0; d < 3; ++d) {
+            const double2 a = red[d][0], gr = red[3 + d][0];
+            // -j k A + grad Phi / (j k) = (k A.y - gr.y / k, -k A.x + gr.x / k)
+            out[((size_t)c * npts + ip) * 3 + d] = make_double2(k * a.y - gr.y / k, -k * a.x + gr.x / k);
+        }
+}
+
 GeoPtrs geo_of(Op& op) {
     return GeoPtrs{op.d_centres.as<double>(), op.d_types.as<int>(), op.d_sides.as<double>()};
 }
@@ -951,6 +1052,12 @@ void rhs_kernel_launch(Op& op, const double* d_khat, const double* d_pol, int nr
     int64_t total = op.n() * nrhs;
     rhs_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(op.dmesh, geo_of(op), op.N, op.k, d_khat, d_pol,
                                                                 nrhs, (double2*)b, ld);
+    VIE_CHECK_LAUNCH();
+}
+
+void near_field_launch(Op& op, const void* d_I, int nrhs, const double* d_pts, int npts, void* d_out, cudaStream_t s) {
+    near_field_kernel<<<dim3(npts, nrhs), 256, 0, s>>>(op.dmesh, geo_of(op), op.N, op.k, (const double2*)d_I, nrhs,
+                                                       d_pts, npts, (double2*)d_out);
     VIE_CHECK_LAUNCH();
 }
 

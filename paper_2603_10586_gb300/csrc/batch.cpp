@@ -125,6 +125,7 @@ int solve_batch(const std::vector<Op*>& ops, const vie_incident* incs, const int
     for (int p = 0; p < B; ++p) {
         if (nrhs[p] < 1) fail(VIE_ERR_INVALID_ARG, "every problem of a batch needs a right-hand side");
         check_solve_opts(*ops[p], o, nrhs[p]);
+        if (o->method != 0) fail(VIE_ERR_INVALID_ARG, "batched solves use GMRES (method 0)");
         K += nrhs[p];
     }
     if (K > 1024) fail(VIE_ERR_INVALID_ARG, "a batch takes at most 1024 right-hand sides in total");

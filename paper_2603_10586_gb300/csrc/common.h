@@ -145,6 +145,7 @@ struct Op {
     DevMesh dmesh{};                   // pointers into the buffers above
     // self blocks (per type, np x np col-major)
     DevBuf d_zself64, d_inv64, d_zself32, d_inv32;
+    DevBuf d_zselfH64, d_zselfH32, d_adj;  // conjugate-transposed self blocks, conj(x) scratch (adjoint apply)
     std::vector<std::vector<int>> atoms_of_type;
     DevBuf d_atoms_by_type;            // atom indices grouped by type
     std::vector<int> type_atom_off;    // [T+1]
@@ -187,6 +188,7 @@ struct Op {
     // packed variant: each item's A operand pre-split into bf16 planes in the
     // shared-memory stage layout (32 KiB per 32-wide K stage), copied by bulk TMA
     DevBuf d_u1_pk, d_u2_pk, d_u1_pack, d_u2_pack;  // stage offsets per item, planes
+    DevBuf d_w1_items, d_w1_cta, d_w1_pk, d_w2_items, d_w2_cta, d_w2_pk;  // one CTA per SM (warp-specialised)
     long long u1_stages = 0, u2_stages = 0;
     bool umma_packed = false, umma_pack_failed = false;
     int n_u1_items = 0, n_u2_items = 0, n_cta_u = 0;
@@ -254,6 +256,7 @@ void dense_apply_c64(Op& op, const float2* x, float2* y, cudaStream_t s);
 void dense_apply_c128(Op& op, const double2* x, double2* y, cudaStream_t s);
 void rhs_kernel_launch(Op& op, const double* d_khat, const double* d_pol, int nrhs, void* b, int64_t ld,
                        cudaStream_t s);
+void near_field_launch(Op& op, const void* d_I, int nrhs, const double* d_pts, int npts, void* d_out, cudaStream_t s);
 void far_field_launch(Op& op, const void* d_I, int nrhs, const double* d_dirs, int npts, void* d_out,
                       cudaStream_t s);
 void v0_dot_launch(Op& op, const void* d_I, const double* d_khat, const double* d_pol, int nrhs,
@@ -263,6 +266,10 @@ void v0_dot_launch(Op& op, const void* d_I, const double* d_khat, const double* 
 void invert_self_blocks(Op& op);   // d_inv64 from d_zself64 (Gauss-Jordan, partial pivoting)
 void convert_c128_to_c64(const void* src, void* dst, int64_t n, cudaStream_t s);
 void convert_c64_to_c128(const void* src, void* dst, int64_t n, cudaStream_t s);
+// dst = conj(src) (n complex values; c128 selects double2, else float2)
+void conj_copy(const void* src, void* dst, int64_t n, bool c128, cudaStream_t s);
+// dst[t] = src[t]^H for T np x np column-major blocks
+void conj_transpose_blocks(const void* src, void* dst, int T, int np, bool c128, cudaStream_t s);
 template <class TM, class TX>
 void self_gemm(Op& op, const TM* M, const TX* X, int64_t ldx, const TX* C, int64_t ldc, TX* Y, int64_t ldy,
                int nrhs, int mode, cudaStream_t s);
@@ -294,6 +301,7 @@ void umma_prepare(Op& op, cudaStream_t s);
 bool umma_pack(Op& op, cudaStream_t s);
 size_t umma_pack_bytes(const Op& op);
 void apply_far_umma_packed(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
+void apply_far_umma_ws(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
 // complex float32 far apply reading each shared factor once per group of up to
 // Op::kShareGroup translated copies (one right-hand side at a time)
 void apply_far_shared(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);

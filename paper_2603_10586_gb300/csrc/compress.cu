@@ -38,7 +38,7 @@ namespace vie {
 namespace {
 
 constexpr int kChunk = 32;    // columns orthonormalised at a time
-constexpr int kRankCap = 2048; // largest rank a block may take (larger: error)
+constexpr int kRankCap = 8192; // largest rank a block may take (larger: error)
 
 // ------------------------------------------------------------------ kernels
 __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {

@@ -208,7 +208,7 @@ void lpt_assign(const std::vector<double>& w, int nproc, std::vector<int>& owner
 // weighted by their factor bytes.
 // ---------------------------------------------------------------------------
 static void pack_lpt(const std::vector<int4>& items, const std::vector<double>& w, int ncta,
-                     std::vector<int4>& out_items, std::vector<int>& cta_ptr) {
+                     std::vector<int4>& out_items, std::vector<int>& cta_ptr, std::vector<int>* perm = nullptr) {
     std::vector<int> owner;
     std::vector<double> loads;
     lpt_assign(w, ncta, owner, loads);
@@ -220,8 +220,12 @@ static void pack_lpt(const std::vector<int4>& items, const std::vector<double>& 
     for (int i : order) per[owner[i]].push_back(i);
     out_items.clear();
     cta_ptr.assign(ncta + 1, 0);
+    if (perm) perm->clear();
     for (int c = 0; c < ncta; ++c) {
-        for (int i : per[c]) out_items.push_back(items[i]);
+        for (int i : per[c]) {
+            out_items.push_back(items[i]);
+            if (perm) perm->push_back(i);
+        }
         cta_ptr[c + 1] = (int)out_items.size();
     }
 }
@@ -449,10 +453,13 @@ void build_umma_lists(Op& op) {
             w2.push_back((double)(p1 - p0 + 32) * (K + 1.0));
         }
     }
-    std::vector<int4> q1, q2;
-    std::vector<int> e1, e2;
-    pack_lpt(it1, w1, op.n_cta_u, q1, e1);
-    pack_lpt(it2, w2, op.n_cta_u, q2, e2);
+    std::vector<int4> q1, q2, r1, r2;
+    std::vector<int> e1, e2, f1, f2, p1, p2, pr1, pr2;
+    pack_lpt(it1, w1, op.n_cta_u, q1, e1, &p1);
+    pack_lpt(it2, w2, op.n_cta_u, q2, e2, &p2);
+    // the same items mapped to one CTA per SM (warp-specialised kernels)
+    pack_lpt(it1, w1, op.ctx->n_sm, r1, f1, &pr1);
+    pack_lpt(it2, w2, op.ctx->n_sm, r2, f2, &pr2);
     op.n_u1_items = (int)q1.size();
     op.n_u2_items = (int)q2.size();
     upload(op.d_u1_rowoff, rowoff.empty() ? std::vector<long long>{0} : rowoff);
@@ -477,6 +484,22 @@ void build_umma_lists(Op& op) {
     op.u2_stages = pk2.back();
     upload(op.d_u1_pk, pk1);
     upload(op.d_u2_pk, pk2);
+    // stage offsets of the one-CTA-per-SM lists: the planes stay where the
+    // first list put them (item i of that list at pk[i])
+    auto remap = [](const std::vector<int>& perm_from, const std::vector<int>& perm_to,
+                    const std::vector<long long>& pk) {
+        std::vector<int> pos(perm_from.size());
+        for (size_t i = 0; i < perm_from.size(); ++i) pos[perm_from[i]] = (int)i;
+        std::vector<long long> out(perm_to.size() + 1, pk.back());
+        for (size_t i = 0; i < perm_to.size(); ++i) out[i] = pk[pos[perm_to[i]]];
+        return out;
+    };
+    upload(op.d_w1_items, r1.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : r1);
+    upload(op.d_w1_cta, f1);
+    upload(op.d_w1_pk, remap(p1, pr1, pk1));
+    upload(op.d_w2_items, r2.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : r2);
+    upload(op.d_w2_cta, f2);
+    upload(op.d_w2_pk, remap(p2, pr2, pk2));
     op.umma_packed = false;
     op.umma_pack_failed = false;
     op.d_u1_pack.release();

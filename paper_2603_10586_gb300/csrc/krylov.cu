@@ -8,8 +8,16 @@
 //
 // Reductions are two-stage with a fixed partition of the rows, so every
 // result is the same from run to run.
+//
+// The basis is stored in one of two float64-accurate forms: float64 (the
+// all-float64 solve) or double-float (float4 per complex value, hi + lo: the
+// mixed-precision solve, whose inner applies are float32 anyway).  The
+// double-float projections and updates run on the float32 pipes, which on
+// this GPU are far faster than its float64 units; they carry ~48 significant
+// bits per operation, and their sums are reduced in float64.
 #include "common.h"
 #include "cplx.cuh"
+#include "dfloat.cuh"
 #include "krylov.h"
 
 namespace vie {
@@ -79,6 +87,162 @@ __global__ void __launch_bounds__(kT) k_gather(KrylovArgs a, const double2* __re
         const double2 e = sc * src[r];
         v[r] = e;
         st(x, r, e);
+    }
+}
+
+// ---- double-float basis ----------------------------------------------------
+// k_gather for a double-float basis: column j (j > 0, stored unnormalised by
+// the previous step) is scaled in place; column 0 comes from W (float64)
+__global__ void __launch_bounds__(kT) k_gather_df(KrylovArgs a, const double2* __restrict__ W, float2* __restrict__ Xg) {
+    const int i = blockIdx.y;
+    const int c = a.cols[i];
+    const Rows R = rows_of(a, c);
+    const int64_t n = R.len, stride = (int64_t)gridDim.x * kT;
+    float2* x = Xg + (int64_t)i * a.n + R.lo;
+    if (!a.cycling[i]) {
+        for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += stride) x[r] = make_float2(0.f, 0.f);
+        return;
+    }
+    const int j = a.ctr[KR_J];
+    float4* v = reinterpret_cast<float4*>(R.V) + (int64_t)j * n;
+    const double sc = a.inv[i];
+    if (j == 0) {
+        const double2* src = W + (int64_t)c * a.n + R.lo;
+        for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += stride) {
+            const float4 e = df_from(sc * src[r]);
+            v[r] = e;
+            x[r] = make_float2(e.x, e.y);
+        }
+    } else {
+        const float sh = (float)sc, sl = (float)(sc - (double)sh);
+        for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += stride) {
+            const float4 e = df_scale(v[r], sh, sl);
+            v[r] = e;
+            x[r] = make_float2(e.x, e.y);
+        }
+    }
+}
+
+// partial h[col] = sum_r conj(V[r, col]) w[r], double-float products and
+// per-thread sums, float64 across threads; pass 1 takes w from the float32
+// operator output (exact in double-float) and stores it as basis column j+1
+template <bool kFirst>
+__global__ void __launch_bounds__(kT) k_mdot_df(KrylovArgs a, const float2* __restrict__ Y) {
+    const int i = blockIdx.z, cg = blockIdx.y;
+    if (!a.cycling[i]) return;
+    const int j = a.ctr[KR_J];
+    const int ncols = j + 1;
+    if (cg * kCG >= ncols) return;
+    const Rows R = rows_of(a, a.cols[i]);
+    const int64_t n = R.len;
+    const float4* V = reinterpret_cast<const float4*>(R.V);
+    float4* w = reinterpret_cast<float4*>(R.V) + (int64_t)(j + 1) * n;
+    const float2* y = kFirst ? Y + (int64_t)i * a.n + R.lo : nullptr;
+    const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
+    float4 acc[kCG];
+#pragma unroll
+    for (int c = 0; c < kCG; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += 2 * kT) {
+        const bool second = r + kT < r1;
+        float4 wv, wv2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kFirst) {
+            const float2 y1 = y[r];
+            wv = make_float4(y1.x, y1.y, 0.f, 0.f);
+            if (second) {
+                const float2 y2 = y[r + kT];
+                wv2 = make_float4(y2.x, y2.y, 0.f, 0.f);
+            }
+            if (cg == 0) {
+                w[r] = wv;
+                if (second) w[r + kT] = wv2;
+            }
+        } else {
+            wv = w[r];
+            if (second) wv2 = w[r + kT];
+        }
+        float4 v1[kCG], v2[kCG];
+#pragma unroll
+        for (int c = 0; c < kCG; ++c) {
+            const int col = cg * kCG + c;
+            v1[c] = col < ncols ? V[(int64_t)col * n + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+            v2[c] = (col < ncols && second) ? V[(int64_t)col * n + r + kT] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int c = 0; c < kCG; ++c) {
+            df_cmac_conj(acc[c], v1[c], wv);
+            df_cmac_conj(acc[c], v2[c], wv2);
+        }
+    }
+    __shared__ double2 sh[kT / 32][kCG];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < kCG; ++c) {
+        double re = (double)acc[c].x + (double)acc[c].z, im = (double)acc[c].y + (double)acc[c].w;
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_down_sync(0xffffffffu, re, o);
+            im += __shfl_down_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) sh[wid][c] = make_double2(re, im);
+    }
+    __syncthreads();
+    if (threadIdx.x < kCG) {
+        const int col = cg * kCG + threadIdx.x;
+        if (col < ncols) {
+            double2 s = make_double2(0.0, 0.0);
+            for (int w2 = 0; w2 < kT / 32; ++w2) s += sh[w2][threadIdx.x];
+            a.part[((int64_t)i * a.hs + col) * gridDim.x + blockIdx.x] = s;
+        }
+    }
+}
+
+// w -= V h (columns 0..j) in double-float; pass 2 also forms the squared-norm
+// partials of w (float64)
+template <bool kSecond>
+__global__ void __launch_bounds__(kT) k_maxpy_df(KrylovArgs a) {
+    const int i = blockIdx.y;
+    if (!a.cycling[i]) return;
+    const int j = a.ctr[KR_J];
+    __shared__ float4 hs[kMaxRestart + 1];
+    __shared__ double sh[kT / 32];
+    for (int c = threadIdx.x; c <= j; c += kT) hs[c] = df_from(a.h[(int64_t)i * a.hs + c]);
+    __syncthreads();
+    const Rows R = rows_of(a, a.cols[i]);
+    const int64_t n = R.len;
+    const float4* V = reinterpret_cast<const float4*>(R.V);
+    float4* w = reinterpret_cast<float4*>(R.V) + (int64_t)(j + 1) * n;
+    double nacc = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) {
+        float4 acc = w[r];
+        for (int c = 0; c <= j; ++c) df_cmsub(acc, V[(int64_t)c * n + r], hs[c]);
+        acc = df_normed(acc);
+        w[r] = acc;
+        if (kSecond) {
+            const double2 d = df_to(acc);
+            nacc += d.x * d.x + d.y * d.y;
+        }
+    }
+    if (kSecond) {
+        const double s = block_sum(nacc, sh);
+        if (threadIdx.x == 0) a.npart[(int64_t)i * a.nblk_max + blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kT) k_xupdate_df(KrylovArgs a, double2* __restrict__ X) {
+    const int i = blockIdx.y;
+    const int jd = a.jdone[i];
+    if (jd == 0) return;
+    __shared__ double2 ys[kMaxRestart];
+    for (int l = threadIdx.x; l < jd; l += kT) ys[l] = a.y[(int64_t)i * a.hs + l];
+    __syncthreads();
+    const Rows R = rows_of(a, a.cols[i]);
+    const int64_t n = R.len;
+    const float4* V = reinterpret_cast<const float4*>(R.V);
+    double2* x = X + (int64_t)a.cols[i] * a.n + R.lo;
+    for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) {
+        double2 acc = x[r];
+        for (int l = 0; l < jd; ++l) cfma(acc, df_to(V[(int64_t)l * n + r]), ys[l]);
+        x[r] = acc;
     }
 }
 
@@ -436,8 +600,14 @@ void kr_cycle_start(const KrylovArgs& a, int k, cudaStream_t s) {
 
 void kr_gather(const KrylovArgs& a, const double2* W, void* Xg, bool c64, int k, int nblk, cudaStream_t s) {
     dim3 grid(nblk, k);
-    if (c64) k_gather<float2><<<grid, kT, 0, s>>>(a, W, static_cast<float2*>(Xg));
-    else k_gather<double2><<<grid, kT, 0, s>>>(a, W, static_cast<double2*>(Xg));
+    if (a.df) {
+        if (!c64) fail(VIE_ERR_STATE, "a double-float basis feeds float32 applies");
+        k_gather_df<<<grid, kT, 0, s>>>(a, W, static_cast<float2*>(Xg));
+    } else if (c64) {
+        k_gather<float2><<<grid, kT, 0, s>>>(a, W, static_cast<float2*>(Xg));
+    } else {
+        k_gather<double2><<<grid, kT, 0, s>>>(a, W, static_cast<double2*>(Xg));
+    }
     VIE_CHECK_LAUNCH();
 }
 
@@ -445,19 +615,23 @@ void kr_project(const KrylovArgs& a, const void* Y, bool c64, int pass, int k, i
     const int ncg = (a.m + kCG - 1) / kCG;
     dim3 gd(nchunk, ncg, k);
     if (pass == 1) {
-        if (c64) k_mdot<float2, true><<<gd, kT, 0, s>>>(a, static_cast<const float2*>(Y));
+        if (a.df) k_mdot_df<true><<<gd, kT, 0, s>>>(a, static_cast<const float2*>(Y));
+        else if (c64) k_mdot<float2, true><<<gd, kT, 0, s>>>(a, static_cast<const float2*>(Y));
         else k_mdot<double2, true><<<gd, kT, 0, s>>>(a, static_cast<const double2*>(Y));
         VIE_CHECK_LAUNCH();
         k_reduce<true><<<k, kT, 0, s>>>(a, nchunk);
         VIE_CHECK_LAUNCH();
-        k_maxpy<false><<<dim3(nblk, k), kT, 0, s>>>(a);
+        if (a.df) k_maxpy_df<false><<<dim3(nblk, k), kT, 0, s>>>(a);
+        else k_maxpy<false><<<dim3(nblk, k), kT, 0, s>>>(a);
         VIE_CHECK_LAUNCH();
     } else {
-        k_mdot<double2, false><<<gd, kT, 0, s>>>(a, nullptr);
+        if (a.df) k_mdot_df<false><<<gd, kT, 0, s>>>(a, nullptr);
+        else k_mdot<double2, false><<<gd, kT, 0, s>>>(a, nullptr);
         VIE_CHECK_LAUNCH();
         k_reduce<false><<<k, kT, 0, s>>>(a, nchunk);
         VIE_CHECK_LAUNCH();
-        k_maxpy<true><<<dim3(nblk, k), kT, 0, s>>>(a);
+        if (a.df) k_maxpy_df<true><<<dim3(nblk, k), kT, 0, s>>>(a);
+        else k_maxpy<true><<<dim3(nblk, k), kT, 0, s>>>(a);
         VIE_CHECK_LAUNCH();
         k_nsq<<<k, kT, 0, s>>>(a, nblk, 1);
         VIE_CHECK_LAUNCH();
@@ -473,7 +647,8 @@ void kr_givens(const KrylovArgs& a, int k, int nblk, cudaGraphConditionalHandle 
 void kr_update(const KrylovArgs& a, double2* X, int k, int nblk, cudaStream_t s) {
     k_backsub<<<(k + 63) / 64, 64, 0, s>>>(a, k);
     VIE_CHECK_LAUNCH();
-    k_xupdate<<<dim3(nblk, k), kT, 0, s>>>(a, X);
+    if (a.df) k_xupdate_df<<<dim3(nblk, k), kT, 0, s>>>(a, X);
+    else k_xupdate<<<dim3(nblk, k), kT, 0, s>>>(a, X);
     VIE_CHECK_LAUNCH();
 }
 

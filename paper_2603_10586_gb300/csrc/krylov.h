@@ -32,10 +32,11 @@ struct KrylovArgs {
     const long long* col_voff;
     int m;            // restart length (<= kMaxRestart)
     int hs;           // per-slot stride of h, y and the projection partials (>= m + 1)
+    int df;           // 1: the basis is double-float (float4 per value), 0: float64
     int nblk_max;     // row blocks the norm partials are laid out for
     double tol;
     int maxit;
-    double2* V;       // per column: col_len x (m+1) float64 basis
+    double2* V;       // per column: col_len x (m+1) basis (float64, or double-float in the same bytes)
     double2* H;       // [slot][m][m+1] Hessenberg columns (rotated in place)
     double2* g;       // [slot][m+1] rotated right-hand side of the least-squares problem
     double2* cs;      // [slot][m] Givens cosines
@@ -120,6 +121,8 @@ void check_solve_opts(const Op& op, const vie_solve_opts* o, int nrhs);
 // restarted GMRES of every column of b (device, n x nrhs) into X
 GmresOutcome run_gmres(Op& op, const ColumnLayout& lay, const double2* b, double2* X, const vie_solve_opts& o,
                        int nrhs);
+// left-preconditioned BiCGStab of every column of b (device, n x nrhs) into X (bicgstab.cu)
+GmresOutcome run_bicgstab(Op& op, const double2* b, double2* X, const vie_solve_opts& o, int nrhs);
 // stats of columns [c0, c1); returns VIE_OK or VIE_ERR_NOT_CONVERGED
 int fill_stats(const GmresOutcome& r, int c0, int c1, double tol, double t0, vie_solve_stats* st);
 

@@ -1,3 +1,4 @@
+#include <algorithm>
 // Dense kernels around the self blocks (paper Sec. 4, eq. diagprecond):
 // explicit inverse of each distinct Z_ii by Gauss-Jordan elimination with
 // partial pivoting (float64), precision conversions, and the per-type block
@@ -205,6 +206,40 @@ void convert_c128_to_c64(const void* src, void* dst, int64_t n, cudaStream_t s) 
 void convert_c64_to_c128(const void* src, void* dst, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
     c64_to_c128<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float2*)src, (double2*)dst, n);
+    VIE_CHECK_LAUNCH();
+}
+
+template <class T2>
+__global__ void k_conj(const T2* src, T2* dst, int64_t n) {  // may run in place
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T2 v = src[i];
+        dst[i] = mk(v.x, -v.y);
+    }
+}
+
+template <class T2>
+__global__ void k_conj_transpose(const T2* __restrict__ src, T2* __restrict__ dst, int np) {
+    const int64_t base = (int64_t)blockIdx.y * np * np;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)np * np;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e % np, c = e / np;
+        const T2 v = src[base + c + r * np];  // element (c, r) of the source
+        dst[base + e] = mk(v.x, -v.y);
+    }
+}
+
+void conj_copy(const void* src, void* dst, int64_t n, bool c128, cudaStream_t s) {
+    if (n <= 0) return;
+    const unsigned g = (unsigned)std::min<int64_t>(8192, (n + 255) / 256);
+    if (c128) k_conj<double2><<<g, 256, 0, s>>>((const double2*)src, (double2*)dst, n);
+    else k_conj<float2><<<g, 256, 0, s>>>((const float2*)src, (float2*)dst, n);
+    VIE_CHECK_LAUNCH();
+}
+
+void conj_transpose_blocks(const void* src, void* dst, int T, int np, bool c128, cudaStream_t s) {
+    const dim3 g((unsigned)std::min<int64_t>(1024, ((int64_t)np * np + 255) / 256), T);
+    if (c128) k_conj_transpose<double2><<<g, 256, 0, s>>>((const double2*)src, (double2*)dst, np);
+    else k_conj_transpose<float2><<<g, 256, 0, s>>>((const float2*)src, (float2*)dst, np);
     VIE_CHECK_LAUNCH();
 }
 

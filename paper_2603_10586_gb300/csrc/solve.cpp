@@ -57,7 +57,7 @@ struct Gmres {
 
     Gmres(Op& op_, const vie_solve_opts& o_, int nrhs_, const ColumnLayout& lay_)
         : op(op_), o(o_), lay(lay_), s(op_.ctx->stream), n(op_.n()), nrhs(nrhs_), n_sm(op_.ctx->n_sm) {
-        m = std::max(1, std::min(o.restart > 0 ? o.restart : 60, 63));
+        m = std::max(1, std::min(o.restart > 0 ? o.restart : 60, kMaxRestart));
         c64 = !(o.precision == VIE_C128 || !o.precond);
         const int S = nrhs;
         const int nblk_max = kr_nblk(n, 1, n_sm);
@@ -83,9 +83,10 @@ struct Gmres {
         g.alloc((size_t)S * (m + 1) * sizeof(double2));
         cs.alloc((size_t)S * m * sizeof(double2));
         sn.alloc((size_t)S * m * sizeof(double2));
-        h.alloc((size_t)S * 64 * sizeof(double2));
-        y.alloc((size_t)S * 64 * sizeof(double2));
-        part.alloc((size_t)S * 64 * nchunk_max * sizeof(double2));
+        const int hstride = m + 1;
+        h.alloc((size_t)S * hstride * sizeof(double2));
+        y.alloc((size_t)S * hstride * sizeof(double2));
+        part.alloc((size_t)S * hstride * nchunk_max * sizeof(double2));
         npart.alloc((size_t)S * nblk_max * sizeof(double));
         rpart.alloc((size_t)S * nblk_max * sizeof(double));
         nsq.alloc(S * sizeof(double));
@@ -121,6 +122,9 @@ struct Gmres {
         a.colr_cycle = lay.nprob > 1 ? colr_cycle.as<int2>() : nullptr;
         a.colr = lay.nprob > 1 ? colr.as<int2>() : nullptr;
         a.m = m;
+        a.hs = m + 1;
+        // float32 inner applies: the Gram-Schmidt in double-float on the float32 pipes
+        a.df = c64 ? 1 : 0;
         a.nblk_max = nblk_max;
         a.tol = o.tol > 0 ? o.tol : 1e-6;
         a.maxit = o.max_iters > 0 ? o.max_iters : 2000;
@@ -265,12 +269,18 @@ struct Gmres {
         VIE_CUDA(cudaMemcpyAsync(h_pinned, ctr.p, KR_NCTR * sizeof(int), cudaMemcpyDeviceToHost, s));
         VIE_CUDA(cudaMemcpyAsync(h_pinned + KR_NCTR, done.p, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
         VIE_CUDA(cudaStreamSynchronize(s));
-        if (h_pinned[KR_NAN]) fail(VIE_ERR_NAN, "non-finite residual in GMRES");
+        // a tensor-core kernel that gave up waiting leaves its output incomplete
+        // (and may thereby cause the non-finite values seen next): report it
+        // first, and clear the word so that the operator stays usable
         if (op.d_err.p) {
             int e = 0;
             VIE_CUDA(cudaMemcpy(&e, op.d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-            if (e) fail(VIE_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs");
+            if (e) {
+                VIE_CUDA(cudaMemset(op.d_err.p, 0, sizeof(int)));
+                fail(VIE_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its operands or MMAs");
+            }
         }
+        if (h_pinned[KR_NAN]) fail(VIE_ERR_NAN, "non-finite residual in GMRES");
     }
 
     // a batched operator's kernels take each problem's right-hand sides from
@@ -353,6 +363,7 @@ void check_solve_opts(const Op& op, const vie_solve_opts* o, int nrhs) {
         fail(VIE_ERR_INVALID_ARG, "solve precision must be VIE_C64, VIE_BF16X3 or VIE_C128");
     if (o->launch != 0 && o->launch != 1) fail(VIE_ERR_INVALID_ARG, "solve launch must be 0 (graph) or 1 (host loop)");
     if (nrhs < 1 || nrhs > 1024) fail(VIE_ERR_INVALID_ARG, "a solve takes 1 to 1024 right-hand sides");
+    if (o->method != 0 && o->method != 1) fail(VIE_ERR_INVALID_ARG, "solve method must be 0 (GMRES) or 1 (BiCGStab)");
 }
 
 GmresOutcome run_gmres(Op& op, const ColumnLayout& lay, const double2* b, double2* X, const vie_solve_opts& o,
@@ -420,7 +431,8 @@ int solve(Op& op, const vie_incident* inc, int nrhs, const vie_solve_opts* o, vo
         X = xdev.as<double2>();
     }
     const ColumnLayout lay = ColumnLayout::single(n, nrhs);
-    const GmresOutcome r = run_gmres(op, lay, b.as<double2>(), X, *o, nrhs);
+    const GmresOutcome r = o->method == 1 ? run_bicgstab(op, b.as<double2>(), X, *o, nrhs)
+                                          : run_gmres(op, lay, b.as<double2>(), X, *o, nrhs);
     if (!o->out_on_device) {
         VIE_CUDA(cudaMemcpyAsync(I_out, X, (size_t)n * nrhs * sizeof(double2), cudaMemcpyDeviceToHost, s));
         VIE_CUDA(cudaStreamSynchronize(s));

@@ -26,14 +26,15 @@ int bucket(int nrhs) {
 bool admissible(int precision, int v) {
     if ((v >= VIE_VAR_SIMT_R1 && v <= VIE_VAR_SIMT_R8) || v == VIE_VAR_SIMT_SHARED) return true;
     return precision == VIE_BF16X3 &&
-           (v == VIE_VAR_MMA_BF16X3 || v == VIE_VAR_TCGEN05_BF16X3 || v == VIE_VAR_TCGEN05_PACKED_BF16X3);
+           (v == VIE_VAR_MMA_BF16X3 || v == VIE_VAR_TCGEN05_BF16X3 || v == VIE_VAR_TCGEN05_PACKED_BF16X3 ||
+            v == VIE_VAR_TCGEN05_WS_BF16X3);
 }
 
 int default_variant(const Op& op, int precision, int nrhs) {
     // one right-hand side: read shared factors once per group of copies when
     // the operator has translated copies
     if (nrhs == 1) return op.share_mean > 1.5 ? VIE_VAR_SIMT_SHARED : VIE_VAR_SIMT_R1;
-    if (precision == VIE_BF16X3 && nrhs >= 8) return VIE_VAR_TCGEN05_PACKED_BF16X3;
+    if (precision == VIE_BF16X3 && nrhs >= 8) return VIE_VAR_TCGEN05_WS_BF16X3;
     return VIE_VAR_SIMT_R4;
 }
 
@@ -54,6 +55,7 @@ void far32(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrh
         case VIE_VAR_TCGEN05_BF16X3: apply_far_umma(op, x, ldx, F, ldf, nrhs, s); break;
         case VIE_VAR_TCGEN05_PACKED_BF16X3: apply_far_umma_packed(op, x, ldx, F, ldf, nrhs, s); break;
         case VIE_VAR_SIMT_SHARED: apply_far_shared(op, x, ldx, F, ldf, nrhs, s); break;
+        case VIE_VAR_TCGEN05_WS_BF16X3: apply_far_umma_ws(op, x, ldx, F, ldf, nrhs, s); break;
         default: fail(VIE_ERR_STATE, "unknown far-apply variant");
     }
 }
@@ -64,7 +66,7 @@ int tune_far(Op& op, int precision, int nrhs, cudaStream_t s, std::vector<int>& 
     if (nrhs < 1 || nrhs > 1024) fail(VIE_ERR_INVALID_ARG, "vie_tune: 1 to 1024 right-hand sides");
     cand.clear();
     ms.clear();
-    for (int v = VIE_VAR_SIMT_R1; v <= VIE_VAR_SIMT_SHARED; ++v) {
+    for (int v = VIE_VAR_SIMT_R1; v <= VIE_VAR_TCGEN05_WS_BF16X3; ++v) {
         if (!admissible(precision, v)) continue;
         if (v >= VIE_VAR_SIMT_R2 && v <= VIE_VAR_SIMT_R8 && nrhs == 1) continue;  // same as R1
         if (v == VIE_VAR_SIMT_SHARED && nrhs > 1) continue;  // one column at a time

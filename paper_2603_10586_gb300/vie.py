@@ -29,9 +29,12 @@ C64, C128, BF16X3, C64_ACC64 = 1, 2, 3, 4
 VAR_SIMT_R1, VAR_SIMT_R2, VAR_SIMT_R4, VAR_SIMT_R8, VAR_MMA_BF16X3, VAR_TCGEN05_BF16X3 = 1, 2, 3, 4, 5, 6
 VAR_TCGEN05_PACKED_BF16X3 = 7
 VAR_SIMT_SHARED = 8
+VAR_TCGEN05_WS_BF16X3 = 9
 NOALLOC_SCRATCH_ELEMS = 1 << 22   # VIE_NOALLOC_SCRATCH_ELEMS
 FUSE_PRECOND = 1
 DENSE = 2
+ADJOINT = 4
+GMRES, BICGSTAB = 0, 1
 
 
 class VieError(RuntimeError):
@@ -56,7 +59,8 @@ class OpInfo(C.Structure):
                 ("factor_entries", C.c_int64), ("self_entries", C.c_int64), ("gain", C.c_double),
                 ("rank_min", C.c_int), ("rank_max", C.c_int), ("rank_mean", C.c_double),
                 ("factor_precision", C.c_int), ("tol", C.c_double), ("apply_bytes", C.c_int64),
-                ("t_assemble_s", C.c_double), ("t_compress_s", C.c_double), ("stored_entries", C.c_int64)]
+                ("t_assemble_s", C.c_double), ("t_compress_s", C.c_double), ("stored_entries", C.c_int64),
+                ("packed_bytes", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -68,7 +72,8 @@ class IncidentC(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_iters", C.c_int), ("precision", C.c_int),
-                ("out_on_device", C.c_int), ("precond", C.c_int), ("launch", C.c_int), ("autotune", C.c_int)]
+                ("out_on_device", C.c_int), ("precond", C.c_int), ("launch", C.c_int), ("autotune", C.c_int),
+                ("method", C.c_int)]
 
 
 class TuneResult(C.Structure):
@@ -285,10 +290,10 @@ class Operator:
                                       _stream(stream)))
 
     def solve(self, khat, pol, tol=1e-6, restart=60, max_iters=2000, precision=C64, precond=1, out_ptr=None,
-              launch=0, autotune=0):
+              launch=0, autotune=0, method=GMRES):
         """Returns (I (numpy complex128 n x nrhs, or None with out_ptr), stats dict, status)."""
         inc, keep, nrhs = _incident_struct(khat, pol)
-        o = SolveOpts(tol, restart, max_iters, precision, 1 if out_ptr else 0, precond, launch, autotune)
+        o = SolveOpts(tol, restart, max_iters, precision, 1 if out_ptr else 0, precond, launch, autotune, method)
         st = SolveStats()
         out = None
         if out_ptr is None:
@@ -316,6 +321,16 @@ class Operator:
         out = np.zeros((nrhs, d.shape[0], 3), np.complex128)
         self.ctx.check(self.L.vie_fields(self.h, None, I.ctypes.data_as(C.c_void_p), nrhs, _dp(d.ravel()),
                                          d.shape[0], 0, out.ctypes.data_as(C.c_void_p), None))
+        return out
+
+    def near_field(self, I, points):
+        """vie_fields mode 1: scattered field at points outside the atoms, (nrhs, npts, 3)."""
+        I = np.ascontiguousarray(np.asarray(I, np.complex128).reshape(self.n, -1).T)
+        nrhs = I.shape[0]
+        d = np.ascontiguousarray(np.asarray(points, np.float64).reshape(-1, 3))
+        out = np.zeros((nrhs, d.shape[0], 3), np.complex128)
+        self.ctx.check(self.L.vie_fields(self.h, None, I.ctypes.data_as(C.c_void_p), nrhs, _dp(d.ravel()),
+                                         d.shape[0], 1, out.ctypes.data_as(C.c_void_p), None))
         return out
 
     def export_block(self, kind, a, b=0, precision=C128):
@@ -374,7 +389,7 @@ def solve_batch(ops, incidents, tol=1e-6, restart=60, max_iters=2000, precision=
         outs.append(np.zeros((n_r, ops[p].n), np.complex128))
     handles = (C.c_void_p * B)(*[op.h.value for op in ops])
     optrs = (C.c_void_p * B)(*[o.ctypes.data for o in outs])
-    so = SolveOpts(tol, restart, max_iters, precision, 0, 1, launch, 0)
+    so = SolveOpts(tol, restart, max_iters, precision, 0, 1, launch, 0, 0)
     stats = (SolveStats * B)()
     status = ctx.check(ctx.L.vie_solve_batch(handles, B, incs, nr, C.byref(so), optrs, stats),
                        ok=(VIE_OK, VIE_ERR_NOT_CONVERGED))
@@ -425,7 +440,7 @@ class Server:
         self.ctx = ctx
         self.L = ctx.L
         self.h = C.c_void_p()
-        so = solve or SolveOpts(1e-6, 60, 2000, C64, 0, 1)
+        so = solve or SolveOpts(1e-6, 60, 2000, C64, 0, 1, 0, 0, 0)
         o = ServeOpts(max_inflight, hbm_budget, tol, so)
         ctx.check(self.L.vie_serve(C.byref(self.h), ctx.h, C.byref(o)))
         self._keep = {}

@@ -3,7 +3,7 @@ RHS, BF16x3 lockstep multi-RHS, the batched union and a served request) on an
 8 x 8 array of 3^3-voxel cubes and an 8 x 8 graded array (three cube sides),
 against the oracle's dense direct solution of the same discrete system
 (Sec. 6.2: the reference solution is the LU solve), and the tensor-core apply
-and the far-field amplitude against the oracle element by element.
+the far-field amplitude and the near field against the oracle element by element.
 
 The dense solutions (6,912 unknowns each) are written by
 tests/golden/make_multilevel_golden.py, which calls only the oracle.
@@ -160,4 +160,23 @@ def test_far_field_amplitude_matches_oracle(ctx, tiny_dense):
     E = op.far_field(I, dirs)[0]                       # npts x 3
     ref = OF.far_field(P, I[:, 0], dirs)
     assert np.max(np.abs(E - ref)) <= 1e-10 * np.max(np.abs(ref))
+    op.close()
+
+
+def test_near_field_matches_oracle(ctx, tiny_dense):
+    # vie_fields mode 1 element by element against the oracle's near field of
+    # the same current, at points above, beside and between the atoms
+    P, Z, b, kh, pol = tiny_dense
+    op = vie.Operator(ctx, workloads.config("tiny")[0])
+    op.compress(1e-4, vie.C64)
+    I, _, status = op.solve(kh[None], pol[None], tol=1e-8)
+    assert status == vie.VIE_OK
+    pts = np.array([[0.0, 0.0, 0.5], [0.3, -0.2, 0.25], [1.5, 0.0, 0.0], [0.0, 0.0, 0.0], [-3.0, 2.0, 1.0]])
+    E = op.near_field(I, pts)[0]
+    ref = OF.near_field(P, I[:, 0], pts)
+    assert np.max(np.abs(E - ref)) <= 1e-10 * np.max(np.abs(ref))
+    # a refused point set leaves the context usable
+    with pytest.raises(vie.VieError):
+        op.near_field(I, np.array([[np.nan, 0.0, 0.0]]))
+    assert np.allclose(op.near_field(I, pts[:1])[0], E[:1], rtol=1e-14, atol=0)
     op.close()

@@ -361,14 +361,15 @@ def test_autotune_variants_agree(ctx, tiny_dense):
     # split-precision variants are admissible for VIE_BF16X3 only
     with pytest.raises(vie.VieError):
         op.tune(vie.C64, nrhs, force=vie.VAR_TCGEN05_BF16X3)
-    for v in (vie.VAR_MMA_BF16X3, vie.VAR_TCGEN05_BF16X3, vie.VAR_TCGEN05_PACKED_BF16X3):
+    for v in (vie.VAR_MMA_BF16X3, vie.VAR_TCGEN05_BF16X3, vie.VAR_TCGEN05_PACKED_BF16X3,
+              vie.VAR_TCGEN05_WS_BF16X3):
         op.tune(vie.BF16X3, nrhs, force=v)
         Y = th.zeros_like(X)
         op.apply(X.data_ptr(), Y.data_ptr(), nrhs, vie.BF16X3, vie.FUSE_PRECOND)
         th.cuda.synchronize()
         assert rel(Y.cpu().numpy(), out[vie.VAR_SIMT_R4]) < 5e-5
     res = op.tune(vie.BF16X3, 64)
-    assert res["variant"] in range(1, 8) and len(res["ms"]) == 7
+    assert res["variant"] in range(1, 10) and len(res["ms"]) == 8
     kh, pol = workloads.angle_sweep(2, 30.0)
     I, st, status = op.solve(kh, pol, tol=1e-6, precision=vie.BF16X3, autotune=1)
     assert status == vie.VIE_OK
@@ -417,23 +418,28 @@ def test_shared_factor_apply(ctx, tiny_dense):
     op.close()
 
 
-def test_tcgen05_packed_equals_unpacked(ctx):
+def test_tcgen05_packed_and_warp_specialised_equal_unpacked(ctx):
     # the packed variant feeds the tensor core the same bf16 planes in the same
-    # MMA order (moved by bulk copies instead of split by the warps): bit-identical
+    # MMA order (moved by bulk copies instead of split by the warps), and so does
+    # the warp-specialised one (producer warps, MMA warp, epilogue warps, two
+    # accumulator buffers): bit-identical, fused and unfused, for column counts
+    # that fill one 64-column pass, a pass plus a ragged tail, and a partial pass
     import torch as th
     g = workloads.square_array(8, 4)
     op = vie.Operator(ctx, g)
     op.compress(1e-4, vie.C64)
-    for nrhs in (64, 70):
+    for nrhs in (8, 16, 64, 70):
         X = th.from_numpy(workloads.random_complex(op.n, 11, cols=nrhs).T.astype(np.complex64).copy()).cuda()
-        out = {}
-        for v in (vie.VAR_TCGEN05_BF16X3, vie.VAR_TCGEN05_PACKED_BF16X3):
-            op.tune(vie.BF16X3, nrhs, force=v)
-            Y = th.zeros_like(X)
-            op.apply(X.data_ptr(), Y.data_ptr(), nrhs, vie.BF16X3, vie.FUSE_PRECOND)
-            th.cuda.synchronize()
-            out[v] = Y.cpu().numpy()
-        assert np.array_equal(out[vie.VAR_TCGEN05_BF16X3], out[vie.VAR_TCGEN05_PACKED_BF16X3])
+        for fl in (vie.FUSE_PRECOND, 0):
+            out = {}
+            for v in (vie.VAR_TCGEN05_BF16X3, vie.VAR_TCGEN05_PACKED_BF16X3, vie.VAR_TCGEN05_WS_BF16X3):
+                op.tune(vie.BF16X3, nrhs, force=v)
+                Y = th.zeros_like(X)
+                op.apply(X.data_ptr(), Y.data_ptr(), nrhs, vie.BF16X3, fl)
+                th.cuda.synchronize()
+                out[v] = Y.cpu().numpy()
+            assert np.array_equal(out[vie.VAR_TCGEN05_BF16X3], out[vie.VAR_TCGEN05_PACKED_BF16X3]), (nrhs, fl)
+            assert np.array_equal(out[vie.VAR_TCGEN05_PACKED_BF16X3], out[vie.VAR_TCGEN05_WS_BF16X3]), (nrhs, fl)
     op.close()
 
 
