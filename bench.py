@@ -14,7 +14,9 @@ Workloads (`--workload`, default multirhs):
             sides (32 polar angles x 2 polarisations), tolerance 1e-4, far
             apply of the inner GMRES on the tensor cores (BF16x3)
   graded    64 x 64 graded array (three cube sides along a lens phase), 4^3
-            voxels, 983,040 unknowns, 16 right-hand sides, tolerance 1e-3
+            voxels, 983,040 unknowns, 16 right-hand sides, tolerance 1e-3; its
+            resonant atoms keep GMRES above 1e-6 within the 3,000-iteration
+            budget, reported as "converged": false
   scale     16 x 16 array of 6^3-voxel cubes, 193,536 unknowns, 1 right-hand
             side, complex float32 applies
 `roofline` is the compressed apply of the inner iteration (the solve's
@@ -62,7 +64,7 @@ WORKLOADS = {
     "graded": dict(
         geometry=lambda: workloads.graded_array(64, 4, 0),
         incident=lambda: workloads.random_directions(16, 0),
-        tol=1e-3, precision="BF16X3", restart=300,
+        tol=1e-3, precision="BF16X3", restart=300, max_iters=3000, may_not_converge=True,
         desc="64x64 graded array (cube sides 0.15/0.2/0.25 along a lens phase, F from seed 0), 4^3 voxels, "
              "983040 unknowns, 16 RHS (seed 0, within 20 deg of normal incidence); compression tolerance 1e-3 "
              "(at 1e-4 the factors would need ~970 GB)",
@@ -445,11 +447,18 @@ def run_serving(args):
     srv.stop()
     lat = sorted(r["t_done"] - r["t_submit"] for r in res)
     span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    busy = max(r["t_done"] for r in res) - min(r["t_start"] for r in res)
     rhs = sum(r["nrhs"] for r in res)
     ok = sum(1 for r in res if r["status"] == 0)
     line = {"metric": "serving solves/s", "value": rhs / span, "unit": "solves/s", "n_gpus": 1,
             "requests": len(res), "completed_ok": ok, "requests_per_s": len(res) / span,
+            "sustainable_requests_per_s": len(res) / busy, "offered_requests_per_s": 20.0,
+            "retries": sum(r["retries"] for r in res),
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "service_s": {"p50": float(np.percentile([r["t_done"] - r["t_start"] for r in res], 50)),
+                          "p99": float(np.percentile([r["t_done"] - r["t_start"] for r in res], 99))},
+            "footprints": [{"ns": q.ns, "nrhs": r["nrhs"], "model": r["footprint"], "peak": r["peak"]}
+                           for q, r in zip(reqs, res)],
             "higher_is_better": True, "dtype": "c64", "data": "synthetic",
             "config": {"workload": "serving", "slots": args.slots, "rate_hz": 20.0,
                        "arrays": "8x8..48x48 cubes of 3^3 voxels", "tol_compress": 1e-4,
@@ -505,6 +514,46 @@ def run_batch(args):
     return 0
 
 
+def run_methods(args):
+    """--methods: the Krylov methods on one operator of the workload, all
+    right-hand sides, inner applies as the workload's: lockstep GMRES (each
+    right-hand side in its own Krylov space), block GMRES (one space for all)
+    and BiCGStab.  Reports time, iterations, applies, residual and the largest
+    relative difference from the lockstep solution; the operator is built
+    once, outside the timed solves."""
+    import torch
+    from paper_2603_10586_gb300 import vie
+    torch.cuda.set_device(0)
+    ctx = vie.Context(0)
+    wl = WORKLOADS[args.workload]
+    kh, pol = wl["incident"]()
+    prec = getattr(vie, wl["precision"])
+    op = vie.Operator(ctx, wl["geometry"]())
+    op.compress(wl["tol"], vie.C64)
+    maxit = wl.get("max_iters", 20000)
+    out = {"metric": "Krylov methods", "workload": args.workload, "nrhs": len(kh), "methods": {}}
+    ref = None
+    for name, method, restart in (("gmres_lockstep", vie.GMRES, wl["restart"]), ("block_gmres", vie.BLOCK_GMRES, 60),
+                                  ("bicgstab", vie.BICGSTAB, 0)):
+        mi = maxit if method != vie.BLOCK_GMRES else max(1, maxit // 4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        I, st, status = op.solve(kh, pol, tol=TOL_SOLVE, precision=prec, restart=restart, max_iters=mi, method=method)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        if ref is None:
+            ref = I
+        diff = max(float(np.linalg.norm(I[:, c] - ref[:, c]) / np.linalg.norm(ref[:, c])) for c in range(len(kh)))
+        out["methods"][name] = {"s": t, "status": status, "iterations": st["iterations"], "applies": st["applies"],
+                                "refinements": st["refinements"], "residual": st["residual"],
+                                "true_residual": st["true_residual"], "max_rel_diff_vs_lockstep": diff,
+                                "solves_per_s": len(kh) / t}
+    print(json.dumps(out), flush=True)
+    op.close()
+    ctx.close()
+    return 0
+
+
 def run_profile(args):
     """--profile: one untimed solve from geometry of the workload followed by 10
     inner-iteration applies, for ncu captures (no warm-up, no timing, no
@@ -527,7 +576,10 @@ def run_profile(args):
     k = len(kh)
     if args.profile_case != "small":
         out = torch.empty((k, op.n), dtype=torch.complex128, device="cuda")
-        op.solve(kh, pol, tol=TOL_SOLVE, precision=prec, restart=wl["restart"], out_ptr=out.data_ptr())
+        # host-launched Arnoldi steps (launch = 1: the same kernels as the graph) so that a
+        # profiler's launch list sees every kernel of the solve
+        op.solve(kh, pol, tol=TOL_SOLVE, precision=prec, restart=wl["restart"], out_ptr=out.data_ptr(), launch=1,
+                 max_iters=wl.get("max_iters", 20000))
     x = torch.randn((k, op.n), dtype=torch.complex64, device="cuda")
     y = torch.empty_like(x)
     for _ in range(10 if args.profile_case != "small" else 3):
@@ -574,6 +626,7 @@ def main():
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--batch", action="store_true", help="sequential against batched solves of the serving mix")
     ap.add_argument("--batch-max-side", type=int, default=48, help="largest array side of the --batch mix")
+    ap.add_argument("--methods", action="store_true", help="lockstep GMRES, block GMRES and BiCGStab compared")
     ap.add_argument("--profile", action="store_true", help="one untimed step for ncu captures")
     ap.add_argument("--profile-case", default="full", choices=["full", "small"])
     args = ap.parse_args()
@@ -585,6 +638,8 @@ def main():
         return run_serving(args)
     if args.batch:
         return run_batch(args)
+    if args.methods:
+        return run_methods(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -613,8 +668,9 @@ def main():
         op = vie.Operator(ctx, g)
         op.compress(wl["tol"], vie.C64)
         I, stats, status = op.solve(kh, pol, tol=TOL_SOLVE, restart=wl["restart"], precision=prec,
-                                    max_iters=20000, out_ptr=None if host else out.data_ptr())
-        if status != vie.VIE_OK:
+                                    max_iters=wl.get("max_iters", 20000), out_ptr=None if host else out.data_ptr())
+        state["converged"] = status == vie.VIE_OK
+        if status != vie.VIE_OK and not wl.get("may_not_converge"):
             raise RuntimeError(f"solve did not converge: {stats['residual']}")
         state["stats"], state["info"] = stats, op.info()
         if "keep" in state:
@@ -749,7 +805,7 @@ def main():
             "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
             "breakdown_s": {"assemble": info["t_assemble_s"], "compress": info["t_compress_s"],
                             "solve": stats["t_solve_s"]},
-            "solver": {"iterations": stats["iterations"], "applies": stats["applies"],
+            "solver": {"converged": state["converged"], "iterations": stats["iterations"], "applies": stats["applies"],
                        "refinements": stats["refinements"], "residual": stats["residual"],
                        "true_residual": stats["true_residual"]},
             "accuracy": accuracy,

@@ -108,7 +108,9 @@ enum vie_variant {
 
 typedef struct vie_ctx_opts {
     int device;            /* CUDA device ordinal */
-    size_t hbm_budget;     /* bytes the context may allocate (0 = free memory - 4 GiB) */
+    size_t hbm_budget;     /* bytes the context may allocate: an allocation beyond it fails with
+                              VIE_ERR_OOM before cudaMalloc is asked (0 = no cap; free memory - 4 GiB
+                              sizes the compression batches) */
     int verbose;           /* 0 quiet, 1 stage timings on stderr */
     int no_sharing;        /* 0 (default): far blocks that are translated copies of one another
                               (same level, same atom types, same relative atom positions, as in a
@@ -162,8 +164,10 @@ typedef struct vie_solve_opts {
     double tol;                /* relative residual ||P^-1 (b - Zs I)|| / ||P^-1 b|| (1e-6) */
     int restart;               /* GMRES restart length m (e.g. 60); larger than 512 is taken as 512 */
     int max_iters;             /* iteration cap (e.g. 2000) */
-    int precision;             /* VIE_C64: FP32 inner applies with FP64 Krylov and FP64
-                                  residual refinement; VIE_BF16X3: as VIE_C64 but the far part of
+    int precision;             /* VIE_C64: FP32 inner applies with FP64-accurate Krylov and FP64
+                                  residual refinement (a cycle that ends while every residual is above
+                                  100 x tol restarts from a residual in the inner precision; only a
+                                  float64-accurate residual ends a solve); VIE_BF16X3: as VIE_C64 but the far part of
                                   the inner applies on the tensor cores (split bf16, FP32 accumulation);
                                   VIE_C128: all-FP64 (needs C128 factors) */
     int out_on_device;         /* 1: I_out is a device pointer, 0: host pointer */
@@ -173,10 +177,14 @@ typedef struct vie_solve_opts {
                                   1: the host launches every step and reads the continue flag */
     int autotune;              /* 1: run vie_tune for the first cycle's right-hand-side count
                                   (unless already tuned) before the solve */
-    int method;                /* 0: restarted GMRES (Sec. 6, the paper's choice); 1: BiCGStab, the
+    int method;                /* 0: restarted GMRES (Sec. 6, the paper's choice), each right-hand side
+                                  in its own Krylov space, all advanced in lockstep; 1: BiCGStab, the
                                   method Sec. 6 compares it with (same preconditioner, precisions and
                                   stopping test; two applies per iteration; restart and launch are
-                                  not used; vie_solve only) */
+                                  not used); 2: block GMRES, one Krylov space shared by all right-hand
+                                  sides (float64 block Gram-Schmidt; restart counts block steps and is
+                                  capped so that (restart + 1) nrhs <= 512; launch is not used).
+                                  Methods 1 and 2: vie_solve only */
 } vie_solve_opts;
 
 /* Result of vie_tune. */
@@ -356,7 +364,11 @@ int vie_lpt_assign(const double* w, int64_t n, int n_proc, int* owner, double* l
 /* ---- serving (continuous batching) ------------------------------------------
  * Requests (geometry + plane waves) are admitted while the modelled HBM
  * footprint of their compressed operator, inverses and Krylov state fits
- * the budget; admitted requests run concurrently, each on its own CUDA stream. */
+ * the budget; admitted requests run concurrently, each on its own CUDA stream.
+ * A request's allocations are capped at its admitted footprint; one that
+ * reaches the cap goes back to the head of the queue with twice the footprint
+ * (at most the budget) and runs again when that much is free; one that fails
+ * with the whole budget returns VIE_ERR_ADMISSION. */
 typedef struct vie_serve_opts {
     int max_inflight;          /* concurrent requests (slots) */
     size_t hbm_budget;         /* bytes for all in-flight requests (0 = context budget) */
@@ -378,7 +390,10 @@ typedef struct vie_result {
     double* I;                 /* host c128 n x nrhs, owned by the server until vie_result_free */
     vie_solve_stats stats;
     double t_submit_s, t_start_s, t_done_s; /* server clock */
-    int64_t footprint_bytes;
+    int64_t footprint_bytes;   /* footprint the request finally ran with */
+    int retries;               /* times it went back to the queue after its allocations met the
+                                  admitted footprint (each retry doubles it) */
+    int64_t peak_bytes;        /* device bytes the request held at most */
 } vie_result;
 
 int vie_serve(vie_server** out, vie_ctx* ctx, const vie_serve_opts* opts);

@@ -37,6 +37,15 @@ void op_apply_fused32(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t
     self_gemm<float2, float2>(op, op.d_inv32.as<float2>(), x, n, F, n, y, n, nrhs, 1, s);
 }
 
+void op_apply_plain32(Op& op, const float2* x, float2* y, int nrhs, int precision, cudaStream_t s) {
+    if (op.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "float32 applies need VIE_C64 factors");
+    const int64_t n = op.n();
+    ensure_F(op, (size_t)n * nrhs * sizeof(float2));
+    float2* F = op.d_F.as<float2>();
+    far32(op, x, n, F, n, nrhs, precision, s);
+    self_gemm<float2, float2>(op, op.d_zself32.as<float2>(), x, n, F, n, y, n, nrhs, 0, s);
+}
+
 void op_apply_fused_bf16x3(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s) {
     if (op.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "VIE_BF16X3 applies need VIE_C64 factors");
     const int64_t n = op.n();
@@ -90,6 +99,7 @@ namespace {
 template <class F>
 int guarded(vie_ctx* ctx, F&& f) {
     cudaGetLastError();  // an earlier failure elsewhere is not this call's error
+    AllocScope scope(ctx ? &ctx->c : nullptr);
     try {
         f();
         if (ctx) ctx->c.err.clear();
@@ -107,6 +117,18 @@ int guarded(vie_ctx* ctx, F&& f) {
 }
 
 vie_ctx* ctx_of(vie_op* op) { return op ? static_cast<vie_ctx*>(op->o.ctx->owner) : nullptr; }
+
+}  // namespace
+
+// server use: the cap of a slot context is the footprint its request was
+// admitted with; the peak shows what the request really held
+void ctx_set_cap(vie_ctx* ctx, int64_t cap) {
+    ctx->c.cap = cap;
+    ctx->c.peak = ctx->c.allocated.load();
+}
+int64_t ctx_peak(vie_ctx* ctx) { return ctx->c.peak.load(); }
+
+namespace {
 
 void set_device(Ctx& c) { VIE_CUDA(cudaSetDevice(c.device)); }
 
@@ -151,6 +173,7 @@ int vie_create(vie_ctx** out, const vie_ctx_opts* opts) {
         VIE_CUDA(cudaMemGetInfo(&fr, &tot));
         size_t reserve = (size_t)4 << 30;
         c.budget = (opts && opts->hbm_budget) ? opts->hbm_budget : (fr > 2 * reserve ? fr - reserve : fr / 2);
+        c.cap = (opts && opts->hbm_budget) ? (int64_t)opts->hbm_budget : 0;
     });
     if (st != VIE_OK) {
         // keep the message readable through a stub context

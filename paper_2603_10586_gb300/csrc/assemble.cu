@@ -864,8 +864,8 @@ __global__ void near_field_kernel(DevMesh m, GeoPtrs geo, int N, double k, const
     if (threadIdx.x == 0)
         for (int d = 0; d < 3; ++d) {
             const double2 a = red[d][0], gr = red[3 + d][0];
-            // -j k A + grad Phi / (j k) = (k A.y - gr.y / k, -k A.x + gr.x / k)
-            out[((size_t)c * npts + ip) * 3 + d] = make_double2(k * a.y - gr.y / k, -k * a.x + gr.x / k);
+            // -j k A + grad Phi / (j k) = (k A.y + gr.y / k, -k A.x - gr.x / k)
+            out[((size_t)c * npts + ip) * 3 + d] = make_double2(k * a.y + gr.y / k, -k * a.x - gr.x / k);
         }
 }
 

@@ -57,16 +57,25 @@ extern std::atomic<long long> g_kernel_launches;
 // ---------------------------------------------------------------------------
 // device buffer (RAII)
 // ---------------------------------------------------------------------------
+struct Ctx;
+// Device allocation; charged to the context whose C-ABI call is running on
+// this thread (see AllocScope), which may cap its total (VIE_ERR_OOM before
+// cudaMalloc is asked).
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    Ctx* owner = nullptr;
     DevBuf() = default;
     explicit DevBuf(size_t b) { alloc(b); }
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes), owner(o.owner) { o.p = nullptr; o.bytes = 0; o.owner = nullptr; }
     DevBuf& operator=(DevBuf&& o) noexcept {
-        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        if (this != &o) {
+            release();
+            p = o.p; bytes = o.bytes; owner = o.owner;
+            o.p = nullptr; o.bytes = 0; o.owner = nullptr;
+        }
         return *this;
     }
     ~DevBuf() { release(); }
@@ -220,6 +229,18 @@ struct Ctx {
     int verbose = 0;
     int no_sharing = 0;
     void* owner = nullptr;  // the C-ABI handle holding this context
+    // device bytes held by this context's buffers, the largest seen, and the cap
+    // (0: none) above which an allocation is refused with VIE_ERR_OOM
+    std::atomic<int64_t> allocated{0}, peak{0};
+    std::atomic<int64_t> cap{0};
+};
+
+// The context charged for device allocations made by this thread while a
+// C-ABI call of that context runs (set by the call's entry, restored on exit).
+struct AllocScope {
+    Ctx* prev;
+    explicit AllocScope(Ctx* c);
+    ~AllocScope();
 };
 
 // device-side block description used by the apply kernels

@@ -22,22 +22,48 @@ double now_s() {
     return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
+static thread_local Ctx* t_alloc_ctx = nullptr;
+
+AllocScope::AllocScope(Ctx* c) : prev(t_alloc_ctx) { t_alloc_ctx = c; }
+AllocScope::~AllocScope() { t_alloc_ctx = prev; }
+
 void DevBuf::alloc(size_t b) {
     release();
     if (b == 0) b = 1;
+    Ctx* c = t_alloc_ctx;
+    if (c) {
+        const int64_t cap = c->cap.load();
+        const int64_t now = c->allocated.fetch_add((int64_t)b) + (int64_t)b;
+        if (cap > 0 && now > cap) {
+            c->allocated.fetch_sub((int64_t)b);
+            fail(VIE_ERR_OOM, "allocation of " + std::to_string(b) + " bytes would exceed the context's cap of " +
+                                  std::to_string(cap) + " bytes");
+        }
+    }
     cudaError_t e = cudaMalloc(&p, b);
     if (e != cudaSuccess) {
         p = nullptr;
+        if (c) c->allocated.fetch_sub((int64_t)b);
         cudaGetLastError();
         fail(VIE_ERR_OOM, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
     }
     bytes = b;
+    owner = c;
+    if (c) {
+        int64_t pk = c->peak.load(), cur = c->allocated.load();
+        while (cur > pk && !c->peak.compare_exchange_weak(pk, cur)) {
+        }
+    }
 }
 
 void DevBuf::release() {
-    if (p) cudaFree(p);
+    if (p) {
+        cudaFree(p);
+        if (owner) owner->allocated.fetch_sub((int64_t)bytes);
+    }
     p = nullptr;
     bytes = 0;
+    owner = nullptr;
 }
 
 // ---------------------------------------------------------------------------

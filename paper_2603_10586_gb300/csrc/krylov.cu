@@ -532,15 +532,18 @@ __global__ void __launch_bounds__(kT) k_scatter_norm(KrylovArgs a, const double2
     if (threadIdx.x == 0) a.npart[(int64_t)i * a.nblk_max + blockIdx.x] = s;
 }
 
+// init = 1: the first residual (sets beta0); 2: a residual from the inner
+// precision, which never ends a column's solve (only a float64-accurate one
+// may); 0: a float64-accurate refinement residual
 __global__ void k_cycle_end(KrylovArgs a, int k, int nblk, int init) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0 && !init) a.ctr[KR_REFIN] += 1;
+    if (i == 0 && init == 0) a.ctr[KR_REFIN] += 1;
     if (i >= k) return;
     const int c = a.cols[i];
     const double bn = sqrt(a.nsq[i]);
     if (!isfinite(bn)) a.ctr[KR_NAN] = 1;
     a.beta[c] = bn;
-    if (init) {
+    if (init == 1) {
         a.beta0[c] = bn;
         a.res[c] = bn > 0.0 ? 1.0 : 0.0;
         a.done[c] = bn > 0.0 ? 0 : 1;
@@ -548,7 +551,7 @@ __global__ void k_cycle_end(KrylovArgs a, int k, int nblk, int init) {
     } else {
         const double r = a.beta0[c] > 0.0 ? bn / a.beta0[c] : 0.0;
         a.res[c] = r;
-        a.done[c] = (r <= a.tol || a.iters[c] >= a.maxit || bn == 0.0) ? 1 : 0;
+        a.done[c] = ((init == 0 && r <= a.tol) || a.iters[c] >= a.maxit || bn == 0.0) ? 1 : 0;
     }
 }
 

@@ -88,7 +88,8 @@ void kr_gather_cols(const KrylovArgs& a, const double2* src, double2* dst, int k
 void kr_sub_cols(const KrylovArgs& a, const double2* b, const double2* T, double2* R, int k, int nblk, cudaStream_t s);
 // W[:, cols[i]] = Wl[:, i] (W may equal Wl with cols the identity) and its squared-norm partials
 void kr_scatter_norm(const KrylovArgs& a, const double2* Wl, double2* W, int k, int nblk, cudaStream_t s);
-// beta, res and done of the slots' columns from the norm partials; init also sets beta0
+// beta, res and done of the slots' columns from the norm partials; init = 1 also
+// sets beta0; init = 2 marks a residual of the inner precision (it ends no solve)
 void kr_cycle_end(const KrylovArgs& a, int k, int nblk, int init, cudaStream_t s);
 // norms of the k columns of A (n x k, column i holding the rows of column
 // cols ? cols[i] : i) into d_out[cols ? cols[i] : i]; d_part holds k * nblk doubles
@@ -121,12 +122,16 @@ void check_solve_opts(const Op& op, const vie_solve_opts* o, int nrhs);
 // restarted GMRES of every column of b (device, n x nrhs) into X
 GmresOutcome run_gmres(Op& op, const ColumnLayout& lay, const double2* b, double2* X, const vie_solve_opts& o,
                        int nrhs);
+// block GMRES over one Krylov space shared by the nrhs columns (blockgmres.cpp)
+GmresOutcome run_block_gmres(Op& op, const double2* b, double2* X, const vie_solve_opts& o, int nrhs);
 // left-preconditioned BiCGStab of every column of b (device, n x nrhs) into X (bicgstab.cu)
 GmresOutcome run_bicgstab(Op& op, const double2* b, double2* X, const vie_solve_opts& o, int nrhs);
 // stats of columns [c0, c1); returns VIE_OK or VIE_ERR_NOT_CONVERGED
 int fill_stats(const GmresOutcome& r, int c0, int c1, double tol, double t0, vie_solve_stats* st);
 
 // operator applications used by the solver (solve.cpp / api.cpp)
+// y = Zs x in complex float32 or with the far part in BF16x3 (precision), x, y: n x nrhs, ld = n
+void op_apply_plain32(Op& op, const float2* x, float2* y, int nrhs, int precision, cudaStream_t s);
 // y = P^-1 Zs x in complex float32 (fused preconditioner), x, y: n x nrhs, ld = n
 void op_apply_fused32(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s);
 // y = P^-1 Zs x with the far part on the tensor cores (BF16x3), float32 vectors

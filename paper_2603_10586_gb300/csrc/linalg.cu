@@ -11,14 +11,7 @@ namespace vie {
 
 namespace {
 
-// augmented matrix Maug = [A | I], np x 2np, column-major (ld = np)
-__global__ void gj_init(const double2* A, double2* M, int np) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)np * 2 * np) return;
-    int i = (int)(t % np), j = (int)(t / np);
-    M[t] = j < np ? A[i + (int64_t)j * np] : make_double2(i == j - np ? 1.0 : 0.0, 0.0);
-}
-
+// The augmented matrix Maug = [A | I] is np x 2np, column-major (ld = np).
 // one block: pick the pivot of column k, swap rows, normalise the pivot row,
 // save the elimination factors of column k
 __global__ void gj_pivot(double2* M, int np, int k, double2* fac, int* status) {
@@ -82,10 +75,19 @@ __global__ void gj_eliminate(double2* M, int np, int k, const double2* fac) {
     M[i + (int64_t)j * np] = v;
 }
 
-__global__ void gj_extract(const double2* M, double2* inv, int np) {
+// Maug = [A | I] and the extraction of A^-1, through device pointer tables (a
+// captured graph replays them for several blocks)
+__global__ void gj_init_ptr(const double2* const* A, double2* M, int np) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)np * 2 * np) return;
+    int i = (int)(t % np), j = (int)(t / np);
+    M[t] = j < np ? (*A)[i + (int64_t)j * np] : make_double2(i == j - np ? 1.0 : 0.0, 0.0);
+}
+
+__global__ void gj_extract_ptr(const double2* M, double2* const* inv, int np) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)np * np) return;
-    inv[t] = M[t + (int64_t)np * np];
+    (*inv)[t] = M[t + (int64_t)np * np];
 }
 
 __global__ void c128_to_c64(const double2* s, float2* d, int64_t n) {
@@ -177,20 +179,49 @@ void invert_self_blocks(Op& op) {
     op.d_inv64.alloc((size_t)op.T * np * np * sizeof(double2));
     DevBuf M((size_t)np * 2 * np * sizeof(double2)), fac(np * sizeof(double2)), st(sizeof(int));
     VIE_CUDA(cudaMemsetAsync(st.p, 0, sizeof(int), s));
+    // the 2 np pivot and elimination launches of a type are captured once into
+    // a CUDA graph and replayed for every type (one graph launch per type
+    // instead of 2 np kernel launches); the graph reads the type's block
+    // through the pointer table `src`
+    DevBuf src(sizeof(const double2*)), dst(sizeof(double2*));
+    cudaGraphExec_t exec = nullptr;
+    {
+        VIE_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t graph = nullptr;
+        try {
+            const int64_t tot = (int64_t)np * 2 * np;
+            gj_init_ptr<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src.as<const double2*>(), M.as<double2>(), np);
+            for (int k = 0; k < np; ++k) {
+                gj_pivot<<<1, 1024, 0, s>>>(M.as<double2>(), np, k, fac.as<double2>(), st.as<int>());
+                int64_t work = (int64_t)np * (2 * np - k);
+                gj_eliminate<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(M.as<double2>(), np, k,
+                                                                            fac.as<double2>());
+            }
+            gj_extract_ptr<<<(unsigned)(((int64_t)np * np + 255) / 256), 256, 0, s>>>(M.as<double2>(),
+                                                                                     dst.as<double2*>(), np);
+        } catch (...) {
+            cudaStreamEndCapture(s, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            throw;
+        }
+        VIE_CUDA(cudaStreamEndCapture(s, &graph));
+        cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) fail(VIE_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    struct ExecGuard {
+        cudaGraphExec_t e;
+        ~ExecGuard() { cudaGraphExecDestroy(e); }
+    } guard{exec};
     for (int t = 0; t < op.T; ++t) {
         const double2* A = op.d_zself64.as<double2>() + (size_t)t * np * np;
-        int64_t tot = (int64_t)np * 2 * np;
-        gj_init<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A, M.as<double2>(), np);
-        for (int k = 0; k < np; ++k) {
-            gj_pivot<<<1, 1024, 0, s>>>(M.as<double2>(), np, k, fac.as<double2>(), st.as<int>());
-            int64_t work = (int64_t)np * (2 * np - k);
-            gj_eliminate<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(M.as<double2>(), np, k, fac.as<double2>());
-        }
-        VIE_COUNT_LAUNCH(2 * np);
-        VIE_CHECK_LAUNCH();
-        gj_extract<<<(unsigned)(((int64_t)np * np + 255) / 256), 256, 0, s>>>(
-            M.as<double2>(), op.d_inv64.as<double2>() + (size_t)t * np * np, np);
-        VIE_CHECK_LAUNCH();
+        double2* Inv = op.d_inv64.as<double2>() + (size_t)t * np * np;
+        VIE_CUDA(cudaMemcpyAsync(src.p, &A, sizeof(A), cudaMemcpyHostToDevice, s));
+        VIE_CUDA(cudaMemcpyAsync(dst.p, &Inv, sizeof(Inv), cudaMemcpyHostToDevice, s));
+        VIE_CUDA(cudaGraphLaunch(exec, s));
+        VIE_CUDA(cudaStreamSynchronize(s));  // the pointer table is rewritten for the next type
+        VIE_COUNT_LAUNCH(2 * np + 2);
     }
     int status = 0;
     VIE_CUDA(cudaMemcpyAsync(&status, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -7,7 +7,15 @@
 // Krylov basis, solver vectors, compression workspace) fits in what the
 // in-flight requests leave of the budget.  A request that cannot fit even
 // alone is rejected (VIE_ERR_ADMISSION).  Every wait is bounded.
+//
+// The slot's context refuses allocations beyond the footprint its request
+// was admitted with, so an under-estimate cannot take memory that another
+// request was promised: the allocation fails with VIE_ERR_OOM on the host,
+// and the request goes back to the head of the queue with twice the
+// footprint (at most the whole budget), to run again once that much is free.
+// A request that fails this way with the whole budget is rejected.
 #include <chrono>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -18,12 +26,17 @@
 
 #include "common.h"
 
+// slot-context hooks of the library (api.cpp)
+void ctx_set_cap(vie_ctx* ctx, int64_t cap);
+int64_t ctx_peak(vie_ctx* ctx);
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
 
 struct Pending {
     uint64_t ticket;
+    int retries = 0;
     std::vector<double> centres, sides, eps, khat, pol;
     std::vector<int> types, nv;
     int n_atoms, n_types, nrhs;
@@ -50,6 +63,11 @@ int64_t model_footprint(const Pending& p, int restart) {
     // compression workspace: the largest batch of formed blocks
     int64_t big = std::min<int64_t>(n, (int64_t)16 * np);
     b += std::min<int64_t>(big * big * 8 * 4, (int64_t)8 << 30);
+    // a test of the back-off path scales the model down (VIE_TEST_FOOTPRINT_SCALE)
+    if (const char* e = std::getenv("VIE_TEST_FOOTPRINT_SCALE")) {
+        const double f = std::atof(e);
+        if (f > 0) b = std::max<int64_t>(1 << 20, (int64_t)(b * f));
+    }
     return b;
 }
 
@@ -96,6 +114,7 @@ struct vie_server {
             res.footprint_bytes = p.footprint;
             vie_geometry g{p.n_atoms, p.centres.data(), p.types.data(), p.n_types, p.sides.data(), p.nv.data(),
                            p.eps.data()};
+            ctx_set_cap(ctx, p.footprint);
             vie_op* op = nullptr;
             int st = vie_assemble(ctx, &g, p.wavelength, &op);
             if (st == VIE_OK) st = vie_compress(op, opts.tol > 0 ? opts.tol : 1e-4, VIE_C64);
@@ -110,11 +129,28 @@ struct vie_server {
                 st = vie_solve(op, &inc, p.nrhs, &so, res.I, &res.stats);
             }
             if (op) vie_op_destroy(op);
+            res.peak_bytes = ctx_peak(ctx);
+            if (st == VIE_ERR_OOM) {
+                std::free(res.I);
+                res.I = nullptr;
+                std::lock_guard<std::mutex> lk(mu);
+                inflight_bytes -= p.footprint;
+                if (p.footprint < budget) {
+                    // back off: wait at the head of the queue for twice the memory
+                    p.footprint = std::min<int64_t>(budget, 2 * p.footprint);
+                    p.retries += 1;
+                    queue.push_front(std::move(p));
+                    cv_work.notify_all();
+                    continue;
+                }
+                st = VIE_ERR_ADMISSION;  // did not fit with the whole budget
+            }
             res.status = st;
+            res.retries = p.retries;
             res.t_done_s = clock_s();
             {
                 std::lock_guard<std::mutex> lk(mu);
-                inflight_bytes -= p.footprint;
+                if (res.status != VIE_ERR_ADMISSION) inflight_bytes -= p.footprint;
                 Done& d = results[p.ticket];
                 d.r = res;
                 d.ready = true;

@@ -54,6 +54,7 @@ struct Gmres {
     KrylovArgs a{};
     std::map<int, CycleGraph> graphs;
     int* h_pinned = nullptr;  // [KR_NCTR + nrhs] host-visible copy of counters and done flags
+    std::vector<double> h_res; // latest residual per column (relative)
 
     Gmres(Op& op_, const vie_solve_opts& o_, int nrhs_, const ColumnLayout& lay_)
         : op(op_), o(o_), lay(lay_), s(op_.ctx->stream), n(op_.n()), nrhs(nrhs_), n_sm(op_.ctx->n_sm) {
@@ -192,24 +193,41 @@ struct Gmres {
         kr_givens(a, k, nblk, hnd, use_handle, st);
     }
 
-    // x += V y, then the float64 refinement residual W = M^-1 (b - Zs x) of the slots' columns
-    void launch_post(int k, const double2* b, double2* X, cudaStream_t st) {
+    // x += V y, then the residual W = M^-1 (b - Zs x) of the slots' columns that
+    // starts the next cycle: float64-accurate (the refinement step), or, while
+    // the residual is still far above the tolerance (cheap), with the inner
+    // apply's precision, which is accurate enough to restart from and never
+    // ends a solve
+    void launch_post(int k, const double2* b, double2* X, cudaStream_t st, bool cheap) {
         const int nblk = kr_nblk(n, k, n_sm);
         restore_colr(st);
         kr_update(a, X, k, nblk, st);
+        launch_residual(k, b, X, st, cheap);
+    }
+    void launch_residual(int k, const double2* b, const double2* X, cudaStream_t st, bool cheap) {
+        const int nblk = kr_nblk(n, k, n_sm);
         kr_gather_cols(a, X, Xl.as<double2>(), k, nblk, st);
-        op_apply64(op, Xl.as<double2>(), T.as<double2>(), k, st);
+        if (cheap) {
+            float2* x32 = reinterpret_cast<float2*>(Xg.p);
+            float2* y32 = reinterpret_cast<float2*>(Yg.p);
+            convert_c128_to_c64(Xl.p, x32, n * k, st);
+            op_apply_plain32(op, x32, y32, k, o.precision == VIE_BF16X3 ? VIE_BF16X3 : VIE_C64, st);
+            convert_c64_to_c128(y32, T.p, n * k, st);
+        } else {
+            op_apply64(op, Xl.as<double2>(), T.as<double2>(), k, st);
+        }
         kr_sub_cols(a, b, T.as<double2>(), Rl.as<double2>(), k, nblk, st);
         kr_colnorms(a, Rl.as<double2>(), k, nblk, a.cols, rpart.as<double>(), a.rnorm, st);
         if (o.precond) op_precond64(op, Rl.as<double2>(), Wl.as<double2>(), k, st);
         else VIE_CUDA(cudaMemcpyAsync(Wl.p, Rl.p, (size_t)n * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
         kr_scatter_norm(a, Wl.as<double2>(), W.as<double2>(), k, nblk, st);
-        kr_cycle_end(a, k, nblk, 0, st);
+        kr_cycle_end(a, k, nblk, cheap ? 2 : 0, st);
     }
 
     // one restart cycle as a CUDA graph: pre -> while (continue) { Arnoldi step } -> post
-    CycleGraph& graph_for(int k, const double2* b, double2* X) {
-        auto it = graphs.find(k);
+    CycleGraph& graph_for(int k, const double2* b, double2* X, bool cheap) {
+        const int key = 2 * k + (cheap ? 1 : 0);
+        auto it = graphs.find(key);
         if (it != graphs.end()) return it->second;
         if (!s_body) VIE_CUDA(cudaStreamCreateWithFlags(&s_body, cudaStreamNonBlocking));
         CycleGraph cg;
@@ -245,7 +263,7 @@ struct Gmres {
             VIE_CUDA(cudaStreamEndCapture(s_body, &body));
             const long long c2 = g_kernel_launches.load();
             VIE_CUDA(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-            launch_post(k, b, X, s);
+            launch_post(k, b, X, s, cheap);
             const long long c3 = g_kernel_launches.load();
             VIE_CUDA(cudaStreamEndCapture(s, &graph));
             cg.pre = c1 - c0;
@@ -262,12 +280,14 @@ struct Gmres {
         cudaError_t e = cudaGraphInstantiate(&cg.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) fail(VIE_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-        return graphs.emplace(k, cg).first->second;
+        return graphs.emplace(key, cg).first->second;
     }
 
     void read_state() {
         VIE_CUDA(cudaMemcpyAsync(h_pinned, ctr.p, KR_NCTR * sizeof(int), cudaMemcpyDeviceToHost, s));
         VIE_CUDA(cudaMemcpyAsync(h_pinned + KR_NCTR, done.p, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+        h_res.resize(nrhs);
+        VIE_CUDA(cudaMemcpyAsync(h_res.data(), res.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
         VIE_CUDA(cudaStreamSynchronize(s));
         // a tensor-core kernel that gave up waiting leaves its output incomplete
         // (and may thereby cause the non-finite values seen next): report it
@@ -334,6 +354,13 @@ struct Gmres {
             VIE_CUDA(cudaMemcpyAsync(cols.p, live.data(), k * sizeof(int), cudaMemcpyHostToDevice, s));
             set_colr(live);
             const int it0 = h_pinned[KR_IT];
+            // the residual that ends this cycle in the inner precision while every
+            // live column is still above 1000 x the tolerance (that residual only
+            // starts the next cycle; the solve ends on a float64-accurate one)
+            double worst = 0.0;
+            for (int c : live) worst = std::max(worst, h_res[c]);
+            const double near = 100.0 * a.tol;
+            const bool cheap = c64 && worst > near && it0 + m < a.maxit;
             if (o.launch == 1) {
                 launch_pre(k, s);
                 do {
@@ -341,13 +368,25 @@ struct Gmres {
                     VIE_CUDA(cudaMemcpyAsync(h_pinned, ctr.p, KR_NCTR * sizeof(int), cudaMemcpyDeviceToHost, s));
                     VIE_CUDA(cudaStreamSynchronize(s));
                 } while (h_pinned[KR_CONT] && !h_pinned[KR_NAN]);
-                launch_post(k, b, X, s);
+                launch_post(k, b, X, s, cheap);
                 read_state();
             } else {
-                CycleGraph& cg = graph_for(k, b, X);
+                CycleGraph& cg = graph_for(k, b, X, cheap);
                 VIE_CUDA(cudaGraphLaunch(cg.exec, s));
                 read_state();
                 VIE_COUNT_LAUNCH(cg.pre + cg.post + cg.body * (long long)(h_pinned[KR_IT] - it0));
+            }
+            if (cheap) {
+                // a column that came near the tolerance gets its float64-accurate
+                // residual now, from the same iterate, so that no Arnoldi step is
+                // spent on a solution that may already be converged
+                bool close = false;
+                for (int c : live) close |= h_res[c] <= near;
+                if (close) {
+                    restore_colr(s);
+                    launch_residual(k, b, X, s, false);
+                    read_state();
+                }
             }
         }
     }
@@ -363,7 +402,8 @@ void check_solve_opts(const Op& op, const vie_solve_opts* o, int nrhs) {
         fail(VIE_ERR_INVALID_ARG, "solve precision must be VIE_C64, VIE_BF16X3 or VIE_C128");
     if (o->launch != 0 && o->launch != 1) fail(VIE_ERR_INVALID_ARG, "solve launch must be 0 (graph) or 1 (host loop)");
     if (nrhs < 1 || nrhs > 1024) fail(VIE_ERR_INVALID_ARG, "a solve takes 1 to 1024 right-hand sides");
-    if (o->method != 0 && o->method != 1) fail(VIE_ERR_INVALID_ARG, "solve method must be 0 (GMRES) or 1 (BiCGStab)");
+    if (o->method < 0 || o->method > 2)
+        fail(VIE_ERR_INVALID_ARG, "solve method must be 0 (GMRES), 1 (BiCGStab) or 2 (block GMRES)");
 }
 
 GmresOutcome run_gmres(Op& op, const ColumnLayout& lay, const double2* b, double2* X, const vie_solve_opts& o,
@@ -431,8 +471,9 @@ int solve(Op& op, const vie_incident* inc, int nrhs, const vie_solve_opts* o, vo
         X = xdev.as<double2>();
     }
     const ColumnLayout lay = ColumnLayout::single(n, nrhs);
-    const GmresOutcome r = o->method == 1 ? run_bicgstab(op, b.as<double2>(), X, *o, nrhs)
-                                          : run_gmres(op, lay, b.as<double2>(), X, *o, nrhs);
+    const GmresOutcome r = o->method == 1   ? run_bicgstab(op, b.as<double2>(), X, *o, nrhs)
+                           : o->method == 2 ? run_block_gmres(op, b.as<double2>(), X, *o, nrhs)
+                                            : run_gmres(op, lay, b.as<double2>(), X, *o, nrhs);
     if (!o->out_on_device) {
         VIE_CUDA(cudaMemcpyAsync(I_out, X, (size_t)n * nrhs * sizeof(double2), cudaMemcpyDeviceToHost, s));
         VIE_CUDA(cudaStreamSynchronize(s));

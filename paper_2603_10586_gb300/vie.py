@@ -34,7 +34,7 @@ NOALLOC_SCRATCH_ELEMS = 1 << 22   # VIE_NOALLOC_SCRATCH_ELEMS
 FUSE_PRECOND = 1
 DENSE = 2
 ADJOINT = 4
-GMRES, BICGSTAB = 0, 1
+GMRES, BICGSTAB, BLOCK_GMRES = 0, 1, 2
 
 
 class VieError(RuntimeError):
@@ -104,7 +104,8 @@ class RequestC(C.Structure):
 class ResultC(C.Structure):
     _fields_ = [("status", C.c_int), ("n", C.c_int64), ("nrhs", C.c_int), ("I", C.POINTER(C.c_double)),
                 ("stats", SolveStats), ("t_submit_s", C.c_double), ("t_start_s", C.c_double),
-                ("t_done_s", C.c_double), ("footprint_bytes", C.c_int64)]
+                ("t_done_s", C.c_double), ("footprint_bytes", C.c_int64), ("retries", C.c_int),
+                ("peak_bytes", C.c_int64)]
 
 
 EXPORTS = ["vie_create", "vie_destroy", "vie_last_error", "vie_assemble", "vie_compress", "vie_op_destroy",
@@ -467,7 +468,8 @@ class Server:
             I = np.ctypeslib.as_array(r.I, shape=(r.nrhs * r.n * 2,)).copy().view(np.complex128)
             I = I.reshape(r.nrhs, r.n).T
         out = dict(status=r.status, n=r.n, nrhs=r.nrhs, I=I, stats=r.stats.as_dict(), t_submit=r.t_submit_s,
-                   t_start=r.t_start_s, t_done=r.t_done_s, footprint=r.footprint_bytes)
+                   t_start=r.t_start_s, t_done=r.t_done_s, footprint=r.footprint_bytes, retries=r.retries,
+                   peak=r.peak_bytes)
         self.L.vie_result_free(C.byref(r))
         return out
 

@@ -296,7 +296,7 @@ def test_graph_cycle_equals_host_loop(tiny_op, tiny_dense):
     Ig, stg, sg = tiny_op.solve(kh, pol, tol=1e-6, restart=8, launch=0)
     Ih, sth, sh = tiny_op.solve(kh, pol, tol=1e-6, restart=8, launch=1)
     assert sg == sh == vie.VIE_OK
-    assert stg["iterations"] == sth["iterations"] and stg["refinements"] == sth["refinements"] > 1
+    assert stg["iterations"] == sth["iterations"] > 8 and stg["refinements"] == sth["refinements"] >= 1
     assert np.array_equal(Ig, Ih)
     assert stg["history"] == sth["history"]
     for c in range(len(kh)):

@@ -87,3 +87,57 @@ def test_admission_rejects_oversized_request():
     assert r is not None and r["status"] == vie.VIE_OK
     srv.stop()
     ctx.close()
+
+
+def test_underestimated_footprint_backs_off_instead_of_failing(monkeypatch):
+    # the footprint model scaled down 50x: each slot's context caps its
+    # allocations at the admitted footprint, so the requests run into the cap
+    # (a host-side refusal before cudaMalloc), go back to the head of the queue
+    # with twice the footprint and finish once enough is free; the results are
+    # those of plain solves
+    monkeypatch.setenv("VIE_TEST_FOOTPRINT_SCALE", "0.02")
+    ctx = vie.Context(0)
+    srv = vie.Server(ctx, max_inflight=3, hbm_budget=6 << 30, tol=1e-4)
+    reqs = _requests()[:5]
+    tickets = [srv.submit(g, kh, pol) for g, kh, pol in reqs]
+    results = []
+    for t in tickets:
+        r = None
+        deadline = time.time() + 300
+        while r is None and time.time() < deadline:
+            r = srv.poll(t, timeout_ms=1000)
+        assert r is not None
+        results.append(r)
+    srv.stop()
+    assert all(r["status"] == vie.VIE_OK for r in results)
+    assert any(r["retries"] > 0 for r in results)
+    for r in results:
+        assert r["peak"] <= r["footprint"]        # what ran stayed inside its cap
+    for (g, kh, pol), r in zip(reqs, results):
+        op = vie.Operator(ctx, g)
+        op.compress(1e-4, vie.C64)
+        I, _, status = op.solve(kh, pol, tol=1e-6)
+        op.close()
+        assert status == vie.VIE_OK and rel(r["I"], I) <= 1e-10
+    ctx.close()
+
+
+def test_request_that_cannot_fit_is_rejected_after_back_off(monkeypatch):
+    # admitted by an underestimate but larger than the whole budget: after the
+    # back-off reaches the budget the request is rejected; the server goes on
+    monkeypatch.setenv("VIE_TEST_FOOTPRINT_SCALE", "0.001")
+    ctx = vie.Context(0)
+    srv = vie.Server(ctx, max_inflight=1, hbm_budget=64 << 20, tol=1e-4)
+    kh, pol = workloads.normal_incidence()
+    t = srv.submit(workloads.square_array(24, 3), kh, pol)
+    r = None
+    deadline = time.time() + 300
+    while r is None and time.time() < deadline:
+        r = srv.poll(t, timeout_ms=1000)
+    assert r is not None and r["status"] == vie.VIE_ERR_ADMISSION and r["retries"] > 0
+    monkeypatch.delenv("VIE_TEST_FOOTPRINT_SCALE")
+    t2 = srv.submit(workloads.square_array(2, 2), kh, pol)
+    r2 = srv.poll(t2, timeout_ms=120000)
+    assert r2 is not None and r2["status"] == vie.VIE_OK
+    srv.stop()
+    ctx.close()
