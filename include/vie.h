@@ -84,18 +84,21 @@ enum vie_variant {
     VIE_VAR_TCGEN05_BF16X3 = 6, /* tcgen05 MMAs with tensor-memory accumulators, 128-row tiles */
     VIE_VAR_TCGEN05_PACKED_BF16X3 = 7, /* as 6, with the factors split once into bf16 planes in the
                                           shared-memory stage layout and moved by bulk TMA copies (needs
-                                          ~1.1x the factor memory; runs as 6 when that is not free) */
+                                          ~1.1x the factor memory; runs as 6 when that is not free;
+                                          default for more than 32 right-hand sides) */
     VIE_VAR_SIMT_SHARED = 8 /* complex float32, one right-hand side at a time: far blocks that share
                                their factors (translated copies) are applied together, each factor
                                element read once per group of up to 4 copies; partial products are
                                summed per target atom in a fixed order (default for one right-hand
                                side when the operator has translated copies) */,
-    VIE_VAR_TCGEN05_WS_BF16X3 = 9 /* the MMAs and planes of 7 in a warp-specialised persistent kernel
-                                     (one CTA per SM): a producer warp group fills a four-stage
-                                     shared-memory ring (bulk TMA copies of the A planes, split B),
-                                     one thread issues the MMAs, four warps drain two tensor-memory
-                                     accumulator buffers; bit-identical to 7 (default for 8+
-                                     right-hand sides; runs as 6 when the planes do not fit) */
+    VIE_VAR_TCGEN05_WS_BF16X3 = 9 /* the planes of 7 in a warp-specialised persistent kernel (one CTA
+                                     per SM): a warp moves the A planes by bulk TMA into a ring of 3 to
+                                     5 stages (5 up to 16 right-hand sides, 4 up to 48), up to four warp
+                                     pairs gather and split B into two stacked plane sets, one thread
+                                     issues four wide MMAs per K step (each A plane read once), four
+                                     warps drain two tensor-memory accumulator buffers; equal to 7 to
+                                     float32 rounding (default for 8 to 32 right-hand sides; runs as 6
+                                     when the planes do not fit) */
 };
 
 /* vie_apply flags */

@@ -324,6 +324,8 @@ int vie_compress(vie_op* op, double tol, int factor_precision) {
         if (factor_precision != VIE_C64 && factor_precision != VIE_C128)
             fail(VIE_ERR_INVALID_ARG, "factor precision must be VIE_C64 or VIE_C128");
         double t0 = now_s();
+        drop_unions(*op->o.ctx, &op->o);
+        ++op->o.gen;
         compress_operator(op->o, tol, factor_precision);
         op->o.t_compress = now_s() - t0;
         if (op->o.ctx->verbose)
@@ -337,6 +339,10 @@ void vie_op_destroy(vie_op* op) {
     vie_ctx* ctx = ctx_of(op);
     cudaSetDevice(op->o.ctx->device);
     cudaStreamSynchronize(op->o.ctx->stream);
+    {
+        AllocScope scope(op->o.ctx);
+        drop_unions(*op->o.ctx, &op->o);
+    }
     delete op;
     if (ctx->ops.fetch_sub(1) == 1 && ctx->closed.load()) free_ctx(ctx);
 }

@@ -665,13 +665,16 @@ __global__ void __launch_bounds__(kThr) u2p_kernel(const int4* __restrict__ item
 // One persistent CTA per SM; the roles run concurrently and meet on mbarriers
 // instead of CTA-wide barriers:
 //   warp 4     one thread starts the bulk copy of the pre-split A planes of
-//              every K stage (32 KiB) into the next free slot of a four-stage
-//              ring, running ahead of everything else;
-//   warps 5-12 four groups of two warps load, split and store the B operand
-//              (x gathered over the source atoms, or t) of a stage; group q
-//              serves ring slot q, so the loads of four stages are in flight
-//              at once;
-//   warp 13    one thread issues the 24 MMAs of a stage once its A copy has
+//              every K stage (32 KiB) into the next free slot of a ring of 3
+//              to 5 stages (as many as fit beside the B planes of the widest
+//              tile), running ahead of everything else;
+//   warps 5-12 up to four groups of two warps (no more than the ring has
+//              stages) load, split and store the B operand (x gathered over
+//              the source atoms, or t) of a stage; group q takes the stages
+//              g = q mod G and gathers a stage's values into registers before
+//              it waits for the stage's slot, so the loads of G stages are in
+//              flight while the MMAs run;
+//   warp 13    one thread issues the 8 MMAs of a stage once its A copy has
 //              landed and its B planes are stored, and commits them to the
 //              slot's "empty" barrier (the producers refill it) and, at the end
 //              of a tile, to the tile's accumulator barrier;
@@ -679,23 +682,102 @@ __global__ void __launch_bounds__(kThr) u2p_kernel(const int4* __restrict__ item
 //              owns lanes 32w..32w+31) and store it.  Tensor memory holds two
 //              accumulator buffers, so the MMAs of the next tile run while the
 //              previous one drains.
-// The MMAs, their order and the planes are those of u1p/u2p, so the results
-// are bit-identical to them.
+// The MMAs are fewer and wider than in u1p/u2p.  With B stored as two stacks
+// of planes, S1 = [Br_hi; Bi_hi; Br_lo; Bi_lo] and S2 = [-Bi_hi; Br_hi; -Bi_lo;
+// Br_lo] (N = ncol rows each; the negation is exact in bf16), a K step is four
+// MMAs into one accumulator of 4 ncol columns [Re_a | Im_a | Re_b | Im_b]:
+//   Ar_hi x S1 (N = 4 ncol), Ai_hi x S2 (4 ncol), Ar_lo x S1[0:2 ncol],
+//   Ai_lo x S2[0:2 ncol],
+// and the epilogue adds Re = Re_a + Re_b, Im = Im_a + Im_b.  The products are
+// those of the twelve-MMA form (hi.hi + hi.lo + lo.hi of every real product);
+// each A plane is read by one MMA instead of two to four, which nearly halves
+// the tensor core's shared-memory operand traffic.  The float32 sums are
+// grouped differently, so the results agree with u1p/u2p to rounding.
 // Every wait gives up after `lim` clock cycles: the waiting role raises the
 // CTA's abort flag, every role leaves its loop at its next check, and before
 // the tensor memory is freed and the CTA exits, the bulk copies that were
 // started and the MMAs that were issued are waited for (with the normal ~1 s
 // limit).  The error word then tells the host.
-constexpr int kWsStages = 4;
+constexpr int kWsMaxStages = 6;
 constexpr int kWsThr = 448;  // 14 warps
 constexpr int kWsWarpTma = 4, kWsWarpB0 = 5, kWsWarpMma = 13;
-constexpr int kWsTmemCols = 256;
-constexpr size_t kWsSmemBytes = kWsStages * kStageBytes;  // 192 KiB
+constexpr int kWsGroups = (kWsWarpMma - kWsWarpB0) / 2;  // B-producer groups of two warps
+constexpr int kWsAccCols = 4 * kN;                // one accumulator: [Re_a | Im_a | Re_b | Im_b]
+constexpr int kWsTmemCols = 2 * kWsAccCols;       // two accumulator buffers: 512 columns
+constexpr int kWsSmemBytes = 224 * 1024;         // the ring
+// The ring: ns stages of `stride` bytes.  A stage holds the A planes exactly as
+// the packed layout (one 32 KiB bulk copy), then the two B stacks of 16 nmax
+// chunks each (4 plane slots x nmax rows x 4 K chunks; chunk (slot, row, q) of
+// a stack sits at q (4 nmma) + slot nmma + row).  nmax, the widest tile's
+// column count rounded up to 16, sets the stride, and the stage count is what
+// fits: 5 stages for up to 16 right-hand sides, 4 up to 48, 3 up to 64.
+struct WsRing {
+    unsigned char* base;
+    uint32_t stride, bstack;  // bytes per stage; chunks per B stack
+    uint32_t ns;              // stages
+    __device__ __forceinline__ uint4* a(uint32_t slot) const { return reinterpret_cast<uint4*>(base + slot * stride); }
+    __device__ __forceinline__ uint4* b(uint32_t slot, int k) const {
+        return reinterpret_cast<uint4*>(base + slot * stride + kStageBytesA) + k * bstack;
+    }
+};
+__host__ __device__ constexpr uint32_t ws_stride(int nmax) { return kStageBytesA + 2u * 16u * nmax * 16u; }
+__host__ __device__ constexpr int ws_stages(int nmax) {
+    return (int)(kWsSmemBytes / ws_stride(nmax)) < kWsMaxStages ? (int)(kWsSmemBytes / ws_stride(nmax))
+                                                                 : kWsMaxStages;
+}
+static_assert(ws_stages(64) >= 3 && ws_stages(16) == 5, "ring sizes");
+static_assert(ws_stride(16) % 1024 == 0, "stage alignment");
+
+__device__ __forceinline__ uint4 neg_bf16x8(uint4 v) {
+    return make_uint4(v.x ^ 0x80008000u, v.y ^ 0x80008000u, v.z ^ 0x80008000u, v.w ^ 0x80008000u);
+}
+
+// 8 complex values of B (column `row`, K chunk q) into both stacks
+__device__ __forceinline__ void put8_ws(uint4* b0, uint4* b1, int nmma, int row, int q, const float2 (&v)[8]) {
+    uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        split2(v[2 * e].x, v[2 * e + 1].x, rh[e], rl[e]);
+        split2(v[2 * e].y, v[2 * e + 1].y, ih[e], il[e]);
+    }
+    const uint4 RH = make_uint4(rh[0], rh[1], rh[2], rh[3]), RL = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+    const uint4 IH = make_uint4(ih[0], ih[1], ih[2], ih[3]), IL = make_uint4(il[0], il[1], il[2], il[3]);
+    const int base = q * 4 * nmma + row;
+    b0[base] = RH;
+    b0[base + nmma] = IH;
+    b0[base + 2 * nmma] = RL;
+    b0[base + 3 * nmma] = IL;
+    b1[base] = neg_bf16x8(IH);
+    b1[base + nmma] = RH;
+    b1[base + 2 * nmma] = neg_bf16x8(IL);
+    b1[base + 3 * nmma] = RL;
+}
+
+// the 8 MMAs of one stage (two K steps of 16) into the accumulator at tm
+__device__ __forceinline__ void issue_stage_ws(const uint4* a, const uint4* b0, const uint4* b1, uint32_t tm, int nmma,
+                                               bool first) {
+    const uint32_t id4 = idesc(4 * nmma, false), id2 = idesc(2 * nmma, false);
+    const uint32_t lbob = (uint32_t)(4 * nmma * 16);
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+        uint64_t A[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) A[p] = sdesc(smem_u32(a + p * kChunksA) + ks * 2 * kLboA, kLboA);
+        const uint64_t B1 = sdesc(smem_u32(b0) + ks * 2 * lbob, lbob);
+        const uint64_t B2 = sdesc(smem_u32(b1) + ks * 2 * lbob, lbob);
+        const uint32_t acc0 = (first && ks == 0) ? 0u : 1u;
+        // planes: 0 re hi, 1 re lo, 2 im hi, 3 im lo
+        umma(tm, A[0], B1, id4, acc0);
+        umma(tm, A[2], B2, id4, 1u);
+        umma(tm, A[1], B1, id2, 1u);
+        umma(tm, A[3], B2, id2, 1u);
+    }
+}
 
 struct WsCtl {
-    uint64_t full_a[kWsStages];  // A copy of the slot landed (1 arrival + bytes)
-    uint64_t full_b[kWsStages];  // B planes of the slot stored (the slot's 2 producer warps)
-    uint64_t empty[kWsStages];   // MMAs that read the slot are done (1 commit)
+    uint64_t full_a[kWsMaxStages];  // A copy of the slot landed (1 arrival + bytes)
+    uint64_t full_b[kWsMaxStages];  // B planes of the slot stored (the stage's 2 producer warps)
+    uint64_t empty[kWsMaxStages];   // MMAs that read the slot are done (1 commit)
     uint64_t acc_full[2];        // accumulator buffer holds a finished tile (1 commit)
     uint64_t acc_empty[2];       // epilogue has read the buffer (4 epilogue warps)
     uint32_t tmem;
@@ -775,9 +857,9 @@ __device__ void ws_tiles2(const int4* items, int it0, int it1, const int* tidx, 
     }
 }
 
-__device__ void ws_setup(WsCtl& ctl) {
+__device__ void ws_setup(WsCtl& ctl, uint32_t ns) {
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kWsStages; ++i) {
+        for (uint32_t i = 0; i < ns; ++i) {
             mbar_init_n(smem_u32(&ctl.full_a[i]), 1);
             mbar_init_n(smem_u32(&ctl.full_b[i]), 2);
             mbar_init_n(smem_u32(&ctl.empty[i]), 1);
@@ -804,15 +886,15 @@ __device__ void ws_setup(WsCtl& ctl) {
 
 // wait for what is still in flight (started copies, issued MMAs), free the
 // tensor memory, report an abort
-__device__ void ws_teardown(WsCtl& ctl, int* err) {
+__device__ void ws_teardown(WsCtl& ctl, uint32_t ns, int* err) {
     __syncthreads();
     if (threadIdx.x == kWsWarpTma * 32) {  // the thread that started the copies
         for (uint32_t g = ctl.g_mma; g < ctl.g_tma; ++g)
-            mbar_wait_lim(smem_u32(&ctl.full_a[g % kWsStages]), (g / kWsStages) & 1, kWaitCycles);
+            mbar_wait_lim(smem_u32(&ctl.full_a[g % ns]), (g / ns) & 1, kWaitCycles);
     }
     if (threadIdx.x == kWsWarpMma * 32 && ctl.g_mma > 0) {  // the thread that issued the MMAs
         const uint32_t g = ctl.g_mma - 1;
-        mbar_wait_lim(smem_u32(&ctl.empty[g % kWsStages]), (g / kWsStages) & 1, kWaitCycles);
+        mbar_wait_lim(smem_u32(&ctl.empty[g % ns]), (g / ns) & 1, kWaitCycles);
     }
     if (threadIdx.x == 0 && ctl.abort) atomicExch(err, 1);
     fence_before();
@@ -827,7 +909,7 @@ __device__ void ws_teardown(WsCtl& ctl, int* err) {
 // CTA's tiles (ws_tiles1 / ws_tiles2 bound to their arguments); Out: stores row
 // r, column c of the tile (value) to its destination.
 template <class TileT, class Enum, class Out>
-__device__ void ws_run(WsCtl& ctl, Stage* stages, const uint4* pack, const long long* pk, long long lim,
+__device__ void ws_run(WsCtl& ctl, const WsRing& ring, const uint4* pack, const long long* pk, long long lim,
                        Enum&& enumerate, Out&& out) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     volatile int* abort = &ctl.abort;
@@ -838,13 +920,13 @@ __device__ void ws_run(WsCtl& ctl, Stage* stages, const uint4* pack, const long 
             enumerate([&](const TileT& T, int it, int) -> bool {
                 const uint4* packA = pack + pk[it] * kStageChunksA;
                 for (int st = 0; st < T.nst; ++st, ++g) {
-                    const uint32_t slot = g % kWsStages;
-                    if (g >= kWsStages && !mbar_wait_lim(smem_u32(&ctl.empty[slot]), ((g / kWsStages) - 1) & 1, lim))
+                    const uint32_t slot = g % ring.ns;
+                    if (g >= ring.ns && !mbar_wait_lim(smem_u32(&ctl.empty[slot]), ((g / ring.ns) - 1) & 1, lim))
                         *abort = 1;
                     if (*abort) return false;
                     const uint32_t mb = smem_u32(&ctl.full_a[slot]);
                     mbar_expect_tx(mb, kStageBytesA);
-                    tma_bulk(smem_u32(&stages[slot].a[0][0]), packA + (int64_t)st * kStageChunksA, kStageBytesA, mb);
+                    tma_bulk(smem_u32(ring.a(slot)), packA + (int64_t)st * kStageChunksA, kStageBytesA, mb);
                     ctl.g_tma = g + 1;
                 }
                 return true;
@@ -852,38 +934,52 @@ __device__ void ws_run(WsCtl& ctl, Stage* stages, const uint4* pack, const long 
         }
         __syncwarp();
     } else if (warp >= kWsWarpB0 && warp < kWsWarpMma) {
-        // ---- B operands: group q (two warps, 64 threads) fills ring slot q
+        // ---- B operands: group q (two warps, 64 threads) takes the stages
+        // g = q mod G and fills ring slot g mod ns, G = min(4, ns) groups.  It
+        // loads a stage's values into registers before it waits for the slot,
+        // so the gather from L2 overlaps the MMAs that still read the slot.
+        // G <= ns keeps every wait on a slot's "empty" barrier within one
+        // phase of it: the group's previous stage g - G waited for the MMAs of
+        // stage g - G - ns >= g - 2 ns, so the phase of stage g - ns that this
+        // wait asks for is the barrier's current or last completed one, never
+        // one that a parity test would confuse with an older phase.
         const int q = (warp - kWsWarpB0) >> 1;
         const int gtid = tid - (kWsWarpB0 + 2 * q) * 32;
+        const uint32_t ngroups = ring.ns < (uint32_t)kWsGroups ? ring.ns : (uint32_t)kWsGroups;
         uint32_t g = 0;
-        enumerate([&](const TileT& T, int, int) -> bool {
+        if ((uint32_t)q < ngroups) enumerate([&](const TileT& T, int, int) -> bool {
             for (int st = 0; st < T.nst; ++st, ++g) {
-                if ((int)(g % kWsStages) != q) continue;
-                if (g >= kWsStages) {
-                    bool ok = true;
-                    if (lane == 0) ok = mbar_wait_lim(smem_u32(&ctl.empty[q]), ((g / kWsStages) - 1) & 1, lim);
-                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-                    if (!ok) *abort = 1;
-                }
-                if (*abort) return false;
-                Stage& S = stages[q];
+                if (g % ngroups != (uint32_t)q) continue;
+                const uint32_t slot = g % ring.ns;
                 // all loads of the stage first (up to four segments of 8 values
-                // per thread), then the split and the stores
-                const int nseg = T.nmma * 4;
+                // per thread), then the wait, the split and the stores;
+                // neighbouring threads take neighbouring columns of one K
+                // chunk, so their 16-byte stores fill whole shared-memory
+                // wavefronts
+                const int nm = T.nmma, nseg = nm * 4;
                 float2 vb[4][8];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int seg = gtid + 64 * u;
-                    if (seg < nseg) T.src.load_b(seg >> 2, seg & 3, st * kKS, vb[u]);
+                    if (seg < nseg) T.src.load_b(seg % nm, seg / nm, st * kKS, vb[u]);
                 }
+                if (g >= ring.ns) {
+                    bool ok = true;
+                    if (lane == 0) ok = mbar_wait_lim(smem_u32(&ctl.empty[slot]), ((g / ring.ns) - 1) & 1, lim);
+                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                    if (!ok) *abort = 1;
+                }
+                if (*abort) return false;
+                uint4* b0 = ring.b(slot, 0);
+                uint4* b1 = ring.b(slot, 1);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int seg = gtid + 64 * u;
-                    if (seg < nseg) put8<kChunksB>(S.b, (seg & 3) * kN + (seg >> 2), vb[u]);
+                    if (seg < nseg) put8_ws(b0, b1, nm, seg % nm, seg / nm, vb[u]);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&ctl.full_b[q]));
+                if (lane == 0) mbar_arrive(smem_u32(&ctl.full_b[slot]));
             }
             return true;
         });
@@ -898,16 +994,16 @@ __device__ void ws_run(WsCtl& ctl, Stage* stages, const uint4* pack, const long 
                     *abort = 1;
                     return false;
                 }
-                const uint32_t tm = ctl.tmem + ab * (uint32_t)kTmemCols;
+                const uint32_t tm = ctl.tmem + ab * (uint32_t)kWsAccCols;
                 for (int st = 0; st < T.nst; ++st, ++g) {
-                    const uint32_t slot = g % kWsStages, par = (g / kWsStages) & 1;
+                    const uint32_t slot = g % ring.ns, par = (g / ring.ns) & 1;
                     if (*abort || !mbar_wait_lim(smem_u32(&ctl.full_a[slot]), par, lim) ||
                         !mbar_wait_lim(smem_u32(&ctl.full_b[slot]), par, lim)) {
                         *abort = 1;
                         return false;
                     }
                     fence_after();
-                    issue_stage(stages[slot], tm, T.nmma, st == 0);
+                    issue_stage_ws(ring.a(slot), ring.b(slot, 0), ring.b(slot, 1), tm, T.nmma, st == 0);
                     umma_commit(smem_u32(&ctl.empty[slot]));
                     ctl.g_mma = g + 1;
                 }
@@ -938,16 +1034,19 @@ __device__ void ws_run(WsCtl& ctl, Stage* stages, const uint4* pack, const long 
                 return false;
             }
             fence_after();
-            const uint32_t base = ctl.tmem + ab * (uint32_t)kTmemCols + lane_base;
+            const uint32_t base = ctl.tmem + ab * (uint32_t)kWsAccCols + lane_base;
+            const int nm = T.nmma;
             for (int cb = 0; cb < ncol; cb += 16) {
-                float vr[16], vi[16];
-                tmem_ld16(base + cb, vr);
-                tmem_ld16(base + kN + cb, vi);
+                float ra[16], ia[16], rb[16], ib[16];
+                tmem_ld16(base + cb, ra);
+                tmem_ld16(base + nm + cb, ia);
+                tmem_ld16(base + 2 * nm + cb, rb);
+                tmem_ld16(base + 3 * nm + cb, ib);
                 tmem_wait_ld();
                 if (r < T.rows) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
-                        if (cb + i < ncol) out(T, r, cb + i, make_float2(vr[i], vi[i]));
+                        if (cb + i < ncol) out(T, r, cb + i, make_float2(ra[i] + rb[i], ia[i] + ib[i]));
                 }
             }
             fence_before();
@@ -966,17 +1065,18 @@ __global__ void __launch_bounds__(kWsThr, 1) u1w_kernel(const FarBlockDev* __res
                                                         const uint4* __restrict__ pack, const int* __restrict__ rowt,
                                                         const float2* __restrict__ x, int64_t ldx, int np,
                                                         float2* __restrict__ t, int64_t ldt, int nrhs,
-                                                        const int2* __restrict__ colr, int* err, long long lim) {
+                                                        const int2* __restrict__ colr, int nmax, int* err,
+                                                        long long lim) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    Stage* stages = reinterpret_cast<Stage*>(smem);
+    const WsRing ring{smem, ws_stride(nmax), 16u * nmax, (uint32_t)ws_stages(nmax)};
     __shared__ WsCtl ctl;
-    ws_setup(ctl);
+    ws_setup(ctl, ring.ns);
     const int it0 = cta_ptr[blockIdx.x], it1 = cta_ptr[blockIdx.x + 1];
     ws_run<WsTile1>(
-        ctl, stages, pack, pk, lim,
+        ctl, ring, pack, pk, lim,
         [&](auto&& role) { ws_tiles1(blocks, batoms, items, it0, it1, rowt, x, ldx, np, nrhs, colr, &ctl.abort, role); },
         [&](const WsTile1& T, int r, int c, float2 v) { t[(int64_t)T.rt[r] + (int64_t)(T.src.c0 + c) * ldt] = v; });
-    ws_teardown(ctl, err);
+    ws_teardown(ctl, ring.ns, err);
 }
 
 __global__ void __launch_bounds__(kWsThr, 1) u2w_kernel(const int4* __restrict__ items, const int* __restrict__ cta_ptr,
@@ -985,17 +1085,18 @@ __global__ void __launch_bounds__(kWsThr, 1) u2w_kernel(const int4* __restrict__
                                                         const long long* __restrict__ kptr,
                                                         const float2* __restrict__ t, int64_t ldt, int np,
                                                         float2* __restrict__ F, int64_t ldf, int nrhs,
-                                                        const int2* __restrict__ colr, int* err, long long lim) {
+                                                        const int2* __restrict__ colr, int nmax, int* err,
+                                                        long long lim) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    Stage* stages = reinterpret_cast<Stage*>(smem);
+    const WsRing ring{smem, ws_stride(nmax), 16u * nmax, (uint32_t)ws_stages(nmax)};
     __shared__ WsCtl ctl;
-    ws_setup(ctl);
+    ws_setup(ctl, ring.ns);
     const int it0 = cta_ptr[blockIdx.x], it1 = cta_ptr[blockIdx.x + 1];
     ws_run<WsTile2>(
-        ctl, stages, pack, pk, lim,
+        ctl, ring, pack, pk, lim,
         [&](auto&& role) { ws_tiles2(items, it0, it1, tidx, kptr, t, ldt, np, nrhs, colr, &ctl.abort, role); },
         [&](const WsTile2& T, int r, int c, float2 v) { F[T.rb + r + (int64_t)(T.src.c0 + c) * ldf] = v; });
-    ws_teardown(ctl, err);
+    ws_teardown(ctl, ring.ns, err);
 }
 
 std::once_flag g_umma_attr_once;
@@ -1114,17 +1215,21 @@ void apply_far_umma_ws(Op& op, const float2* x, int64_t ldx, float2* F, int64_t 
     if (op.d_t.bytes < need) op.d_t.alloc(need);
     const long long lim = ws_wait_limit();
     const int nc = op.ctx->n_sm;
+    // the widest tile: 64 columns, or all of them when fewer (a tile never
+    // spans two problems' column ranges, so it is no wider than this either)
+    const int nmax = std::max(16, (std::min(nrhs, kN) + 15) / 16 * 16);
+    const size_t smem = (size_t)ws_stages(nmax) * ws_stride(nmax);
     if (op.n_u1_items > 0) {
-        u1w_kernel<<<nc, kWsThr, kWsSmemBytes, s>>>(
+        u1w_kernel<<<nc, kWsThr, smem, s>>>(
             op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(), op.d_w1_items.as<int4>(), op.d_w1_cta.as<int>(),
             op.d_w1_pk.as<long long>(), op.d_u1_pack.as<uint4>(), op.d_u1_rowt.as<int>(), x, ldx, op.np,
-            op.d_t.as<float2>(), op.t_total, nrhs, op.colr, op.d_err.as<int>(), lim);
+            op.d_t.as<float2>(), op.t_total, nrhs, op.colr, nmax, op.d_err.as<int>(), lim);
         VIE_CHECK_LAUNCH();
     }
-    u2w_kernel<<<nc, kWsThr, kWsSmemBytes, s>>>(
+    u2w_kernel<<<nc, kWsThr, smem, s>>>(
         op.d_w2_items.as<int4>(), op.d_w2_cta.as<int>(), op.d_w2_pk.as<long long>(), op.d_u2_pack.as<uint4>(),
         op.d_u2_tidx.as<int>(), op.d_u2_kptr.as<long long>(), op.d_t.as<float2>(), op.t_total, op.np, F, ldf, nrhs,
-        op.colr, op.d_err.as<int>(), lim);
+        op.colr, nmax, op.d_err.as<int>(), lim);
     VIE_CHECK_LAUNCH();
 }
 

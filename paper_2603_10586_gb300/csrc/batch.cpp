@@ -118,6 +118,43 @@ std::unique_ptr<Op> make_union(const std::vector<Op*>& ops) {
     return U;
 }
 
+void drop_unions(Ctx& c, const Op* o) {
+    auto& v = c.unions;
+    v.erase(std::remove_if(v.begin(), v.end(),
+                           [o](const Ctx::Union& u) { return std::find(u.ops.begin(), u.ops.end(), o) != u.ops.end(); }),
+            v.end());
+}
+
+namespace {
+
+// The joined operator of `ops`: the cached one if the same operators (in the
+// same order, with the same factors) were batched before, else a new one that
+// replaces the least recently used of at most kUnionCache entries.  Its work
+// lists and self-block copies are built once and reused across calls.
+constexpr size_t kUnionCache = 4;
+
+Op* get_union(const std::vector<Op*>& ops) {
+    Ctx& c = *ops[0]->ctx;
+    std::vector<const Op*> key(ops.begin(), ops.end());
+    std::vector<uint64_t> gens;
+    for (const Op* p : ops) gens.push_back(p->gen);
+    for (Ctx::Union& u : c.unions)
+        if (u.ops == key && u.gens == gens) {
+            u.used = ++c.union_clock;
+            return u.U.get();
+        }
+    std::unique_ptr<Op> U = make_union(ops);
+    if (c.unions.size() >= kUnionCache) {
+        auto lru = std::min_element(c.unions.begin(), c.unions.end(),
+                                    [](const Ctx::Union& a, const Ctx::Union& b) { return a.used < b.used; });
+        c.unions.erase(lru);
+    }
+    c.unions.push_back(Ctx::Union{std::move(key), std::move(gens), std::move(U), ++c.union_clock});
+    return c.unions.back().U.get();
+}
+
+}  // namespace
+
 int solve_batch(const std::vector<Op*>& ops, const vie_incident* incs, const int* nrhs, const vie_solve_opts* o,
                 void** I_out, vie_solve_stats* st) {
     const int B = (int)ops.size();
@@ -131,7 +168,7 @@ int solve_batch(const std::vector<Op*>& ops, const vie_incident* incs, const int
     if (K > 1024) fail(VIE_ERR_INVALID_ARG, "a batch takes at most 1024 right-hand sides in total");
     if (o->precision == VIE_C128) fail(VIE_ERR_INVALID_ARG, "batched solves use VIE_C64 or VIE_BF16X3");
     const double t0 = now_s();
-    std::unique_ptr<Op> U = make_union(ops);
+    Op* U = get_union(ops);
     cudaStream_t s = U->ctx->stream;
     const int64_t n = U->n();
     // columns grouped by problem; problem p owns rows [lo_p, lo_p + n_p)

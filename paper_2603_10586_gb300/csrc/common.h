@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <string>
 #include <type_traits>
+#include <memory>
 #include <vector>
 
 #include "../../include/vie.h"
@@ -135,6 +136,7 @@ struct Ctx;
 
 struct Op {
     Ctx* ctx = nullptr;
+    uint64_t gen = 0;  // bumped by every compression (joined operators built from older factors are stale)
     // geometry
     int N = 0, T = 0, np = 0, L = 0;
     std::vector<double> centres;       // [3N]
@@ -233,6 +235,17 @@ struct Ctx {
     // (0: none) above which an allocation is refused with VIE_ERR_OOM
     std::atomic<int64_t> allocated{0}, peak{0};
     std::atomic<int64_t> cap{0};
+    // joined operators of recent vie_solve_batch calls (block-diagonal unions of
+    // their problems), reused while the same operators with the same factors
+    // come again; declared last so that they are freed first
+    struct Union {
+        std::vector<const Op*> ops;
+        std::vector<uint64_t> gens;
+        std::unique_ptr<Op> U;
+        uint64_t used = 0;
+    };
+    std::vector<Union> unions;
+    uint64_t union_clock = 0;
 };
 
 // The context charged for device allocations made by this thread while a
@@ -336,6 +349,8 @@ void apply_far_bf16x3(Op& op, const float2* x, int64_t ldx, float2* F, int64_t l
 void compress_operator(Op& op, double tol, int prec);
 
 // solve.cpp
+// forget the joined operators that contain `o` (before it is destroyed or recompressed)
+void drop_unions(Ctx& c, const Op* o);
 int solve_batch(const std::vector<Op*>& ops, const vie_incident* incs, const int* nrhs, const vie_solve_opts* o,
                 void** I_out, vie_solve_stats* st);
 int solve(Op& op, const vie_incident* inc, int nrhs, const vie_solve_opts* o, void* I_out,

@@ -228,10 +228,21 @@ __global__ void __launch_bounds__(kT) k_maxpy_df(KrylovArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(kT) k_xupdate_df(KrylovArgs a, double2* __restrict__ X) {
+// X[:, cols[i]] += V y; with D, the correction V y of slot i is also written
+// there in float32 (the input of a residual update), zero for a slot that did
+// no step
+__global__ void __launch_bounds__(kT) k_xupdate_df(KrylovArgs a, double2* __restrict__ X, float2* __restrict__ D) {
     const int i = blockIdx.y;
     const int jd = a.jdone[i];
-    if (jd == 0) return;
+    if (jd == 0) {
+        if (D) {
+            const Rows R = rows_of(a, a.cols[i]);
+            float2* d = D + (int64_t)i * a.n + R.lo;
+            for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < R.len; r += (int64_t)gridDim.x * kT)
+                d[r] = make_float2(0.f, 0.f);
+        }
+        return;
+    }
     __shared__ double2 ys[kMaxRestart];
     for (int l = threadIdx.x; l < jd; l += kT) ys[l] = a.y[(int64_t)i * a.hs + l];
     __syncthreads();
@@ -239,11 +250,31 @@ __global__ void __launch_bounds__(kT) k_xupdate_df(KrylovArgs a, double2* __rest
     const int64_t n = R.len;
     const float4* V = reinterpret_cast<const float4*>(R.V);
     double2* x = X + (int64_t)a.cols[i] * a.n + R.lo;
+    float2* d = D ? D + (int64_t)i * a.n + R.lo : nullptr;
     for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) {
-        double2 acc = x[r];
+        double2 acc = make_double2(0.0, 0.0);
         for (int l = 0; l < jd; ++l) cfma(acc, df_to(V[(int64_t)l * n + r]), ys[l]);
-        x[r] = acc;
+        x[r] += acc;
+        if (d) d[r] = make_float2((float)acc.x, (float)acc.y);
     }
+}
+
+// Wf[:, cols[i]] -= E[:, i] and its squared-norm partials (residual update)
+__global__ void __launch_bounds__(kT) k_sub_scatter_norm(KrylovArgs a, const double2* __restrict__ E, double2* Wf) {
+    const int i = blockIdx.y;
+    const Rows R = rows_of(a, a.cols[i]);
+    const int64_t n = R.len;
+    const double2* src = E + (int64_t)i * a.n + R.lo;
+    double2* dst = Wf + (int64_t)a.cols[i] * a.n + R.lo;
+    __shared__ double sh[kT / 32];
+    double acc = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * kT + threadIdx.x; r < n; r += (int64_t)gridDim.x * kT) {
+        const double2 v = dst[r] - src[r];
+        dst[r] = v;
+        acc += v.x * v.x + v.y * v.y;
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) a.npart[(int64_t)i * a.nblk_max + blockIdx.x] = s;
 }
 
 // partial h[col] = sum_r conj(V[r, col]) w[r] over one row chunk, 8 columns per CTA.
@@ -534,7 +565,9 @@ __global__ void __launch_bounds__(kT) k_scatter_norm(KrylovArgs a, const double2
 
 // init = 1: the first residual (sets beta0); 2: a residual from the inner
 // precision, which never ends a column's solve (only a float64-accurate one
-// may); 0: a float64-accurate refinement residual
+// may); 0: a float64-accurate refinement residual; 3: a float64-accurate
+// residual updated by the inner-precision image of the cycle's correction
+// (its error is bounded by the host to 1% of the tolerance)
 __global__ void k_cycle_end(KrylovArgs a, int k, int nblk, int init) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0 && init == 0) a.ctr[KR_REFIN] += 1;
@@ -551,7 +584,9 @@ __global__ void k_cycle_end(KrylovArgs a, int k, int nblk, int init) {
     } else {
         const double r = a.beta0[c] > 0.0 ? bn / a.beta0[c] : 0.0;
         a.res[c] = r;
-        a.done[c] = ((init == 0 && r <= a.tol) || a.iters[c] >= a.maxit || bn == 0.0) ? 1 : 0;
+        // init = 3: an updated residual, trusted to within 1% of the tolerance
+        const bool conv = (init == 0 && r <= a.tol) || (init == 3 && r <= 0.99 * a.tol);
+        a.done[c] = (conv || a.iters[c] >= a.maxit || bn == 0.0) ? 1 : 0;
     }
 }
 
@@ -647,11 +682,30 @@ void kr_givens(const KrylovArgs& a, int k, int nblk, cudaGraphConditionalHandle 
     VIE_CHECK_LAUNCH();
 }
 
-void kr_update(const KrylovArgs& a, double2* X, int k, int nblk, cudaStream_t s) {
+void kr_update(const KrylovArgs& a, double2* X, int k, int nblk, cudaStream_t s, float2* D) {
     k_backsub<<<(k + 63) / 64, 64, 0, s>>>(a, k);
     VIE_CHECK_LAUNCH();
-    if (a.df) k_xupdate_df<<<dim3(nblk, k), kT, 0, s>>>(a, X);
+    if (a.df) k_xupdate_df<<<dim3(nblk, k), kT, 0, s>>>(a, X, D);
+    else if (D) fail(VIE_ERR_STATE, "the correction output needs the double-float basis");
     else k_xupdate<<<dim3(nblk, k), kT, 0, s>>>(a, X);
+    VIE_CHECK_LAUNCH();
+}
+
+__global__ void k_rnorm_from_nsq(KrylovArgs a, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) a.rnorm[a.cols[i]] = sqrt(a.nsq[i]);
+}
+
+void kr_rnorm_from_partials(const KrylovArgs& a, int k, int nblk, cudaStream_t s) {
+    k_nsq<<<k, kT, 0, s>>>(a, nblk, 0);
+    VIE_CHECK_LAUNCH();
+    k_rnorm_from_nsq<<<(k + 255) / 256, 256, 0, s>>>(a, k);
+    VIE_CHECK_LAUNCH();
+}
+
+void kr_sub_scatter_norm(const KrylovArgs& a, const double2* E, double2* Wf, int k, int nblk, cudaStream_t s) {
+    if (nblk > a.nblk_max) fail(VIE_ERR_STATE, "norm partials exceed their buffer");
+    k_sub_scatter_norm<<<dim3(nblk, k), kT, 0, s>>>(a, E, Wf);
     VIE_CHECK_LAUNCH();
 }
 

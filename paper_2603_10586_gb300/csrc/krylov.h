@@ -80,8 +80,13 @@ void kr_project(const KrylovArgs& a, const void* Y, bool c64, int pass, int k, i
 // Givens update of the Hessenberg column, residual estimate, end-of-step test;
 // with use_handle the continue flag also drives the enclosing graph loop
 void kr_givens(const KrylovArgs& a, int k, int nblk, cudaGraphConditionalHandle hnd, int use_handle, cudaStream_t s);
-// X[:, cols[i]] += V_i y_i with y_i = H_i^-1 g_i
-void kr_update(const KrylovArgs& a, double2* X, int k, int nblk, cudaStream_t s);
+// X[:, cols[i]] += V_i y_i with y_i = H_i^-1 g_i; with D (double-float basis only)
+// the correction V_i y_i is also written to D[:, i] in float32
+void kr_update(const KrylovArgs& a, double2* X, int k, int nblk, cudaStream_t s, float2* D = nullptr);
+// rnorm[cols[i]] = the square root of slot i's squared-norm partials
+void kr_rnorm_from_partials(const KrylovArgs& a, int k, int nblk, cudaStream_t s);
+// Wf[:, cols[i]] -= E[:, i] and its squared-norm partials
+void kr_sub_scatter_norm(const KrylovArgs& a, const double2* E, double2* Wf, int k, int nblk, cudaStream_t s);
 // dst[:, i] = src[:, cols[i]] (the rows of that column)
 void kr_gather_cols(const KrylovArgs& a, const double2* src, double2* dst, int k, int nblk, cudaStream_t s);
 // R[:, i] = b[:, cols[i]] - T[:, i]
@@ -89,7 +94,8 @@ void kr_sub_cols(const KrylovArgs& a, const double2* b, const double2* T, double
 // W[:, cols[i]] = Wl[:, i] (W may equal Wl with cols the identity) and its squared-norm partials
 void kr_scatter_norm(const KrylovArgs& a, const double2* Wl, double2* W, int k, int nblk, cudaStream_t s);
 // beta, res and done of the slots' columns from the norm partials; init = 1 also
-// sets beta0; init = 2 marks a residual of the inner precision (it ends no solve)
+// sets beta0; init = 2 marks a residual of the inner precision (it ends no
+// solve); init = 3 an updated float64 residual (it ends a solve below 0.99 tol)
 void kr_cycle_end(const KrylovArgs& a, int k, int nblk, int init, cudaStream_t s);
 // norms of the k columns of A (n x k, column i holding the rows of column
 // cols ? cols[i] : i) into d_out[cols ? cols[i] : i]; d_part holds k * nblk doubles

@@ -50,11 +50,14 @@ struct Gmres {
     DevBuf V, H, g, cs, sn, h, y, part, npart, nsq, rpart, inv, cycling, jdone, cols, iters, done, beta0, beta, res, rnorm,
         bnorm, hist, ctr, col_lo, col_len, col_voff, colr, colr_cycle, col_prob;
     std::vector<int2> h_colr;
-    DevBuf Xg, Yg, Xl, T, Rl, Wl, W;
+    DevBuf Xg, Yg, Xl, T, Rl, Wl, W, Rf, enorm;
     KrylovArgs a{};
     std::map<int, CycleGraph> graphs;
     int* h_pinned = nullptr;  // [KR_NCTR + nrhs] host-visible copy of counters and done flags
     std::vector<double> h_res; // latest residual per column (relative)
+    std::vector<double> h_beta0, bound;  // ||P^-1 b|| and the error bound of the updated residual
+    bool have_base = false;              // Rf and W hold float64-accurate residuals (possibly updated)
+    double eps_low = 1e-4;
 
     Gmres(Op& op_, const vie_solve_opts& o_, int nrhs_, const ColumnLayout& lay_)
         : op(op_), o(o_), lay(lay_), s(op_.ctx->stream), n(op_.n()), nrhs(nrhs_), n_sm(op_.ctx->n_sm) {
@@ -112,6 +115,10 @@ struct Gmres {
         Rl.alloc(vec);
         Wl.alloc(vec);
         W.alloc(vec);
+        if (c64) {
+            Rf.alloc(vec);  // b - Zs x per column, the base of residual updates
+            enorm.alloc(nrhs * sizeof(double));
+        }
         op_reserve(op, nrhs, o.precision, s);
         VIE_CUDA(cudaMemsetAsync(ctr.p, 0, KR_NCTR * sizeof(int), s));
         VIE_CUDA(cudaMemsetAsync(hist.p, 0, 512 * sizeof(double), s));
@@ -198,12 +205,36 @@ struct Gmres {
     // the residual is still far above the tolerance (cheap), with the inner
     // apply's precision, which is accurate enough to restart from and never
     // ends a solve
-    void launch_post(int k, const double2* b, double2* X, cudaStream_t st, bool cheap) {
+    // post modes: the residual that ends a cycle
+    enum { kPostAccurate = 0, kPostCheap = 1, kPostUpdate = 2 };
+    void launch_post(int k, const double2* b, double2* X, cudaStream_t st, int mode) {
         const int nblk = kr_nblk(n, k, n_sm);
         restore_colr(st);
-        kr_update(a, X, k, nblk, st);
-        launch_residual(k, b, X, st, cheap);
+        if (mode != kPostUpdate) {
+            kr_update(a, X, k, nblk, st);
+            launch_residual(k, b, X, st, mode == kPostCheap);
+            return;
+        }
+        // W -= P^-1 Zs d and R -= Zs d for the cycle's correction d = V y,
+        // both products in the inner precision: the error they add is below
+        // ~1e-4 of |P^-1 Zs d|, which the host accumulates and bounds
+        float2* d32 = reinterpret_cast<float2*>(Xg.p);
+        float2* e32 = reinterpret_cast<float2*>(Yg.p);
+        float2* t32 = reinterpret_cast<float2*>(Xl.p);
+        kr_update(a, X, k, nblk, st, d32);
+        const int prec = o.precision == VIE_BF16X3 ? VIE_BF16X3 : VIE_C64;
+        if (prec == VIE_BF16X3) op_apply_fused_bf16x3(op, d32, e32, k, st);
+        else op_apply_fused32(op, d32, e32, k, st);
+        op_apply_plain32(op, d32, t32, k, prec, st);
+        convert_c64_to_c128(e32, Wl.p, n * k, st);
+        convert_c64_to_c128(t32, T.p, n * k, st);
+        kr_colnorms(a, Wl.as<double2>(), k, nblk, a.cols, rpart.as<double>(), enorm.as<double>(), st);
+        kr_sub_scatter_norm(a, T.as<double2>(), Rf.as<double2>(), k, nblk, st);
+        kr_rnorm_from_partials(a, k, nblk, st);
+        kr_sub_scatter_norm(a, Wl.as<double2>(), W.as<double2>(), k, nblk, st);
+        kr_cycle_end(a, k, nblk, 3, st);
     }
+
     void launch_residual(int k, const double2* b, const double2* X, cudaStream_t st, bool cheap) {
         const int nblk = kr_nblk(n, k, n_sm);
         kr_gather_cols(a, X, Xl.as<double2>(), k, nblk, st);
@@ -218,6 +249,7 @@ struct Gmres {
         }
         kr_sub_cols(a, b, T.as<double2>(), Rl.as<double2>(), k, nblk, st);
         kr_colnorms(a, Rl.as<double2>(), k, nblk, a.cols, rpart.as<double>(), a.rnorm, st);
+        if (!cheap && Rf.p) kr_scatter_norm(a, Rl.as<double2>(), Rf.as<double2>(), k, nblk, st);  // update base
         if (o.precond) op_precond64(op, Rl.as<double2>(), Wl.as<double2>(), k, st);
         else VIE_CUDA(cudaMemcpyAsync(Wl.p, Rl.p, (size_t)n * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
         kr_scatter_norm(a, Wl.as<double2>(), W.as<double2>(), k, nblk, st);
@@ -225,8 +257,8 @@ struct Gmres {
     }
 
     // one restart cycle as a CUDA graph: pre -> while (continue) { Arnoldi step } -> post
-    CycleGraph& graph_for(int k, const double2* b, double2* X, bool cheap) {
-        const int key = 2 * k + (cheap ? 1 : 0);
+    CycleGraph& graph_for(int k, const double2* b, double2* X, int mode) {
+        const int key = 3 * k + mode;
         auto it = graphs.find(key);
         if (it != graphs.end()) return it->second;
         if (!s_body) VIE_CUDA(cudaStreamCreateWithFlags(&s_body, cudaStreamNonBlocking));
@@ -263,7 +295,7 @@ struct Gmres {
             VIE_CUDA(cudaStreamEndCapture(s_body, &body));
             const long long c2 = g_kernel_launches.load();
             VIE_CUDA(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-            launch_post(k, b, X, s, cheap);
+            launch_post(k, b, X, s, mode);
             const long long c3 = g_kernel_launches.load();
             VIE_CUDA(cudaStreamEndCapture(s, &graph));
             cg.pre = c1 - c0;
@@ -339,6 +371,14 @@ struct Gmres {
         kr_scatter_norm(a, W.as<double2>(), W.as<double2>(), nrhs, nb1, s);
         kr_cycle_end(a, nrhs, nb1, 1, s);
         read_state();
+        h_beta0.resize(nrhs);
+        VIE_CUDA(cudaMemcpyAsync(h_beta0.data(), beta0.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+        VIE_CUDA(cudaStreamSynchronize(s));
+        bound.assign(nrhs, 0.0);
+        have_base = false;
+        // relative error of one inner-precision product, with margin (measured: BF16x3
+        // <= 5e-5, float32 <= 1e-6)
+        eps_low = o.precision == VIE_BF16X3 ? 1e-4 : 1e-5;
         std::vector<int> live;
         while (true) {
             live.clear();
@@ -357,10 +397,18 @@ struct Gmres {
             // the residual that ends this cycle in the inner precision while every
             // live column is still above 1000 x the tolerance (that residual only
             // starts the next cycle; the solve ends on a float64-accurate one)
-            double worst = 0.0;
-            for (int c : live) worst = std::max(worst, h_res[c]);
+            double worst = 0.0, bworst = 0.0;
+            for (int c : live) {
+                worst = std::max(worst, h_res[c]);
+                bworst = std::max(bworst, bound[c]);
+            }
             const double near = 100.0 * a.tol;
             const bool cheap = c64 && worst > near && it0 + m < a.maxit;
+            // near the tolerance: one float64-accurate residual, then updates of it
+            // while their accumulated error bound stays below 1% of the tolerance
+            const int mode = cheap ? kPostCheap
+                                   : (c64 && have_base && bworst + eps_low * worst <= 0.01 * a.tol) ? kPostUpdate
+                                                                                                  : kPostAccurate;
             if (o.launch == 1) {
                 launch_pre(k, s);
                 do {
@@ -368,15 +416,25 @@ struct Gmres {
                     VIE_CUDA(cudaMemcpyAsync(h_pinned, ctr.p, KR_NCTR * sizeof(int), cudaMemcpyDeviceToHost, s));
                     VIE_CUDA(cudaStreamSynchronize(s));
                 } while (h_pinned[KR_CONT] && !h_pinned[KR_NAN]);
-                launch_post(k, b, X, s, cheap);
+                launch_post(k, b, X, s, mode);
                 read_state();
             } else {
-                CycleGraph& cg = graph_for(k, b, X, cheap);
+                CycleGraph& cg = graph_for(k, b, X, mode);
                 VIE_CUDA(cudaGraphLaunch(cg.exec, s));
                 read_state();
                 VIE_COUNT_LAUNCH(cg.pre + cg.post + cg.body * (long long)(h_pinned[KR_IT] - it0));
             }
-            if (cheap) {
+            if (mode == kPostUpdate) {
+                // error bound of the update: eps_low |P^-1 Zs d| relative to ||P^-1 b||
+                std::vector<double> en(nrhs);
+                VIE_CUDA(cudaMemcpyAsync(en.data(), enorm.p, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+                VIE_CUDA(cudaStreamSynchronize(s));
+                for (int c : live) bound[c] += h_beta0[c] > 0 ? eps_low * en[c] / h_beta0[c] : 0.0;
+            } else if (mode == kPostAccurate) {
+                have_base = true;
+                for (int c : live) bound[c] = 0.0;
+            } else {
+                have_base = false;
                 // a column that came near the tolerance gets its float64-accurate
                 // residual now, from the same iterate, so that no Arnoldi step is
                 // spent on a solution that may already be converged
@@ -386,6 +444,8 @@ struct Gmres {
                     restore_colr(s);
                     launch_residual(k, b, X, s, false);
                     read_state();
+                    have_base = true;
+                    for (int c : live) bound[c] = 0.0;
                 }
             }
         }

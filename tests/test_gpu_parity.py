@@ -418,17 +418,19 @@ def test_shared_factor_apply(ctx, tiny_dense):
     op.close()
 
 
-def test_tcgen05_packed_and_warp_specialised_equal_unpacked(ctx):
+def test_tcgen05_packed_and_warp_specialised_agree_with_unpacked(ctx):
     # the packed variant feeds the tensor core the same bf16 planes in the same
-    # MMA order (moved by bulk copies instead of split by the warps), and so does
-    # the warp-specialised one (producer warps, MMA warp, epilogue warps, two
-    # accumulator buffers): bit-identical, fused and unfused, for column counts
-    # that fill one 64-column pass, a pass plus a ragged tail, and a partial pass
+    # MMA order (moved by bulk copies instead of split by the warps):
+    # bit-identical; the warp-specialised one forms the same products with four
+    # wide MMAs per K step (two accumulator halves added in the epilogue): equal
+    # to float32 rounding; fused and unfused, for column counts that fill one
+    # 64-column pass, a pass plus a ragged tail, and partial passes (the
+    # warp-specialised ring holds 5 stages up to 16 columns, 4 up to 48, 3 above)
     import torch as th
     g = workloads.square_array(8, 4)
     op = vie.Operator(ctx, g)
     op.compress(1e-4, vie.C64)
-    for nrhs in (8, 16, 64, 70):
+    for nrhs in (8, 16, 24, 40, 64, 70):
         X = th.from_numpy(workloads.random_complex(op.n, 11, cols=nrhs).T.astype(np.complex64).copy()).cuda()
         for fl in (vie.FUSE_PRECOND, 0):
             out = {}
@@ -439,7 +441,7 @@ def test_tcgen05_packed_and_warp_specialised_equal_unpacked(ctx):
                 th.cuda.synchronize()
                 out[v] = Y.cpu().numpy()
             assert np.array_equal(out[vie.VAR_TCGEN05_BF16X3], out[vie.VAR_TCGEN05_PACKED_BF16X3]), (nrhs, fl)
-            assert np.array_equal(out[vie.VAR_TCGEN05_PACKED_BF16X3], out[vie.VAR_TCGEN05_WS_BF16X3]), (nrhs, fl)
+            assert rel(out[vie.VAR_TCGEN05_WS_BF16X3], out[vie.VAR_TCGEN05_PACKED_BF16X3]) < 5e-6, (nrhs, fl)
     op.close()
 
 
