@@ -69,6 +69,13 @@ WORKLOADS = {
              "983040 unknowns, 16 RHS (seed 0, within 20 deg of normal incidence); compression tolerance 1e-3 "
              "(at 1e-4 the factors would need ~970 GB)",
         model=dict(mnr=2.4e13, factor_entries=7.12e9, iterations=3000)),
+    "vogel": dict(
+        geometry=lambda: workloads.vogel_gold(2000, nv=3),
+        incident=workloads.normal_incidence,
+        tol=1e-4, precision="C64", restart=300, max_iters=3000,
+        desc="Vogel spiral of 2000 gold meta-atoms (eps = -9.428 - 1.513j, radius lambda/6, equal-volume cubes of "
+             "3^3 voxels), 216000 unknowns, 1 RHS at normal incidence; aperiodic, so no two far blocks share factors",
+        model=dict(mnr=1.0e13, factor_entries=3.56e9, iterations=183)),
     "scale": dict(
         geometry=lambda: workloads.square_array(16, 6),
         incident=workloads.normal_incidence,
@@ -257,7 +264,7 @@ print(json.dumps({"t_near": tn, "t_far_sample": max(tf - tn, 0.0)}))
 def _geom_spec(name):
     """How the oracle subprocess regenerates the workload's geometry."""
     return {"multirhs": ("square_array", [32, 4]), "graded": ("graded_array", [64, 4, 0]),
-            "scale": ("square_array", [16, 6])}[name]
+            "scale": ("square_array", [16, 6]), "vogel": ("vogel_gold", [2000, 3])}[name]
 
 
 def _run_oracle(code, args, threads, timeout=600):
@@ -471,7 +478,7 @@ def run_serving(args):
 def run_batch(args):
     """--batch: the serving mix (arrays of 8x8..SxS cubes of 3^3 voxels, S =
     --batch-max-side (48), lambda ~ U[0.9, 1.1], eps ~ U[8, 14], 1-8 RHS;
-    --requests problems, seed 7) solved one vie_solve after another and as one
+    --batch-requests problems (8), seed 7) solved one vie_solve after another and as one
     vie_solve_batch (block-diagonal union, one persistent apply launch per phase
     over all problems), operators built beforehand.  Reports right-hand sides
     per second both ways, each the median of three runs, and the largest
@@ -480,7 +487,7 @@ def run_batch(args):
     from paper_2603_10586_gb300 import vie
     torch.cuda.set_device(0)
     ctx = vie.Context(0)
-    reqs = workloads.serving_stream(args.requests, seed=7, ns_range=(8, args.batch_max_side))
+    reqs = workloads.serving_stream(args.batch_requests, seed=7, ns_range=(8, args.batch_max_side))
     ops = []
     for r in reqs:
         op = vie.Operator(ctx, r.geometry)
@@ -569,7 +576,8 @@ def run_profile(args):
     kh, pol = wl["incident"]()
     if args.profile_case == "small":
         g = {"multirhs": lambda: workloads.square_array(16, 4), "graded": lambda: workloads.graded_array(24, 4, 0),
-             "scale": lambda: workloads.square_array(8, 6)}[args.workload]()
+             "scale": lambda: workloads.square_array(8, 6),
+             "vogel": lambda: workloads.vogel_gold(500, nv=3)}[args.workload]()
     else:
         g = wl["geometry"]()
     prec = getattr(vie, wl["precision"])
@@ -628,6 +636,7 @@ def main():
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--batch", action="store_true", help="sequential against batched solves of the serving mix")
     ap.add_argument("--batch-max-side", type=int, default=48, help="largest array side of the --batch mix")
+    ap.add_argument("--batch-requests", type=int, default=8, help="problems of the --batch mix")
     ap.add_argument("--methods", action="store_true", help="lockstep GMRES, block GMRES and BiCGStab compared")
     ap.add_argument("--max-iters", type=int, default=0, help="iteration budget of --methods (0: the workload's)")
     ap.add_argument("--profile", action="store_true", help="one untimed step for ncu captures")

@@ -301,11 +301,21 @@ constexpr uint32_t kStageBytesA = kStageChunksA * 16;  // 32 KiB
 __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
-// bulk copy global -> shared memory, completion counted on the mbarrier
+// bulk copy global -> shared memory, completion counted on the mbarrier.  The
+// factor planes are read once per apply, so their lines are marked first to
+// leave L2, in favour of the gathered x / t rows that many tiles read.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
 __device__ __forceinline__ void tma_bulk(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(mbar)
-                 : "memory");
+    const uint64_t pol = l2_evict_first_policy();
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(dst),
+        "l"(src), "r"(bytes), "r"(mbar), "l"(pol)
+        : "memory");
 }
 
 // One output tile (rows x ncol) over K = nK: stages g0, g0+1, ... of this CTA.

@@ -234,15 +234,24 @@ void lpt_assign(const std::vector<double>& w, int nproc, std::vector<int>& owner
 // weighted by their factor bytes.
 // ---------------------------------------------------------------------------
 static void pack_lpt(const std::vector<int4>& items, const std::vector<double>& w, int ncta,
-                     std::vector<int4>& out_items, std::vector<int>& cta_ptr, std::vector<int>* perm = nullptr) {
+                     std::vector<int4>& out_items, std::vector<int>& cta_ptr, std::vector<int>* perm = nullptr,
+                     const std::vector<uint64_t>* key = nullptr) {
     std::vector<int> owner;
     std::vector<double> loads;
     lpt_assign(w, ncta, owner, loads);
     std::vector<std::vector<int>> per(ncta);
-    // within a CTA keep the heaviest items first
+    // within a CTA keep the heaviest items first, or, given a spatial key, the
+    // items in key order: every CTA then sweeps the array in the same
+    // direction at about the same pace (its items' weights are spread evenly
+    // over the keys), so the vector rows the CTAs gather at any one time come
+    // from one region and stay in L2 (the order inside a CTA does not change
+    // its load)
     std::vector<int> order(items.size());
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
+    if (key)
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return (*key)[a] < (*key)[b]; });
+    else
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
     for (int i : order) per[owner[i]].push_back(i);
     out_items.clear();
     cta_ptr.assign(ncta + 1, 0);
@@ -254,6 +263,33 @@ static void pack_lpt(const std::vector<int4>& items, const std::vector<double>& 
         }
         cta_ptr[c + 1] = (int)out_items.size();
     }
+}
+
+// Z-order (Morton) code of every atom centre, from its x, y position in the
+// array's bounding box quantised to 16 bits per axis
+static std::vector<uint64_t> atom_zorder(const Op& op) {
+    // (a joined operator of several problems keeps no centres: one key for all)
+    if (op.centres.size() < 3 * (size_t)op.N) return std::vector<uint64_t>(op.N, 0);
+    double lo[2] = {std::numeric_limits<double>::max(), std::numeric_limits<double>::max()};
+    double hi[2] = {-lo[0], -lo[1]};
+    for (int a = 0; a < op.N; ++a)
+        for (int d = 0; d < 2; ++d) {
+            lo[d] = std::min(lo[d], op.centres[3 * a + d]);
+            hi[d] = std::max(hi[d], op.centres[3 * a + d]);
+        }
+    std::vector<uint64_t> z(op.N);
+    for (int a = 0; a < op.N; ++a) {
+        uint32_t q[2];
+        for (int d = 0; d < 2; ++d) {
+            const double span = hi[d] - lo[d];
+            const double f = span > 0 ? (op.centres[3 * a + d] - lo[d]) / span : 0.0;
+            q[d] = (uint32_t)std::min(65535.0, std::max(0.0, std::floor(f * 65535.0 + 0.5)));
+        }
+        uint64_t code = 0;
+        for (int bit = 15; bit >= 0; --bit) code = (code << 2) | (((q[1] >> bit) & 1u) << 1) | ((q[0] >> bit) & 1u);
+        z[a] = code;
+    }
+    return z;
 }
 
 void build_apply_lists(Op& op) {
@@ -431,12 +467,16 @@ void build_umma_lists(Op& op) {
         std::vector<int> key(op.block_atoms.begin() + b.s_off, op.block_atoms.begin() + b.s_off + b.ns);
         groups[key].push_back(i);
     }
+    const std::vector<uint64_t> zc = atom_zorder(op);
     std::vector<long long> rowoff;
     std::vector<int> rowt;
     std::vector<int4> it1;
     std::vector<double> w1;
+    std::vector<uint64_t> key1, key2;  // spatial keys: the source atoms' lowest Z-order code, the atom's
     for (const auto& kv : groups) {
         const int rep = kv.second.front();
+        uint64_t zmin = ~0ull;
+        for (int a : kv.first) zmin = std::min(zmin, zc[a]);
         const int64_t start = (int64_t)rowoff.size();
         for (int i : kv.second) {
             const auto& b = op.blocks[i];
@@ -450,6 +490,7 @@ void build_umma_lists(Op& op) {
             const int nr = (int)std::min<int64_t>(kRows, total - r0);
             it1.push_back(make_int4(rep, (int)(start + r0), nr, op.block_prob.empty() ? 0 : op.block_prob[rep]));
             w1.push_back((double)(nr + 32) * op.blocks[rep].n);
+            key1.push_back(zmin);
         }
     }
     // phase 2: per atom every (block, rank index) as one virtual K axis
@@ -477,15 +518,16 @@ void build_umma_lists(Op& op) {
             const int p1 = std::min(op.np, p0 + kRows);
             it2.push_back(make_int4(a, p0, p1, op.atom_prob.empty() ? 0 : op.atom_prob[a]));
             w2.push_back((double)(p1 - p0 + 32) * (K + 1.0));
+            key2.push_back(zc[a]);
         }
     }
     std::vector<int4> q1, q2, r1, r2;
     std::vector<int> e1, e2, f1, f2, p1, p2, pr1, pr2;
-    pack_lpt(it1, w1, op.n_cta_u, q1, e1, &p1);
-    pack_lpt(it2, w2, op.n_cta_u, q2, e2, &p2);
+    pack_lpt(it1, w1, op.n_cta_u, q1, e1, &p1, &key1);
+    pack_lpt(it2, w2, op.n_cta_u, q2, e2, &p2, &key2);
     // the same items mapped to one CTA per SM (warp-specialised kernels)
-    pack_lpt(it1, w1, op.ctx->n_sm, r1, f1, &pr1);
-    pack_lpt(it2, w2, op.ctx->n_sm, r2, f2, &pr2);
+    pack_lpt(it1, w1, op.ctx->n_sm, r1, f1, &pr1, &key1);
+    pack_lpt(it2, w2, op.ctx->n_sm, r2, f2, &pr2, &key2);
     op.n_u1_items = (int)q1.size();
     op.n_u2_items = (int)q2.size();
     upload(op.d_u1_rowoff, rowoff.empty() ? std::vector<long long>{0} : rowoff);

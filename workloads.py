@@ -83,6 +83,24 @@ def vogel_spiral(n_atoms, radius=0.1, nv=1, eps=12.0, wavelength=1.0):
                     np.array([nv], np.int32), np.array([eps], complex), float(wavelength))
 
 
+# Sec. 6.1: spheres of radius 100 nm at a wavelength of 600 nm, gold with
+# eps_r = -9.428 + 1.513 i at that frequency.  The paper's "+ i" belongs to the
+# exp(-i w t) convention; under this code's exp(j w t) a lossy medium has
+# Im eps < 0, so the same gold is -9.428 - 1.513 j.
+GOLD_600NM = complex(-9.428, -1.513)
+
+
+def vogel_gold(n_atoms, nv=2, wavelength=1.0):
+    """The Sec. 6.1 workload on this voxel basis: n_atoms gold meta-atoms of
+    radius R = wavelength / 6 on the Vogel spiral (c = sqrt(3) R), each a cube
+    of the sphere's volume (side (4 pi / 3)^(1/3) R) standing in for the
+    sphere."""
+    R = wavelength / 6.0
+    g = vogel_spiral(n_atoms, radius=R, nv=nv, eps=GOLD_600NM, wavelength=wavelength)
+    return Geometry(g.centres, g.types, np.array([(4.0 * np.pi / 3.0) ** (1.0 / 3.0) * R]), g.nvs, g.eps,
+                    g.wavelength)
+
+
 def single_cube(side, nv, eps=12.0, wavelength=1.0):
     return Geometry(np.zeros((1, 3)), np.zeros(1, np.int32), np.array([side], float),
                     np.array([nv], np.int32), np.array([eps], complex), float(wavelength))
