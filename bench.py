@@ -46,6 +46,13 @@ import workloads  # noqa: E402
 
 TOL_SOLVE = 1e-6
 DEFAULT_WORKLOAD = "multirhs"
+# Measured DRAM bytes (read + write) of one fused apply, keyed by (workload,
+# right-hand sides, BF16x3): u1w_kernel<2> 27.24 + 1.17 GB, u2w_kernel<2> 30.32
+# + 0.12 GB, type_gemm<float2> 0.25 + 0.10 GB in one ncu pass
+# (dram__bytes_read.sum + dram__bytes_write.sum) over the 64-RHS apply of the
+# 32 x 32 array, `bench.py --profile`.  Only valid for the kernels it was taken
+# on; remove an entry when they change.
+APPLY_TRAFFIC = {("multirhs", 64, True): 59.2e9}
 
 # Per workload: geometry, incident waves, compression tolerance, inner-apply
 # precision ("C64" or "BF16X3"), restart length and, for the CPU oracle's
@@ -740,13 +747,16 @@ def main():
     alg_bytes = 8.0 * (info["factor_entries"] + info["n_types"] * info["np"] ** 2) + 16.0 * info["n"] * nrhs
     achieved = alg_bytes / (apply_ms * 1e-3) / 1e9
     # the library's default far-apply kernel for this many right-hand sides
-    far = ("u1w/u2w (tcgen05 BF16x3, warp-specialised, bulk-TMA A planes)" if nrhs <= 32 else
-           "u1p/u2p (tcgen05 BF16x3, bulk-TMA planes)")
+    far = ("u1w/u2w<1> (tcgen05 BF16x3, warp-specialised, bulk-TMA A planes)" if nrhs <= 16 else
+           "u1w/u2w<2> (tcgen05 BF16x3, warp-specialised, two row tiles per B tile, bulk-TMA A planes)")
+    # DRAM bytes of one fused apply (far kernels + type_gemm) from a one-pass ncu capture of
+    # `bench.py --profile` on the same workload and kernels
+    traffic = APPLY_TRAFFIC.get((args.workload, nrhs, prec == vie.BF16X3))
     roof = {"kernel": (f"far apply {far} + type_gemm, fused P^-1 Zs x, {nrhs} RHS") if prec == vie.BF16X3
             else "far apply + type_gemm, fused P^-1 Zs x (c64, 1 RHS)",
             "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "peak_kind": peak_kind, "algorithmic_bytes": alg_bytes, "apply_ms": apply_ms,
-            "traffic": None,
+            "traffic": traffic,
             "note": "algorithmic bytes: every far block's factors once (8 (m+n) r), the distinct self/inverse "
                     "blocks once, x read and y written once per right-hand side"}
     if prec == vie.BF16X3:

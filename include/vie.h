@@ -84,8 +84,7 @@ enum vie_variant {
     VIE_VAR_TCGEN05_BF16X3 = 6, /* tcgen05 MMAs with tensor-memory accumulators, 128-row tiles */
     VIE_VAR_TCGEN05_PACKED_BF16X3 = 7, /* as 6, with the factors split once into bf16 planes in the
                                           shared-memory stage layout and moved by bulk TMA copies (needs
-                                          ~1.1x the factor memory; runs as 6 when that is not free;
-                                          default for more than 32 right-hand sides) */
+                                          ~1.1x the factor memory; runs as 6 when that is not free) */
     VIE_VAR_SIMT_SHARED = 8 /* complex float32, one right-hand side at a time: far blocks that share
                                their factors (translated copies) are applied together, each factor
                                element read once per group of up to 4 copies; partial products are
@@ -97,8 +96,14 @@ enum vie_variant {
                                      pairs gather and split B into two stacked plane sets, one thread
                                      issues four wide MMAs per K step (each A plane read once), four
                                      warps drain two tensor-memory accumulator buffers; equal to 7 to
-                                     float32 rounding (default for 8 to 32 right-hand sides; runs as 6
-                                     when the planes do not fit) */
+                                     float32 rounding (default for 8 to 16 right-hand sides; runs as 6
+                                     when the planes do not fit) */,
+    VIE_VAR_TCGEN05_WS2_BF16X3 = 10 /* 9 with two 128-row tiles of factor rows sharing each B tile (the
+                                       two row tiles of a target atom, or two consecutive row tiles of
+                                       a source group), 16 K values per stage: the B operand is gathered
+                                       and split once for twice the rows; equal to 9 to float32
+                                       rounding (default for more than 16 right-hand sides; runs as 6
+                                       when the planes do not fit) */
 };
 
 /* vie_apply flags */
@@ -194,8 +199,8 @@ typedef struct vie_solve_opts {
 typedef struct vie_tune_result {
     int variant;               /* the variant now used for (precision, nrhs) */
     int n_candidates;
-    int candidates[8];         /* vie_variant values that were timed */
-    double ms[8];              /* best of three timed far applies per candidate */
+    int candidates[16];        /* vie_variant values that were timed */
+    double ms[16];             /* best of three timed far applies per candidate */
 } vie_tune_result;
 
 typedef struct vie_solve_stats {

@@ -712,31 +712,58 @@ constexpr int kWsMaxStages = 6;
 constexpr int kWsThr = 448;  // 14 warps
 constexpr int kWsWarpTma = 4, kWsWarpB0 = 5, kWsWarpMma = 13;
 constexpr int kWsGroups = (kWsWarpMma - kWsWarpB0) / 2;  // B-producer groups of two warps
-constexpr int kWsAccCols = 4 * kN;                // one accumulator: [Re_a | Im_a | Re_b | Im_b]
-constexpr int kWsTmemCols = 2 * kWsAccCols;       // two accumulator buffers: 512 columns
-constexpr int kWsSmemBytes = 224 * 1024;         // the ring
-// The ring: ns stages of `stride` bytes.  A stage holds the A planes exactly as
-// the packed layout (one 32 KiB bulk copy), then the two B stacks of 16 nmax
-// chunks each (4 plane slots x nmax rows x 4 K chunks; chunk (slot, row, q) of
-// a stack sits at q (4 nmma) + slot nmma + row).  nmax, the widest tile's
-// column count rounded up to 16, sets the stride, and the stage count is what
-// fits: 5 stages for up to 16 right-hand sides, 4 up to 48, 3 up to 64.
+constexpr int kWsTmemCols = 512;                          // accumulators [Re_a | Im_a | Re_b | Im_b] of 4 nmax columns
+constexpr int kWsSmemBytes = 224 * 1024;                  // the ring
+
+// Two tile shapes share the code.  MT = 1: one 128-row M tile per B tile and
+// 32 K values per stage (two MMA K steps).  MT = 2: two M tiles (256 rows: the
+// two row tiles of one target atom, or two consecutive row tiles of one
+// source group) share one B tile, 16 K values per stage (one K step), so the
+// B operand is gathered and split once for twice the factor rows.  Either way
+// a stage carries 32 KiB of A planes.
+template <int MT>
+struct WsGeom {
+    static constexpr int KS = 32 / MT;                                  // K values per stage
+    static constexpr int KQ = KS / 8;                                   // 16-byte K chunks per row and stage
+    static constexpr int KSTEPS = KS / 16;                              // MMA K steps per stage
+    static constexpr uint32_t kPlaneBytes = (uint32_t)kM * KS * 2;      // one bf16 plane of one M tile
+    static constexpr uint32_t kTileBytes = 4 * kPlaneBytes;             // its four planes
+    static constexpr uint32_t kABytes = MT * kTileBytes;                // 32 KiB
+    // stage bytes: the A planes, then two B stacks of 4 KQ nmax chunks
+    __host__ __device__ static constexpr uint32_t stride(int nmax) { return kABytes + 2u * 4u * KQ * nmax * 16u; }
+    __host__ __device__ static constexpr int stages(int nmax) {
+        return (int)(kWsSmemBytes / stride(nmax)) < kWsMaxStages ? (int)(kWsSmemBytes / stride(nmax)) : kWsMaxStages;
+    }
+    // accumulator buffers: each holds MT accumulators of 4 nmax columns
+    __host__ __device__ static constexpr int nbuf(int nmax) { return kWsTmemCols / (MT * 4 * nmax) >= 2 ? 2 : 1; }
+};
+static_assert(WsGeom<1>::stages(64) == 3 && WsGeom<1>::stages(16) == 5, "ring sizes");
+static_assert(WsGeom<2>::stages(64) == 4 && WsGeom<2>::stages(16) == 6, "ring sizes");
+static_assert(WsGeom<1>::kABytes == kStageBytesA && WsGeom<2>::kABytes == kStageBytesA, "A bytes per stage");
+static_assert(WsGeom<2>::stride(16) % 1024 == 0 && WsGeom<1>::stride(16) % 1024 == 0, "stage alignment");
+
+// The ring: ns stages of `stride` bytes.  A stage holds the A planes (MT = 1:
+// the packed layout of one 32-K stage, one bulk copy; MT = 2: per M tile the
+// half of a packed stage that holds 16 of its K values, four copies), then the
+// two B stacks; chunk (slot, row, q) of a stack sits at q (4 nmma) + slot nmma
+// + row.  nmax, the widest tile's column count rounded up to 16, sets the
+// stride, and the stage count is what fits: for MT = 1, 5 stages up to 16
+// right-hand sides, 4 up to 48, 3 up to 64; for MT = 2, 6, 5 and 4.
 struct WsRing {
     unsigned char* base;
     uint32_t stride, bstack;  // bytes per stage; chunks per B stack
     uint32_t ns;              // stages
+    uint32_t abytes;          // A bytes per stage
     __device__ __forceinline__ uint4* a(uint32_t slot) const { return reinterpret_cast<uint4*>(base + slot * stride); }
     __device__ __forceinline__ uint4* b(uint32_t slot, int k) const {
-        return reinterpret_cast<uint4*>(base + slot * stride + kStageBytesA) + k * bstack;
+        return reinterpret_cast<uint4*>(base + slot * stride + abytes) + k * bstack;
     }
 };
-__host__ __device__ constexpr uint32_t ws_stride(int nmax) { return kStageBytesA + 2u * 16u * nmax * 16u; }
-__host__ __device__ constexpr int ws_stages(int nmax) {
-    return (int)(kWsSmemBytes / ws_stride(nmax)) < kWsMaxStages ? (int)(kWsSmemBytes / ws_stride(nmax))
-                                                                 : kWsMaxStages;
+template <int MT>
+__device__ __forceinline__ WsRing ws_ring(unsigned char* smem, int nmax) {
+    return WsRing{smem, WsGeom<MT>::stride(nmax), 4u * WsGeom<MT>::KQ * nmax, (uint32_t)WsGeom<MT>::stages(nmax),
+                  WsGeom<MT>::kABytes};
 }
-static_assert(ws_stages(64) >= 3 && ws_stages(16) == 5, "ring sizes");
-static_assert(ws_stride(16) % 1024 == 0, "stage alignment");
 
 __device__ __forceinline__ uint4 neg_bf16x8(uint4 v) {
     return make_uint4(v.x ^ 0x80008000u, v.y ^ 0x80008000u, v.z ^ 0x80008000u, v.w ^ 0x80008000u);
@@ -763,29 +790,26 @@ __device__ __forceinline__ void put8_ws(uint4* b0, uint4* b1, int nmma, int row,
     b1[base + 3 * nmma] = RL;
 }
 
-// the 8 MMAs of one stage (two K steps of 16) into the accumulator at tm
-__device__ __forceinline__ void issue_stage_ws(const uint4* a, const uint4* b0, const uint4* b1, uint32_t tm, int nmma,
-                                               bool first) {
+// the four wide MMAs of one K step (16) of M tile planes `a` (plane stride
+// `pb` bytes) against the B stacks at byte offset `boff` into the accumulator
+// at tm
+__device__ __forceinline__ void mma_kstep_ws(uint32_t a, uint32_t pb, uint32_t b0, uint32_t b1, uint32_t tm,
+                                             int nmma, uint32_t acc0) {
     const uint32_t id4 = idesc(4 * nmma, false), id2 = idesc(2 * nmma, false);
     const uint32_t lbob = (uint32_t)(4 * nmma * 16);
+    uint64_t A[4];
 #pragma unroll
-    for (int ks = 0; ks < 2; ++ks) {
-        uint64_t A[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) A[p] = sdesc(smem_u32(a + p * kChunksA) + ks * 2 * kLboA, kLboA);
-        const uint64_t B1 = sdesc(smem_u32(b0) + ks * 2 * lbob, lbob);
-        const uint64_t B2 = sdesc(smem_u32(b1) + ks * 2 * lbob, lbob);
-        const uint32_t acc0 = (first && ks == 0) ? 0u : 1u;
-        // planes: 0 re hi, 1 re lo, 2 im hi, 3 im lo
-        umma(tm, A[0], B1, id4, acc0);
-        umma(tm, A[2], B2, id4, 1u);
-        umma(tm, A[1], B1, id2, 1u);
-        umma(tm, A[3], B2, id2, 1u);
-    }
+    for (int p = 0; p < 4; ++p) A[p] = sdesc(a + p * pb, kLboA);
+    const uint64_t B1 = sdesc(b0, lbob), B2 = sdesc(b1, lbob);
+    // planes: 0 re hi, 1 re lo, 2 im hi, 3 im lo
+    umma(tm, A[0], B1, id4, acc0);
+    umma(tm, A[2], B2, id4, 1u);
+    umma(tm, A[1], B1, id2, 1u);
+    umma(tm, A[3], B2, id2, 1u);
 }
 
 struct WsCtl {
-    uint64_t full_a[kWsMaxStages];  // A copy of the slot landed (1 arrival + bytes)
+    uint64_t full_a[kWsMaxStages];  // A copies of the slot landed (1 arrival + bytes)
     uint64_t full_b[kWsMaxStages];  // B planes of the slot stored (the stage's 2 producer warps)
     uint64_t empty[kWsMaxStages];   // MMAs that read the slot are done (1 commit)
     uint64_t acc_full[2];        // accumulator buffer holds a finished tile (1 commit)
@@ -816,26 +840,36 @@ __device__ __forceinline__ bool mbar_wait_lim(uint32_t mbar, uint32_t parity, lo
     }
 }
 
-// The tiles of this CTA, in the same order for every role: (item, 64-column
-// pass).  Tile::nst = K stages (0: nothing to multiply, the output is zero).
+// The tiles of this CTA, in the same order for every role: (item, or pair of
+// items with one B operand, 64-column pass).  nst = K stages (0: nothing to
+// multiply, the output is zero); rows[m] = 0 marks an absent second M tile;
+// pk[m] = the M tile's first stage in the packed planes.
 struct WsTile1 {
     Phase1 src;
-    int nst, nmma, rows;
-    const int* rt;
+    int nst, nmma;
+    int rows[2];
+    const int* rt[2];
+    long long pk[2];
 };
 
-template <class Role>
-__device__ void ws_tiles1(const FarBlockDev* blocks, const int* batoms, const int4* items, int it0, int it1,
-                          const int* rowt, const float2* x, int64_t ldx, int np, int nrhs, const int2* colr,
-                          volatile int* abort, Role&& role) {
+template <int MT, class Role>
+__device__ void ws_tiles1(const FarBlockDev* blocks, const int* batoms, const int4* items, const int4* items_b,
+                          const long long* pk, const long long* pk_b, int it0, int it1, const int* rowt,
+                          const float2* x, int64_t ldx, int np, int nrhs, const int2* colr, volatile int* abort,
+                          Role&& role) {
     for (int it = it0; it < it1 && !*abort; ++it) {
         const int4 item = items[it];
+        const int4 ib = MT == 2 ? items_b[it] : make_int4(0, 0, 0, 0);
         const FarBlockDev B = blocks[item.x];
         const int2 cr = colr ? colr[item.w] : make_int2(0, nrhs);
         for (int c0 = cr.x; c0 < cr.y && !*abort; c0 += kN) {
             WsTile1 T{Phase1{nullptr, nullptr, rowt, batoms + B.s_off, x, ldx, np, B.n, item.y, item.z, c0,
                              min(kN, cr.y - c0)},
-                      (B.n + kKS - 1) / kKS, 0, item.z, rowt + item.y};
+                      (B.n + WsGeom<MT>::KS - 1) / WsGeom<MT>::KS,
+                      0,
+                      {item.z, ib.z},
+                      {rowt + item.y, rowt + ib.y},
+                      {pk[it], MT == 2 ? pk_b[it] : 0}};
             T.nmma = max(16, (T.src.ncol + 15) / 16 * 16);
             if (!role(T, it, c0)) return;
         }
@@ -844,23 +878,30 @@ __device__ void ws_tiles1(const FarBlockDev* blocks, const int* batoms, const in
 
 struct WsTile2 {
     Phase2 src;
-    int nst, nmma, rows;
-    int64_t rb;
+    int nst, nmma;
+    int rows[2];
+    int64_t rb[2];
+    long long pk[2];
 };
 
-template <class Role>
-__device__ void ws_tiles2(const int4* items, int it0, int it1, const int* tidx, const long long* kptr,
-                          const float2* t, int64_t ldt, int np, int nrhs, const int2* colr, volatile int* abort,
-                          Role&& role) {
+template <int MT, class Role>
+__device__ void ws_tiles2(const int4* items, const int4* items_b, const long long* pk, const long long* pk_b,
+                          int it0, int it1, const int* tidx, const long long* kptr, const float2* t, int64_t ldt,
+                          int np, int nrhs, const int2* colr, volatile int* abort, Role&& role) {
     for (int it = it0; it < it1 && !*abort; ++it) {
         const int4 item = items[it];
+        const int4 ib = MT == 2 ? items_b[it] : make_int4(item.x, 0, 0, 0);
         const int a = item.x, p0 = item.y, rows = item.z - item.y;
         const long long kb = kptr[a];
         const int nK = (int)(kptr[a + 1] - kb);
         const int2 cr = colr ? colr[item.w] : make_int2(0, nrhs);
         for (int c0 = cr.x; c0 < cr.y && !*abort; c0 += kN) {
             WsTile2 T{Phase2{nullptr, nullptr, tidx, t, ldt, kb, nK, p0, rows, c0, min(kN, cr.y - c0)},
-                      (nK + kKS - 1) / kKS, 0, rows, (int64_t)a * np + p0};
+                      (nK + WsGeom<MT>::KS - 1) / WsGeom<MT>::KS,
+                      0,
+                      {rows, ib.z - ib.y},
+                      {(int64_t)a * np + p0, (int64_t)a * np + ib.y},
+                      {pk[it], MT == 2 ? pk_b[it] : 0}};
             T.nmma = max(16, (T.src.ncol + 15) / 16 * 16);
             if (!role(T, it, c0)) return;
         }
@@ -915,28 +956,43 @@ __device__ void ws_teardown(WsCtl& ctl, uint32_t ns, int* err) {
                      : "memory");
 }
 
-// The three roles over one phase's tiles.  Tiles: a callable enumerating the
-// CTA's tiles (ws_tiles1 / ws_tiles2 bound to their arguments); Out: stores row
-// r, column c of the tile (value) to its destination.
-template <class TileT, class Enum, class Out>
-__device__ void ws_run(WsCtl& ctl, const WsRing& ring, const uint4* pack, const long long* pk, long long lim,
-                       Enum&& enumerate, Out&& out) {
+// The roles over one phase's tiles.  enumerate: a callable enumerating the
+// CTA's tiles (ws_tiles1 / ws_tiles2 bound to their arguments); out(T, m, r,
+// c, v): stores row r of M tile m, column c of the tile, to its destination.
+template <int MT, class TileT, class Enum, class Out>
+__device__ void ws_run(WsCtl& ctl, const WsRing& ring, int nmax, const uint4* pack, long long lim, Enum&& enumerate,
+                       Out&& out) {
+    using G = WsGeom<MT>;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     volatile int* abort = &ctl.abort;
+    const uint32_t accs = 4u * nmax;  // columns of one accumulator
+    const uint32_t nbuf = (uint32_t)G::nbuf(nmax);
     if (warp == kWsWarpTma) {
         // ---- A copies, one thread
         if (lane == 0) {
             uint32_t g = 0;
-            enumerate([&](const TileT& T, int it, int) -> bool {
-                const uint4* packA = pack + pk[it] * kStageChunksA;
+            enumerate([&](const TileT& T, int, int) -> bool {
                 for (int st = 0; st < T.nst; ++st, ++g) {
                     const uint32_t slot = g % ring.ns;
                     if (g >= ring.ns && !mbar_wait_lim(smem_u32(&ctl.empty[slot]), ((g / ring.ns) - 1) & 1, lim))
                         *abort = 1;
                     if (*abort) return false;
                     const uint32_t mb = smem_u32(&ctl.full_a[slot]);
-                    mbar_expect_tx(mb, kStageBytesA);
-                    tma_bulk(smem_u32(ring.a(slot)), packA + (int64_t)st * kStageChunksA, kStageBytesA, mb);
+                    if (MT == 1) {
+                        mbar_expect_tx(mb, kStageBytesA);
+                        tma_bulk(smem_u32(ring.a(slot)), pack + (T.pk[0] + st) * kStageChunksA, kStageBytesA, mb);
+                    } else {
+                        // M tile m, plane p: chunks 2h kM .. 2h kM + 2 kM of plane p of
+                        // packed stage st / 2 (h = st mod 2), 4 KiB
+                        const int nt = T.rows[1] > 0 ? 2 : 1;
+                        mbar_expect_tx(mb, nt * G::kTileBytes);
+                        for (int m = 0; m < nt; ++m)
+                            for (int p = 0; p < 4; ++p)
+                                tma_bulk(smem_u32(ring.a(slot)) + m * G::kTileBytes + p * G::kPlaneBytes,
+                                         pack + (T.pk[m] + st / 2) * kStageChunksA + p * kChunksA +
+                                             (st & 1) * 2 * kM,
+                                         G::kPlaneBytes, mb);
+                    }
                     ctl.g_tma = g + 1;
                 }
                 return true;
@@ -966,12 +1022,12 @@ __device__ void ws_run(WsCtl& ctl, const WsRing& ring, const uint4* pack, const 
                 // neighbouring threads take neighbouring columns of one K
                 // chunk, so their 16-byte stores fill whole shared-memory
                 // wavefronts
-                const int nm = T.nmma, nseg = nm * 4;
+                const int nm = T.nmma, nseg = nm * G::KQ;
                 float2 vb[4][8];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int seg = gtid + 64 * u;
-                    if (seg < nseg) T.src.load_b(seg % nm, seg / nm, st * kKS, vb[u]);
+                    if (seg < nseg) T.src.load_b(seg % nm, seg / nm, st * G::KS, vb[u]);
                 }
                 if (g >= ring.ns) {
                     bool ok = true;
@@ -999,12 +1055,13 @@ __device__ void ws_run(WsCtl& ctl, const WsRing& ring, const uint4* pack, const 
             uint32_t g = 0, t = 0;
             enumerate([&](const TileT& T, int, int) -> bool {
                 if (T.nst == 0) return true;
-                const uint32_t ab = t & 1;
-                if (t >= 2 && !mbar_wait_lim(smem_u32(&ctl.acc_empty[ab]), ((t >> 1) - 1) & 1, lim)) {
+                const uint32_t ab = t % nbuf, use = t / nbuf;
+                if (use >= 1 && !mbar_wait_lim(smem_u32(&ctl.acc_empty[ab]), (use - 1) & 1, lim)) {
                     *abort = 1;
                     return false;
                 }
-                const uint32_t tm = ctl.tmem + ab * (uint32_t)kWsAccCols;
+                const uint32_t tm = ctl.tmem + ab * MT * accs;
+                const int nt = T.rows[1] > 0 && MT == 2 ? 2 : 1;
                 for (int st = 0; st < T.nst; ++st, ++g) {
                     const uint32_t slot = g % ring.ns, par = (g / ring.ns) & 1;
                     if (*abort || !mbar_wait_lim(smem_u32(&ctl.full_a[slot]), par, lim) ||
@@ -1013,7 +1070,14 @@ __device__ void ws_run(WsCtl& ctl, const WsRing& ring, const uint4* pack, const 
                         return false;
                     }
                     fence_after();
-                    issue_stage_ws(ring.a(slot), ring.b(slot, 0), ring.b(slot, 1), tm, T.nmma, st == 0);
+                    const uint32_t a = smem_u32(ring.a(slot)), b0 = smem_u32(ring.b(slot, 0)),
+                                   b1 = smem_u32(ring.b(slot, 1));
+                    const uint32_t lbob = (uint32_t)(4 * T.nmma * 16);
+#pragma unroll
+                    for (int ks = 0; ks < G::KSTEPS; ++ks)
+                        for (int m = 0; m < nt; ++m)
+                            mma_kstep_ws(a + m * G::kTileBytes + ks * 2 * kLboA, G::kPlaneBytes, b0 + ks * 2 * lbob,
+                                         b1 + ks * 2 * lbob, tm + m * accs, T.nmma, (st == 0 && ks == 0) ? 0u : 1u);
                     umma_commit(smem_u32(&ctl.empty[slot]));
                     ctl.g_mma = g + 1;
                 }
@@ -1030,33 +1094,37 @@ __device__ void ws_run(WsCtl& ctl, const WsRing& ring, const uint4* pack, const 
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
         enumerate([&](const TileT& T, int, int) -> bool {
             const int ncol = T.src.ncol;
+            const int nt = T.rows[1] > 0 && MT == 2 ? 2 : 1;
             if (T.nst == 0) {
-                if (r < T.rows)
-                    for (int c = 0; c < ncol; ++c) out(T, r, c, make_float2(0.f, 0.f));
+                for (int m = 0; m < nt; ++m)
+                    if (r < T.rows[m])
+                        for (int c = 0; c < ncol; ++c) out(T, m, r, c, make_float2(0.f, 0.f));
                 return true;
             }
-            const uint32_t ab = t & 1;
+            const uint32_t ab = t % nbuf, use = t / nbuf;
             bool ok = true;
-            if (lane == 0) ok = mbar_wait_lim(smem_u32(&ctl.acc_full[ab]), (t >> 1) & 1, lim);
+            if (lane == 0) ok = mbar_wait_lim(smem_u32(&ctl.acc_full[ab]), use & 1, lim);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) {
                 *abort = 1;
                 return false;
             }
             fence_after();
-            const uint32_t base = ctl.tmem + ab * (uint32_t)kWsAccCols + lane_base;
             const int nm = T.nmma;
-            for (int cb = 0; cb < ncol; cb += 16) {
-                float ra[16], ia[16], rb[16], ib[16];
-                tmem_ld16(base + cb, ra);
-                tmem_ld16(base + nm + cb, ia);
-                tmem_ld16(base + 2 * nm + cb, rb);
-                tmem_ld16(base + 3 * nm + cb, ib);
-                tmem_wait_ld();
-                if (r < T.rows) {
+            for (int m = 0; m < nt; ++m) {
+                const uint32_t base = ctl.tmem + (ab * MT + m) * accs + lane_base;
+                for (int cb = 0; cb < ncol; cb += 16) {
+                    float ra[16], ia[16], rb[16], ib[16];
+                    tmem_ld16(base + cb, ra);
+                    tmem_ld16(base + nm + cb, ia);
+                    tmem_ld16(base + 2 * nm + cb, rb);
+                    tmem_ld16(base + 3 * nm + cb, ib);
+                    tmem_wait_ld();
+                    if (r < T.rows[m]) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (cb + i < ncol) out(T, r, cb + i, make_float2(ra[i] + rb[i], ia[i] + ib[i]));
+                        for (int i = 0; i < 16; ++i)
+                            if (cb + i < ncol) out(T, m, r, cb + i, make_float2(ra[i] + rb[i], ia[i] + ib[i]));
+                    }
                 }
             }
             fence_before();
@@ -1068,29 +1136,41 @@ __device__ void ws_run(WsCtl& ctl, const WsRing& ring, const uint4* pack, const 
     }
 }
 
+template <int MT>
 __global__ void __launch_bounds__(kWsThr, 1) u1w_kernel(const FarBlockDev* __restrict__ blocks,
                                                         const int* __restrict__ batoms, const int4* __restrict__ items,
+                                                        const int4* __restrict__ items_b,
                                                         const int* __restrict__ cta_ptr,
                                                         const long long* __restrict__ pk,
+                                                        const long long* __restrict__ pk_b,
                                                         const uint4* __restrict__ pack, const int* __restrict__ rowt,
                                                         const float2* __restrict__ x, int64_t ldx, int np,
                                                         float2* __restrict__ t, int64_t ldt, int nrhs,
                                                         const int2* __restrict__ colr, int nmax, int* err,
                                                         long long lim) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const WsRing ring{smem, ws_stride(nmax), 16u * nmax, (uint32_t)ws_stages(nmax)};
+    const WsRing ring = ws_ring<MT>(smem, nmax);
     __shared__ WsCtl ctl;
     ws_setup(ctl, ring.ns);
     const int it0 = cta_ptr[blockIdx.x], it1 = cta_ptr[blockIdx.x + 1];
-    ws_run<WsTile1>(
-        ctl, ring, pack, pk, lim,
-        [&](auto&& role) { ws_tiles1(blocks, batoms, items, it0, it1, rowt, x, ldx, np, nrhs, colr, &ctl.abort, role); },
-        [&](const WsTile1& T, int r, int c, float2 v) { t[(int64_t)T.rt[r] + (int64_t)(T.src.c0 + c) * ldt] = v; });
+    ws_run<MT, WsTile1>(
+        ctl, ring, nmax, pack, lim,
+        [&](auto&& role) {
+            ws_tiles1<MT>(blocks, batoms, items, items_b, pk, pk_b, it0, it1, rowt, x, ldx, np, nrhs, colr,
+                          &ctl.abort, role);
+        },
+        [&](const WsTile1& T, int m, int r, int c, float2 v) {
+            t[(int64_t)T.rt[m][r] + (int64_t)(T.src.c0 + c) * ldt] = v;
+        });
     ws_teardown(ctl, ring.ns, err);
 }
 
-__global__ void __launch_bounds__(kWsThr, 1) u2w_kernel(const int4* __restrict__ items, const int* __restrict__ cta_ptr,
+template <int MT>
+__global__ void __launch_bounds__(kWsThr, 1) u2w_kernel(const int4* __restrict__ items,
+                                                        const int4* __restrict__ items_b,
+                                                        const int* __restrict__ cta_ptr,
                                                         const long long* __restrict__ pk,
+                                                        const long long* __restrict__ pk_b,
                                                         const uint4* __restrict__ pack, const int* __restrict__ tidx,
                                                         const long long* __restrict__ kptr,
                                                         const float2* __restrict__ t, int64_t ldt, int np,
@@ -1098,14 +1178,16 @@ __global__ void __launch_bounds__(kWsThr, 1) u2w_kernel(const int4* __restrict__
                                                         const int2* __restrict__ colr, int nmax, int* err,
                                                         long long lim) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const WsRing ring{smem, ws_stride(nmax), 16u * nmax, (uint32_t)ws_stages(nmax)};
+    const WsRing ring = ws_ring<MT>(smem, nmax);
     __shared__ WsCtl ctl;
     ws_setup(ctl, ring.ns);
     const int it0 = cta_ptr[blockIdx.x], it1 = cta_ptr[blockIdx.x + 1];
-    ws_run<WsTile2>(
-        ctl, ring, pack, pk, lim,
-        [&](auto&& role) { ws_tiles2(items, it0, it1, tidx, kptr, t, ldt, np, nrhs, colr, &ctl.abort, role); },
-        [&](const WsTile2& T, int r, int c, float2 v) { F[T.rb + r + (int64_t)(T.src.c0 + c) * ldf] = v; });
+    ws_run<MT, WsTile2>(
+        ctl, ring, nmax, pack, lim,
+        [&](auto&& role) {
+            ws_tiles2<MT>(items, items_b, pk, pk_b, it0, it1, tidx, kptr, t, ldt, np, nrhs, colr, &ctl.abort, role);
+        },
+        [&](const WsTile2& T, int m, int r, int c, float2 v) { F[T.rb[m] + r + (int64_t)(T.src.c0 + c) * ldf] = v; });
     ws_teardown(ctl, ring.ns, err);
 }
 
@@ -1121,8 +1203,10 @@ void umma_prepare(Op& op, cudaStream_t s) {
         cudaFuncSetAttribute(u2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         cudaFuncSetAttribute(u1p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         cudaFuncSetAttribute(u2p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-        cudaFuncSetAttribute(u1w_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemBytes);
-        cudaFuncSetAttribute(u2w_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemBytes);
+        cudaFuncSetAttribute(u1w_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemBytes);
+        cudaFuncSetAttribute(u2w_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemBytes);
+        cudaFuncSetAttribute(u1w_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemBytes);
+        cudaFuncSetAttribute(u2w_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemBytes);
     });
     if (!op.d_err.p) {
         op.d_err.alloc(sizeof(int));
@@ -1215,7 +1299,10 @@ static long long ws_wait_limit() {
     return kWaitCycles;
 }
 
-void apply_far_umma_ws(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s) {
+// MT = 1: variant 9 over the one-CTA-per-SM item lists; MT = 2: variant 10
+// over the lists of item pairs that share their B operand.
+template <int MT>
+static void apply_far_ws(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s) {
     if (!umma_pack(op, s)) {  // not enough memory for the packed planes: the kernel that splits A itself
         apply_far_umma(op, x, ldx, F, ldf, nrhs, s);
         return;
@@ -1228,19 +1315,32 @@ void apply_far_umma_ws(Op& op, const float2* x, int64_t ldx, float2* F, int64_t 
     // the widest tile: 64 columns, or all of them when fewer (a tile never
     // spans two problems' column ranges, so it is no wider than this either)
     const int nmax = std::max(16, (std::min(nrhs, kN) + 15) / 16 * 16);
-    const size_t smem = (size_t)ws_stages(nmax) * ws_stride(nmax);
+    const size_t smem = (size_t)WsGeom<MT>::stages(nmax) * WsGeom<MT>::stride(nmax);
+    const bool two = MT == 2;
     if (op.n_u1_items > 0) {
-        u1w_kernel<<<nc, kWsThr, smem, s>>>(
-            op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(), op.d_w1_items.as<int4>(), op.d_w1_cta.as<int>(),
-            op.d_w1_pk.as<long long>(), op.d_u1_pack.as<uint4>(), op.d_u1_rowt.as<int>(), x, ldx, op.np,
-            op.d_t.as<float2>(), op.t_total, nrhs, op.colr, nmax, op.d_err.as<int>(), lim);
+        u1w_kernel<MT><<<nc, kWsThr, smem, s>>>(
+            op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
+            (two ? op.d_x1_items : op.d_w1_items).as<int4>(), two ? op.d_x1_items_b.as<int4>() : nullptr,
+            (two ? op.d_x1_cta : op.d_w1_cta).as<int>(), (two ? op.d_x1_pk : op.d_w1_pk).as<long long>(),
+            two ? op.d_x1_pk_b.as<long long>() : nullptr, op.d_u1_pack.as<uint4>(), op.d_u1_rowt.as<int>(), x, ldx,
+            op.np, op.d_t.as<float2>(), op.t_total, nrhs, op.colr, nmax, op.d_err.as<int>(), lim);
         VIE_CHECK_LAUNCH();
     }
-    u2w_kernel<<<nc, kWsThr, smem, s>>>(
-        op.d_w2_items.as<int4>(), op.d_w2_cta.as<int>(), op.d_w2_pk.as<long long>(), op.d_u2_pack.as<uint4>(),
-        op.d_u2_tidx.as<int>(), op.d_u2_kptr.as<long long>(), op.d_t.as<float2>(), op.t_total, op.np, F, ldf, nrhs,
-        op.colr, nmax, op.d_err.as<int>(), lim);
+    u2w_kernel<MT><<<nc, kWsThr, smem, s>>>(
+        (two ? op.d_x2_items : op.d_w2_items).as<int4>(), two ? op.d_x2_items_b.as<int4>() : nullptr,
+        (two ? op.d_x2_cta : op.d_w2_cta).as<int>(), (two ? op.d_x2_pk : op.d_w2_pk).as<long long>(),
+        two ? op.d_x2_pk_b.as<long long>() : nullptr, op.d_u2_pack.as<uint4>(), op.d_u2_tidx.as<int>(),
+        op.d_u2_kptr.as<long long>(), op.d_t.as<float2>(), op.t_total, op.np, F, ldf, nrhs, op.colr, nmax,
+        op.d_err.as<int>(), lim);
     VIE_CHECK_LAUNCH();
+}
+
+void apply_far_umma_ws(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s) {
+    apply_far_ws<1>(op, x, ldx, F, ldf, nrhs, s);
+}
+
+void apply_far_umma_ws2(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s) {
+    apply_far_ws<2>(op, x, ldx, F, ldf, nrhs, s);
 }
 
 }  // namespace vie

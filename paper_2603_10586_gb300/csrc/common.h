@@ -200,6 +200,10 @@ struct Op {
     // shared-memory stage layout (32 KiB per 32-wide K stage), copied by bulk TMA
     DevBuf d_u1_pk, d_u2_pk, d_u1_pack, d_u2_pack;  // stage offsets per item, planes
     DevBuf d_w1_items, d_w1_cta, d_w1_pk, d_w2_items, d_w2_cta, d_w2_pk;  // one CTA per SM (warp-specialised)
+    // pairs of items that share their B operand (two M tiles per B tile), one CTA per SM: first and
+    // second item (rows 0 when absent) and their packed stage offsets
+    DevBuf d_x1_items, d_x1_items_b, d_x1_cta, d_x1_pk, d_x1_pk_b;
+    DevBuf d_x2_items, d_x2_items_b, d_x2_cta, d_x2_pk, d_x2_pk_b;
     long long u1_stages = 0, u2_stages = 0;
     bool umma_packed = false, umma_pack_failed = false;
     int n_u1_items = 0, n_u2_items = 0, n_cta_u = 0;
@@ -336,6 +340,7 @@ bool umma_pack(Op& op, cudaStream_t s);
 size_t umma_pack_bytes(const Op& op);
 void apply_far_umma_packed(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
 void apply_far_umma_ws(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
+void apply_far_umma_ws2(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
 // complex float32 far apply reading each shared factor once per group of up to
 // Op::kShareGroup translated copies (one right-hand side at a time)
 void apply_far_shared(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);

@@ -568,6 +568,54 @@ void build_umma_lists(Op& op) {
     upload(op.d_w2_items, r2.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : r2);
     upload(op.d_w2_cta, f2);
     upload(op.d_w2_pk, remap(p2, pr2, pk2));
+    // pairs of items with one B operand (the paired-tile kernels): two
+    // consecutive row tiles of one source group (phase 1) or of one target
+    // atom (phase 2); a leftover tile goes alone, its second item with 0 rows
+    auto pair_lists = [&](const std::vector<int4>& items, const std::vector<double>& w,
+                          const std::vector<uint64_t>& key, const std::vector<int>& perm_from,
+                          const std::vector<long long>& pk, auto same_b, auto empty_of, DevBuf& d_items,
+                          DevBuf& d_items_b, DevBuf& d_cta, DevBuf& d_pk, DevBuf& d_pk_b) {
+        std::vector<int> pos(perm_from.size());
+        for (size_t i = 0; i < perm_from.size(); ++i) pos[perm_from[i]] = (int)i;
+        std::vector<int2> pairs;
+        std::vector<int4> first;
+        std::vector<double> pw;
+        std::vector<uint64_t> pkey;
+        for (size_t i = 0; i < items.size(); ++i) {
+            const bool two = i + 1 < items.size() && same_b(items[i], items[i + 1]);
+            pairs.push_back(make_int2((int)i, two ? (int)i + 1 : -1));
+            first.push_back(items[i]);
+            pw.push_back(w[i] + (two ? w[i + 1] : 0.0));
+            pkey.push_back(key[i]);
+            if (two) ++i;
+        }
+        std::vector<int4> out;
+        std::vector<int> cta, perm;
+        pack_lpt(first, pw, op.ctx->n_sm, out, cta, &perm, &pkey);
+        std::vector<int4> ib(out.size());
+        std::vector<long long> pa(out.size() + 1, pk.back()), pb(out.size() + 1, 0);
+        for (size_t k = 0; k < out.size(); ++k) {
+            const int2 pr = pairs[perm[k]];
+            pa[k] = pk[pos[pr.x]];
+            ib[k] = pr.y >= 0 ? items[pr.y] : empty_of(items[pr.x]);
+            pb[k] = pr.y >= 0 ? pk[pos[pr.y]] : 0;
+        }
+        upload(d_items, out.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : out);
+        upload(d_items_b, ib.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : ib);
+        upload(d_cta, cta);
+        upload(d_pk, pa);
+        upload(d_pk_b, pb);
+    };
+    // phase 1 items (rep block, first row, rows, problem); phase 2 (atom, p0, p1, problem)
+    pair_lists(
+        it1, w1, key1, p1, pk1,
+        [](const int4& a, const int4& b) { return a.x == b.x && b.y == a.y + a.z; },
+        [](const int4& a) { return make_int4(a.x, a.y, 0, a.w); }, op.d_x1_items, op.d_x1_items_b, op.d_x1_cta,
+        op.d_x1_pk, op.d_x1_pk_b);
+    pair_lists(
+        it2, w2, key2, p2, pk2, [](const int4& a, const int4& b) { return a.x == b.x && b.y == a.z; },
+        [](const int4& a) { return make_int4(a.x, 0, 0, a.w); }, op.d_x2_items, op.d_x2_items_b, op.d_x2_cta,
+        op.d_x2_pk, op.d_x2_pk_b);
     op.umma_packed = false;
     op.umma_pack_failed = false;
     op.d_u1_pack.release();

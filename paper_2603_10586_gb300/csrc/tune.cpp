@@ -27,19 +27,20 @@ bool admissible(int precision, int v) {
     if ((v >= VIE_VAR_SIMT_R1 && v <= VIE_VAR_SIMT_R8) || v == VIE_VAR_SIMT_SHARED) return true;
     return precision == VIE_BF16X3 &&
            (v == VIE_VAR_MMA_BF16X3 || v == VIE_VAR_TCGEN05_BF16X3 || v == VIE_VAR_TCGEN05_PACKED_BF16X3 ||
-            v == VIE_VAR_TCGEN05_WS_BF16X3);
+            v == VIE_VAR_TCGEN05_WS_BF16X3 || v == VIE_VAR_TCGEN05_WS2_BF16X3);
 }
 
 int default_variant(const Op& op, int precision, int nrhs) {
     // one right-hand side: read shared factors once per group of copies when
     // the operator has translated copies
     if (nrhs == 1) return op.share_mean > 1.5 ? VIE_VAR_SIMT_SHARED : VIE_VAR_SIMT_R1;
-    // BF16x3: the warp-specialised kernel streams the A planes fastest while the
-    // B operand is narrow (its ring holds 4-5 stages up to 32 columns); at 64
-    // columns the packed kernel measured faster (15.7 against 18.9 ms per apply
-    // of the 32 x 32 array of 4^3 cubes)
+    // BF16x3: the warp-specialised kernel with one row tile per B tile streams
+    // the A planes fastest while the B operand is narrow (8.6 ms per apply of
+    // the 32 x 32 array of 4^3 cubes at 16 columns); wider, the gathers of B
+    // bound it and two row tiles per B tile win (9.7 / 11.3 / 12.7 ms at 32 /
+    // 48 / 64 columns, against 11.2 / 16.4 / 19.8 ms)
     if (precision == VIE_BF16X3 && nrhs >= 8)
-        return nrhs <= 32 ? VIE_VAR_TCGEN05_WS_BF16X3 : VIE_VAR_TCGEN05_PACKED_BF16X3;
+        return nrhs <= 16 ? VIE_VAR_TCGEN05_WS_BF16X3 : VIE_VAR_TCGEN05_WS2_BF16X3;
     return VIE_VAR_SIMT_R4;
 }
 
@@ -61,6 +62,7 @@ void far32(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrh
         case VIE_VAR_TCGEN05_PACKED_BF16X3: apply_far_umma_packed(op, x, ldx, F, ldf, nrhs, s); break;
         case VIE_VAR_SIMT_SHARED: apply_far_shared(op, x, ldx, F, ldf, nrhs, s); break;
         case VIE_VAR_TCGEN05_WS_BF16X3: apply_far_umma_ws(op, x, ldx, F, ldf, nrhs, s); break;
+        case VIE_VAR_TCGEN05_WS2_BF16X3: apply_far_umma_ws2(op, x, ldx, F, ldf, nrhs, s); break;
         default: fail(VIE_ERR_STATE, "unknown far-apply variant");
     }
 }
@@ -71,7 +73,7 @@ int tune_far(Op& op, int precision, int nrhs, cudaStream_t s, std::vector<int>& 
     if (nrhs < 1 || nrhs > 1024) fail(VIE_ERR_INVALID_ARG, "vie_tune: 1 to 1024 right-hand sides");
     cand.clear();
     ms.clear();
-    for (int v = VIE_VAR_SIMT_R1; v <= VIE_VAR_TCGEN05_WS_BF16X3; ++v) {
+    for (int v = VIE_VAR_SIMT_R1; v <= VIE_VAR_TCGEN05_WS2_BF16X3; ++v) {
         if (!admissible(precision, v)) continue;
         if (v >= VIE_VAR_SIMT_R2 && v <= VIE_VAR_SIMT_R8 && nrhs == 1) continue;  // same as R1
         if (v == VIE_VAR_SIMT_SHARED && nrhs > 1) continue;  // one column at a time
@@ -146,7 +148,7 @@ int tune_entry(Op& op, int precision, int nrhs, int force, vie_tune_result* res,
     }
     if (res) {
         res->variant = v;
-        res->n_candidates = (int)std::min<size_t>(8, cand.size());
+        res->n_candidates = (int)std::min<size_t>(16, cand.size());
         for (int i = 0; i < res->n_candidates; ++i) {
             res->candidates[i] = cand[i];
             res->ms[i] = ms[i];

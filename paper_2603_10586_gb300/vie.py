@@ -30,6 +30,7 @@ VAR_SIMT_R1, VAR_SIMT_R2, VAR_SIMT_R4, VAR_SIMT_R8, VAR_MMA_BF16X3, VAR_TCGEN05_
 VAR_TCGEN05_PACKED_BF16X3 = 7
 VAR_SIMT_SHARED = 8
 VAR_TCGEN05_WS_BF16X3 = 9
+VAR_TCGEN05_WS2_BF16X3 = 10
 NOALLOC_SCRATCH_ELEMS = 1 << 22   # VIE_NOALLOC_SCRATCH_ELEMS
 FUSE_PRECOND = 1
 DENSE = 2
@@ -77,8 +78,8 @@ class SolveOpts(C.Structure):
 
 
 class TuneResult(C.Structure):
-    _fields_ = [("variant", C.c_int), ("n_candidates", C.c_int), ("candidates", C.c_int * 8),
-                ("ms", C.c_double * 8)]
+    _fields_ = [("variant", C.c_int), ("n_candidates", C.c_int), ("candidates", C.c_int * 16),
+                ("ms", C.c_double * 16)]
 
 
 class SolveStats(C.Structure):

@@ -362,14 +362,14 @@ def test_autotune_variants_agree(ctx, tiny_dense):
     with pytest.raises(vie.VieError):
         op.tune(vie.C64, nrhs, force=vie.VAR_TCGEN05_BF16X3)
     for v in (vie.VAR_MMA_BF16X3, vie.VAR_TCGEN05_BF16X3, vie.VAR_TCGEN05_PACKED_BF16X3,
-              vie.VAR_TCGEN05_WS_BF16X3):
+              vie.VAR_TCGEN05_WS_BF16X3, vie.VAR_TCGEN05_WS2_BF16X3):
         op.tune(vie.BF16X3, nrhs, force=v)
         Y = th.zeros_like(X)
         op.apply(X.data_ptr(), Y.data_ptr(), nrhs, vie.BF16X3, vie.FUSE_PRECOND)
         th.cuda.synchronize()
         assert rel(Y.cpu().numpy(), out[vie.VAR_SIMT_R4]) < 5e-5
     res = op.tune(vie.BF16X3, 64)
-    assert res["variant"] in range(1, 10) and len(res["ms"]) == 8
+    assert res["variant"] in range(1, 11) and len(res["ms"]) == 9
     kh, pol = workloads.angle_sweep(2, 30.0)
     I, st, status = op.solve(kh, pol, tol=1e-6, precision=vie.BF16X3, autotune=1)
     assert status == vie.VIE_OK
@@ -423,9 +423,10 @@ def test_tcgen05_packed_and_warp_specialised_agree_with_unpacked(ctx):
     # MMA order (moved by bulk copies instead of split by the warps):
     # bit-identical; the warp-specialised one forms the same products with four
     # wide MMAs per K step (two accumulator halves added in the epilogue): equal
-    # to float32 rounding; fused and unfused, for column counts that fill one
-    # 64-column pass, a pass plus a ragged tail, and partial passes (the
-    # warp-specialised ring holds 5 stages up to 16 columns, 4 up to 48, 3 above)
+    # to float32 rounding, and so is the paired-tile one (two row tiles per B
+    # tile, 16 K values per stage); fused and unfused, for column counts that
+    # fill one 64-column pass, a pass plus a ragged tail, and partial passes
+    # (the rings hold 3 to 6 stages by column count)
     import torch as th
     g = workloads.square_array(8, 4)
     op = vie.Operator(ctx, g)
@@ -434,7 +435,8 @@ def test_tcgen05_packed_and_warp_specialised_agree_with_unpacked(ctx):
         X = th.from_numpy(workloads.random_complex(op.n, 11, cols=nrhs).T.astype(np.complex64).copy()).cuda()
         for fl in (vie.FUSE_PRECOND, 0):
             out = {}
-            for v in (vie.VAR_TCGEN05_BF16X3, vie.VAR_TCGEN05_PACKED_BF16X3, vie.VAR_TCGEN05_WS_BF16X3):
+            for v in (vie.VAR_TCGEN05_BF16X3, vie.VAR_TCGEN05_PACKED_BF16X3, vie.VAR_TCGEN05_WS_BF16X3,
+                      vie.VAR_TCGEN05_WS2_BF16X3):
                 op.tune(vie.BF16X3, nrhs, force=v)
                 Y = th.zeros_like(X)
                 op.apply(X.data_ptr(), Y.data_ptr(), nrhs, vie.BF16X3, fl)
@@ -442,6 +444,7 @@ def test_tcgen05_packed_and_warp_specialised_agree_with_unpacked(ctx):
                 out[v] = Y.cpu().numpy()
             assert np.array_equal(out[vie.VAR_TCGEN05_BF16X3], out[vie.VAR_TCGEN05_PACKED_BF16X3]), (nrhs, fl)
             assert rel(out[vie.VAR_TCGEN05_WS_BF16X3], out[vie.VAR_TCGEN05_PACKED_BF16X3]) < 5e-6, (nrhs, fl)
+            assert rel(out[vie.VAR_TCGEN05_WS2_BF16X3], out[vie.VAR_TCGEN05_PACKED_BF16X3]) < 5e-6, (nrhs, fl)
     op.close()
 
 
