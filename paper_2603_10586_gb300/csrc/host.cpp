@@ -265,6 +265,14 @@ static void pack_lpt(const std::vector<int4>& items, const std::vector<double>& 
     }
 }
 
+// Load of one tensor-core tile in K stages: every stage moves the same bytes
+// (A planes padded to 128 rows) and takes the same MMAs whatever the tile's
+// real row count, so the rows do not enter; a tile also pays its accumulator
+// drain, about two stages.  A pair of row tiles (the paired-tile kernels, 16
+// K values per stage) costs twice the stages of its first tile.
+static double tile_cost(int64_t K, int ks) { return (double)((K + ks - 1) / ks) + 2.0; }
+static double pair_cost(double single32) { return 2.0 * (single32 - 2.0) + 2.0; }
+
 // Z-order (Morton) code of every atom centre, from its x, y position in the
 // array's bounding box quantised to 16 bits per axis
 static std::vector<uint64_t> atom_zorder(const Op& op) {
@@ -489,7 +497,7 @@ void build_umma_lists(Op& op) {
         for (int64_t r0 = 0; r0 < total; r0 += kRows) {
             const int nr = (int)std::min<int64_t>(kRows, total - r0);
             it1.push_back(make_int4(rep, (int)(start + r0), nr, op.block_prob.empty() ? 0 : op.block_prob[rep]));
-            w1.push_back((double)(nr + 32) * op.blocks[rep].n);
+            w1.push_back(tile_cost(op.blocks[rep].n, 32));
             key1.push_back(zmin);
         }
     }
@@ -517,7 +525,7 @@ void build_umma_lists(Op& op) {
         for (int p0 = 0; p0 < op.np; p0 += kRows) {
             const int p1 = std::min(op.np, p0 + kRows);
             it2.push_back(make_int4(a, p0, p1, op.atom_prob.empty() ? 0 : op.atom_prob[a]));
-            w2.push_back((double)(p1 - p0 + 32) * (K + 1.0));
+            w2.push_back(tile_cost((int64_t)K, 32));
             key2.push_back(zc[a]);
         }
     }
@@ -585,7 +593,7 @@ void build_umma_lists(Op& op) {
             const bool two = i + 1 < items.size() && same_b(items[i], items[i + 1]);
             pairs.push_back(make_int2((int)i, two ? (int)i + 1 : -1));
             first.push_back(items[i]);
-            pw.push_back(w[i] + (two ? w[i + 1] : 0.0));
+            pw.push_back(pair_cost(w[i]));
             pkey.push_back(key[i]);
             if (two) ++i;
         }

@@ -130,6 +130,7 @@ template <bool kFirst>
 __global__ void __launch_bounds__(kT) k_mdot_df(KrylovArgs a, const float2* __restrict__ Y) {
     const int i = blockIdx.z, cg = blockIdx.y;
     if (!a.cycling[i]) return;
+    if (!kFirst && a.reorth && !a.reorth[i]) return;
     const int j = a.ctr[KR_J];
     const int ncols = j + 1;
     if (cg * kCG >= ncols) return;
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(kT) k_mdot_df(KrylovArgs a, const float2* __re
     float4 acc[kCG];
 #pragma unroll
     for (int c = 0; c < kCG; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    double wn = 0.0;  // pass 1: ||w||^2 partials (blocks of column group 0)
     for (int64_t r = r0 + threadIdx.x; r < r1; r += 2 * kT) {
         const bool second = r + kT < r1;
         float4 wv, wv2 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -156,6 +158,7 @@ __global__ void __launch_bounds__(kT) k_mdot_df(KrylovArgs a, const float2* __re
             if (cg == 0) {
                 w[r] = wv;
                 if (second) w[r + kT] = wv2;
+                wn += (double)wv.x * wv.x + (double)wv.y * wv.y + (double)wv2.x * wv2.x + (double)wv2.y * wv2.y;
             }
         } else {
             wv = w[r];
@@ -185,6 +188,12 @@ __global__ void __launch_bounds__(kT) k_mdot_df(KrylovArgs a, const float2* __re
         }
         if (lane == 0) sh[wid][c] = make_double2(re, im);
     }
+    // pass 1: the squared norm of w goes to partial slot j + 1 (<= m < hs), beside the dots
+    __shared__ double shn[kT / 32];
+    if (kFirst && cg == 0) {
+        for (int o = 16; o > 0; o >>= 1) wn += __shfl_down_sync(0xffffffffu, wn, o);
+        if (lane == 0) shn[wid] = wn;
+    }
     __syncthreads();
     if (threadIdx.x < kCG) {
         const int col = cg * kCG + threadIdx.x;
@@ -194,6 +203,11 @@ __global__ void __launch_bounds__(kT) k_mdot_df(KrylovArgs a, const float2* __re
             a.part[((int64_t)i * a.hs + col) * gridDim.x + blockIdx.x] = s;
         }
     }
+    if (kFirst && cg == 0 && threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w2 = 0; w2 < kT / 32; ++w2) t += shn[w2];
+        a.part[((int64_t)i * a.hs + ncols) * gridDim.x + blockIdx.x] = make_double2(t, 0.0);
+    }
 }
 
 // w -= V h (columns 0..j) in double-float; pass 2 also forms the squared-norm
@@ -202,6 +216,7 @@ template <bool kSecond>
 __global__ void __launch_bounds__(kT) k_maxpy_df(KrylovArgs a) {
     const int i = blockIdx.y;
     if (!a.cycling[i]) return;
+    if (kSecond && a.reorth && !a.reorth[i]) return;  // pass 1's norm partials stand
     const int j = a.ctr[KR_J];
     __shared__ float4 hs[kMaxRestart + 1];
     __shared__ double sh[kT / 32];
@@ -217,15 +232,12 @@ __global__ void __launch_bounds__(kT) k_maxpy_df(KrylovArgs a) {
         for (int c = 0; c <= j; ++c) df_cmsub(acc, V[(int64_t)c * n + r], hs[c]);
         acc = df_normed(acc);
         w[r] = acc;
-        if (kSecond) {
-            const double2 d = df_to(acc);
-            nacc += d.x * d.x + d.y * d.y;
-        }
+        const double2 d = df_to(acc);
+        nacc += d.x * d.x + d.y * d.y;
     }
-    if (kSecond) {
-        const double s = block_sum(nacc, sh);
-        if (threadIdx.x == 0) a.npart[(int64_t)i * a.nblk_max + blockIdx.x] = s;
-    }
+    // the norm of w after this pass: the step's last pass writes the partials k_nsq sums
+    const double s = block_sum(nacc, sh);
+    if (threadIdx.x == 0) a.npart[(int64_t)i * a.nblk_max + blockIdx.x] = s;
 }
 
 // X[:, cols[i]] += V y; with D, the correction V y of slot i is also written
@@ -347,13 +359,20 @@ __global__ void __launch_bounds__(kT) k_mdot(KrylovArgs a, const TW* __restrict_
 }
 
 // h = sum of the chunk partials (one warp per basis column); the Hessenberg
-// column accumulates both passes
+// column accumulates both passes.
+// Double-float basis: pass 2 runs only where pass 1 cancelled much of w
+// (selective reorthogonalisation, the criterion of Daniel, Gragg, Kaufman and
+// Stewart, 1976): ||w - V h||^2 = ||w||^2 - ||h||^2 against ||w||^2 / 2.
 template <bool kFirst>
 __global__ void __launch_bounds__(kT) k_reduce(KrylovArgs a, int nchunk) {
     const int i = blockIdx.x;
     if (!a.cycling[i]) return;
+    const bool sel = a.df && a.reorth;
+    if (!kFirst && sel && !a.reorth[i]) return;
     const int j = a.ctr[KR_J];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ double hn[kT / 32];
+    double hsq = 0.0;
     for (int col = wid; col <= j; col += kT / 32) {
         const double2* p = a.part + ((int64_t)i * a.hs + col) * nchunk;
         double re = 0.0, im = 0.0;
@@ -371,6 +390,18 @@ __global__ void __launch_bounds__(kT) k_reduce(KrylovArgs a, int nchunk) {
             double2* Hc = a.H + ((int64_t)i * a.m + j) * (a.m + 1);
             if (kFirst) Hc[col] = s;
             else Hc[col] += s;
+            hsq += re * re + im * im;
+        }
+    }
+    if (kFirst && sel) {
+        if (lane == 0) hn[wid] = hsq;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double h2 = 0.0, w2 = 0.0;
+            for (int x = 0; x < kT / 32; ++x) h2 += hn[x];
+            const double2* p = a.part + ((int64_t)i * a.hs + j + 1) * nchunk;
+            for (int x = 0; x < nchunk; ++x) w2 += p[x].x;
+            a.reorth[i] = (w2 - h2 < 0.5 * w2) || !(w2 > 0.0) || !isfinite(w2 - h2) ? 1 : 0;
         }
     }
 }
@@ -567,7 +598,8 @@ __global__ void __launch_bounds__(kT) k_scatter_norm(KrylovArgs a, const double2
 // precision, which never ends a column's solve (only a float64-accurate one
 // may); 0: a float64-accurate refinement residual; 3: a float64-accurate
 // residual updated by the inner-precision image of the cycle's correction
-// (its error is bounded by the host to 1% of the tolerance)
+// (the host keeps its accumulated error bound below half the tolerance, and it
+// ends a column only when it plus that bound is within the tolerance)
 __global__ void k_cycle_end(KrylovArgs a, int k, int nblk, int init) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0 && init == 0) a.ctr[KR_REFIN] += 1;
@@ -584,8 +616,11 @@ __global__ void k_cycle_end(KrylovArgs a, int k, int nblk, int init) {
     } else {
         const double r = a.beta0[c] > 0.0 ? bn / a.beta0[c] : 0.0;
         a.res[c] = r;
-        // init = 3: an updated residual, trusted to within 1% of the tolerance
-        const bool conv = (init == 0 && r <= a.tol) || (init == 3 && r <= 0.99 * a.tol);
+        // init = 3: an updated residual; it converges when it plus its error bound
+        // (the earlier cycles' and this cycle's eps_low |P^-1 Zs d|) is within the tolerance
+        const double ub = init == 3 ? a.ubound[c] + (a.beta0[c] > 0.0 ? a.eps_low * a.enorm[c] / a.beta0[c] : 0.0)
+                                    : 0.0;
+        const bool conv = (init == 0 && r <= a.tol) || (init == 3 && r + ub <= a.tol);
         a.done[c] = (conv || a.iters[c] >= a.maxit || bn == 0.0) ? 1 : 0;
     }
 }
@@ -663,7 +698,7 @@ void kr_project(const KrylovArgs& a, const void* Y, bool c64, int pass, int k, i
         else k_maxpy<false><<<dim3(nblk, k), kT, 0, s>>>(a);
         VIE_CHECK_LAUNCH();
     } else {
-        if (a.df) k_mdot_df<false><<<gd, kT, 0, s>>>(a, nullptr);
+        if (a.df) k_mdot_df<false><<<gd, kT, 0, s>>>(a, nullptr);  // returns at once where pass 2 is not needed
         else k_mdot<double2, false><<<gd, kT, 0, s>>>(a, nullptr);
         VIE_CHECK_LAUNCH();
         k_reduce<false><<<k, kT, 0, s>>>(a, nchunk);

@@ -36,6 +36,9 @@ struct KrylovArgs {
     int nblk_max;     // row blocks the norm partials are laid out for
     double tol;
     int maxit;
+    double eps_low;   // error bound of one inner-precision product (updated residuals)
+    double* ubound;   // [nrhs] accumulated error bound of a column's updated residual (host-written)
+    double* enorm;    // [nrhs] |P^-1 Zs d| of the cycle's correction (updated residuals)
     double2* V;       // per column: col_len x (m+1) basis (float64, or double-float in the same bytes)
     double2* H;       // [slot][m][m+1] Hessenberg columns (rotated in place)
     double2* g;       // [slot][m+1] rotated right-hand side of the least-squares problem
@@ -48,6 +51,7 @@ struct KrylovArgs {
     double* nsq;      // [slot] their total
     double* inv;      // [slot] scale the next gather applies to its basis column
     int* cycling;     // [slot] still iterating in this cycle
+    int* reorth;      // [slot] double-float basis: the step needs Gram-Schmidt pass 2 (null: always)
     int* jdone;       // [slot] Arnoldi steps done in this cycle
     int* cols;        // [slot] right-hand-side column of the slot
     int* iters;       // [nrhs] Arnoldi steps per column (all cycles)
@@ -95,7 +99,8 @@ void kr_sub_cols(const KrylovArgs& a, const double2* b, const double2* T, double
 void kr_scatter_norm(const KrylovArgs& a, const double2* Wl, double2* W, int k, int nblk, cudaStream_t s);
 // beta, res and done of the slots' columns from the norm partials; init = 1 also
 // sets beta0; init = 2 marks a residual of the inner precision (it ends no
-// solve); init = 3 an updated float64 residual (it ends a solve below 0.99 tol)
+// solve); init = 3 an updated float64 residual (it ends a solve when it plus its
+// error bound, ubound + eps_low enorm / beta0, is within the tolerance)
 void kr_cycle_end(const KrylovArgs& a, int k, int nblk, int init, cudaStream_t s);
 // norms of the k columns of A (n x k, column i holding the rows of column
 // cols ? cols[i] : i) into d_out[cols ? cols[i] : i]; d_part holds k * nblk doubles

@@ -23,6 +23,7 @@
 // sit in a conditional while-node driven by the Givens kernel.  The host only
 // reads the per-column convergence flags between cycles.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -47,10 +48,11 @@ struct Gmres {
     int64_t n;
     int m, nrhs, n_sm;
     bool c64;  // inner applies on float32 vectors
-    DevBuf V, H, g, cs, sn, h, y, part, npart, nsq, rpart, inv, cycling, jdone, cols, iters, done, beta0, beta, res, rnorm,
+    DevBuf V, H, g, cs, sn, h, y, part, npart, nsq, rpart, inv, cycling, reorth, jdone, cols, iters, done, beta0, beta, res,
+        rnorm,
         bnorm, hist, ctr, col_lo, col_len, col_voff, colr, colr_cycle, col_prob;
     std::vector<int2> h_colr;
-    DevBuf Xg, Yg, Xl, T, Rl, Wl, W, Rf, enorm;
+    DevBuf Xg, Yg, Xl, T, Rl, Wl, W, Rf, enorm, ubound;
     KrylovArgs a{};
     std::map<int, CycleGraph> graphs;
     int* h_pinned = nullptr;  // [KR_NCTR + nrhs] host-visible copy of counters and done flags
@@ -96,6 +98,7 @@ struct Gmres {
         nsq.alloc(S * sizeof(double));
         inv.alloc(S * sizeof(double));
         cycling.alloc(S * sizeof(int));
+        reorth.alloc(S * sizeof(int));
         jdone.alloc(S * sizeof(int));
         cols.alloc(S * sizeof(int));
         iters.alloc(nrhs * sizeof(int));
@@ -118,6 +121,7 @@ struct Gmres {
         if (c64) {
             Rf.alloc(vec);  // b - Zs x per column, the base of residual updates
             enorm.alloc(nrhs * sizeof(double));
+            ubound.alloc(nrhs * sizeof(double));
         }
         op_reserve(op, nrhs, o.precision, s);
         VIE_CUDA(cudaMemsetAsync(ctr.p, 0, KR_NCTR * sizeof(int), s));
@@ -136,6 +140,11 @@ struct Gmres {
         a.nblk_max = nblk_max;
         a.tol = o.tol > 0 ? o.tol : 1e-6;
         a.maxit = o.max_iters > 0 ? o.max_iters : 2000;
+        // relative error of one inner-precision product, with margin (measured: BF16x3
+        // <= 5e-5, float32 <= 1e-6): the weight of an updated residual's error bound
+        a.eps_low = o.precision == VIE_BF16X3 ? 1e-4 : 1e-5;
+        a.ubound = c64 ? ubound.as<double>() : nullptr;
+        a.enorm = c64 ? enorm.as<double>() : nullptr;
         a.V = V.as<double2>();
         a.H = H.as<double2>();
         a.g = g.as<double2>();
@@ -148,6 +157,7 @@ struct Gmres {
         a.nsq = nsq.as<double>();
         a.inv = inv.as<double>();
         a.cycling = cycling.as<int>();
+        a.reorth = reorth.as<int>();
         a.jdone = jdone.as<int>();
         a.cols = cols.as<int>();
         a.iters = iters.as<int>();
@@ -376,9 +386,7 @@ struct Gmres {
         VIE_CUDA(cudaStreamSynchronize(s));
         bound.assign(nrhs, 0.0);
         have_base = false;
-        // relative error of one inner-precision product, with margin (measured: BF16x3
-        // <= 5e-5, float32 <= 1e-6)
-        eps_low = o.precision == VIE_BF16X3 ? 1e-4 : 1e-5;
+        eps_low = a.eps_low;
         std::vector<int> live;
         while (true) {
             live.clear();
@@ -404,11 +412,16 @@ struct Gmres {
             }
             const double near = 100.0 * a.tol;
             const bool cheap = c64 && worst > near && it0 + m < a.maxit;
-            // near the tolerance: one float64-accurate residual, then updates of it
-            // while their accumulated error bound stays below 1% of the tolerance
-            const int mode = cheap ? kPostCheap
-                                   : (c64 && have_base && bworst + eps_low * worst <= 0.01 * a.tol) ? kPostUpdate
-                                                                                                  : kPostAccurate;
+            // from a float64-accurate residual on, updates of it while their
+            // accumulated error bound (eps_low |P^-1 Zs d| per cycle, |P^-1 Zs d| ~
+            // the residual the cycle removes) stays below half the tolerance; an
+            // updated residual ends a column only when it plus its bound is within
+            // the tolerance.  Before that base exists: the inner-precision residual
+            // while any column is far from the tolerance, else a float64 one.
+            const bool upd = c64 && have_base && bworst + eps_low * worst <= 0.5 * a.tol;
+            const int mode = upd ? kPostUpdate : cheap ? kPostCheap : kPostAccurate;
+            if (mode == kPostUpdate)
+                VIE_CUDA(cudaMemcpyAsync(ubound.p, bound.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, s));
             if (o.launch == 1) {
                 launch_pre(k, s);
                 do {
@@ -424,6 +437,19 @@ struct Gmres {
                 read_state();
                 VIE_COUNT_LAUNCH(cg.pre + cg.post + cg.body * (long long)(h_pinned[KR_IT] - it0));
             }
+            if (op.ctx->verbose) {
+                int n1 = 0, n2 = 0, n3 = 0;
+                for (int c : live) {
+                    n1 += h_res[c] <= near;
+                    n2 += h_res[c] <= 10.0 * a.tol;
+                    n3 += h_res[c] <= 2.0 * a.tol;
+                }
+                fprintf(stderr,
+                        "[vie] cycle: %d columns, steps %d..%d, restart residual %s (worst %.2e, bound %.2e; columns "
+                        "<= 100/10/2 tol: %d/%d/%d)\n",
+                        k, it0, h_pinned[KR_IT], mode == kPostCheap ? "inner" : mode == kPostUpdate ? "updated" : "float64",
+                        worst, bworst, n1, n2, n3);
+            }
             if (mode == kPostUpdate) {
                 // error bound of the update: eps_low |P^-1 Zs d| relative to ||P^-1 b||
                 std::vector<double> en(nrhs);
@@ -435,15 +461,20 @@ struct Gmres {
                 for (int c : live) bound[c] = 0.0;
             } else {
                 have_base = false;
-                // a column that came near the tolerance gets its float64-accurate
-                // residual now, from the same iterate, so that no Arnoldi step is
-                // spent on a solution that may already be converged
-                bool close = false;
-                for (int c : live) close |= h_res[c] <= near;
+                // when a quarter or more of the live columns came near the tolerance
+                // (where the inner-precision residual no longer tells), they get a
+                // float64-accurate residual now, from the same iterate, so that the
+                // converged ones stop before the next cycle; a few near columns do not
+                // repay the float64 product (it costs about a cycle's applies) and go
+                // on with the rest
+                int nclose = 0;
+                for (int c : live) nclose += h_res[c] <= near ? 1 : 0;
+                const bool close = 4 * nclose >= (int)live.size();
                 if (close) {
                     restore_colr(s);
                     launch_residual(k, b, X, s, false);
                     read_state();
+                    if (op.ctx->verbose) fprintf(stderr, "[vie] cycle: float64 residual of the same iterate\n");
                     have_base = true;
                     for (int c : live) bound[c] = 0.0;
                 }
