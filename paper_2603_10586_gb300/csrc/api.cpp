@@ -46,6 +46,18 @@ void op_apply_plain32(Op& op, const float2* x, float2* y, int nrhs, int precisio
     self_gemm<float2, float2>(op, op.d_zself32.as<float2>(), x, n, F, n, y, n, nrhs, 0, s);
 }
 
+// E x = P^-1 Zs x - x = Z_D^-1 (far part) x in the inner precision: the fused
+// apply without its identity term (the Arnoldi steps of the mixed-precision
+// GMRES build the Krylov space of E, the same as that of I + E)
+void op_apply_shift32(Op& op, const float2* x, float2* y, int nrhs, int precision, cudaStream_t s) {
+    if (op.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "float32 applies need VIE_C64 factors");
+    const int64_t n = op.n();
+    ensure_F(op, (size_t)n * nrhs * sizeof(float2));
+    float2* F = op.d_F.as<float2>();
+    far32(op, x, n, F, n, nrhs, precision, s);
+    self_gemm<float2, float2>(op, op.d_inv32.as<float2>(), F, n, nullptr, 0, y, n, nrhs, 2, s);  // y = Z_D^-1 F
+}
+
 void op_apply_fused_bf16x3(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s) {
     if (op.fprec != VIE_C64) fail(VIE_ERR_INVALID_ARG, "VIE_BF16X3 applies need VIE_C64 factors");
     const int64_t n = op.n();

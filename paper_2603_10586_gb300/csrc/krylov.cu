@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kT) k_reduce(KrylovArgs a, int nchunk) {
             const double2 s = make_double2(re, im);
             a.h[(int64_t)i * a.hs + col] = s;
             double2* Hc = a.H + ((int64_t)i * a.m + j) * (a.m + 1);
-            if (kFirst) Hc[col] = s;
+            if (kFirst) Hc[col] = (a.shift && col == j) ? make_double2(s.x + 1.0, s.y) : s;
             else Hc[col] += s;
             hsq += re * re + im * im;
         }

@@ -33,6 +33,7 @@ struct KrylovArgs {
     int m;            // restart length (<= kMaxRestart)
     int hs;           // per-slot stride of h, y and the projection partials (>= m + 1)
     int df;           // 1: the basis is double-float (float4 per value), 0: float64
+    int shift;        // 1: the step applies E = P^-1 Zs - I; the Hessenberg column adds the identity
     int nblk_max;     // row blocks the norm partials are laid out for
     double tol;
     int maxit;
@@ -147,6 +148,8 @@ void op_apply_plain32(Op& op, const float2* x, float2* y, int nrhs, int precisio
 void op_apply_fused32(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s);
 // y = P^-1 Zs x with the far part on the tensor cores (BF16x3), float32 vectors
 void op_apply_fused_bf16x3(Op& op, const float2* x, float2* y, int nrhs, cudaStream_t s);
+// P^-1 Zs x - x (= Z_D^-1 times the far part of Zs x) in the inner precision (VIE_C64 or VIE_BF16X3)
+void op_apply_shift32(Op& op, const float2* x, float2* y, int nrhs, int precision, cudaStream_t s);
 // y = Zs x with float64 vectors; factors in their stored precision (float64 accumulation)
 void op_apply64(Op& op, const double2* x, double2* y, int nrhs, cudaStream_t s);
 // y = P^-1 Zs x in float64 (needs C128 factors for an all-float64 solve)

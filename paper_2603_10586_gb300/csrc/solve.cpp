@@ -144,6 +144,13 @@ struct Gmres {
         // <= 5e-5, float32 <= 1e-6): the weight of an updated residual's error bound
         a.eps_low = o.precision == VIE_BF16X3 ? 1e-4 : 1e-5;
         a.ubound = c64 ? ubound.as<double>() : nullptr;
+        // mixed precision: the Arnoldi steps apply E = P^-1 Zs - I (the block-Jacobi
+        // preconditioned operator is I plus the preconditioned far part), whose
+        // Krylov space is the same; the new vector then carries no copy of the
+        // previous one for Gram-Schmidt to cancel, the inner-precision error
+        // scales with |E v| instead of |v|, and the Hessenberg of I + E is that
+        // of E plus the identity
+        a.shift = c64 ? 1 : 0;
         a.enorm = c64 ? enorm.as<double>() : nullptr;
         a.V = V.as<double2>();
         a.H = H.as<double2>();
@@ -183,10 +190,10 @@ struct Gmres {
         if (!c64) {
             if (o.precond) op_apply_fused64(op, Xg.as<double2>(), Yg.as<double2>(), k, st);
             else op_apply64(op, Xg.as<double2>(), Yg.as<double2>(), k, st);
-        } else if (o.precision == VIE_BF16X3) {
-            op_apply_fused_bf16x3(op, Xg.as<float2>(), Yg.as<float2>(), k, st);
         } else {
-            op_apply_fused32(op, Xg.as<float2>(), Yg.as<float2>(), k, st);
+            // E = P^-1 Zs - I; the Hessenberg adds the identity back (a.shift)
+            op_apply_shift32(op, Xg.as<float2>(), Yg.as<float2>(), k,
+                             o.precision == VIE_BF16X3 ? VIE_BF16X3 : VIE_C64, st);
         }
     }
 
