@@ -369,14 +369,28 @@ __global__ void __launch_bounds__(256, 2) p2m_kernel(const FarBlockDev* __restri
                     const FarBlockDev B = blocks[en.x];
                     const TF* Q = factors + B.q_off + (int64_t)en.y * np + row;
                     const TX* tb = t + B.tvec_off + (int64_t)c0 * ldt;
-                    for (int k = kg; k < B.rank; k += 4) {
-                        Pair<TF> q = ldpair_stream(Q + (int64_t)k * B.m);
+                    // two rank steps (k, k + 4) per iteration: both steps' loads are in
+                    // flight before the products; each accumulator still adds k, k + 4,
+                    // k + 8, ... in order
+                    for (int k = kg; k < B.rank; k += 8) {
+                        const bool two = k + 4 < B.rank;
+                        const Pair<TF> q0 = ldpair_stream(Q + (int64_t)k * B.m);
+                        const Pair<TF> q1 = ldpair_stream(Q + (int64_t)(two ? k + 4 : k) * B.m);
+                        TX tv0[NR], tv1[NR];
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            tv0[r] = tb[k + (int64_t)(r < nr ? r : 0) * ldt];
+                            tv1[r] = tb[(two ? k + 4 : k) + (int64_t)(r < nr ? r : 0) * ldt];
+                        }
 #pragma unroll
                         for (int r = 0; r < NR; ++r) {
                             if (r < nr) {
-                                const TX tv = tb[k + (int64_t)r * ldt];
-                                mac(a0[r], q.a, tv);
-                                mac(a1[r], q.b, tv);
+                                mac(a0[r], q0.a, tv0[r]);
+                                mac(a1[r], q0.b, tv0[r]);
+                                if (two) {
+                                    mac(a0[r], q1.a, tv1[r]);
+                                    mac(a1[r], q1.b, tv1[r]);
+                                }
                             }
                         }
                     }
@@ -631,15 +645,16 @@ void apply_far(Op& op, const TX* x, int64_t ldx, TX* F, int64_t ldf, int nrhs, c
     const TF* fac = op.fac<TF>();
     const int nc = op.n_cta;
     if (nrhs > 1) {
+        const int ncm = op.n_cta_m;
         if (op.n_p1_items > 0) {
-            p1m_kernel<TF, TX, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
-                                                     op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, x, ldx,
-                                                     op.np, op.d_t.as<TX>(), op.t_total, nrhs, op.colr);
+            p1m_kernel<TF, TX, 4><<<ncm, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
+                                                      op.d_p1m_items.as<int4>(), op.d_p1m_cta.as<int>(), fac, x, ldx,
+                                                      op.np, op.d_t.as<TX>(), op.t_total, nrhs, op.colr);
             VIE_CHECK_LAUNCH();
         }
-        p2m_kernel<TF, TX, TX, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(),
-                                                 op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(),
-                                                 fac, op.d_t.as<TX>(), op.t_total, op.np, F, ldf, nrhs, op.colr);
+        p2m_kernel<TF, TX, TX, 4><<<ncm, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_p2m_items.as<int4>(),
+                                                  op.d_p2m_cta.as<int>(), op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(),
+                                                  fac, op.d_t.as<TX>(), op.t_total, op.np, F, ldf, nrhs, op.colr);
         VIE_CHECK_LAUNCH();
         return;
     }
@@ -668,14 +683,15 @@ void apply_far_simt32(Op& op, const float2* x, int64_t ldx, float2* F, int64_t l
     float2* t = op.d_t.as<float2>();
     const int nc = op.n_cta;
     const FarBlockDev* bl = op.d_blocks.as<FarBlockDev>();
-#define VIE_P1M(NR)                                                                                              \
-    p1m_kernel<float2, float2, NR><<<nc, 256, 0, s>>>(bl, op.d_block_atoms.as<int>(), op.d_p1_items.as<int4>(), \
-                                                      op.d_p1_cta.as<int>(), fac, x, ldx, op.np, t, op.t_total, nrhs, \
-                                                      op.colr)
-#define VIE_P2M(NR)                                                                                               \
-    p2m_kernel<float2, float2, float2, NR><<<nc, 256, 0, s>>>(bl, op.d_p2_items.as<int4>(), op.d_p2_cta.as<int>(), \
-                                                              op.d_p2_csr.as<int>(), op.d_p2_ent.as<int2>(), fac, t,  \
-                                                              op.t_total, op.np, F, ldf, nrhs, op.colr)
+#define VIE_P1M(NR)                                                                                                   \
+    p1m_kernel<float2, float2, NR><<<op.n_cta_m, 256, 0, s>>>(bl, op.d_block_atoms.as<int>(), op.d_p1m_items.as<int4>(), \
+                                                              op.d_p1m_cta.as<int>(), fac, x, ldx, op.np, t, op.t_total, \
+                                                              nrhs, op.colr)
+#define VIE_P2M(NR)                                                                                                  \
+    p2m_kernel<float2, float2, float2, NR><<<op.n_cta_m, 256, 0, s>>>(bl, op.d_p2m_items.as<int4>(),                \
+                                                                      op.d_p2m_cta.as<int>(), op.d_p2_csr.as<int>(), \
+                                                                      op.d_p2_ent.as<int2>(), fac, t, op.t_total,   \
+                                                                      op.np, F, ldf, nrhs, op.colr)
     if (op.n_p1_items > 0) {
         switch (nr) {
             case 1: p1_kernel<float2, float2, 4><<<nc, 256, 0, s>>>(bl, op.d_block_atoms.as<int>(),
@@ -732,14 +748,16 @@ void apply_far_df(Op& op, const double2* x, int64_t ldx, double2* F, int64_t ldf
     k_split_hl<<<op.ctx->n_sm * 8, 256, 0, s>>>(x, ldx, n, nrhs, xs);
     VIE_CHECK_LAUNCH();
     if (nrhs > 1) {
+        const int ncm = op.n_cta_m;
         if (op.n_p1_items > 0) {
-            p1m_kernel<float2, float4, 4><<<nc, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(), op.d_block_atoms.as<int>(),
-                                                             op.d_p1_items.as<int4>(), op.d_p1_cta.as<int>(), fac, xs,
-                                                             n, op.np, t, op.t_total, nrhs, op.colr);
+            p1m_kernel<float2, float4, 4><<<ncm, 256, 0, s>>>(op.d_blocks.as<FarBlockDev>(),
+                                                              op.d_block_atoms.as<int>(), op.d_p1m_items.as<int4>(),
+                                                              op.d_p1m_cta.as<int>(), fac, xs, n, op.np, t,
+                                                              op.t_total, nrhs, op.colr);
             VIE_CHECK_LAUNCH();
         }
-        p2m_kernel<float2, float4, double2, 4><<<nc, 256, 0, s>>>(
-            op.d_blocks.as<FarBlockDev>(), op.d_p2_items.as<int4>(), op.d_p2_cta.as<int>(), op.d_p2_csr.as<int>(),
+        p2m_kernel<float2, float4, double2, 4><<<ncm, 256, 0, s>>>(
+            op.d_blocks.as<FarBlockDev>(), op.d_p2m_items.as<int4>(), op.d_p2m_cta.as<int>(), op.d_p2_csr.as<int>(),
             op.d_p2_ent.as<int2>(), fac, t, op.t_total, op.np, F, ldf, nrhs, op.colr);
         VIE_CHECK_LAUNCH();
         return;

@@ -199,6 +199,9 @@ struct Op {
     // packed variant: each item's A operand pre-split into bf16 planes in the
     // shared-memory stage layout (32 KiB per 32-wide K stage), copied by bulk TMA
     DevBuf d_u1_pk, d_u2_pk, d_u1_pack, d_u2_pack;  // stage offsets per item, planes
+    // the SIMT lists mapped to two CTAs per SM (the multi-RHS SIMT kernels)
+    int n_cta_m = 0;
+    DevBuf d_p1m_items, d_p1m_cta, d_p2m_items, d_p2m_cta;
     DevBuf d_w1_items, d_w1_cta, d_w1_pk, d_w2_items, d_w2_cta, d_w2_pk;  // one CTA per SM (warp-specialised)
     // pairs of items that share their B operand (two M tiles per B tile), one CTA per SM: first and
     // second item (rows 0 when absent) and their packed stage offsets

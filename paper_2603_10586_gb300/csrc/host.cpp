@@ -338,6 +338,17 @@ void build_apply_lists(Op& op) {
     op.n_p1_items = (int)p1.size();
     upload(op.d_p1_items, p1.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : p1);
     upload(op.d_p1_cta, c1);
+    // the same items on two CTAs per SM: the multi-RHS kernels hold two CTAs
+    // per SM (their register use), and a third list entry per SM would run as
+    // a second wave
+    op.n_cta_m = op.ctx->n_sm * 2;
+    {
+        std::vector<int4> q;
+        std::vector<int> c;
+        pack_lpt(it1, w1, op.n_cta_m, q, c);
+        upload(op.d_p1m_items, q.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : q);
+        upload(op.d_p1m_cta, c);
+    }
 
     // phase 2: per atom the (block, slot) entries, then row chunks
     std::vector<std::vector<int2>> ent(op.N);
@@ -371,6 +382,13 @@ void build_apply_lists(Op& op) {
     op.n_p2_items = (int)p2.size();
     upload(op.d_p2_items, p2);
     upload(op.d_p2_cta, c2);
+    {
+        std::vector<int4> q;
+        std::vector<int> c;
+        pack_lpt(it2, w2, op.n_cta_m, q, c);
+        upload(op.d_p2m_items, q);
+        upload(op.d_p2m_cta, c);
+    }
 
     // tensor-core path: 64-row output tiles (rows of R_b, rows of an atom)
     op.n_cta_tc = op.ctx->n_sm * 4;
