@@ -771,6 +771,19 @@ def main():
     else:
         roof["stored_factor_bytes"] = 8 * info["stored_entries"]
         roof["stored_frac"] = 8 * info["stored_entries"] / (apply_ms * 1e-3) / 1e9 / hbm
+        if info["stored_entries"] < info["factor_entries"]:
+            # translated copies share factors and the single-RHS kernels read a shared
+            # factor once per group of up to four copies: the per-block bytes are not
+            # what the kernel moves, so the headline fraction is taken on the stored
+            # factor bytes (a lower bound of what it moves) and the per-block one kept aside
+            stored = 8.0 * (info["stored_entries"] + info["n_types"] * info["np"] ** 2) + 16.0 * info["n"] * nrhs
+            roof["per_block_achieved"], roof["per_block_frac"] = achieved, achieved / hbm
+            roof["achieved"] = stored / (apply_ms * 1e-3) / 1e9
+            roof["frac"] = roof["achieved"] / hbm
+            roof["algorithmic_bytes"] = stored
+            roof["note"] = ("bytes of the stored factors once (translated copies share storage), the distinct "
+                            "self/inverse blocks once, x read and y written once; per_block_*: every block's "
+                            "factors once, which the shared-factor kernels do not read")
 
     # accuracy of the result: the all-float64 single-RHS GPU solve (c128 factors)
     accuracy = {"residual_preconditioned": stats["residual"], "true_residual": stats["true_residual"],

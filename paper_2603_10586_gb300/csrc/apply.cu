@@ -312,14 +312,17 @@ __global__ void __launch_bounds__(256, 2) p1m_kernel(const FarBlockDev* __restri
                     Pair<TF> ra = ldpair_stream(row0 + c);
                     Pair<TF> rb = ldpair_stream(row1 + c);
                     const TX* xb = x + (int64_t)S[slot] * np + off + (int64_t)c0 * ldx;
+                    // all right-hand sides' x pairs of this step in flight before the products
+                    Pair<TX> xv[NR];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) xv[r] = ldpair(xb + (int64_t)(r < nr ? r : 0) * ldx);
 #pragma unroll
                     for (int r = 0; r < NR; ++r) {
                         if (r < nr) {
-                            Pair<TX> xv = ldpair(xb + (int64_t)r * ldx);
-                            mac_conj(a0[r], ra.a, xv.a);
-                            mac_conj(a0[r], ra.b, xv.b);
-                            mac_conj(a1[r], rb.a, xv.a);
-                            mac_conj(a1[r], rb.b, xv.b);
+                            mac_conj(a0[r], ra.a, xv[r].a);
+                            mac_conj(a0[r], ra.b, xv[r].b);
+                            mac_conj(a1[r], rb.a, xv[r].a);
+                            mac_conj(a1[r], rb.b, xv[r].b);
                         }
                     }
                     off += 64;
@@ -468,14 +471,18 @@ __global__ void __launch_bounds__(256, 3) p1c_kernel(const FarBlockDev* __restri
             for (; c < B.n; c += 64) {
                 const Pair<float2> ra = ldpair_stream(row0 + c);
                 const Pair<float2> rb = ldpair_stream(row1 + c);
+                // every member's x pair in flight before the products (S[r] of a
+                // missing member repeats the last one, so the loads stay in bounds)
+                Pair<float2> xv[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) xv[r] = ldpair(x + (int64_t)S[r][slot] * np + off);
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     if (r < nm) {
-                        const Pair<float2> xv = ldpair(x + (int64_t)S[r][slot] * np + off);
-                        mac_conj(a0[r], ra.a, xv.a);
-                        mac_conj(a0[r], ra.b, xv.b);
-                        mac_conj(a1[r], rb.a, xv.a);
-                        mac_conj(a1[r], rb.b, xv.b);
+                        mac_conj(a0[r], ra.a, xv[r].a);
+                        mac_conj(a0[r], ra.b, xv[r].b);
+                        mac_conj(a1[r], rb.a, xv[r].a);
+                        mac_conj(a1[r], rb.b, xv[r].b);
                     }
                 }
                 off += 64;
@@ -534,14 +541,19 @@ __global__ void __launch_bounds__(256, 3) p2c_kernel(const FarBlockDev* __restri
 #pragma unroll
                 for (int u = 0; u < 4; ++u) q[u] = ldpair_stream(Q + (int64_t)(k + 4 * u) * B.m);
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < 4; ++u) {
+                    // the members' t values loaded unconditionally, so that they can be
+                    // issued ahead (to[r] of a missing member repeats the last one)
+                    float2 tv[NR];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) tv[r] = t[to[r] + k + 4 * u];
 #pragma unroll
                     for (int r = 0; r < NR; ++r)
                         if (r < nm) {
-                            const float2 tv = t[to[r] + k + 4 * u];
-                            mac(a0[r], q[u].a, tv);
-                            mac(a1[r], q[u].b, tv);
+                            mac(a0[r], q[u].a, tv[r]);
+                            mac(a1[r], q[u].b, tv[r]);
                         }
+                }
             }
             for (; k < B.rank; k += 4) {
                 const Pair<float2> q = ldpair_stream(Q + (int64_t)k * B.m);

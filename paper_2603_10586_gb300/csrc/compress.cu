@@ -39,6 +39,20 @@ namespace {
 
 constexpr int kChunk = 32;    // columns orthonormalised at a time
 constexpr int kRankCap = 8192; // largest rank a block may take (larger: error)
+// A batch first reserves basis room for a quarter of its blocks' smaller
+// dimension, at least kRankTry (the basis buffers and the batch size scale with
+// the room); a block that needs more sends its batch back for a second pass
+// with room for kRankCap.
+constexpr int kRankTry = 2048;
+// the first pass's room for blocks of rfull = min(m, n), or VIE_TEST_RANK_TRY
+// (a test sets it low to run the second pass)
+static int rank_try(int rfull) {
+    if (const char* e = std::getenv("VIE_TEST_RANK_TRY")) {
+        const int v = std::atoi(e);
+        if (v > 0) return std::min(v, kRankCap);
+    }
+    return std::min(kRankCap, std::max(kRankTry, rfull / 4));
+}
 
 // ------------------------------------------------------------------ kernels
 __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
@@ -654,14 +668,16 @@ struct Compressor {
         return false;
     }
 
-    // compress one batch of equally sized blocks
-    void batch(const std::vector<int>& ids, int s0_hint) {
+    // compress one batch of equally sized blocks with basis room for `cap`
+    // ranks; returns false, having stored nothing, when a block needs more and
+    // cap < kRankCap (the caller then runs the batch again with kRankCap)
+    bool batch(const std::vector<int>& ids, int s0_hint, int cap = kRankCap) {
         double t0 = mark();
         const int nb = (int)ids.size();
         const FarBlock& b0 = op.blocks[ids[0]];
         const int m = b0.m, n = b0.n, np = op.np;
         const int rfull = std::min(m, n);
-        const int rcap = std::min(rfull, kRankCap);
+        const int rcap = std::min(rfull, std::min(cap, kRankCap));
         const int rcap_pad = ((rcap + kChunk - 1) / kChunk) * kChunk;
         const int64_t mn = (int64_t)m * n;
 
@@ -734,7 +750,14 @@ struct Compressor {
             int scols = step == 0 ? s0 : std::min(256, std::max(kChunk, ((rlive / 2 + kChunk - 1) / kChunk) * kChunk));
             scols = std::min(scols, rcap_pad - rmax);
             if (scols <= 0) {
-                // every unconverged block has a full basis: exact
+                // the unconverged blocks fill the reserved room: with room for every
+                // column of the block the basis is exact; otherwise run again with
+                // more room (or, at kRankCap, give up)
+                if (rcap < rfull) {
+                    if (cap < kRankCap) return false;
+                    fail(VIE_ERR_BREAKDOWN,
+                         "far block needs a rank above " + std::to_string(kRankCap) + " at this tolerance");
+                }
                 for (int q = 0; q < nb; ++q) conv[q] = 1;
                 break;
             }
@@ -846,6 +869,7 @@ struct Compressor {
                 for (int q = 0; q < nb; ++q) {
                     if (!conv[q] && he[q] / kChunk <= thr * hnorm[q]) conv[q] = 1;
                     if (!conv[q] && r[q] + kChunk > rcap_pad) {
+                        if (rcap < rfull && cap < kRankCap) return false;  // again, with room for kRankCap
                         if (rcap < rfull)
                             fail(VIE_ERR_BREAKDOWN, "far block needs a rank above " + std::to_string(kRankCap) +
                                                         " at this tolerance");
@@ -1032,6 +1056,7 @@ struct Compressor {
                     "sketch %.3f R %.3f pack %.3f s\n", b0.level, nb, m, n, s0, step, (double)rsum / nb, rmx,
                     t1 - t0, t2 - t1, t3 - t2, t4 - t3);
         }
+        return true;
     }
 
     // Translated copies: two far blocks with the same level, the same atom
@@ -1100,21 +1125,36 @@ struct Compressor {
             std::vector<int> ids = g.second;
             int lev = std::get<0>(g.first), m = std::get<1>(g.first), n = std::get<2>(g.first);
             std::tuple<int, int, int> cls{lev, std::get<3>(g.first), std::get<4>(g.first)};
-            size_t rcap = std::min(std::min(m, n), kRankCap + kChunk);
-            size_t per = ((size_t)m * n + (size_t)m * rcap + (size_t)n * rcap + (size_t)m * 2 * kChunk) * sizeof(T2);
-            int bs = (int)std::max<size_t>(1, std::min<size_t>(4096, budget / per));  // blocks run along grid y
-            if (const char* e = std::getenv("VIE_COMPRESS_MAX_BATCH")) bs = std::max(1, std::min(bs, std::atoi(e)));
+            // blocks per batch for basis room of `cap` ranks (blocks run along grid y)
+            auto batch_size = [&](int cap) {
+                const size_t rc = std::min<size_t>(std::min(m, n), (size_t)cap + kChunk);
+                const size_t per = ((size_t)m * n + (size_t)m * rc + (size_t)n * rc + (size_t)m * 2 * kChunk) * sizeof(T2);
+                int b = (int)std::max<size_t>(1, std::min<size_t>(4096, budget / per));
+                if (const char* e = std::getenv("VIE_COMPRESS_MAX_BATCH")) b = std::max(1, std::min(b, std::atoi(e)));
+                return b;
+            };
+            auto hint_of = [&]() {
+                auto it = class_rank.find(cls);
+                return it == class_rank.end() ? kChunk : ((it->second + kChunk + kChunk - 1) / kChunk) * kChunk;
+            };
+            const int try_cap = rank_try(std::min(m, n));
+            // run a sub-batch with room for kRankTry ranks; if one of its blocks needs
+            // more, again in batches sized for kRankCap
+            auto run = [&](const std::vector<int>& sub) {
+                if (batch(sub, hint_of(), try_cap)) return;
+                const int bw = batch_size(kRankCap);
+                for (size_t j0 = 0; j0 < sub.size(); j0 += bw)
+                    batch(std::vector<int>(sub.begin() + j0, sub.begin() + std::min(sub.size(), j0 + bw)), hint_of(),
+                          kRankCap);
+            };
+            const int bs = batch_size(try_cap);
             size_t i0 = 0;
             if (op.ctx->no_sharing && !class_rank.count(cls) && ids.size() > 1 && (size_t)m * n >= ((size_t)1 << 20)) {
-                batch({ids[0]}, kChunk);  // pilot
+                run({ids[0]});  // pilot
                 i0 = 1;
             }
-            for (; i0 < ids.size(); i0 += bs) {
-                std::vector<int> sub(ids.begin() + i0, ids.begin() + std::min(ids.size(), i0 + bs));
-                auto it = class_rank.find(cls);
-                int hint = it == class_rank.end() ? kChunk : ((it->second + kChunk + kChunk - 1) / kChunk) * kChunk;
-                batch(sub, hint);
-            }
+            for (; i0 < ids.size(); i0 += bs)
+                run(std::vector<int>(ids.begin() + i0, ids.begin() + std::min(ids.size(), i0 + bs)));
         }
         // consolidate into one factor store: derived representatives take their
         // mirror class's rank, shared blocks their representative's rank and storage

@@ -180,3 +180,22 @@ def test_near_field_matches_oracle(ctx, tiny_dense):
         op.near_field(I, np.array([[np.nan, 0.0, 0.0]]))
     assert np.allclose(op.near_field(I, pts[:1])[0], E[:1], rtol=1e-14, atol=0)
     op.close()
+
+
+def test_compression_second_pass_for_high_ranks(ctx, ops, monkeypatch):
+    # a batch whose blocks need more basis room than its first pass reserved
+    # (forced here: room for 32 ranks) is compressed again with the full room;
+    # the operator then solves like the one compressed in one pass
+    name = "mid_8x8_nv3"
+    kh, pol, ref = golden(name)
+    monkeypatch.setenv("VIE_TEST_RANK_TRY", "32")
+    op = vie.Operator(ctx, GEOM[name]())
+    info = op.compress(1e-4, vie.C64)
+    monkeypatch.delenv("VIE_TEST_RANK_TRY")
+    base = ops[name][1]
+    assert max(b["rank"] for b in op.far_blocks(with_factors=False)) > 32
+    assert abs(info["factor_entries"] - base["factor_entries"]) <= 0.1 * base["factor_entries"]
+    I, st, status = op.solve(kh[:1], pol[:1], tol=1e-6)
+    assert status == vie.VIE_OK
+    assert rel(I[:, 0], ref[:, 0]) <= 5e-4
+    op.close()
