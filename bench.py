@@ -570,6 +570,67 @@ def run_methods(args):
     return 0
 
 
+def run_builders(args):
+    """--builders: the two far-block builders on one operator of the workload,
+    each compressing from geometry: the adaptive randomised range finder
+    (vie_compress) and the cross approximation with full pivoting of Sec. 6.5
+    (vie_compress_cross).  One untimed range-finder compression first (library
+    and cuBLAS set-up), then each builder --builder-reps times (median).  Reports
+    compression time, ranks, factor entries and, for the cross approximation,
+    the bandwidth of its residual passes (bytes read and written / device time
+    of its step loops) against the measured HBM peak; then one solve per builder
+    (the workload's right-hand sides and inner precision) with its residuals and
+    the largest relative difference between the two solutions."""
+    import torch
+    from paper_2603_10586_gb300 import vie
+    torch.cuda.set_device(0)
+    ctx = vie.Context(0)
+    wl = WORKLOADS[args.workload]
+    kh, pol = wl["incident"]()
+    prec = getattr(vie, wl["precision"])
+    g = wl["geometry"]()
+    hbm, _, _, peak_kind = peaks()
+    warm = vie.Operator(ctx, g)
+    warm.compress(wl["tol"], vie.C64)
+    warm.close()
+    out = {"metric": "compression builders", "workload": args.workload, "tol_compress": wl["tol"],
+           "reps": args.builder_reps, "builders": {}}
+    sols = {}
+    for name, method in (("range_finder", vie.COMPRESS_RANGE_FINDER), ("cross_full_pivoting", vie.COMPRESS_CROSS)):
+        ts = []
+        for rep in range(args.builder_reps):
+            op = vie.Operator(ctx, g)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = op.compress(wl["tol"], vie.C64, method=method)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            if rep + 1 < args.builder_reps:
+                op.close()
+        I, st, status = op.solve(kh, pol, tol=TOL_SOLVE, precision=prec, restart=wl["restart"],
+                                 max_iters=wl.get("max_iters", 20000))
+        sols[name] = I
+        rec = {"compress_s": float(np.median(ts)), "compress_s_all": ts, "rank_mean": info["rank_mean"],
+               "rank_max": info["rank_max"], "factor_entries": info["factor_entries"],
+               "stored_entries": info["stored_entries"], "solve_status": status,
+               "iterations": st["iterations"], "residual": st["residual"], "true_residual": st["true_residual"]}
+        if method == vie.COMPRESS_CROSS:
+            gbs = info["cross_bytes"] / max(info["t_cross_s"], 1e-12) / 1e9
+            rec["residual_passes"] = {"bytes": info["cross_bytes"], "device_s": info["t_cross_s"], "GB/s": gbs,
+                                      "peak_GB/s": hbm, "frac": gbs / hbm, "peak_kind": peak_kind,
+                                      "note": "each step reads and writes every active block's residual once "
+                                              "(m n complex float32 entries); the device time includes the "
+                                              "select kernels and the host's reads of the active count"}
+        out["builders"][name] = rec
+        op.close()
+    a, b = sols["range_finder"], sols["cross_full_pivoting"]
+    out["max_rel_diff_between_solutions"] = max(
+        float(np.linalg.norm(a[:, c] - b[:, c]) / np.linalg.norm(a[:, c])) for c in range(a.shape[1]))
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_profile(args):
     """--profile: one untimed solve from geometry of the workload followed by 10
     inner-iteration applies, for ncu captures (no warm-up, no timing, no
@@ -646,6 +707,9 @@ def main():
     ap.add_argument("--batch-requests", type=int, default=8, help="problems of the --batch mix")
     ap.add_argument("--methods", action="store_true", help="lockstep GMRES, block GMRES and BiCGStab compared")
     ap.add_argument("--max-iters", type=int, default=0, help="iteration budget of --methods (0: the workload's)")
+    ap.add_argument("--builders", action="store_true",
+                    help="range finder against cross approximation (full pivoting) as the far-block builder")
+    ap.add_argument("--builder-reps", type=int, default=1, help="compressions per builder of --builders")
     ap.add_argument("--profile", action="store_true", help="one untimed step for ncu captures")
     ap.add_argument("--profile-case", default="full", choices=["full", "small"])
     args = ap.parse_args()
@@ -659,6 +723,8 @@ def main():
         return run_batch(args)
     if args.methods:
         return run_methods(args)
+    if args.builders:
+        return run_builders(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -160,7 +160,16 @@ typedef struct vie_op_info {
     int64_t packed_bytes;      /* bytes of the bf16 planes the packed tensor-core apply streams per
                                   application (every far block's own planes, tiles padded to 128 rows
                                   and K to 32); 0 until a VIE_BF16X3 apply has built them */
+    int compress_method;       /* vie_compress_method of the stored factors */
+    double cross_bytes;        /* cross approximation: residual bytes its passes read and wrote */
+    double t_cross_s;          /* cross approximation: device time of its step loops */
 } vie_op_info;
+
+/* How vie_compress / vie_compress_cross built the far-block factors. */
+enum vie_compress_method {
+    VIE_COMPRESS_RANGE_FINDER = 0, /* adaptive randomised range finder, Q orthonormal */
+    VIE_COMPRESS_CROSS = 1         /* cross approximation with full pivoting (Sec. 6.5) */
+};
 
 /* Plane-wave incident fields E0 = p exp(-j k khat . r), one per right-hand side. */
 typedef struct vie_incident {
@@ -236,6 +245,21 @@ int vie_assemble(vie_ctx* ctx, const vie_geometry* g, double wavelength, vie_op*
  * estimate).  factor_precision: VIE_C64 or VIE_C128.  May be called again
  * with another tolerance or precision; the old factors are freed. */
 int vie_compress(vie_op* op, double tol, int factor_precision);
+
+/* vie_compress_cross (Sec. 6.5: local assembly of each far block, then its
+ * "full-cross" approximation): forms every far block on the device, in
+ * batches, and compresses it by cross approximation with full pivoting.  Step k
+ * takes the entry of largest modulus of the residual E_k (ties: smallest
+ * column, then smallest row) and subtracts the cross through it,
+ * E_{k+1} = E_k - E_k[:, j] E_k[i, :] / E_k[i, j]; a block stops at the first
+ * k with ||E_k||_F <= tol ||A||_F, a bound that holds on the formed block up to
+ * the float rounding of the residual (no stochastic estimate).  The factors are
+ * stored as Q = U (m x r, not orthonormal) and R = V^T (r x n) in the layout
+ * vie_compress writes, so every apply, solve and export works unchanged.
+ * Arguments, errors and reuse as for vie_compress; VIE_ERR_NAN if a formed
+ * block has non-finite entries.  The residual passes cost r m n entries read
+ * and written per block (vie_op_info.cross_bytes / t_cross_s). */
+int vie_compress_cross(vie_op* op, double tol, int factor_precision);
 
 void vie_op_destroy(vie_op* op);
 int vie_op_get_info(const vie_op* op, vie_op_info* info);

@@ -328,7 +328,7 @@ int vie_assemble(vie_ctx* ctx, const vie_geometry* g, double wavelength, vie_op*
     return st;
 }
 
-int vie_compress(vie_op* op, double tol, int factor_precision) {
+static int compress_with(vie_op* op, double tol, int factor_precision, int method) {
     if (!op) return VIE_ERR_INVALID_ARG;
     return guarded(ctx_of(op), [&] {
         set_device(*op->o.ctx);
@@ -338,12 +338,20 @@ int vie_compress(vie_op* op, double tol, int factor_precision) {
         double t0 = now_s();
         drop_unions(*op->o.ctx, &op->o);
         ++op->o.gen;
-        compress_operator(op->o, tol, factor_precision);
+        compress_operator(op->o, tol, factor_precision, method);
         op->o.t_compress = now_s() - t0;
         if (op->o.ctx->verbose)
             fprintf(stderr, "[vie] compress: %lld factor entries  %.3f s\n", (long long)op->o.factor_entries,
                     op->o.t_compress);
     });
+}
+
+int vie_compress(vie_op* op, double tol, int factor_precision) {
+    return compress_with(op, tol, factor_precision, VIE_COMPRESS_RANGE_FINDER);
+}
+
+int vie_compress_cross(vie_op* op, double tol, int factor_precision) {
+    return compress_with(op, tol, factor_precision, VIE_COMPRESS_CROSS);
 }
 
 void vie_op_destroy(vie_op* op) {
@@ -393,6 +401,9 @@ int vie_op_get_info(const vie_op* op, vie_op_info* info) {
     info->t_compress_s = o.t_compress;
     info->stored_entries = o.stored_entries;
     info->packed_bytes = o.umma_packed ? (int64_t)umma_pack_bytes(o) : 0;
+    info->compress_method = o.cmethod;
+    info->cross_bytes = o.cross_bytes;
+    info->t_cross_s = o.t_cross;
     return VIE_OK;
 }
 

@@ -225,6 +225,11 @@ struct Op {
     DevBuf d_xs;  // float64 vectors split into float32 head + tail (double-float apply)
     size_t t_cap = 0, F_cap = 0;
     double t_assemble = 0, t_compress = 0;
+    // compression method of the stored factors (0: range finder, 1: cross
+    // approximation) and, for the cross approximation, the bytes its residual
+    // passes moved and the time of its step loops
+    int cmethod = 0;
+    double cross_bytes = 0, t_cross = 0;
     int64_t n() const { return (int64_t)N * np; }
 };
 
@@ -353,8 +358,27 @@ void apply_far_df(Op& op, const double2* x, int64_t ldx, double2* F, int64_t ldf
 // apply_tc.cu: several right-hand sides on the tensor cores (BF16x3)
 void apply_far_bf16x3(Op& op, const float2* x, int64_t ldx, float2* F, int64_t ldf, int nrhs, cudaStream_t s);
 
-// compress.cu
-void compress_operator(Op& op, double tol, int prec);
+// compress.cu; method 0: adaptive randomised range finder, 1: cross
+// approximation with full pivoting (cross.cu)
+void compress_operator(Op& op, double tol, int prec, int method = 0);
+
+// cross.cu: cross approximation with full pivoting of nb formed m x n blocks
+// (column-major, E + q m n; overwritten by their residuals) to
+// ||A - U V^T||_F <= tol ||A||_F with d_anorm2[q] = ||A_q||_F^2, at most rcap
+// crosses (rcap <= rfull = min(m, n)).  Column k of block q goes to
+// U + q us + k m (u_k) and VH + q vs + k n (conj(v_k)); rank[q] receives the
+// block's rank.  flags: 1 a block needed more than rcap (< rfull) crosses,
+// 2 a residual was not finite.
+struct CrossStats {
+    int flags = 0;
+    double seconds = 0;    // step loop, device time between events
+    double bytes = 0;      // residual bytes read and written
+    int64_t passes = 0;    // residual passes (blocks x steps)
+};
+template <class T2>
+CrossStats cross_full_batch(T2* E, int nb, int m, int n, const double* d_anorm2, double tol, int rcap, int rfull,
+                            T2* U, int64_t us, T2* VH, int64_t vs, std::vector<int>& rank, int n_sm,
+                            cudaStream_t s);
 
 // solve.cpp
 // forget the joined operators that contain `o` (before it is destroyed or recompressed)

@@ -551,6 +551,7 @@ struct Compressor {
     std::vector<std::pair<int, int64_t>> where;  // per block: (store, offset of Q); R^H follows Q
     std::map<std::tuple<int, int, int>, int> class_rank;  // (level, offsets) -> largest rank seen
     uint64_t seed = 0x5eed0001ull;
+    bool cross = false;  // cross approximation with full pivoting instead of the range finder
 
     Compressor(Op& o, double t) : op(o), tol(t), s(o.ctx->stream), h(o.ctx->blas) {}
 
@@ -668,6 +669,65 @@ struct Compressor {
         return false;
     }
 
+    // Copy the factors of one batch into a new staging store: for block q of
+    // ids, the live columns j < r[q] of Q (Q + q qs + j m, m rows) and of R^H
+    // (RH + q rs + j n, n rows), where alive (per block alive_stride flags,
+    // null: every column) marks the live ones.  Sets the blocks' ranks and
+    // staging places and returns the ranks.
+    std::vector<int> stash(const std::vector<int>& ids, int m, int n, const DevBuf& Q, int64_t qs, const DevBuf& RH,
+                           int64_t rs, const std::vector<int>& r, const unsigned char* alive, int64_t alive_stride) {
+        const int nb = (int)ids.size();
+        auto live = [&](int q, int j) { return alive == nullptr || alive[(size_t)q * alive_stride + j] != 0; };
+        std::vector<int> rank(nb, 0);
+        int64_t total = 0;
+        for (int q = 0; q < nb; ++q) {
+            for (int j = 0; j < r[q]; ++j) rank[q] += live(q, j) ? 1 : 0;
+            total += (int64_t)rank[q] * (m + n);
+            total = (total + 31) / 32 * 32;
+        }
+        DevBuf store((size_t)std::max<int64_t>(total, 32) * sizeof(T2));
+        std::vector<long long> so, dof;  // Q columns then R^H columns
+        std::vector<long long> so2, dof2;
+        int64_t off = 0;
+        int sidx = (int)stores.size();
+        for (int q = 0; q < nb; ++q) {
+            FarBlock& b = op.blocks[ids[q]];
+            b.rank = rank[q];
+            where[ids[q]] = {sidx, off};
+            int kk = 0;
+            for (int j = 0; j < r[q]; ++j) {
+                if (!live(q, j)) continue;
+                so.push_back((long long)q * qs + (long long)j * m);
+                dof.push_back(off + (int64_t)kk * m);
+                so2.push_back((long long)q * rs + (long long)j * n);
+                dof2.push_back(off + (int64_t)rank[q] * m + (int64_t)kk * n);
+                ++kk;
+            }
+            off += (int64_t)rank[q] * (m + n);
+            off = (off + 31) / 32 * 32;
+            int& cr = class_rank[{b.level, b.dist, b.dmin}];
+            cr = std::max(cr, rank[q]);
+        }
+        if (!so.empty()) {
+            DevBuf a1, a2, a3, a4;
+            upload(a1, so);
+            upload(a2, dof);
+            upload(a3, so2);
+            upload(a4, dof2);
+            for (size_t c0 = 0; c0 < so.size(); c0 += 65535) {
+                int cnt = (int)std::min<size_t>(65535, so.size() - c0);
+                k_gather_cols<T2><<<dim3(std::min(64, (m + 255) / 256), cnt), 256, 0, s>>>(
+                    nullptr, m, a1.as<long long>() + c0, a2.as<long long>() + c0, store.as<T2>(), Q.as<T2>());
+                k_gather_cols<T2><<<dim3(std::min(64, (n + 255) / 256), cnt), 256, 0, s>>>(
+                    nullptr, n, a3.as<long long>() + c0, a4.as<long long>() + c0, store.as<T2>(), RH.as<T2>());
+                VIE_CHECK_LAUNCH();
+            }
+            VIE_CUDA(cudaStreamSynchronize(s));
+        }
+        stores.push_back(std::move(store));
+        return rank;
+    }
+
     // compress one batch of equally sized blocks with basis room for `cap`
     // ranks; returns false, having stored nothing, when a block needs more and
     // cap < kRankCap (the caller then runs the batch again with kRankCap)
@@ -683,7 +743,7 @@ struct Compressor {
 
         // float32 path: the formed blocks become split bf16 planes
         const char* sp = std::getenv("VIE_COMPRESS_SPLIT");
-        const bool split = std::is_same<T, float>::value && m <= kSplitMaxRows && m % 2 == 0 &&
+        const bool split = !cross && std::is_same<T, float>::value && m <= kSplitMaxRows && m % 2 == 0 &&
                            !(sp && sp[0] == '0');
         bool in_planes = false;
         // 1. form the blocks (col-major m x n, ld = m) and their squared norms
@@ -711,6 +771,37 @@ struct Compressor {
         VIE_CHECK_LAUNCH();
         std::vector<double> hnorm(nb);
         VIE_CUDA(cudaMemcpyAsync(hnorm.data(), normA.p, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (cross) {
+            // 2'. cross approximation with full pivoting: Q = U, R^H = conj(V)
+            DevBuf U((size_t)nb * m * rcap_pad * sizeof(T2)), VH((size_t)nb * n * rcap_pad * sizeof(T2));
+            std::vector<int> rk;
+            const CrossStats cs = cross_full_batch<T2>(A.as<T2>(), nb, m, n, normA.as<double>(), tol, rcap, rfull,
+                                                       U.as<T2>(), (int64_t)m * rcap_pad, VH.as<T2>(),
+                                                       (int64_t)n * rcap_pad, rk, op.ctx->n_sm, s);
+            if (cs.flags & 2) fail(VIE_ERR_NAN, "cross approximation: a far block has non-finite entries");
+            if (cs.flags & 1) {
+                if (cap < kRankCap) return false;  // again, with room for kRankCap
+                fail(VIE_ERR_BREAKDOWN, "far block needs a rank above " + std::to_string(kRankCap) +
+                                            " at this tolerance");
+            }
+            op.cross_bytes += cs.bytes;
+            op.t_cross += cs.seconds;
+            A.release();
+            double t2 = mark();
+            tim[1] += t2 - t1;
+            stash(ids, m, n, U, (int64_t)m * rcap_pad, VH, (int64_t)n * rcap_pad, rk, nullptr, 0);
+            double t4 = mark();
+            tim[3] += t4 - t2;
+            if (op.ctx->verbose) {
+                int rsum = 0, rmx = 0;
+                for (int q = 0; q < nb; ++q) { rsum += rk[q]; rmx = std::max(rmx, rk[q]); }
+                fprintf(stderr, "[vie]   level %d batch %d x (%d x %d): cross steps %lld mean rank %.1f max %d | "
+                        "form %.3f cross %.3f (%.0f GB/s) pack %.3f s\n", b0.level, nb, m, n,
+                        (long long)cs.passes, (double)rsum / nb, rmx, t1 - t0, t2 - t1,
+                        cs.bytes / std::max(cs.seconds, 1e-12) * 1e-9, t4 - t2);
+            }
+            return true;
+        }
         const bf16* Ap = reinterpret_cast<const bf16*>(A.p);
         if (split && !in_planes) {  // formed in place as complex float32: split now
             const size_t smem = (size_t)m * sizeof(float2);
@@ -1000,53 +1091,8 @@ struct Compressor {
         A.release();
 
         // 4. compact the live columns into a staging store
-        std::vector<int> rank(nb, 0);
-        int64_t total = 0;
-        for (int q = 0; q < nb; ++q) {
-            for (int j = 0; j < r[q]; ++j) rank[q] += halive[(size_t)q * rcap_pad + j] ? 1 : 0;
-            total += (int64_t)rank[q] * (m + n);
-            total = (total + 31) / 32 * 32;
-        }
-        DevBuf store((size_t)std::max<int64_t>(total, 32) * sizeof(T2));
-        std::vector<long long> so, dof;  // Q columns then R^H columns
-        std::vector<long long> so2, dof2;
-        int64_t off = 0;
-        int sidx = (int)stores.size();
-        for (int q = 0; q < nb; ++q) {
-            FarBlock& b = op.blocks[ids[q]];
-            b.rank = rank[q];
-            where[ids[q]] = {sidx, off};
-            int kk = 0;
-            for (int j = 0; j < r[q]; ++j) {
-                if (!halive[(size_t)q * rcap_pad + j]) continue;
-                so.push_back((long long)q * m * rcap_pad + (long long)j * m);
-                dof.push_back(off + (int64_t)kk * m);
-                so2.push_back((long long)q * n * rmax + (long long)j * n);
-                dof2.push_back(off + (int64_t)rank[q] * m + (int64_t)kk * n);
-                ++kk;
-            }
-            off += (int64_t)rank[q] * (m + n);
-            off = (off + 31) / 32 * 32;
-            int& cr = class_rank[{b.level, b.dist, b.dmin}];
-            cr = std::max(cr, rank[q]);
-        }
-        if (!so.empty()) {
-            DevBuf a1, a2, a3, a4;
-            upload(a1, so);
-            upload(a2, dof);
-            upload(a3, so2);
-            upload(a4, dof2);
-            for (size_t c0 = 0; c0 < so.size(); c0 += 65535) {
-                int cnt = (int)std::min<size_t>(65535, so.size() - c0);
-                k_gather_cols<T2><<<dim3(std::min(64, (m + 255) / 256), cnt), 256, 0, s>>>(
-                    nullptr, m, a1.as<long long>() + c0, a2.as<long long>() + c0, store.as<T2>(), Q.as<T2>());
-                k_gather_cols<T2><<<dim3(std::min(64, (n + 255) / 256), cnt), 256, 0, s>>>(
-                    nullptr, n, a3.as<long long>() + c0, a4.as<long long>() + c0, store.as<T2>(), RH.as<T2>());
-                VIE_CHECK_LAUNCH();
-            }
-            VIE_CUDA(cudaStreamSynchronize(s));
-        }
-        stores.push_back(std::move(store));
+        const std::vector<int> rank = stash(ids, m, n, Q, (int64_t)m * rcap_pad, RH, (int64_t)n * rmax, r,
+                                            halive.data(), rcap_pad);
         double t4 = mark();
         tim[3] += t4 - t3;
         if (op.ctx->verbose) {
@@ -1213,7 +1259,7 @@ struct Compressor {
 
 }  // namespace
 
-void compress_operator(Op& op, double tol, int prec) {
+void compress_operator(Op& op, double tol, int prec, int method) {
     VIE_BLAS(cublasSetStream(op.ctx->blas, op.ctx->stream));
     // float32-accurate GEMMs on the bf16 tensor cores (BF16x9), float64-accurate
     // fixed-point emulation for the c128 path, where cuBLAS finds them faster
@@ -1233,11 +1279,16 @@ void compress_operator(Op& op, double tol, int prec) {
     }
     op.d_factors.release();
     for (auto& b : op.blocks) b.rank = 0;
+    op.cmethod = method;
+    op.cross_bytes = 0;
+    op.t_cross = 0;
     if (prec == VIE_C128) {
         Compressor<double> c(op, tol);
+        c.cross = method == 1;
         c.run();
     } else {
         Compressor<float> c(op, tol);
+        c.cross = method == 1;
         c.run();
     }
     op.fprec = prec == VIE_C128 ? VIE_C128 : VIE_C64;

@@ -31,6 +31,7 @@ VAR_TCGEN05_PACKED_BF16X3 = 7
 VAR_SIMT_SHARED = 8
 VAR_TCGEN05_WS_BF16X3 = 9
 VAR_TCGEN05_WS2_BF16X3 = 10
+COMPRESS_RANGE_FINDER, COMPRESS_CROSS = 0, 1
 NOALLOC_SCRATCH_ELEMS = 1 << 22   # VIE_NOALLOC_SCRATCH_ELEMS
 FUSE_PRECOND = 1
 DENSE = 2
@@ -61,7 +62,8 @@ class OpInfo(C.Structure):
                 ("rank_min", C.c_int), ("rank_max", C.c_int), ("rank_mean", C.c_double),
                 ("factor_precision", C.c_int), ("tol", C.c_double), ("apply_bytes", C.c_int64),
                 ("t_assemble_s", C.c_double), ("t_compress_s", C.c_double), ("stored_entries", C.c_int64),
-                ("packed_bytes", C.c_int64)]
+                ("packed_bytes", C.c_int64), ("compress_method", C.c_int), ("cross_bytes", C.c_double),
+                ("t_cross_s", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -109,7 +111,8 @@ class ResultC(C.Structure):
                 ("peak_bytes", C.c_int64)]
 
 
-EXPORTS = ["vie_create", "vie_destroy", "vie_last_error", "vie_assemble", "vie_compress", "vie_op_destroy",
+EXPORTS = ["vie_create", "vie_destroy", "vie_last_error", "vie_assemble", "vie_compress", "vie_compress_cross",
+           "vie_op_destroy",
            "vie_op_get_info", "vie_apply", "vie_precond", "vie_rhs", "vie_solve", "vie_fields",
            "vie_export_block", "vie_far_block_info", "vie_export_far_block", "vie_serve", "vie_submit",
            "vie_poll", "vie_result_free", "vie_server_stop", "vie_footprint_bytes", "vie_kernel_launches",
@@ -134,6 +137,7 @@ def load():
         "vie_last_error": (C.c_char_p, [vp]),
         "vie_assemble": (C.c_int, [vp, C.POINTER(GeometryC), dbl, C.POINTER(vp)]),
         "vie_compress": (C.c_int, [vp, dbl, C.c_int]),
+        "vie_compress_cross": (C.c_int, [vp, dbl, C.c_int]),
         "vie_op_destroy": (None, [vp]),
         "vie_op_get_info": (C.c_int, [vp, C.POINTER(OpInfo)]),
         "vie_apply": (C.c_int, [vp, vp, vp, C.c_int, i64, C.c_int, C.c_int, vp]),
@@ -255,8 +259,10 @@ class Operator:
         ctx.check(self.L.vie_assemble(ctx.h, C.byref(gs), float(wl), C.byref(self.h)))
         self.info()
 
-    def compress(self, tol=1e-4, precision=C64):
-        self.ctx.check(self.L.vie_compress(self.h, float(tol), int(precision)))
+    def compress(self, tol=1e-4, precision=C64, method=COMPRESS_RANGE_FINDER):
+        """vie_compress (method COMPRESS_RANGE_FINDER) or vie_compress_cross (COMPRESS_CROSS)."""
+        fn = self.L.vie_compress_cross if method == COMPRESS_CROSS else self.L.vie_compress
+        self.ctx.check(fn(self.h, float(tol), int(precision)))
         return self.info()
 
     def info(self):
