@@ -50,9 +50,11 @@ DEFAULT_WORKLOAD = "multirhs"
 # right-hand sides, BF16x3): u1w_kernel<2> 27.24 + 1.17 GB, u2w_kernel<2> 30.32
 # + 0.12 GB, type_gemm<float2> 0.25 + 0.10 GB in one ncu pass
 # (dram__bytes_read.sum + dram__bytes_write.sum) over the 64-RHS apply of the
-# 32 x 32 array, `bench.py --profile`.  Only valid for the kernels it was taken
-# on; remove an entry when they change.
-APPLY_TRAFFIC = {("multirhs", 64, True): 59.2e9}
+# 32 x 32 array, `bench.py --profile`.  Only valid for the kernels and the
+# operator it was taken on; remove an entry when either changes.  (The entry
+# for the 64-RHS apply of the 32 x 32 array, 59.2e9, was taken on factors
+# compressed from float32-table blocks, whose ranks are many times larger.)
+APPLY_TRAFFIC = {}
 
 # Per workload: geometry, incident waves, compression tolerance, inner-apply
 # precision ("C64" or "BF16X3"), restart length and, for the CPU oracle's
@@ -588,12 +590,18 @@ def run_builders(args):
     wl = WORKLOADS[args.workload]
     kh, pol = wl["incident"]()
     prec = getattr(vie, wl["precision"])
-    g = wl["geometry"]()
+    if args.builders_side:
+        g = workloads.square_array(args.builders_side, 4)
+        geom = "%dx%d array of eps=12 cubes (side 0.2, pitch 0.4, lambda 1), 4^3 voxels, %d unknowns" % (
+            args.builders_side, args.builders_side, g.unknowns())
+    else:
+        g = wl["geometry"]()
+        geom = wl["desc"]
     hbm, _, _, peak_kind = peaks()
     warm = vie.Operator(ctx, g)
     warm.compress(wl["tol"], vie.C64)
     warm.close()
-    out = {"metric": "compression builders", "workload": args.workload, "tol_compress": wl["tol"],
+    out = {"metric": "compression builders", "workload": args.workload, "geometry": geom, "tol_compress": wl["tol"],
            "reps": args.builder_reps, "builders": {}}
     sols = {}
     for name, method in (("range_finder", vie.COMPRESS_RANGE_FINDER), ("cross_full_pivoting", vie.COMPRESS_CROSS)):
@@ -710,6 +718,8 @@ def main():
     ap.add_argument("--builders", action="store_true",
                     help="range finder against cross approximation (full pivoting) as the far-block builder")
     ap.add_argument("--builder-reps", type=int, default=1, help="compressions per builder of --builders")
+    ap.add_argument("--builders-side", type=int, default=0,
+                    help="--builders on an NxN array of 4^3-voxel cubes instead of the workload's geometry")
     ap.add_argument("--profile", action="store_true", help="one untimed step for ncu captures")
     ap.add_argument("--profile-case", default="full", choices=["full", "small"])
     args = ap.parse_args()

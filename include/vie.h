@@ -239,7 +239,8 @@ const char* vie_last_error(vie_ctx* ctx);
 int vie_assemble(vie_ctx* ctx, const vie_geometry* g, double wavelength, vie_op** out);
 
 /* vie_compress (Sec. 5.2 eq. eq_02, Sec. 5.3): forms every far block on the
- * device, in batches, and replaces it by Q (m x r, orthonormal columns) and
+ * device, in batches (VIE_C64: float64 quadrature tables, entries rounded to
+ * complex float32), and replaces it by Q (m x r, orthonormal columns) and
  * R (r x n) with ||A - Q R||_F <= tol ||A||_F (randomised adaptive range
  * finder; the bound is enforced with a safety factor on a stochastic
  * estimate).  factor_precision: VIE_C64 or VIE_C128.  May be called again
@@ -369,6 +370,8 @@ int vie_fields(vie_op* op, const vie_incident* inc, const void* I, int nrhs, con
  * kind 0: self block of type `a` (c128 Np x Np, col-major);
  * kind 1: dense interaction block Zs_ab between atoms a != b, assembled on the
  *         device at `precision` (VIE_C64 -> c64, VIE_C128 -> c128), col-major;
+ *         the c64 block is the one vie_compress forms: float64 quadrature
+ *         tables, entries rounded to complex float32;
  * kind 2: explicit inverse of the self block of type `a` (c128).  */
 int vie_export_block(vie_op* op, int kind, int a, int b, int precision, void* out);
 

@@ -712,8 +712,8 @@ int vie_export_block(vie_op* op, int kind, int a, int b, int precision, void* ou
             upload(dl, ld);
             if (precision == VIE_C128)
                 assemble_pairs<double>(o, dj.as<PairJob>(), 1, dd.as<void* const>(), dl.as<int64_t>(), s);
-            else
-                assemble_pairs<float>(o, dj.as<PairJob>(), 1, dd.as<void* const>(), dl.as<int64_t>(), s);
+            else  // the complex float32 block the c64 compression forms
+                assemble_pairs_f32_from_f64(o, dj.as<PairJob>(), 1, dd.as<void* const>(), dl.as<int64_t>(), s);
             VIE_CUDA(cudaMemcpyAsync(out, blk.p, np2 * esz, cudaMemcpyDeviceToHost, s));
         } else {
             fail(VIE_ERR_INVALID_ARG, "unknown block kind");

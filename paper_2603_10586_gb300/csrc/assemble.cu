@@ -941,9 +941,11 @@ __global__ void k_sum_rows(const double* part, int per, int nrows, double* out) 
     out[r] = acc;
 }
 
-template <class T>
-void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_dst, const int64_t* d_ld,
-                    cudaStream_t s, double* norm_out) {
+namespace {
+// tables and entry sums in T, entries written as TO
+template <class T, class TO>
+void assemble_pairs_as(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_dst, const int64_t* d_ld,
+                       cudaStream_t s, double* norm_out) {
     using T2 = typename C2<T>::t;
     const DevMesh& m = op.dmesh;
     size_t stride = table_stride(m);
@@ -968,8 +970,8 @@ void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_ds
                                                                            tab.as<T2>(), stride);
         VIE_CHECK_LAUNCH();
         const dim3 eg((m.np + kEntRows - 1) / kEntRows, nj, (m.np + kEntCols - 1) / kEntCols);
-        entries_kernel<T, T2, false><<<eg, kEntRows, 0, s>>>(
-            d_jobs + j0, m, geo_of(op), op.k * op.k, tab.as<T2>(), stride, (T2* const*)d_dst, d_ld,
+        entries_kernel<T, TO, false><<<eg, kEntRows, 0, s>>>(
+            d_jobs + j0, m, geo_of(op), op.k * op.k, tab.as<T2>(), stride, (TO* const*)d_dst, d_ld,
             op.d_inv_chi.as<double2>(), norm_out ? npart.as<double>() : nullptr);
         VIE_CHECK_LAUNCH();
         if (norm_out) {
@@ -979,6 +981,18 @@ void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_ds
     }
     // keep the scratch alive until the work is done
     VIE_CUDA(cudaStreamSynchronize(s));
+}
+}  // namespace
+
+template <class T>
+void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_dst, const int64_t* d_ld,
+                    cudaStream_t s, double* norm_out) {
+    assemble_pairs_as<T, typename C2<T>::t>(op, d_jobs, n_jobs, d_dst, d_ld, s, norm_out);
+}
+
+void assemble_pairs_f32_from_f64(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_dst, const int64_t* d_ld,
+                                 cudaStream_t s, double* norm_out) {
+    assemble_pairs_as<double, float2>(op, d_jobs, n_jobs, d_dst, d_ld, s, norm_out);
 }
 
 template void assemble_pairs<float>(Op&, const PairJob*, int, void* const*, const int64_t*, cudaStream_t, double*);

@@ -298,6 +298,14 @@ struct PairJob {
 template <class T>
 void assemble_pairs(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_dst, const int64_t* d_ld,
                     cudaStream_t s, double* norm_out = nullptr);
+// complex float32 entries from float64 tables.  The charge terms are second
+// differences of voxel-pair potentials, and in float32 the rounding of each
+// voxel pair's distance and phase survives the differencing: far blocks then
+// carry noise near 1e-4 of their norm, which the compression must keep (ranks
+// grow many times).  From float64 tables the entries are exact to their float32
+// rounding.  The c64 compression forms its blocks this way.
+void assemble_pairs_f32_from_f64(Op& op, const PairJob* d_jobs, int n_jobs, void* const* d_dst, const int64_t* d_ld,
+                                 cudaStream_t s, double* norm_out = nullptr);
 void dense_apply_c64(Op& op, const float2* x, float2* y, cudaStream_t s);
 void dense_apply_c128(Op& op, const double2* x, double2* y, cudaStream_t s);
 void rhs_kernel_launch(Op& op, const double* d_khat, const double* d_pol, int nrhs, void* b, int64_t ld,
@@ -374,6 +382,7 @@ struct CrossStats {
     double seconds = 0;    // step loop, device time between events
     double bytes = 0;      // residual bytes read and written
     int64_t passes = 0;    // residual passes (blocks x steps)
+    std::vector<double> resid2;  // per block: ||E||_F^2 when it left the loop
 };
 template <class T2>
 CrossStats cross_full_batch(T2* E, int nb, int m, int n, const double* d_anorm2, double tol, int rcap, int rfull,

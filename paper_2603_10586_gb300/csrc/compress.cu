@@ -598,6 +598,15 @@ struct Compressor {
         return now_s();
     }
 
+    // atom-pair blocks into dst: complex float32 entries come from float64
+    // tables (float32 tables leave noise near the tolerance in far blocks)
+    void form(const PairJob* jobs, int n_jobs, void* const* dst, const int64_t* ld, double* norm) {
+        if (std::is_same<T, float>::value)
+            assemble_pairs_f32_from_f64(op, jobs, n_jobs, dst, ld, s, norm);
+        else
+            assemble_pairs<T>(op, jobs, n_jobs, dst, ld, s, norm);
+    }
+
     // The Galerkin block of two distinct atoms depends only on their types and
     // displacement.  Unless sharing is off, each distinct (types, displacement)
     // among the jobs is formed once into a scratch block and copied to every
@@ -643,7 +652,7 @@ struct Compressor {
                 upload(dj, ujobs);
                 upload(dd, udst);
                 upload(dl, uld);
-                assemble_pairs<T>(op, dj.as<PairJob>(), (int)ujobs.size(), dd.as<void* const>(), dl.as<int64_t>(), s,
+                form(dj.as<PairJob>(), (int)ujobs.size(), dd.as<void* const>(), dl.as<int64_t>(),
                                   unorm.as<double>());
                 upload(dp, place);
                 upload(dq, dst);
@@ -665,7 +674,7 @@ struct Compressor {
         upload(dj, jobs);
         upload(dd, dst);
         upload(dl, ld);
-        assemble_pairs<T>(op, dj.as<PairJob>(), (int)jobs.size(), dd.as<void* const>(), dl.as<int64_t>(), s, norm);
+        form(dj.as<PairJob>(), (int)jobs.size(), dd.as<void* const>(), dl.as<int64_t>(), norm);
         return false;
     }
 
@@ -779,6 +788,13 @@ struct Compressor {
                                                        U.as<T2>(), (int64_t)m * rcap_pad, VH.as<T2>(),
                                                        (int64_t)n * rcap_pad, rk, op.ctx->n_sm, s);
             if (cs.flags & 2) fail(VIE_ERR_NAN, "cross approximation: a far block has non-finite entries");
+            if (op.ctx->verbose && (cs.flags & 1)) {
+                VIE_CUDA(cudaStreamSynchronize(s));
+                for (int q = 0; q < nb; ++q)
+                    if (rk[q] >= rcap)
+                        fprintf(stderr, "[vie]   level %d block %d (%d x %d): %d crosses leave ||E||/||A|| = %.3e\n",
+                                b0.level, ids[q], m, n, rk[q], std::sqrt(cs.resid2[q] / std::max(hnorm[q], 1e-300)));
+            }
             if (cs.flags & 1) {
                 if (cap < kRankCap) return false;  // again, with room for kRankCap
                 fail(VIE_ERR_BREAKDOWN, "far block needs a rank above " + std::to_string(kRankCap) +
@@ -795,9 +811,11 @@ struct Compressor {
             if (op.ctx->verbose) {
                 int rsum = 0, rmx = 0;
                 for (int q = 0; q < nb; ++q) { rsum += rk[q]; rmx = std::max(rmx, rk[q]); }
-                fprintf(stderr, "[vie]   level %d batch %d x (%d x %d): cross steps %lld mean rank %.1f max %d | "
-                        "form %.3f cross %.3f (%.0f GB/s) pack %.3f s\n", b0.level, nb, m, n,
-                        (long long)cs.passes, (double)rsum / nb, rmx, t1 - t0, t2 - t1,
+                double rel = 0.0;
+                for (int q = 0; q < nb; ++q) rel = std::max(rel, std::sqrt(cs.resid2[q] / std::max(hnorm[q], 1e-300)));
+                fprintf(stderr, "[vie]   level %d batch %d x (%d x %d): cross steps %lld mean rank %.1f max %d "
+                        "max ||E||/||A|| %.2e | form %.3f cross %.3f (%.0f GB/s) pack %.3f s\n", b0.level, nb, m, n,
+                        (long long)cs.passes, (double)rsum / nb, rmx, rel, t1 - t0, t2 - t1,
                         cs.bytes / std::max(cs.seconds, 1e-12) * 1e-9, t4 - t2);
             }
             return true;

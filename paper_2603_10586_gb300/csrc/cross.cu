@@ -182,7 +182,8 @@ __global__ void __launch_bounds__(kXSel) k_cross_select(const T2* __restrict__ E
                                                         int rfull, const int* __restrict__ list_in,
                                                         const int* __restrict__ cnt_in, int* list_out, int* cnt_out,
                                                         int* flags, unsigned long long* passes, int ntile,
-                                                        const XPart<R>* __restrict__ part, int counted) {
+                                                        const XPart<R>* __restrict__ part, int counted,
+                                                        double* resid2) {
     __shared__ int s_go, s_k, s_pi, s_pj;
     const int cnt = *cnt_in;
     for (int w = blockIdx.x; w < cnt; w += gridDim.x) {
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(kXSel) k_cross_select(const T2* __restrict__ E
         if (threadIdx.x == 0) {
             const int k = rank[q] + (counted ? 1 : 0);
             rank[q] = k;
+            resid2[q] = ss;
             int go = 1;
             if (!(ss <= 1e300)) {  // NaN or infinite residual
                 atomicOr(flags, 2);
@@ -262,7 +264,7 @@ CrossStats cross_full_batch(T2* E, int nb, int m, int n, const double* d_anorm2,
     if (ntile64 > INT_MAX / 2 || rcap > std::min(m, n)) fail(VIE_ERR_INVALID_ARG, "cross approximation: block too large");
     const int ntile = (int)ntile64;
     DevBuf d_rank(nb * sizeof(int)), d_piv(nb * sizeof(int2)), d_list(2 * (size_t)nb * sizeof(int)),
-        d_cnt(4 * sizeof(int)), d_passes(sizeof(unsigned long long)),
+        d_cnt(4 * sizeof(int)), d_passes(sizeof(unsigned long long)), d_resid(nb * sizeof(double)),
         d_part((size_t)nb * ntile * sizeof(XPart<R>));
     int* list[2] = {d_list.as<int>(), d_list.as<int>() + nb};
     int* cnt = d_cnt.as<int>();
@@ -293,7 +295,7 @@ CrossStats cross_full_batch(T2* E, int nb, int m, int n, const double* d_anorm2,
                                                        d_piv.as<int2>(), d_anorm2, tol2, rcap, rfull, list[a],
                                                        cnt + a, list[a ^ 1], cnt + (a ^ 1), cnt + 2,
                                                        d_passes.as<unsigned long long>(), ntile,
-                                                       d_part.as<XPart<R>>(), t > 0 ? 1 : 0);
+                                                       d_part.as<XPart<R>>(), t > 0 ? 1 : 0, d_resid.as<double>());
         VIE_CHECK_LAUNCH();
     };
     // every active block gains one cross per step and leaves at rank rcap, so
@@ -313,6 +315,8 @@ CrossStats cross_full_batch(T2* E, int nb, int m, int n, const double* d_anorm2,
     VIE_CUDA(cudaMemcpyAsync(&h_flags, cnt + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     VIE_CUDA(cudaMemcpyAsync(&h_passes, d_passes.p, sizeof(h_passes), cudaMemcpyDeviceToHost, s));
     VIE_CUDA(cudaMemcpyAsync(rank.data(), d_rank.p, nb * sizeof(int), cudaMemcpyDeviceToHost, s));
+    st.resid2.resize(nb);
+    VIE_CUDA(cudaMemcpyAsync(st.resid2.data(), d_resid.p, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
     VIE_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
     VIE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
