@@ -3,9 +3,11 @@
 // columns) and R = Q^H A (r x n) such that ||A - Q R||_F <= tol ||A||_F.
 //
 // The paper does not say how its QR factors are computed for large blocks
-// (it builds them with a cross approximation, Sec. 6.5).  Here a batch of
-// equally sized blocks is formed on the device and compressed together with
-// a blocked adaptive randomised range finder:
+// (it builds them with a cross approximation, Sec. 6.5; that builder is in
+// cross.cu and runs from the same batches).  Here a batch of equally sized
+// blocks is formed on the device (complex float32 blocks from float64
+// quadrature tables) and compressed together with a blocked adaptive
+// randomised range finder:
 //   Y = A Omega (Gaussian test matrix), project Y against the current basis
 //   (classical Gram-Schmidt), estimate the residual energy
 //   ||(I - Q Q^H) A||_F^2 ~ ||Y||_F^2 / s from the projected block, stop when
