@@ -271,7 +271,8 @@ int vie_op_get_info(const vie_op* op, vie_op_info* info);
  * VIE_C64_ACC64 (x, y c128, c64 factors), VIE_BF16X3 (x, y c64, c64 factors;
  * the far part on the tensor cores, relative error ~1e-5).
  * flags: VIE_APPLY_FUSE_PRECOND returns P^-1 Zs x instead of Zs x;
- * VIE_APPLY_DENSE applies the uncompressed matrix (works before vie_compress).
+ * VIE_APPLY_DENSE applies the uncompressed matrix (works before vie_compress;
+ * at VIE_C64 its interaction blocks are the ones vie_compress forms).
  * x and y must be 16-byte aligned (cudaMalloc'd buffers are) and must not
  * overlap; either violation fails with VIE_ERR_INVALID_ARG before anything is
  * launched.  Asynchronous on `stream`. */

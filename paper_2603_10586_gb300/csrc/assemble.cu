@@ -1049,7 +1049,11 @@ void dense_apply(Op& op, const typename C2<T>::t* x, typename C2<T>::t* y, cudaS
                 }
         DevBuf dj;
         upload(dj, jobs);
-        if (!jobs.empty())
+        // the blocks the compression forms (complex float32 entries from float64 tables)
+        if (!jobs.empty() && sizeof(T) == 4)
+            assemble_pairs_f32_from_f64(op, dj.as<PairJob>(), (int)jobs.size(), dd.as<void* const>(),
+                                        dl.as<int64_t>(), s);
+        else if (!jobs.empty())
             assemble_pairs<T>(op, dj.as<PairJob>(), (int)jobs.size(), dd.as<void* const>(), dl.as<int64_t>(), s);
         dense_rows_kernel<T2><<<dim3((np + 127) / 128, na), 128, 0, s>>>(blk.as<T2>(), zself, op.d_types.as<int>(),
                                                                          N, np, a0, x, y);
