@@ -80,6 +80,7 @@ WORKLOADS = {
         desc="64x64 graded array (cube sides 0.15/0.2/0.25 along a lens phase, F from seed 0), 4^3 voxels, "
              "983040 unknowns, 16 RHS (seed 0, within 20 deg of normal incidence); compression tolerance 1e-3 "
              "(at 1e-4 the factors would need ~970 GB)",
+        # counts of the factors from float32 tables (not re-measured from float64 tables)
         model=dict(mnr=2.4e13, factor_entries=7.12e9, iterations=3000)),
     "vogel": dict(
         geometry=lambda: workloads.vogel_gold(2000, nv=3),
@@ -87,12 +88,14 @@ WORKLOADS = {
         tol=1e-4, precision="C64", restart=300, max_iters=3000,
         desc="Vogel spiral of 2000 gold meta-atoms (eps = -9.428 - 1.513j, radius lambda/6, equal-volume cubes of "
              "3^3 voxels), 216000 unknowns, 1 RHS at normal incidence; aperiodic, so no two far blocks share factors",
-        model=dict(mnr=1.0e13, factor_entries=3.56e9, iterations=183)),
+        # counts of the factors from float32 tables (not re-measured from float64 tables)
+        model=dict(mnr=9.38e12, factor_entries=3.56e9, iterations=183)),
     "scale": dict(
         geometry=lambda: workloads.square_array(16, 6),
         incident=workloads.normal_incidence,
         tol=1e-4, precision="C64", restart=60,
         desc="16x16 array of eps=12 cubes (side 0.2, pitch 0.4, lambda 1), 6^3 voxels, 193536 unknowns, 1 RHS",
+        # counts of the factors from float32 tables (not re-measured from float64 tables)
         model=dict(mnr=2.1e12, factor_entries=3.58e9, iterations=52)),
 }
 
